@@ -1,0 +1,330 @@
+"""Benchmark: device-timed input edges/s of one minimum-spanning-forest solve.
+
+Default workload: RMAT, n = 2^24, m = 2^28 undirected edges, (a,b,c,d) =
+(0.57,0.19,0.19,0.05), permuted ids, weights uniform in [1,255], solved with
+Filter-Borůvka (pivot sample 2^16).  One step = one full mst_solve of that graph
+(every step of the method: partitions, Borůvka rounds, filters, output), with
+the input resident in HBM.  The input (3.2 GB) is larger than L2, so no flush
+is needed between steps.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gpu|reference] [--workload NAME]
+
+With N > 1 (torchrun, one rank per GPU) every rank solves its own replica of
+the graph: a single graph does not shard, so the GPUs run independent
+replicas and `value` counts the edges of all replicas.
+
+`--impl reference` times the CPU oracle (Kruskal) on a bounded sample of the
+same workload on the host cores, for the same metric.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "input edges/s per MSF solve (device-timed)"
+UNIT = "edges/s"
+
+WORKLOADS = {
+    # name: (description, generator, solver config)
+    "rmat_filter": ("RMAT n=2^24 m=2^28 (0.57,0.19,0.19,0.05) permuted, w in [1,255], Filter-Boruvka",
+                    lambda W: W.rmat_large(), dict(variant="filter")),
+    "rmat_boruvka": ("RMAT n=2^24 m=2^28 (0.57,0.19,0.19,0.05) permuted, w in [1,255], plain Boruvka",
+                     lambda W: W.rmat_large(), dict(variant="boruvka")),
+    "gnm": ("GNM n=2^16 m=2^20, w in [1,255], plain Boruvka", lambda W: W.gnm_small(), dict(variant="boruvka")),
+    "rgg2d": ("RGG2D n=2^22 degree 8, w in [1,2^32-1], plain Boruvka", lambda W: W.rgg2d_large(),
+              dict(variant="boruvka")),
+    "rgg3d": ("RGG3D n=2^21 degree 8, w in [1,2^32-1], plain Boruvka", lambda W: W.rgg3d_large(),
+              dict(variant="boruvka")),
+}
+
+
+def host_cores() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:  # pragma: no cover
+        return os.cpu_count() or 1
+
+
+def measured_peaks() -> dict:
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return {"hbm_gbs": float(d["hbm_gbs"]), "source": "measured"}
+    return {"hbm_gbs": 6800.0, "source": "fallback"}
+
+
+# ----------------------------------------------------------------- clocks
+
+class ClockSampler:
+    """Samples nvidia-smi clocks and throttle reasons while running."""
+    FIELDS = ("uuid,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, uuid: str | None):
+        self.uuid = uuid
+        self.proc = None
+        self.lines: list[str] = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (FileNotFoundError, OSError):
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict | None:
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=5)
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 8:
+                continue
+            if self.uuid and parts[0] != self.uuid:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = max(mx, float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# --------------------------------------------------------------- reference
+
+def cpu_oracle_rate(g, sample_edges: int, repeats: int = 1) -> tuple[float, float]:
+    """Kruskal (the CPU oracle, single-threaded) on the first `sample_edges`
+    edges of the graph; returns (edges/s, seconds per run)."""
+    import oracle
+    k = min(sample_edges, g.m)
+    src, dst, w = g.src[:k], g.dst[:k], g.w[:k]
+    best = None
+    for _ in range(repeats):
+        t0 = time.perf_counter()
+        oracle.kruskal(g.n, src, dst, w)
+        dt = time.perf_counter() - t0
+        best = dt if best is None else min(best, dt)
+    return k / best, best
+
+
+def reference_main(args, rank: int):
+    if rank != 0:
+        return 0
+    from paper_2302_12199_gb300 import workloads as W
+    desc, gen, cfg = WORKLOADS[args.workload]
+    g = gen(W)
+    sample = min(g.m, args.cpu_sample_edges)
+    for _ in range(args.warmup):
+        cpu_oracle_rate(g, sample)
+    times = []
+    for _ in range(args.steps):
+        _, dt = cpu_oracle_rate(g, sample)
+        times.append(dt)
+    total = sum(times)
+    value = sample * args.steps / total
+    sample_desc = f"first {sample} of the {g.m} edges (n={g.n}), Kruskal, single thread"
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+        "config": {"workload": args.workload, "description": desc, "n": g.n, "m": g.m, **cfg},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample_desc},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# --------------------------------------------------------------------- gpu
+
+def gpu_main(args, rank: int, world: int, local_rank: int):
+    import numpy as np
+    import torch
+
+    from paper_2302_12199_gb300 import workloads as W
+    from paper_2302_12199_gb300.mst import Solver
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+
+    desc, gen, cfg = WORKLOADS[args.workload]
+    g = gen(W)
+    n, m = g.n, g.m
+    src = torch.from_numpy(g.src.view(np.int32)).to(dev)
+    dst = torch.from_numpy(g.dst.view(np.int32)).to(dev)
+    w = torch.from_numpy(g.w.view(np.int32)).to(dev)
+    solver = Solver(local_rank, **cfg)
+    out = solver.alloc_forest(n, m)
+    stream = torch.cuda.current_stream(dev)
+
+    for _ in range(args.warmup):
+        solver.solve(n, src, dst, w, out=out)
+    torch.cuda.synchronize(dev)
+    ref_ids, ref_total = out.to_host()
+
+    uuid = None
+    try:
+        uuid = "GPU-" + str(torch.cuda.get_device_properties(dev).uuid)
+    except Exception:
+        pass
+    sampler = ClockSampler(uuid)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    sampler.start()
+    time.sleep(0.3)
+    solver.profile(True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        solver.solve(n, src, dst, w, out=out)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    solver.profile(False)
+    if dist:
+        dist.barrier()
+    clocks = sampler.stop()
+    ms = e0.elapsed_time(e1)
+    stats = solver.profile_stats()
+    ids, total = out.to_host()
+    if not (np.array_equal(ids, ref_ids) and total == ref_total):
+        raise RuntimeError("timed solves returned a different forest than the warm-up solve")
+
+    ms_max = ms
+    if dist:
+        t = torch.tensor([ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_max = float(t.item())
+    value = m * args.steps * world / (ms_max / 1e3)
+
+    # end to end through the public API with host buffers: H2D of the inputs
+    # from pinned memory and D2H of the forest inside the timed region
+    pin = [torch.from_numpy(a.view(np.int32)).pin_memory() for a in (g.src, g.dst, g.w)]
+    ids_h = torch.empty(max(1, min(m, n - 1)), dtype=torch.int32).pin_memory()
+    solver.solve_host_ptr(n, m, pin[0].data_ptr(), pin[1].data_ptr(), pin[2].data_ptr(), ids_h.data_ptr())
+    e2e_steps = max(1, min(args.steps, args.e2e_steps))
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    cnt = 0
+    for _ in range(e2e_steps):
+        cnt, _tot = solver.solve_host_ptr(n, m, pin[0].data_ptr(), pin[1].data_ptr(), pin[2].data_ptr(),
+                                          ids_h.data_ptr())
+    torch.cuda.synchronize(dev)
+    e2e_s = time.perf_counter() - t0
+    if dist:
+        t = torch.tensor([e2e_s], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e = {"value": m * e2e_steps * world / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 12 * m,
+           "d2h_bytes_per_step": 4 * cnt + 12, "steps": e2e_steps}
+
+    peaks = measured_peaks()
+    kernels = {}
+    all_bytes = 0.0
+    launches = 0
+    for name, (nl, kms, kbytes) in stats.items():
+        launches += nl
+        all_bytes += kbytes
+        if nl:
+            kernels[name] = {"launches_per_step": nl / args.steps, "ms_per_step": kms / args.steps,
+                             "GBps": (kbytes / (kms / 1e3) / 1e9) if kms > 0 else None}
+    dom = max(stats, key=lambda k: stats[k][1])
+    nl, kms, kbytes = stats[dom]
+    achieved = kbytes / (kms / 1e3) / 1e9
+    roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": achieved / peaks["hbm_gbs"], "peak_source": peaks["source"],
+                "traffic": None, "time_share": kms / ms if ms > 0 else None}
+    effective = all_bytes / args.steps / (ms / args.steps / 1e3) / 1e9
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "u32", "data": "synthetic",
+        "config": {"workload": args.workload, "description": desc, "n": n, "m": m, **cfg,
+                   "parallelism": f"replicas{world}" if world > 1 else "single",
+                   "l2": "inputs (12 B/edge) larger than L2, no flush"},
+        "roofline": roofline,
+        "effective_bw": {"GBps": effective, "frac": effective / peaks["hbm_gbs"],
+                         "note": "sum of algorithmic bytes of all kernels / solve time"},
+        "kernels": kernels,
+        "gpu_launches": launches,
+        "e2e": e2e,
+        "clocks": clocks,
+        "msf": {"edges": int(ids.size), "weight": int(total)},
+    }
+    if rank == 0 and not args.no_cpu_baseline:
+        rate, dt = cpu_oracle_rate(g, args.cpu_sample_edges)
+        line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                "sample": f"first {min(g.m, args.cpu_sample_edges)} of the {g.m} edges (n={n}), "
+                                          f"Kruskal, single thread, {dt:.1f} s"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    solver.close()
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
+    ap.add_argument("--workload", default="rmat_filter", choices=sorted(WORKLOADS))
+    ap.add_argument("--e2e-steps", type=int, default=10)
+    ap.add_argument("--cpu-sample-edges", type=int, default=1 << 25)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "gpu":
+        args.warmup = 3
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        return reference_main(args, rank)
+    return gpu_main(args, rank, world, local_rank)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,221 @@
+/*
+ * mst.h -- C ABI of libmstgpu, a single-GPU (GB300, sm_103a) minimum spanning
+ * forest solver built on Borůvka rounds and Filter-Borůvka.
+ *
+ * Problem (Sanders & Schimek, "Engineering Massively Parallel MST Algorithms",
+ * IPDPS 2023, Section 2.2): the input is an undirected weighted graph
+ * G = (V, E) with n vertices and m edges; the output is a minimum spanning tree
+ * of every connected component (a minimum spanning forest, MSF).  Here:
+ *   - vertices are 0-based (the paper numbers them 1..|V|);
+ *   - edge e is (src[e], dst[e], w[e]) with uint32 weight; its id is e;
+ *   - the graph may hold self-loops (ignored) and parallel edges;
+ *   - ties are broken by the strict total order (w, id) (Section 2.3: consistent
+ *     tie breaking makes the MST unique), so the MSF is unique and the solver
+ *     returns exactly its edge ids, ascending, plus the uint64 weight sum.
+ *
+ * Memory: every pointer named d_* is DEVICE memory on the handle's GPU, owned
+ * by the caller; h_* pointers are host memory.  Device arrays must be 4-byte
+ * aligned; 16-byte alignment enables vector loads.  The library allocates its
+ * own scratch memory (stream-ordered) and frees it when the handle is destroyed.
+ *
+ * Streams: `stream` is a cudaStream_t (NULL = the legacy default stream).  Work
+ * is issued on that stream.  A call returns once its results are written: the
+ * round loop reads counters back from the device on that stream between
+ * rounds.  A handle must not be used by two host threads at once.
+ *
+ * Errors: every call returns an mst_status.  Errors detected on the device
+ * (vertex ids out of range, a bounded loop that ran out of iterations) are
+ * read back before the call returns.  No call aborts the process.
+ */
+#ifndef MSTGPU_MST_H
+#define MSTGPU_MST_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct mst_ctx *mst_handle;
+
+typedef enum {
+  MST_OK = 0,
+  MST_ERR_INVALID_ARG = 1,  /* null pointer, bad config value */
+  MST_ERR_VERTEX_RANGE = 2, /* some src[e] or dst[e] >= n */
+  MST_ERR_TOO_LARGE = 3,    /* m >= 2^32 (edge ids are uint32) */
+  MST_ERR_OOM = 4,          /* scratch allocation failed */
+  MST_ERR_CUDA = 5,         /* a CUDA runtime call failed */
+  MST_ERR_INTERNAL = 6,     /* a bounded device loop ran out of iterations */
+  MST_ERR_NOT_SUPPORTED = 7 /* option not available in this build */
+} mst_status;
+
+enum { MST_VARIANT_BORUVKA = 0, MST_VARIANT_FILTER = 1, MST_VARIANT_AUTO = 2 };
+enum { MST_DEDUPE_AUTO = 0, MST_DEDUPE_HASH = 2, MST_DEDUPE_NONE = 3 };
+
+typedef struct {
+  int device;                  /* CUDA device ordinal */
+  int variant;                 /* MST_VARIANT_*: Borůvka (Alg. 1 rounds) or Filter-Borůvka (Alg. 2) */
+  int dedupe;                  /* MST_DEDUPE_*: parallel-edge removal between rounds (Section 2.3, optional) */
+  int tile_contract;           /* -1 auto, 0 off, 1 on: local contraction before the rounds (Section 4.1) */
+  uint32_t tile_vertices;      /* vertices per tile for local contraction */
+  uint32_t pivot_sample;       /* edges sampled per pivot selection (Alg. 2 PivotSelection) */
+  uint64_t seed;               /* seed of the pivot sampling stream */
+  uint64_t filter_min_edges;   /* isSparse: lists shorter than this are not partitioned */
+  float filter_max_avg_degree; /* isSparse: stop partitioning at average degree 2m/n <= this (Section 6.3: 4) */
+} mst_config;
+
+/* Fills *cfg with the defaults (Borůvka variant, automatic dedupe, pivot sample
+ * 2^16, isSparse average degree 4). */
+void mst_config_default(mst_config *cfg);
+
+/* Creates a handle on cfg->device (cfg == NULL: defaults on device 0). */
+mst_status mst_create(mst_handle *out, const mst_config *cfg);
+
+/* Frees the handle and all of its device memory.  NULL is ignored. */
+void mst_destroy(mst_handle h);
+
+/* Replaces the handle's configuration. */
+mst_status mst_set_config(mst_handle h, const mst_config *cfg);
+
+/* Human-readable name of a status code (static storage). */
+const char *mst_status_string(mst_status s);
+
+/* Status of the last call made with this handle. */
+mst_status mst_get_error(mst_handle h);
+
+/* Upper bound on the scratch bytes a solve of (n, m) allocates with the given
+ * configuration (cfg == NULL: defaults), for admission by memory footprint. */
+uint64_t mst_workspace_bytes(uint32_t n, uint64_t m, const mst_config *cfg);
+
+/* Minimum spanning forest of the graph (n, m, d_src, d_dst, d_w)
+ * (Section 2.2 problem; Borůvka rounds of Section 2.3 / Alg. 1, or Alg. 2).
+ *   d_msf_ids       [out] capacity >= min(m, max(n-1, 0)); receives the MSF
+ *                   edge ids in ascending order
+ *   d_msf_count     [out] one uint32: number of ids written
+ *   d_total_weight  [out] one uint64: sum of w over the MSF
+ * n = 0 or m = 0 gives an empty forest of weight 0.  Inputs are not modified. */
+mst_status mst_solve(mst_handle h, uint32_t n, uint64_t m, const uint32_t *d_src, const uint32_t *d_dst,
+                     const uint32_t *d_w, uint32_t *d_msf_ids, uint32_t *d_msf_count, uint64_t *d_total_weight,
+                     void *stream);
+
+/* As mst_solve, with every array in HOST memory: the call copies the inputs to
+ * the device, solves, and copies the forest back before returning.
+ * h_msf_ids needs capacity min(m, max(n-1, 0)). */
+mst_status mst_solve_host(mst_handle h, uint32_t n, uint64_t m, const uint32_t *h_src, const uint32_t *h_dst,
+                          const uint32_t *h_w, uint32_t *h_msf_ids, uint32_t *h_msf_count, uint64_t *h_total_weight,
+                          void *stream);
+
+/* Minimum spanning forests of G independent graphs in one solve.  Graph g has
+ * d_n[g] vertices (graph-local ids 0..d_n[g]-1) and the edges
+ * d_edge_off[g] .. d_edge_off[g+1]-1 of d_src/d_dst/d_w.  The graphs are solved
+ * together as one disjoint union, so their rounds share launches.
+ *   h_n, h_edge_off  HOST copies of the size tables ([G] and [G+1] entries)
+ *   d_msf_ids   [out] capacity >= sum_g min(m_g, n_g - 1); segment g starts at
+ *               d_msf_off[g] and holds graph-local edge ids (index - d_edge_off[g])
+ *   d_msf_off   [out] [G+1] uint64 segment offsets
+ *   d_total_weight [out] [G] uint64 MSF weight of each graph
+ * Errors as mst_solve; a vertex id out of range in any graph fails the call. */
+mst_status mst_solve_batched(mst_handle h, uint32_t num_graphs, const uint32_t *h_n, const uint64_t *h_edge_off,
+                             const uint32_t *d_src, const uint32_t *d_dst, const uint32_t *d_w, uint32_t *d_msf_ids,
+                             uint64_t *d_msf_off, uint64_t *d_total_weight, void *stream);
+
+/* Per-kernel-class timing: when enabled, every kernel launch of a solve is
+ * bracketed by CUDA events on the solve's stream, and the elapsed time,
+ * launch count and algorithmic bytes (the bytes the method must move: edge
+ * records read and written, vertex arrays; label gathers, atomics and hash
+ * probes are not counted) are accumulated per class until reset. */
+enum {
+  MST_K_MIN_EDGES = 0,  /* minEdges from a stored list (first round of a Borůvka call) */
+  MST_K_RELABEL_MIN,    /* relabel + self-loop removal + compaction, fused with the next minEdges */
+  MST_K_HOOK,           /* hooking + active-vertex compaction */
+  MST_K_JUMP,           /* pointer doubling */
+  MST_K_DEDUPE,         /* hash parallel-edge removal (insert and keep passes) */
+  MST_K_PIVOT,          /* pivot sampling and selection */
+  MST_K_PARTITION,      /* light/heavy partition */
+  MST_K_FILTER,         /* filtering of heavy edges */
+  MST_K_FINALIZE,       /* bitmap -> ascending ids + weight */
+  MST_K_COUNT
+};
+typedef struct {
+  uint64_t launches;
+  double ms;    /* summed event time of the class's launches */
+  double bytes; /* summed algorithmic bytes */
+} mst_kernel_stats;
+
+/* enable != 0: start collecting (and clear the totals); 0: stop. */
+mst_status mst_profile_enable(mst_handle h, int enable);
+
+/* Totals of class `kind` (MST_K_*) since the last enable. */
+mst_status mst_profile_get(mst_handle h, int kind, mst_kernel_stats *out);
+
+/* ----------------------------------------------------------------------
+ * Step entry points: one step of the method each, on caller buffers, so that
+ * every step can be checked on its own.  Edge lists are SoA (u, v, w, id) of
+ * length m; d_id may be NULL, meaning id = index.  Lists passed here must have
+ * ascending ids (true of the input and of every list the solver builds).
+ * "key" means the uint64 (w << 32) | id.
+ * -------------------------------------------------------------------- */
+
+/* minEdges (Alg. 1; Section 2.3): d_best[c] = minimum key over the
+ * non-self-loop edges incident to vertex c, or 2^64-1 if none.  d_best: [n]. */
+mst_status mst_step_min_edges(mst_handle h, uint32_t n, uint64_t m, const uint32_t *d_u, const uint32_t *d_v,
+                              const uint32_t *d_w, const uint32_t *d_id, uint64_t *d_best, void *stream);
+
+/* Hook + pointer doubling (Section 2.3; Section 4.2 contractComponents) of one
+ * round: every vertex with an incident edge hooks to the other end of its
+ * minimum edge; a 2-cycle keeps the smaller vertex as root; pointers are then
+ * doubled until every tree is a star.
+ *   d_parent   [out] [n] root of every vertex (itself when it has no edge)
+ *   d_chosen   [in/out] bitmap over edge ids (bit id%32 of word id/32); the
+ *              bits of the chosen edges are set, each edge once */
+mst_status mst_step_contract(mst_handle h, uint32_t n, uint64_t m, const uint32_t *d_u, const uint32_t *d_v,
+                             const uint32_t *d_w, const uint32_t *d_id, uint32_t *d_parent, uint32_t *d_chosen,
+                             void *stream);
+
+/* Relabel (Section 4.3): (u, v) -> (d_label[u], d_label[v]); self-loops are
+ * dropped; the survivors keep their order.  Output arrays need capacity m;
+ * d_out_count receives one uint64. */
+mst_status mst_step_relabel(mst_handle h, uint32_t n, uint64_t m, const uint32_t *d_u, const uint32_t *d_v,
+                            const uint32_t *d_w, const uint32_t *d_id, const uint32_t *d_label, uint32_t *d_ou,
+                            uint32_t *d_ov, uint32_t *d_ow, uint32_t *d_oid, uint64_t *d_out_count, void *stream);
+
+/* Parallel-edge removal (Section 2.3; Section 4.3 Redistribute; Section 6.2
+ * hash table): of the edges joining one unordered pair keep the minimum key;
+ * survivors keep their order and orientation.  Capacity m; one uint64 count. */
+mst_status mst_step_dedupe(mst_handle h, uint64_t m, const uint32_t *d_u, const uint32_t *d_v, const uint32_t *d_w,
+                           const uint32_t *d_id, uint32_t *d_ou, uint32_t *d_ov, uint32_t *d_ow, uint32_t *d_oid,
+                           uint64_t *d_out_count, void *stream);
+
+/* PivotSelection (Alg. 2; Section 5): sample k = 0..sample-1 is the edge at
+ * position floor(splitmix64(state, k) * m / 2^64), where splitmix64(s, k) is
+ * output k of the splitmix64 sequence started at state s; the pivot is the
+ * sample key of rank sample/2 (0-based, ascending).  d_pivot: one uint64. */
+mst_status mst_step_pivot(mst_handle h, uint64_t m, const uint32_t *d_w, const uint32_t *d_id, uint64_t state,
+                          uint32_t sample, uint64_t *d_pivot, void *stream);
+
+/* Light part of the partition (Alg. 2): edges with key <= pivot and u != v,
+ * in order.  Capacity m; one uint64 count. */
+mst_status mst_step_partition(mst_handle h, uint64_t m, const uint32_t *d_u, const uint32_t *d_v, const uint32_t *d_w,
+                              const uint32_t *d_id, uint64_t pivot, uint32_t *d_ou, uint32_t *d_ov, uint32_t *d_ow,
+                              uint32_t *d_oid, uint64_t *d_out_count, void *stream);
+
+/* Filter (Alg. 2; Section 5): edges with key > pivot, relabelled by the
+ * representative array d_P after pointer doubling it to its roots (d_P is
+ * updated in place to the roots); edges inside one component are dropped.
+ * Capacity m; one uint64 count. */
+mst_status mst_step_filter(mst_handle h, uint32_t n, uint64_t m, const uint32_t *d_u, const uint32_t *d_v,
+                           const uint32_t *d_w, const uint32_t *d_id, uint64_t pivot, uint32_t *d_P, uint32_t *d_ou,
+                           uint32_t *d_ov, uint32_t *d_ow, uint32_t *d_oid, uint64_t *d_out_count, void *stream);
+
+/* Output step (Section 2.2 output; Section 6.2 edge ids): the set bits of the
+ * bitmap d_chosen over ids 0..m-1 become ascending ids in d_msf_ids, their
+ * count in d_msf_count (uint32) and their weight sum over d_w in
+ * d_total_weight (uint64). */
+mst_status mst_step_finalize(mst_handle h, uint64_t m, const uint32_t *d_chosen, const uint32_t *d_w,
+                             uint32_t *d_msf_ids, uint32_t *d_msf_count, uint64_t *d_total_weight, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MSTGPU_MST_H */

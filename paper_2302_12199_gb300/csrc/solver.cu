@@ -1,0 +1,974 @@
+// Host side of libmstgpu: the C ABI declared in include/mst.h, the Borůvka
+// round loop (Section 2.3, Alg. 1), the Filter-Borůvka recursion (Alg. 2), the
+// batched disjoint-union solve and the step entry points.
+//
+// Device memory: each handle owns a CUDA memory pool; every solve allocates its
+// scratch from it in stream order and returns it at the end, so repeated solves
+// reuse the same memory without device-wide synchronisation.
+#include <cstddef>
+#include <cstdint>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "internal.h"
+#include "mst.h"
+
+using namespace mstgpu;
+
+struct mst_ctx {
+  int device = 0;
+  mst_config cfg;
+  mst_status last = MST_OK;
+  int sms = 152;
+  cudaMemPool_t pool = nullptr;
+  DevState *ds = nullptr;    // device
+  DevState *hs = nullptr;    // pinned host mirror
+  u64 *status = nullptr;     // scan status words
+  uint64_t status_cap = 0;   // in tiles
+  uint32_t epoch = 0;
+  u64 *sample_buf = nullptr;
+  uint32_t sample_cap = 0;
+  uint64_t pivot_counter = 0;
+  // per-kernel-class event timing (mst_profile_enable)
+  struct ProfRec {
+    int kind;
+    cudaEvent_t a, b;
+    double bytes;
+    int slot1, slot2;
+    double per1, per2;
+  };
+  bool prof_on = false;
+  std::vector<cudaEvent_t> ev_pool;
+  std::vector<ProfRec> prof_pending;
+  mst_kernel_stats prof[MST_K_COUNT];
+};
+
+namespace {
+
+constexpr int TILE_ITEMS = 2048;
+
+#define CK(call)                                   \
+  do {                                             \
+    if ((call) != cudaSuccess) return MST_ERR_CUDA; \
+  } while (0)
+
+#define TRY(expr)                     \
+  do {                                \
+    mst_status _st = (expr);          \
+    if (_st != MST_OK) return _st;    \
+  } while (0)
+
+u64 host_mix64(u64 z) {
+  z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ULL;
+  z = (z ^ (z >> 27)) * 0x94d049bb133111ebULL;
+  return z ^ (z >> 31);
+}
+u64 host_splitmix64_at(u64 s, u64 i) { return host_mix64(s + (i + 1ULL) * 0x9e3779b97f4a7c15ULL); }
+
+uint64_t round_up(uint64_t x, uint64_t a) { return (x + a - 1) / a * a; }
+
+uint64_t next_pow2(uint64_t x) {
+  uint64_t p = 1;
+  while (p < x) p <<= 1;
+  return p;
+}
+
+int ceil_log2(uint64_t x) {
+  int l = 0;
+  while ((1ULL << l) < x) ++l;
+  return l;
+}
+
+// Restores the caller's current device on scope exit.
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+    if (prev != dev) cudaSetDevice(dev);
+  }
+  ~DeviceGuard() {
+    if (prev >= 0) cudaSetDevice(prev);
+  }
+};
+
+// A stream-ordered device allocation from the handle's pool.
+struct Buf {
+  void *p = nullptr;
+  cudaStream_t s = nullptr;
+  Buf() = default;
+  Buf(const Buf &) = delete;
+  Buf &operator=(const Buf &) = delete;
+  ~Buf() { release(); }
+  void release() {
+    if (p) cudaFreeAsync(p, s);
+    p = nullptr;
+  }
+  mst_status alloc(mst_ctx *c, size_t bytes, cudaStream_t st) {
+    release();
+    s = st;
+    if (bytes == 0) bytes = 256;
+    if (cudaMallocFromPoolAsync(&p, bytes, c->pool, st) != cudaSuccess) {
+      cudaGetLastError();
+      p = nullptr;
+      return MST_ERR_OOM;
+    }
+    return MST_OK;
+  }
+  template <class T>
+  T *as() const {
+    return static_cast<T *>(p);
+  }
+};
+
+// An edge list buffer: four uint32 arrays of `cap` entries in one allocation.
+struct ListBuf {
+  Buf mem;
+  uint64_t cap = 0;
+  EdgeOut out{};
+  mst_status alloc(mst_ctx *c, uint64_t n_edges, cudaStream_t s) {
+    const uint64_t stride = round_up(n_edges * 4 + 16, 256);
+    TRY(mem.alloc(c, stride * 4, s));
+    char *b = mem.as<char>();
+    out = EdgeOut{(uint32_t *)b, (uint32_t *)(b + stride), (uint32_t *)(b + 2 * stride), (uint32_t *)(b + 3 * stride)};
+    cap = n_edges;
+    return MST_OK;
+  }
+  EdgeList list() const { return EdgeList{out.u, out.v, out.w, out.id}; }
+};
+
+mst_status ensure_status(mst_ctx *c, uint64_t max_items, cudaStream_t s) {
+  const uint64_t tiles = (max_items + TILE_ITEMS - 1) / TILE_ITEMS + 1;
+  if (tiles <= c->status_cap) return MST_OK;
+  CK(cudaStreamSynchronize(s));
+  if (c->status) cudaFree(c->status);
+  c->status = nullptr;
+  c->status_cap = 0;
+  const uint64_t cap = next_pow2(tiles < 4096 ? 4096 : tiles);
+  if (cudaMalloc(&c->status, cap * sizeof(u64)) != cudaSuccess) {
+    cudaGetLastError();
+    return MST_ERR_OOM;
+  }
+  CK(cudaMemset(c->status, 0, cap * sizeof(u64)));
+  c->status_cap = cap;
+  c->epoch = 0;
+  CK(cudaMemset(c->ds->tile_ctr, 0, sizeof(c->ds->tile_ctr)));
+  return MST_OK;
+}
+
+ScanState next_scan(mst_ctx *c, int total_slot) {
+  if (++c->epoch >= (1u << 30)) {  // epochs wrapped: clear the status words (practically never)
+    cudaDeviceSynchronize();
+    cudaMemset(c->status, 0, c->status_cap * sizeof(u64));
+    cudaMemset(c->ds->tile_ctr, 0, sizeof(c->ds->tile_ctr));
+    c->epoch = 1;
+  }
+  return ScanState{c->status, c->ds->tile_ctr, c->epoch, &c->ds->count[total_slot], &c->ds->err};
+}
+
+cudaEvent_t take_event(mst_ctx *c) {
+  if (!c->ev_pool.empty()) {
+    cudaEvent_t e = c->ev_pool.back();
+    c->ev_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  if (cudaEventCreate(&e) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return e;
+}
+
+// Opens a timing record around the next launch(es) on `s`; -1 when profiling is off.
+int prof_begin(mst_ctx *c, cudaStream_t s) {
+  if (!c->prof_on) return -1;
+  mst_ctx::ProfRec r{};
+  r.a = take_event(c);
+  r.b = take_event(c);
+  if (!r.a || !r.b) return -1;
+  cudaEventRecord(r.a, s);
+  c->prof_pending.push_back(r);
+  return (int)c->prof_pending.size() - 1;
+}
+
+// Closes a record: `bytes` known at launch, plus count[slot] * per for counts the
+// kernel itself produces (read at the next readback).
+void prof_end(mst_ctx *c, cudaStream_t s, int idx, int kind, double bytes, int slot1 = -1, double per1 = 0,
+              int slot2 = -1, double per2 = 0) {
+  if (idx < 0) return;
+  mst_ctx::ProfRec &r = c->prof_pending[idx];
+  cudaEventRecord(r.b, s);
+  r.kind = kind;
+  r.bytes = bytes;
+  r.slot1 = slot1;
+  r.per1 = per1;
+  r.slot2 = slot2;
+  r.per2 = per2;
+}
+
+// After a stream synchronisation: folds the finished records into the totals.
+void prof_resolve(mst_ctx *c) {
+  for (auto &r : c->prof_pending) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, r.a, r.b) != cudaSuccess) {
+      cudaGetLastError();
+      ms = 0.f;
+    }
+    mst_kernel_stats &k = c->prof[r.kind];
+    k.launches += 1;
+    k.ms += ms;
+    double b = r.bytes;
+    if (r.slot1 >= 0) b += (double)c->hs->count[r.slot1] * r.per1;
+    if (r.slot2 >= 0) b += (double)c->hs->count[r.slot2] * r.per2;
+    k.bytes += b;
+    c->ev_pool.push_back(r.a);
+    c->ev_pool.push_back(r.b);
+  }
+  c->prof_pending.clear();
+}
+
+#define PROF(kind, bytes, slot1, per1, slot2, per2, launch)       \
+  do {                                                           \
+    const int _p = prof_begin(c, s);                             \
+    launch;                                                      \
+    prof_end(c, s, _p, kind, bytes, slot1, per1, slot2, per2);   \
+  } while (0)
+
+mst_status readback(mst_ctx *c, cudaStream_t s) {
+  CK(cudaMemcpyAsync(c->hs, c->ds, sizeof(DevState), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  prof_resolve(c);
+  if (c->hs->err & ERR_VERTEX) return MST_ERR_VERTEX_RANGE;
+  if (c->hs->err) return MST_ERR_INTERNAL;
+  return MST_OK;
+}
+
+// Clears the error word, the jump flag and both tile counters (err, jump_flag
+// and tile_ctr are adjacent in DevState).  Called at the start of every solve
+// and step call, so that a launch that failed earlier cannot leave a counter
+// behind for the scans of this call.
+mst_status clear_device_flags(mst_ctx *c, cudaStream_t s) {
+  static_assert(offsetof(DevState, tile_ctr) == 2 * sizeof(uint32_t), "DevState layout");
+  CK(cudaMemsetAsync(c->ds, 0, 4 * sizeof(uint32_t), s));
+  return MST_OK;
+}
+
+bool aligned4(const void *p) { return ((uintptr_t)p & 3u) == 0; }
+
+// Per-solve state: vertex arrays and the chosen-edge bitmap.
+struct Solve {
+  mst_ctx *c;
+  cudaStream_t s;
+  uint32_t n;
+  uint64_t m;
+  Buf best_b, parent_b, act_b[2], bits_b;
+  u64 *best = nullptr;
+  uint32_t *parent = nullptr, *act[2] = {nullptr, nullptr}, *bits = nullptr;
+  int rounds = 0;
+
+  Solve(mst_ctx *c_, cudaStream_t s_, uint32_t n_, uint64_t m_) : c(c_), s(s_), n(n_), m(m_) {}
+
+  mst_status init(uint32_t *parent_external = nullptr, uint32_t *bits_external = nullptr) {
+    TRY(best_b.alloc(c, (size_t)n * 8, s));
+    best = best_b.as<u64>();
+    CK(cudaMemsetAsync(best, 0xff, (size_t)n * 8, s));
+    if (parent_external) {
+      parent = parent_external;
+    } else {
+      TRY(parent_b.alloc(c, (size_t)n * 4, s));
+      parent = parent_b.as<uint32_t>();
+    }
+    launch_iota(parent, n, c->sms, s);
+    for (int i = 0; i < 2; ++i) {
+      TRY(act_b[i].alloc(c, (size_t)n * 4, s));
+      act[i] = act_b[i].as<uint32_t>();
+    }
+    if (bits_external) {
+      bits = bits_external;
+    } else {
+      const size_t words = (m + 31) / 32;
+      TRY(bits_b.alloc(c, words * 4, s));
+      bits = bits_b.as<uint32_t>();
+      CK(cudaMemsetAsync(bits, 0, words * 4, s));
+    }
+    TRY(ensure_status(c, (uint64_t)n > m ? (uint64_t)n : m, s));
+    TRY(clear_device_flags(c, s));
+    return MST_OK;
+  }
+
+  // Pointer jumping over the listed vertices (act == nullptr: all n) until
+  // every one points to its root; the first launch may reset best[].
+  mst_status jump_until_stars(const uint32_t *act_list, const u64 *count_dev, uint64_t count_host, uint64_t max_count,
+                              int reset_best) {
+    CK(cudaMemsetAsync(&c->ds->jump_flag, 0, sizeof(uint32_t), s));
+    const int slot = count_dev ? CNT_ACTIVE : -1;
+    const double fixed = count_dev ? 0.0 : 8.0 * (double)count_host;
+    PROF(MST_K_JUMP, fixed, slot, reset_best ? 20.0 : 12.0, -1, 0.0,
+         launch_jump(act_list, count_dev, count_host, max_count, parent, best, reset_best, &c->ds->jump_flag,
+                     c->sms, s));
+    TRY(readback(c, s));
+    for (int it = 0; c->hs->jump_flag; ++it) {
+      if (it > 64) return MST_ERR_INTERNAL;
+      CK(cudaMemsetAsync(&c->ds->jump_flag, 0, sizeof(uint32_t), s));
+      PROF(MST_K_JUMP, fixed, slot, 12.0, -1, 0.0,
+           launch_jump(act_list, count_dev, count_host, max_count, parent, best, 0, &c->ds->jump_flag, c->sms, s));
+      TRY(readback(c, s));
+    }
+    return MST_OK;
+  }
+
+  bool want_dedupe(int round, uint64_t cur_m) const {
+    switch (c->cfg.dedupe) {
+      case MST_DEDUPE_HASH: return cur_m > 0;
+      case MST_DEDUPE_NONE: return false;
+      default: return round >= 2 && cur_m >= 4096;
+    }
+  }
+
+  // Borůvka rounds (Section 2.3) on the list E of mE edges whose endpoints are
+  // current component roots; merged roots get their new root in parent[].
+  mst_status boruvka(EdgeList E, uint64_t mE, bool validate) {
+    if (mE == 0) return MST_OK;
+    // round 0: minEdges straight from the stored list, then hook and jump
+    PROF(MST_K_MIN_EDGES, 12.0 * (double)mE, -1, 0.0, -1, 0.0,
+         launch_min_edges(E, mE, n, validate ? 1 : 0, best, &c->ds->err, c->sms, s));
+    HookArgs ha{};
+    ha.cand = nullptr;
+    ha.ncand = n;
+    ha.best = best;
+    ha.list = E;
+    ha.parent = parent;
+    ha.chosen_bits = bits;
+    ha.active_out = act[0];
+    ha.st = next_scan(c, CNT_ACTIVE);
+    PROF(MST_K_HOOK, 8.0 * (double)n, CNT_ACTIVE, 8.0, -1, 0.0, launch_hook(ha, n, s));
+    TRY(jump_until_stars(act[0], &c->ds->count[CNT_ACTIVE], 0, n, 1));
+    uint64_t n_act = c->hs->count[CNT_ACTIVE];
+    ++rounds;
+
+    ListBuf X, Y, T;
+    Buf table_b;
+    EdgeList cur = E;
+    uint64_t cur_m = mE;
+    int a = 0;
+    const int bound = 2 * (ceil_log2(n) + 2);
+    for (int r = 1; n_act > 0; ++r) {
+      if (r > bound) return MST_ERR_INTERNAL;
+      ListBuf &out = (cur.u == X.out.u) ? Y : X;
+      if (out.cap < cur_m) TRY(out.alloc(c, cur_m, s));
+      CompactArgs ca{};
+      ca.in = cur;
+      ca.m = cur_m;
+      ca.out = out.out;
+      ca.label = parent;
+      ca.n = n;
+      const double in_bytes = (cur.id ? 16.0 : 12.0) * (double)cur_m;
+      if (!want_dedupe(r, cur_m)) {
+        ca.best = best;
+        ca.st = next_scan(c, CNT_EDGES);
+        PROF(MST_K_RELABEL_MIN, in_bytes, CNT_EDGES, 16.0, -1, 0.0, launch_compact(CM_RELABEL, ca, cur_m, s));
+      } else {
+        // relabel into T while inserting every pair into the hash table, then
+        // keep each pair's minimum (Section 2.3 parallel-edge removal; the
+        // hash variant of Section 6.2) and relax best[] with the final slots
+        if (T.cap < cur_m) TRY(T.alloc(c, cur_m, s));
+        const uint64_t slots = next_pow2(2 * cur_m < 1024 ? 1024 : 2 * cur_m);
+        TRY(table_b.alloc(c, slots * sizeof(HashSlot), s));
+        CK(cudaMemsetAsync(table_b.p, 0xff, slots * sizeof(HashSlot), s));
+        ca.out = T.out;
+        ca.table = table_b.as<HashSlot>();
+        ca.tmask = slots - 1;
+        ca.hash_insert = 1;
+        ca.st = next_scan(c, CNT_TMP);
+        PROF(MST_K_DEDUPE, in_bytes, CNT_TMP, 16.0, -1, 0.0, launch_compact(CM_RELABEL, ca, cur_m, s));
+        CompactArgs cd{};
+        cd.in = T.list();
+        cd.m_dev = &c->ds->count[CNT_TMP];
+        cd.out = out.out;
+        cd.table = ca.table;
+        cd.tmask = ca.tmask;
+        cd.best = best;
+        cd.n = n;
+        cd.st = next_scan(c, CNT_EDGES);
+        PROF(MST_K_DEDUPE, 0.0, CNT_TMP, 16.0, CNT_EDGES, 16.0, launch_compact(CM_DEDUPE, cd, cur_m, s));
+      }
+      HookArgs hb{};
+      hb.cand = act[a];
+      hb.ncand = n_act;
+      hb.best = best;
+      hb.list = out.list();
+      hb.parent = parent;
+      hb.chosen_bits = bits;
+      hb.active_out = act[1 - a];
+      hb.st = next_scan(c, CNT_ACTIVE);
+      PROF(MST_K_HOOK, 12.0 * (double)n_act, CNT_ACTIVE, 8.0, -1, 0.0, launch_hook(hb, n_act, s));
+      TRY(jump_until_stars(act[1 - a], &c->ds->count[CNT_ACTIVE], 0, n_act, 1));
+      table_b.release();
+      a = 1 - a;
+      n_act = c->hs->count[CNT_ACTIVE];
+      cur = out.list();
+      cur_m = c->hs->count[CNT_EDGES];
+      ++rounds;
+      if (cur_m == 0) break;
+    }
+    return MST_OK;
+  }
+
+  bool is_sparse(uint64_t mE) const {
+    return mE < c->cfg.filter_min_edges || 2.0 * (double)mE <= (double)c->cfg.filter_max_avg_degree * (double)n;
+  }
+
+  // Full pointer doubling of parent[] over all n vertices (the contraction of
+  // the representative array P before filtering, Section 5).
+  mst_status compress_all() { return jump_until_stars(nullptr, nullptr, n, n, 0); }
+
+  // Rec-Filter-MST (Alg. 2).
+  mst_status filter(EdgeList E, uint64_t mE, bool is_input, int depth) {
+    if (is_sparse(mE) || depth >= 40) return boruvka(E, mE, is_input);
+    const u64 state = host_splitmix64_at(c->cfg.seed, c->pivot_counter++);
+    PROF(MST_K_PIVOT, 16.0 * (double)c->cfg.pivot_sample, -1, 0.0, -1, 0.0,
+         launch_pivot(E, mE, nullptr, state, c->cfg.pivot_sample, c->sample_buf, &c->ds->pivot, s));
+    const double in_bytes = (E.id ? 16.0 : 12.0) * (double)mE;
+    ListBuf L;
+    TRY(L.alloc(c, mE, s));
+    CompactArgs cp{};
+    cp.in = E;
+    cp.m = mE;
+    cp.out = L.out;
+    cp.pivot_dev = &c->ds->pivot;
+    cp.n = n;
+    cp.validate = is_input ? 1 : 0;
+    cp.st = next_scan(c, CNT_EDGES);
+    PROF(MST_K_PARTITION, in_bytes, CNT_EDGES, 16.0, -1, 0.0, launch_compact(CM_PARTITION, cp, mE, s));
+    TRY(readback(c, s));
+    const uint64_t mL = c->hs->count[CNT_EDGES];
+    const u64 pivot = c->hs->pivot;
+    if (mL == 0 || mL == mE) {  // no progress from this pivot: solve the list directly
+      L.mem.release();
+      return boruvka(E, mE, is_input);
+    }
+    TRY(filter(L.list(), mL, false, depth + 1));
+    L.mem.release();
+    TRY(compress_all());
+    ListBuf H;
+    TRY(H.alloc(c, mE - mL, s));
+    CompactArgs cf{};
+    cf.in = E;
+    cf.m = mE;
+    cf.out = H.out;
+    cf.label = parent;
+    cf.pivot = pivot;
+    cf.n = n;
+    cf.st = next_scan(c, CNT_EDGES);
+    PROF(MST_K_FILTER, in_bytes, CNT_EDGES, 16.0, -1, 0.0, launch_compact(CM_FILTER, cf, mE, s));
+    TRY(readback(c, s));
+    const uint64_t mH = c->hs->count[CNT_EDGES];
+    return filter(H.list(), mH, false, depth + 1);
+  }
+
+  mst_status finalize(const uint32_t *w, uint32_t *out_ids, uint32_t *out_count, u64 *total_weight) {
+    CK(cudaMemsetAsync(total_weight, 0, sizeof(u64), s));
+    PROF(MST_K_FINALIZE, (double)((m + 31) / 32 * 4), CNT_AUX, 4.0, -1, 0.0,
+         launch_finalize(bits, m, w, out_ids, out_count, total_weight, next_scan(c, CNT_AUX), s));
+    return readback(c, s);
+  }
+};
+
+bool use_filter(const mst_config &cfg, uint32_t n, uint64_t m) {
+  if (cfg.variant == MST_VARIANT_FILTER) return true;
+  if (cfg.variant == MST_VARIANT_BORUVKA) return false;
+  return m >= (1ULL << 20) && 2.0 * (double)m > 8.0 * (double)n;
+}
+
+mst_status solve_device(mst_ctx *c, uint32_t n, uint64_t m, const uint32_t *src, const uint32_t *dst,
+                        const uint32_t *w, uint32_t *out_ids, uint32_t *out_count, u64 *total_weight,
+                        cudaStream_t s) {
+  if (m >= (1ULL << 32)) return MST_ERR_TOO_LARGE;
+  if (!out_count || !total_weight || (m > 0 && (!src || !dst || !w || !out_ids))) return MST_ERR_INVALID_ARG;
+  if (!aligned4(src) || !aligned4(dst) || !aligned4(w) || !aligned4(out_ids)) return MST_ERR_INVALID_ARG;
+  if (n == 0 || m == 0) {
+    if (m > 0 && n == 0) return MST_ERR_VERTEX_RANGE;
+    CK(cudaMemsetAsync(out_count, 0, sizeof(uint32_t), s));
+    CK(cudaMemsetAsync(total_weight, 0, sizeof(u64), s));
+    CK(cudaStreamSynchronize(s));
+    return MST_OK;
+  }
+  Solve S(c, s, n, m);
+  TRY(S.init());
+  const EdgeList in{src, dst, w, nullptr};
+  c->pivot_counter = 0;
+  if (use_filter(c->cfg, n, m))
+    TRY(S.filter(in, m, true, 0));
+  else
+    TRY(S.boruvka(in, m, true));
+  return S.finalize(w, out_ids, out_count, total_weight);
+}
+
+mst_status validate_cfg(const mst_config *cfg) {
+  if (cfg->variant < 0 || cfg->variant > 2) return MST_ERR_INVALID_ARG;
+  if (cfg->dedupe != MST_DEDUPE_AUTO && cfg->dedupe != MST_DEDUPE_HASH && cfg->dedupe != MST_DEDUPE_NONE)
+    return MST_ERR_INVALID_ARG;
+  if (cfg->pivot_sample == 0 || cfg->pivot_sample > (1u << 24)) return MST_ERR_INVALID_ARG;
+  if (!(cfg->filter_max_avg_degree > 0.0f)) return MST_ERR_INVALID_ARG;
+  return MST_OK;
+}
+
+mst_status ensure_sample(mst_ctx *c) {
+  if (c->sample_cap >= c->cfg.pivot_sample) return MST_OK;
+  if (c->sample_buf) cudaFree(c->sample_buf);
+  c->sample_buf = nullptr;
+  c->sample_cap = 0;
+  if (cudaMalloc(&c->sample_buf, (size_t)c->cfg.pivot_sample * sizeof(u64)) != cudaSuccess) {
+    cudaGetLastError();
+    return MST_ERR_OOM;
+  }
+  c->sample_cap = c->cfg.pivot_sample;
+  return MST_OK;
+}
+
+mst_status record(mst_ctx *c, mst_status st) {
+  if (st == MST_ERR_CUDA) cudaGetLastError();
+  c->last = st;
+  return st;
+}
+
+// ---------------------------------------------------------------- batched
+
+__global__ void batch_offset_kernel(const uint32_t *src, const uint32_t *dst, const uint64_t *edge_off,
+                                    const uint64_t *vert_off, uint32_t *usrc, uint32_t *udst, const uint32_t *gn,
+                                    uint32_t *err) {
+  const uint32_t g = blockIdx.x;
+  const uint64_t lo = edge_off[g], hi = edge_off[g + 1];
+  const uint32_t vo = (uint32_t)vert_off[g], ng = gn[g];
+  for (uint64_t e = lo + threadIdx.x; e < hi; e += blockDim.x) {
+    const uint32_t a = src[e], b = dst[e];
+    if (a >= ng || b >= ng) atomicOr(err, ERR_VERTEX);
+    usrc[e] = a < ng ? a + vo : vo;
+    udst[e] = b < ng ? b + vo : vo;
+  }
+}
+
+// Splits the ascending union ids by graph: offsets by binary search, local ids
+// and per-graph weight sums.
+__global__ void batch_split_kernel(const uint32_t *ids, const uint32_t *count, const uint64_t *edge_off,
+                                   uint32_t num_graphs, const uint32_t *w, uint32_t *out_ids, uint64_t *msf_off,
+                                   u64 *total_weight) {
+  __shared__ u64 s_sum[32];
+  __shared__ uint64_t s_lo, s_hi;
+  const uint32_t g = blockIdx.x;
+  const uint64_t k = *count;
+  if (threadIdx.x == 0) {
+    for (int side = 0; side < 2; ++side) {
+      const uint64_t target = edge_off[g + side];
+      uint64_t lo = 0, hi = k;
+      while (lo < hi) {
+        const uint64_t mid = (lo + hi) / 2;
+        if ((uint64_t)ids[mid] < target)
+          lo = mid + 1;
+        else
+          hi = mid;
+      }
+      if (side == 0)
+        s_lo = lo;
+      else
+        s_hi = lo;
+    }
+    msf_off[g] = s_lo;
+    if (g == num_graphs - 1) msf_off[num_graphs] = s_hi;
+  }
+  __syncthreads();
+  u64 sum = 0;
+  const uint64_t base = edge_off[g];
+  for (uint64_t i = s_lo + threadIdx.x; i < s_hi; i += blockDim.x) {
+    const uint32_t id = ids[i];
+    sum += w[id];
+    out_ids[i] = (uint32_t)((uint64_t)id - base);
+  }
+  for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+  if ((threadIdx.x & 31) == 0) s_sum[threadIdx.x >> 5] = sum;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    u64 t = 0;
+    for (unsigned i = 0; i < blockDim.x / 32; ++i) t += s_sum[i];
+    total_weight[g] = t;
+  }
+}
+
+}  // namespace
+
+// ===================================================================== ABI
+
+extern "C" {
+
+void mst_config_default(mst_config *cfg) {
+  if (!cfg) return;
+  std::memset(cfg, 0, sizeof(*cfg));
+  cfg->device = 0;
+  cfg->variant = MST_VARIANT_BORUVKA;
+  cfg->dedupe = MST_DEDUPE_AUTO;
+  cfg->tile_contract = 0;
+  cfg->tile_vertices = 4096;
+  cfg->pivot_sample = 1u << 16;
+  cfg->seed = 0x2302121990ULL;
+  cfg->filter_min_edges = 1ULL << 20;
+  cfg->filter_max_avg_degree = 4.0f;
+}
+
+const char *mst_status_string(mst_status s) {
+  switch (s) {
+    case MST_OK: return "ok";
+    case MST_ERR_INVALID_ARG: return "invalid argument";
+    case MST_ERR_VERTEX_RANGE: return "vertex id out of range";
+    case MST_ERR_TOO_LARGE: return "graph too large (m >= 2^32)";
+    case MST_ERR_OOM: return "out of device memory";
+    case MST_ERR_CUDA: return "CUDA runtime error";
+    case MST_ERR_INTERNAL: return "internal error (bounded device loop exhausted)";
+    case MST_ERR_NOT_SUPPORTED: return "not supported";
+  }
+  return "unknown status";
+}
+
+mst_status mst_create(mst_handle *out, const mst_config *cfg) {
+  if (!out) return MST_ERR_INVALID_ARG;
+  *out = nullptr;
+  mst_config def;
+  mst_config_default(&def);
+  if (!cfg) cfg = &def;
+  if (validate_cfg(cfg) != MST_OK) return MST_ERR_INVALID_ARG;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || cfg->device < 0 || cfg->device >= ndev) {
+    cudaGetLastError();
+    return MST_ERR_CUDA;
+  }
+  mst_ctx *c = new (std::nothrow) mst_ctx();
+  if (!c) return MST_ERR_OOM;
+  c->cfg = *cfg;
+  c->device = cfg->device;
+  DeviceGuard g(c->device);
+  cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, c->device);
+  cudaMemPoolProps props{};
+  props.allocType = cudaMemAllocationTypePinned;
+  props.location.type = cudaMemLocationTypeDevice;
+  props.location.id = c->device;
+  bool ok = cudaMemPoolCreate(&c->pool, &props) == cudaSuccess;
+  if (ok) {
+    uint64_t thr = ~0ULL;
+    ok = cudaMemPoolSetAttribute(c->pool, cudaMemPoolAttrReleaseThreshold, &thr) == cudaSuccess;
+  }
+  ok = ok && cudaMalloc(&c->ds, sizeof(DevState)) == cudaSuccess;
+  ok = ok && cudaMemset(c->ds, 0, sizeof(DevState)) == cudaSuccess;
+  ok = ok && cudaMallocHost(&c->hs, sizeof(DevState)) == cudaSuccess;
+  ok = ok && ensure_sample(c) == MST_OK;
+  ok = ok && cudaDeviceSynchronize() == cudaSuccess;
+  if (!ok) {
+    cudaGetLastError();
+    mst_destroy(c);
+    return MST_ERR_CUDA;
+  }
+  *out = c;
+  return MST_OK;
+}
+
+void mst_destroy(mst_handle h) {
+  if (!h) return;
+  {
+    DeviceGuard g(h->device);
+    cudaDeviceSynchronize();
+    if (h->ds) cudaFree(h->ds);
+    if (h->hs) cudaFreeHost(h->hs);
+    if (h->status) cudaFree(h->status);
+    if (h->sample_buf) cudaFree(h->sample_buf);
+    if (h->pool) cudaMemPoolDestroy(h->pool);
+    for (auto &r : h->prof_pending) {
+      h->ev_pool.push_back(r.a);
+      h->ev_pool.push_back(r.b);
+    }
+    for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
+    cudaGetLastError();
+  }
+  delete h;
+}
+
+mst_status mst_set_config(mst_handle h, const mst_config *cfg) {
+  if (!h || !cfg) return MST_ERR_INVALID_ARG;
+  if (validate_cfg(cfg) != MST_OK || cfg->device != h->device) return record(h, MST_ERR_INVALID_ARG);
+  DeviceGuard g(h->device);
+  h->cfg = *cfg;
+  return record(h, ensure_sample(h));
+}
+
+mst_status mst_get_error(mst_handle h) { return h ? h->last : MST_ERR_INVALID_ARG; }
+
+mst_status mst_profile_enable(mst_handle h, int enable) {
+  if (!h) return MST_ERR_INVALID_ARG;
+  h->prof_on = enable != 0;
+  if (h->prof_on) std::memset(h->prof, 0, sizeof(h->prof));
+  return MST_OK;
+}
+
+mst_status mst_profile_get(mst_handle h, int kind, mst_kernel_stats *out) {
+  if (!h || !out || kind < 0 || kind >= MST_K_COUNT) return MST_ERR_INVALID_ARG;
+  *out = h->prof[kind];
+  return MST_OK;
+}
+
+uint64_t mst_workspace_bytes(uint32_t n, uint64_t m, const mst_config *cfg) {
+  mst_config def;
+  mst_config_default(&def);
+  if (!cfg) cfg = &def;
+  const uint64_t vert = (uint64_t)n * (8 + 4 + 4 + 4);  // best, parent, two active lists
+  const uint64_t bits = (m + 31) / 32 * 4;
+  const uint64_t list = 16 * m + 1024;
+  uint64_t edges = 2 * list;                                    // ping-pong lists
+  if (cfg->dedupe != MST_DEDUPE_NONE) edges += list + 32 * m + 16384;  // dedupe list + hash table
+  if (cfg->variant != MST_VARIANT_BORUVKA) edges += 2 * list;   // partition levels and filtered lists
+  return vert + bits + edges;
+}
+
+mst_status mst_solve(mst_handle h, uint32_t n, uint64_t m, const uint32_t *d_src, const uint32_t *d_dst,
+                     const uint32_t *d_w, uint32_t *d_msf_ids, uint32_t *d_msf_count, uint64_t *d_total_weight,
+                     void *stream) {
+  if (!h) return MST_ERR_INVALID_ARG;
+  DeviceGuard g(h->device);
+  return record(h, solve_device(h, n, m, d_src, d_dst, d_w, d_msf_ids, d_msf_count, (u64 *)d_total_weight,
+                                (cudaStream_t)stream));
+}
+
+mst_status mst_solve_host(mst_handle h, uint32_t n, uint64_t m, const uint32_t *h_src, const uint32_t *h_dst,
+                          const uint32_t *h_w, uint32_t *h_msf_ids, uint32_t *h_msf_count, uint64_t *h_total_weight,
+                          void *stream) {
+  if (!h) return MST_ERR_INVALID_ARG;
+  if (!h_msf_count || !h_total_weight || (m > 0 && (!h_src || !h_dst || !h_w || !h_msf_ids)))
+    return record(h, MST_ERR_INVALID_ARG);
+  if (m >= (1ULL << 32)) return record(h, MST_ERR_TOO_LARGE);
+  DeviceGuard g(h->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  const uint64_t cap = m < (uint64_t)(n > 0 ? n - 1 : 0) ? m : (uint64_t)(n > 0 ? n - 1 : 0);
+  Buf in_b, out_b;
+  const uint64_t stride = round_up(m * 4 + 16, 256);
+  mst_status st = in_b.alloc(h, stride * 3, s);
+  if (st == MST_OK) st = out_b.alloc(h, cap * 4 + 256, s);
+  if (st != MST_OK) return record(h, st);
+  char *b = in_b.as<char>();
+  uint32_t *d_src = (uint32_t *)b, *d_dst = (uint32_t *)(b + stride), *d_w = (uint32_t *)(b + 2 * stride);
+  uint32_t *d_out = out_b.as<uint32_t>();
+  uint32_t *d_count = (uint32_t *)((char *)d_out + cap * 4);
+  u64 *d_total = (u64 *)((char *)d_out + round_up(cap * 4 + 4, 8));
+  if (m > 0) {
+    if (cudaMemcpyAsync(d_src, h_src, m * 4, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        cudaMemcpyAsync(d_dst, h_dst, m * 4, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        cudaMemcpyAsync(d_w, h_w, m * 4, cudaMemcpyHostToDevice, s) != cudaSuccess)
+      return record(h, MST_ERR_CUDA);
+  }
+  st = solve_device(h, n, m, d_src, d_dst, d_w, d_out, d_count, d_total, s);
+  if (st != MST_OK) return record(h, st);
+  uint32_t cnt = 0;
+  if (cudaMemcpyAsync(&cnt, d_count, 4, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaMemcpyAsync(h_total_weight, d_total, 8, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess)
+    return record(h, MST_ERR_CUDA);
+  *h_msf_count = cnt;
+  if (cnt > 0 && (cudaMemcpyAsync(h_msf_ids, d_out, (size_t)cnt * 4, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+                  cudaStreamSynchronize(s) != cudaSuccess))
+    return record(h, MST_ERR_CUDA);
+  return record(h, MST_OK);
+}
+
+mst_status mst_solve_batched(mst_handle h, uint32_t num_graphs, const uint32_t *h_n, const uint64_t *h_edge_off,
+                             const uint32_t *d_src, const uint32_t *d_dst, const uint32_t *d_w, uint32_t *d_msf_ids,
+                             uint64_t *d_msf_off, uint64_t *d_total_weight, void *stream) {
+  if (!h) return MST_ERR_INVALID_ARG;
+  if (num_graphs == 0) return record(h, MST_OK);
+  if (!h_n || !h_edge_off || !d_msf_off || !d_total_weight) return record(h, MST_ERR_INVALID_ARG);
+  DeviceGuard g(h->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  const uint64_t m = h_edge_off[num_graphs];
+  if (h_edge_off[0] != 0) return record(h, MST_ERR_INVALID_ARG);
+  std::vector<uint64_t> voff(num_graphs + 1, 0);
+  for (uint32_t gi = 0; gi < num_graphs; ++gi) {
+    if (h_edge_off[gi + 1] < h_edge_off[gi]) return record(h, MST_ERR_INVALID_ARG);
+    voff[gi + 1] = voff[gi] + h_n[gi];
+  }
+  if (voff[num_graphs] >= (1ULL << 32)) return record(h, MST_ERR_TOO_LARGE);
+  if (m >= (1ULL << 32)) return record(h, MST_ERR_TOO_LARGE);
+  if (m > 0 && (!d_src || !d_dst || !d_w || !d_msf_ids)) return record(h, MST_ERR_INVALID_ARG);
+  const uint32_t n = (uint32_t)voff[num_graphs];
+  // tables + union endpoints
+  Buf tab_b, uni_b, ids_b;
+  const size_t tab_bytes = round_up((num_graphs + 1) * 8, 256) * 2 + round_up(num_graphs * 4, 256);
+  mst_status st = tab_b.alloc(h, tab_bytes, s);
+  const uint64_t stride = round_up(m * 4 + 16, 256);
+  if (st == MST_OK) st = uni_b.alloc(h, stride * 2, s);
+  const uint64_t cap = m < (uint64_t)n ? m : (uint64_t)n;
+  if (st == MST_OK) st = ids_b.alloc(h, cap * 4 + 512, s);
+  if (st != MST_OK) return record(h, st);
+  uint64_t *d_eoff = tab_b.as<uint64_t>();
+  uint64_t *d_voff = (uint64_t *)((char *)tab_b.p + round_up((num_graphs + 1) * 8, 256));
+  uint32_t *d_gn = (uint32_t *)((char *)tab_b.p + 2 * round_up((num_graphs + 1) * 8, 256));
+  uint32_t *usrc = uni_b.as<uint32_t>(), *udst = (uint32_t *)((char *)uni_b.p + stride);
+  uint32_t *ids = ids_b.as<uint32_t>();
+  uint32_t *d_count = (uint32_t *)((char *)ids + round_up(cap * 4, 256));
+  u64 *d_sum = (u64 *)((char *)d_count + 256);
+  if (cudaMemcpyAsync(d_eoff, h_edge_off, (num_graphs + 1) * 8, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+      cudaMemcpyAsync(d_voff, voff.data(), (num_graphs + 1) * 8, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+      cudaMemcpyAsync(d_gn, h_n, num_graphs * 4, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+      cudaMemsetAsync(&h->ds->err, 0, 4, s) != cudaSuccess)
+    return record(h, MST_ERR_CUDA);
+  batch_offset_kernel<<<num_graphs, 256, 0, s>>>(d_src, d_dst, d_eoff, d_voff, usrc, udst, d_gn, &h->ds->err);
+  if (readback(h, s) != MST_OK) return record(h, h->hs->err & ERR_VERTEX ? MST_ERR_VERTEX_RANGE : MST_ERR_CUDA);
+  st = solve_device(h, n, m, usrc, udst, d_w, ids, d_count, d_sum, s);
+  if (st != MST_OK) return record(h, st);
+  batch_split_kernel<<<num_graphs, 256, 0, s>>>(ids, d_count, d_eoff, num_graphs, d_w, d_msf_ids, d_msf_off,
+                                                (u64 *)d_total_weight);
+  if (cudaStreamSynchronize(s) != cudaSuccess) return record(h, MST_ERR_CUDA);
+  return record(h, MST_OK);
+}
+
+// ---------------------------------------------------------------- steps
+
+mst_status mst_step_min_edges(mst_handle h, uint32_t n, uint64_t m, const uint32_t *d_u, const uint32_t *d_v,
+                              const uint32_t *d_w, const uint32_t *d_id, uint64_t *d_best, void *stream) {
+  if (!h || !d_best || (m > 0 && (!d_u || !d_v || !d_w))) return MST_ERR_INVALID_ARG;
+  if (m >= (1ULL << 32)) return record(h, MST_ERR_TOO_LARGE);
+  DeviceGuard g(h->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  if (cudaMemsetAsync(d_best, 0xff, (size_t)n * 8, s) != cudaSuccess ||
+      cudaMemsetAsync(&h->ds->err, 0, 4, s) != cudaSuccess)
+    return record(h, MST_ERR_CUDA);
+  launch_min_edges(EdgeList{d_u, d_v, d_w, d_id}, m, n, 1, (u64 *)d_best, &h->ds->err, h->sms, s);
+  launch_best_slot_to_id((u64 *)d_best, n, d_id, h->sms, s);
+  return record(h, readback(h, s));
+}
+
+mst_status mst_step_contract(mst_handle h, uint32_t n, uint64_t m, const uint32_t *d_u, const uint32_t *d_v,
+                             const uint32_t *d_w, const uint32_t *d_id, uint32_t *d_parent, uint32_t *d_chosen,
+                             void *stream) {
+  if (!h || !d_parent || !d_chosen || (m > 0 && (!d_u || !d_v || !d_w))) return MST_ERR_INVALID_ARG;
+  if (m >= (1ULL << 32)) return record(h, MST_ERR_TOO_LARGE);
+  DeviceGuard g(h->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  Solve S(h, s, n, m);
+  mst_status st = S.init(d_parent, d_chosen);
+  if (st != MST_OK) return record(h, st);
+  const EdgeList E{d_u, d_v, d_w, d_id};
+  launch_min_edges(E, m, n, 1, S.best, &h->ds->err, h->sms, s);
+  HookArgs ha{};
+  ha.ncand = n;
+  ha.best = S.best;
+  ha.list = E;
+  ha.parent = d_parent;
+  ha.chosen_bits = d_chosen;
+  ha.active_out = S.act[0];
+  ha.st = next_scan(h, CNT_ACTIVE);
+  launch_hook(ha, n, s);
+  return record(h, S.jump_until_stars(S.act[0], &h->ds->count[CNT_ACTIVE], 0, n, 1));
+}
+
+static mst_status step_compact(mst_handle h, CompactMode mode, uint32_t n, uint64_t m, const uint32_t *d_u,
+                               const uint32_t *d_v, const uint32_t *d_w, const uint32_t *d_id, const uint32_t *label,
+                               uint64_t pivot, uint32_t *d_ou, uint32_t *d_ov, uint32_t *d_ow, uint32_t *d_oid,
+                               uint64_t *d_out_count, void *stream) {
+  if (!h || !d_out_count || (m > 0 && (!d_u || !d_v || !d_w || !d_ou || !d_ov || !d_ow || !d_oid)))
+    return MST_ERR_INVALID_ARG;
+  if (m >= (1ULL << 32)) return record(h, MST_ERR_TOO_LARGE);
+  DeviceGuard g(h->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  mst_status st = ensure_status(h, m, s);
+  if (st != MST_OK) return record(h, st);
+  if (clear_device_flags(h, s) != MST_OK) return record(h, MST_ERR_CUDA);
+  const EdgeList E{d_u, d_v, d_w, d_id};
+  CompactArgs a{};
+  a.in = E;
+  a.m = m;
+  a.out = EdgeOut{d_ou, d_ov, d_ow, d_oid};
+  a.label = label;
+  a.pivot = pivot;
+  a.n = n;
+  a.validate = (mode == CM_RELABEL || mode == CM_FILTER) ? 1 : 0;
+  Buf table_b;
+  if (mode == CM_DEDUPE) {
+    const uint64_t slots = next_pow2(2 * m < 1024 ? 1024 : 2 * m);
+    st = table_b.alloc(h, slots * sizeof(HashSlot), s);
+    if (st != MST_OK) return record(h, st);
+    if (cudaMemsetAsync(table_b.p, 0xff, slots * sizeof(HashSlot), s) != cudaSuccess) return record(h, MST_ERR_CUDA);
+    a.table = table_b.as<HashSlot>();
+    a.tmask = slots - 1;
+    launch_hash_insert(E, m, a.table, a.tmask, &h->ds->err, h->sms, s);
+  }
+  a.st = next_scan(h, CNT_USER);
+  launch_compact(mode, a, m, s);
+  if (cudaMemcpyAsync(d_out_count, &h->ds->count[CNT_USER], 8, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+    return record(h, MST_ERR_CUDA);
+  return record(h, readback(h, s));
+}
+
+mst_status mst_step_relabel(mst_handle h, uint32_t n, uint64_t m, const uint32_t *d_u, const uint32_t *d_v,
+                            const uint32_t *d_w, const uint32_t *d_id, const uint32_t *d_label, uint32_t *d_ou,
+                            uint32_t *d_ov, uint32_t *d_ow, uint32_t *d_oid, uint64_t *d_out_count, void *stream) {
+  if (!d_label && m > 0) return MST_ERR_INVALID_ARG;
+  return step_compact(h, CM_RELABEL, n, m, d_u, d_v, d_w, d_id, d_label, 0, d_ou, d_ov, d_ow, d_oid, d_out_count,
+                      stream);
+}
+
+mst_status mst_step_dedupe(mst_handle h, uint64_t m, const uint32_t *d_u, const uint32_t *d_v, const uint32_t *d_w,
+                           const uint32_t *d_id, uint32_t *d_ou, uint32_t *d_ov, uint32_t *d_ow, uint32_t *d_oid,
+                           uint64_t *d_out_count, void *stream) {
+  return step_compact(h, CM_DEDUPE, 0, m, d_u, d_v, d_w, d_id, nullptr, 0, d_ou, d_ov, d_ow, d_oid, d_out_count,
+                      stream);
+}
+
+mst_status mst_step_partition(mst_handle h, uint64_t m, const uint32_t *d_u, const uint32_t *d_v, const uint32_t *d_w,
+                              const uint32_t *d_id, uint64_t pivot, uint32_t *d_ou, uint32_t *d_ov, uint32_t *d_ow,
+                              uint32_t *d_oid, uint64_t *d_out_count, void *stream) {
+  return step_compact(h, CM_PARTITION, 0, m, d_u, d_v, d_w, d_id, nullptr, pivot, d_ou, d_ov, d_ow, d_oid,
+                      d_out_count, stream);
+}
+
+mst_status mst_step_filter(mst_handle h, uint32_t n, uint64_t m, const uint32_t *d_u, const uint32_t *d_v,
+                           const uint32_t *d_w, const uint32_t *d_id, uint64_t pivot, uint32_t *d_P, uint32_t *d_ou,
+                           uint32_t *d_ov, uint32_t *d_ow, uint32_t *d_oid, uint64_t *d_out_count, void *stream) {
+  if (!h || !d_P) return MST_ERR_INVALID_ARG;
+  DeviceGuard g(h->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  if (n > 0) {
+    Solve S(h, s, n, 0);
+    S.parent = d_P;
+    if (clear_device_flags(h, s) != MST_OK) return record(h, MST_ERR_CUDA);
+    mst_status st = S.compress_all();
+    if (st != MST_OK) return record(h, st);
+  }
+  return step_compact(h, CM_FILTER, n, m, d_u, d_v, d_w, d_id, d_P, pivot, d_ou, d_ov, d_ow, d_oid, d_out_count,
+                      stream);
+}
+
+mst_status mst_step_pivot(mst_handle h, uint64_t m, const uint32_t *d_w, const uint32_t *d_id, uint64_t state,
+                          uint32_t sample, uint64_t *d_pivot, void *stream) {
+  if (!h || !d_pivot || sample == 0 || (m > 0 && !d_w)) return MST_ERR_INVALID_ARG;
+  DeviceGuard g(h->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  Buf sb;
+  mst_status st = sb.alloc(h, (size_t)sample * 8, s);
+  if (st != MST_OK) return record(h, st);
+  launch_pivot(EdgeList{nullptr, nullptr, d_w, d_id}, m, nullptr, state, sample, sb.as<u64>(), (u64 *)d_pivot, s);
+  if (cudaStreamSynchronize(s) != cudaSuccess) return record(h, MST_ERR_CUDA);
+  return record(h, MST_OK);
+}
+
+mst_status mst_step_finalize(mst_handle h, uint64_t m, const uint32_t *d_chosen, const uint32_t *d_w,
+                             uint32_t *d_msf_ids, uint32_t *d_msf_count, uint64_t *d_total_weight, void *stream) {
+  if (!h || !d_msf_count || !d_total_weight || (m > 0 && (!d_chosen || !d_w || !d_msf_ids)))
+    return MST_ERR_INVALID_ARG;
+  DeviceGuard g(h->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  mst_status st = ensure_status(h, (m + 31) / 32, s);
+  if (st != MST_OK) return record(h, st);
+  if (clear_device_flags(h, s) != MST_OK || cudaMemsetAsync(d_total_weight, 0, 8, s) != cudaSuccess)
+    return record(h, MST_ERR_CUDA);
+  launch_finalize(d_chosen, m, d_w, d_msf_ids, d_msf_count, (u64 *)d_total_weight, next_scan(h, CNT_AUX), s);
+  return record(h, readback(h, s));
+}
+
+}  // extern "C"

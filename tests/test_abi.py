@@ -1,0 +1,55 @@
+"""CPU checks of the C ABI boundary: the library builds, loads without a GPU and
+exports every function include/mst.h declares; calls that need no device work
+behave as documented."""
+import ctypes
+
+import pytest
+
+from paper_2302_12199_gb300 import mst
+
+
+@pytest.fixture(scope="module")
+def lib():
+    return mst.load()
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = mst.declared_symbols()
+    assert "mst_solve" in names and "mst_solve_batched" in names and "mst_create" in names
+    for name in names:
+        assert hasattr(lib, name), name
+    assert set(mst._SIGNATURES) >= set(names)
+
+
+def test_default_config(lib):
+    cfg = mst.MstConfig()
+    lib.mst_config_default(ctypes.byref(cfg))
+    assert cfg.variant == 0 and cfg.dedupe == 0
+    assert cfg.pivot_sample == 1 << 16
+    assert cfg.filter_max_avg_degree == 4.0
+
+
+def test_status_strings(lib):
+    for code in range(8):
+        assert lib.mst_status_string(code)
+    assert lib.mst_status_string(0) == b"ok"
+
+
+def test_invalid_arguments_without_device(lib):
+    h = ctypes.c_void_p()
+    assert lib.mst_create(None, None) == 1
+    assert lib.mst_solve(None, 1, 1, None, None, None, None, None, None, None) == 1
+    assert lib.mst_get_error(None) == 1
+    lib.mst_destroy(None)
+    del h
+
+
+def test_workspace_bytes_grows_with_size(lib):
+    cfg = mst.MstConfig()
+    lib.mst_config_default(ctypes.byref(cfg))
+    a = lib.mst_workspace_bytes(1000, 10000, ctypes.byref(cfg))
+    b = lib.mst_workspace_bytes(1000, 20000, ctypes.byref(cfg))
+    c = lib.mst_workspace_bytes(2000, 20000, ctypes.byref(cfg))
+    assert 0 < a < b < c
+    cfg.variant = 1
+    assert lib.mst_workspace_bytes(1000, 20000, ctypes.byref(cfg)) > b

@@ -1,0 +1,287 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU oracle.
+
+Integer graph work, so the bar is bit-exact: the MSF edge-id set and the uint64
+total weight must equal Kruskal's under the (w, id) order, and every step
+entry point must reproduce its numpy step oracle element by element.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from oracle import steps as S
+from paper_2302_12199_gb300 import workloads as W
+from paper_2302_12199_gb300.mst import MstError, Solver
+from tests.golden import fixtures
+
+pytestmark = pytest.mark.gpu
+
+CONFIGS = [
+    dict(variant="boruvka", dedupe="none"),
+    dict(variant="boruvka", dedupe="hash"),
+    dict(variant="boruvka", dedupe="auto"),
+    dict(variant="filter", dedupe="auto", filter_min_edges=1 << 10, pivot_sample=4096),
+    dict(variant="filter", dedupe="none", filter_min_edges=1 << 12),
+]
+CONFIG_IDS = ["boruvka-none", "boruvka-hash", "boruvka-auto", "filter-auto", "filter-none"]
+
+
+@pytest.fixture(scope="module")
+def dev():
+    assert torch.cuda.is_available(), "a CUDA GPU is required for the gpu tests"
+    return torch.device("cuda", 0)
+
+
+@pytest.fixture(scope="module", params=CONFIGS, ids=CONFIG_IDS)
+def solver(request, dev):
+    s = Solver(0, **request.param)
+    yield s
+    s.close()
+
+
+def to_dev(a, dev):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.uint32).view(np.int32)).to(dev)
+
+
+def gpu_msf(s, n, src, dst, w, dev):
+    return s.solve(n, to_dev(src, dev), to_dev(dst, dev), to_dev(w, dev)).to_host()
+
+
+def assert_same_forest(s, n, src, dst, w, dev, what=""):
+    ids, tot = gpu_msf(s, n, src, dst, w, dev)
+    kid, ktot = oracle.kruskal(n, src, dst, w)
+    assert ids.size == kid.size, f"{what}: |F| {ids.size} != {kid.size}"
+    assert np.array_equal(ids, kid), f"{what}: forest ids differ"
+    assert tot == ktot, f"{what}: weight {tot} != {ktot}"
+
+
+# ------------------------------------------------------------ whole solves
+
+@pytest.mark.parametrize("path", fixtures.all_fixtures())
+def test_hand_fixtures(solver, dev, path):
+    n, src, dst, w, msf, total = fixtures.load(path)
+    ids, tot = gpu_msf(solver, n, src, dst, w, dev)
+    assert np.array_equal(ids, msf) and tot == total
+
+
+def test_tiny_random_multigraphs(solver, dev):
+    rng = np.random.default_rng(2302)
+    for _ in range(60):
+        n = int(rng.integers(1, 40))
+        m = int(rng.integers(1, 300))
+        src = rng.integers(0, n, m).astype(np.uint32)
+        dst = rng.integers(0, n, m).astype(np.uint32)
+        w = rng.integers(1, int(rng.choice([2, 4, 256])), m).astype(np.uint32)
+        assert_same_forest(solver, n, src, dst, w, dev, f"n={n} m={m}")
+
+
+@pytest.mark.parametrize("family", ["gnm", "rmat", "rgg2", "rgg3", "forestish", "dense_small"])
+def test_families_several_tiles_ragged(solver, dev, family):
+    g = {
+        "gnm": lambda: W.gnm(1 << 12, (1 << 16) + 123, 5),
+        "rmat": lambda: W.rmat(14, (1 << 18) + 77, 6),
+        "rgg2": lambda: W.rgg(2, 1 << 14, 8.0, 7),
+        "rgg3": lambda: W.rgg(3, 1 << 14, 8.0, 8),
+        "forestish": lambda: W.gnm(1 << 15, 9000, 9),
+        "dense_small": lambda: W.gnm(300, 40000, 10, wmax=3),
+    }[family]()
+    assert_same_forest(solver, g.n, g.src, g.dst, g.w, dev, family)
+
+
+def test_path_increasing_weights_deep_jumps(solver, dev):
+    # min edges form one chain of length n-1 (pointer doubling worst case)
+    n = 200_000
+    src = np.arange(n - 1, dtype=np.uint32)
+    dst = src + 1
+    w = np.arange(1, n, dtype=np.uint32)
+    assert_same_forest(solver, n, src, dst, w, dev, "path+")
+    assert_same_forest(solver, n, src, dst, w[::-1].copy(), dev, "path-")
+    perm = np.random.default_rng(1).permutation(n).astype(np.uint32)
+    assert_same_forest(solver, n, perm[src], perm[dst], w, dev, "path-permuted")
+
+
+def test_star_hub_contention(solver, dev):
+    n = 300_000
+    leaves = np.arange(1, n, dtype=np.uint32)
+    src = np.concatenate([np.zeros(n - 1, np.uint32), leaves, leaves])
+    dst = np.concatenate([leaves, np.zeros(n - 1, np.uint32), np.roll(leaves, 1)])
+    w = (np.arange(src.size, dtype=np.uint64) * 2654435761 % 7 + 1).astype(np.uint32)
+    assert_same_forest(solver, n, src, dst, w, dev, "star")
+
+
+def test_equal_weights_and_parallel_edges(solver, dev):
+    g = W.gnm(5000, 60000, 11)
+    w = np.full(g.m, 9, np.uint32)
+    assert_same_forest(solver, g.n, g.src, g.dst, w, dev, "equal weights")
+    src = np.repeat(g.src[:3000], 5)
+    dst = np.repeat(g.dst[:3000], 5)
+    w2 = np.tile(np.array([5, 3, 3, 7, 3], np.uint32), 3000)
+    assert_same_forest(solver, g.n, src, dst, w2, dev, "parallel")
+
+
+def test_degenerate_inputs(solver, dev):
+    e = np.zeros(0, np.uint32)
+    ids, tot = gpu_msf(solver, 10, e, e, e, dev)
+    assert ids.size == 0 and tot == 0
+    loops = np.array([3, 3, 4, 0], np.uint32)
+    ids, tot = gpu_msf(solver, 5, loops, loops, np.array([1, 2, 3, 4], np.uint32), dev)
+    assert ids.size == 0 and tot == 0
+    ids, tot = gpu_msf(solver, 1, np.zeros(4, np.uint32), np.zeros(4, np.uint32), np.ones(4, np.uint32), dev)
+    assert ids.size == 0 and tot == 0
+    ids, tot = gpu_msf(solver, 2, np.array([0], np.uint32), np.array([1], np.uint32),
+                       np.array([0xFFFFFFFF], np.uint32), dev)
+    assert ids.tolist() == [0] and tot == 0xFFFFFFFF
+
+
+def test_vertex_out_of_range_is_an_error(solver, dev):
+    src = np.array([0, 1, 2], np.uint32)
+    dst = np.array([1, 2, 7], np.uint32)
+    w = np.array([1, 1, 1], np.uint32)
+    with pytest.raises(MstError) as e:
+        gpu_msf(solver, 5, src, dst, w, dev)
+    assert e.value.status == 2
+    # the handle stays usable
+    assert_same_forest(solver, 5, src[:2], dst[:2], w[:2], dev, "after error")
+
+
+def test_solve_host_matches_device(solver, dev):
+    g = W.rmat(12, 50000, 12)
+    ids, tot = solver.solve_host(g.n, g.src, g.dst, g.w)
+    kid, ktot = oracle.kruskal(g.n, g.src, g.dst, g.w)
+    assert np.array_equal(ids, kid) and tot == ktot
+
+
+def test_repeated_solves_are_identical(solver, dev):
+    g = W.gnm(1 << 13, 1 << 17, 13)
+    t = [to_dev(a, dev) for a in (g.src, g.dst, g.w)]
+    first = solver.solve(g.n, *t).to_host()
+    for _ in range(3):
+        again = solver.solve(g.n, *t).to_host()
+        assert np.array_equal(again[0], first[0]) and again[1] == first[1]
+
+
+# ------------------------------------------------------------------ batched
+
+def test_batched_matches_per_graph_oracle(dev):
+    b = W.mix(48, seed=21, log_lo=6, log_hi=12)
+    s = Solver(0)
+    ids, off, tot = s.solve_batched(b.n, b.edge_off, to_dev(b.src, dev), to_dev(b.dst, dev), to_dev(b.w, dev))
+    ids = ids.cpu().numpy().view(np.uint32)
+    off = off.cpu().numpy()
+    tot = tot.cpu().numpy().view(np.uint64)
+    for g in range(b.num_graphs):
+        gg = b.graph(g)
+        kid, ktot = oracle.kruskal(gg.n, gg.src, gg.dst, gg.w)
+        assert np.array_equal(ids[off[g]:off[g + 1]], kid), g
+        assert int(tot[g]) == ktot
+    s.close()
+
+
+# -------------------------------------------------------------------- steps
+
+@pytest.fixture(scope="module")
+def step_solver(dev):
+    s = Solver(0)
+    yield s
+    s.close()
+
+
+def list_on_dev(dev, *arrs):
+    return [to_dev(a, dev) for a in arrs]
+
+
+def host(t):
+    return t.cpu().numpy().view(np.uint32) if t.dtype == torch.int32 else t.cpu().numpy().view(np.uint64)
+
+
+def test_step_min_edges(step_solver, dev):
+    for g in (W.gnm(3000, 40000, 31), W.rmat(12, 30000, 32)):
+        ids = np.arange(g.m, dtype=np.uint32) * 3 + 5  # ascending, not equal to the index
+        best = host(step_solver.min_edges(g.n, *list_on_dev(dev, g.src, g.dst, g.w, ids)))
+        assert np.array_equal(best, S.min_edges(g.n, g.src, g.dst, g.w, ids))
+        best0 = host(step_solver.min_edges(g.n, *list_on_dev(dev, g.src, g.dst, g.w), None))
+        assert np.array_equal(best0, S.min_edges(g.n, g.src, g.dst, g.w, np.arange(g.m, dtype=np.uint32)))
+
+
+def test_step_contract(step_solver, dev):
+    for g in (W.gnm(5000, 20000, 33), W.rgg(2, 8000, 8.0, 34)):
+        ids = np.arange(g.m, dtype=np.uint32)
+        parent, chosen = step_solver.contract(g.n, *list_on_dev(dev, g.src, g.dst, g.w, ids))
+        best = S.min_edges(g.n, g.src, g.dst, g.w, ids)
+        p, ch = S.hook(g.n, g.src, g.dst, g.w, ids, best)
+        assert np.array_equal(host(parent), S.roots(p))
+        bits = host(chosen)
+        got = np.nonzero(np.unpackbits(bits.view(np.uint8), bitorder="little"))[0]
+        assert np.array_equal(got, ch)
+
+
+def test_step_relabel(step_solver, dev):
+    rng = np.random.default_rng(35)
+    g = W.gnm(4000, 70001, 35)
+    label = rng.integers(0, 300, g.n).astype(np.uint32)
+    ids = np.arange(g.m, dtype=np.uint32) * 2
+    out = step_solver.relabel(g.n, *list_on_dev(dev, g.src, g.dst, g.w, ids, label))
+    exp = S.relabel(label, g.src, g.dst, g.w, ids)
+    for a, b in zip(out, exp):
+        assert np.array_equal(host(a), b)
+
+
+def test_step_dedupe(step_solver, dev):
+    rng = np.random.default_rng(36)
+    m = 50_003
+    u = rng.integers(0, 200, m).astype(np.uint32)
+    v = rng.integers(0, 200, m).astype(np.uint32)
+    keep = u != v
+    u, v = u[keep], v[keep]
+    w = rng.integers(1, 5, u.size).astype(np.uint32)
+    ids = np.arange(u.size, dtype=np.uint32)
+    out = step_solver.dedupe(*list_on_dev(dev, u, v, w, ids))
+    exp = S.dedupe(u, v, w, ids)
+    for a, b in zip(out, exp):
+        assert np.array_equal(host(a), b)
+
+
+def test_step_pivot(step_solver, dev):
+    g = W.gnm(1 << 12, 123_457, 37)
+    ids = np.arange(g.m, dtype=np.uint32)
+    for state, sample in ((S.pivot_state(1, 0), 1 << 16), (S.pivot_state(2, 5), 1000), (77, 1), (78, 3)):
+        got = step_solver.pivot(*list_on_dev(dev, g.w, ids), state=state, sample=sample)
+        assert got == int(S.pivot(g.w, ids, state, sample))
+    got = step_solver.pivot(to_dev(g.w, dev), None, state=5, sample=4096)
+    assert got == int(S.pivot(g.w, ids, 5, 4096))
+
+
+def test_step_partition_and_filter(step_solver, dev):
+    g = W.gnm(3000, 60000, 38)
+    ids = np.arange(g.m, dtype=np.uint32)
+    pv = int(S.pivot(g.w, ids, 123, 4096))
+    out = step_solver.partition(*list_on_dev(dev, g.src, g.dst, g.w, ids), pivot=pv)
+    exp = S.partition_light(g.src, g.dst, g.w, ids, pv)
+    for a, b in zip(out, exp):
+        assert np.array_equal(host(a), b)
+    # representative array from Borůvka rounds on the light part
+    P = np.arange(g.n, dtype=np.uint32)
+    uu, vv, ww, ii = exp
+    while uu.size:
+        r, _, (uu, vv, ww, ii) = S.boruvka_round(g.n, uu, vv, ww, ii)
+        moved = r != np.arange(g.n, dtype=np.uint32)
+        P[moved] = r[moved]
+    Pd = to_dev(P, dev)
+    out = step_solver.filter(g.n, *list_on_dev(dev, g.src, g.dst, g.w, ids), pivot=pv, P=Pd)
+    exp = S.filter_heavy(g.src, g.dst, g.w, ids, pv, P)
+    for a, b in zip(out, exp):
+        assert np.array_equal(host(a), b)
+    assert np.array_equal(host(Pd), S.roots(P))
+
+
+def test_step_finalize(step_solver, dev):
+    rng = np.random.default_rng(39)
+    m = 1_000_003
+    w = rng.integers(1, 2**32 - 1, m, dtype=np.uint64).astype(np.uint32)
+    chosen_ids = np.sort(rng.choice(m, 70_000, replace=False)).astype(np.uint32)
+    bits = np.zeros((m + 31) // 32, np.uint32)
+    np.bitwise_or.at(bits, chosen_ids >> 5, (np.uint32(1) << (chosen_ids & 31)).astype(np.uint32))
+    f = step_solver.finalize(m, to_dev(bits, dev), to_dev(w, dev))
+    ids, tot = f.to_host()
+    assert np.array_equal(ids, chosen_ids)
+    assert tot == int(w[chosen_ids].astype(np.uint64).sum())
