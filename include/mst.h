@@ -214,6 +214,33 @@ mst_status mst_step_filter(mst_handle h, uint32_t n, uint64_t m, const uint32_t 
 mst_status mst_step_finalize(mst_handle h, uint64_t m, const uint32_t *d_chosen, const uint32_t *d_w,
                              uint32_t *d_msf_ids, uint32_t *d_msf_count, uint64_t *d_total_weight, void *stream);
 
+/* ----------------------------------------------------------------------
+ * Allocation-free pivot selection.  The paper has no counterpart: this entry
+ * point exists for callers that cannot allocate device memory -- code running
+ * where cudaMalloc must not be called (host callbacks, real-time threads that
+ * may not block on the allocator), or callers that reserve all of their device
+ * memory themselves and so cannot create a handle (mst_create allocates).
+ *
+ * Computes exactly what mst_step_pivot computes (same sampling rule, same
+ * rank), but needs no handle and calls no allocator: its scratch (the sampled
+ * keys) is a fixed device array of MST_PIVOT_NOALLOC_MAX_SAMPLE uint64 entries
+ * (512 KiB) inside the library, which every GPU that loads the library holds
+ * until the process exits.
+ *   m, d_w, d_id, state, sample  as in mst_step_pivot (d_id may be NULL)
+ *   d_pivot  [out] one uint64, device memory, written in stream order
+ * Runs on the current CUDA device and returns without waiting for the GPU.
+ * The first call on a device looks the array's device address up once (with
+ * that device current); make that first call before any stream capture.
+ * All calls share the one array and it keeps the last call's samples: calls
+ * whose work overlaps on the GPU (different streams, or different host threads
+ * without ordering) race on it and may return wrong pivots.
+ * Errors: MST_ERR_TOO_LARGE if sample > MST_PIVOT_NOALLOC_MAX_SAMPLE or
+ * m >= 2^32; MST_ERR_INVALID_ARG for a NULL output, NULL d_w with m > 0 or
+ * sample == 0; MST_ERR_CUDA if the address lookup or the launch fails. */
+#define MST_PIVOT_NOALLOC_MAX_SAMPLE 65536u
+mst_status mst_pivot_noalloc(uint64_t m, const uint32_t *d_w, const uint32_t *d_id, uint64_t state, uint32_t sample,
+                             uint64_t *d_pivot, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -69,6 +69,7 @@ _SIGNATURES = {
     "mst_step_finalize": (_I, [_P, _U64, _P, _P, _P, _P, _P, _P]),
     "mst_profile_enable": (_I, [_P, _I]),
     "mst_profile_get": (_I, [_P, _I, ctypes.POINTER(KernelStats)]),
+    "mst_pivot_noalloc": (_I, [_U64, _P, _P, _U64, _U32, _P, _P]),
 }
 
 
