@@ -40,6 +40,8 @@ WORKLOADS = {
                     lambda W: W.rmat_large(), dict(variant="filter")),
     "rmat_boruvka": ("RMAT n=2^24 m=2^28 (0.57,0.19,0.19,0.05) permuted, w in [1,255], plain Boruvka",
                      lambda W: W.rmat_large(), dict(variant="boruvka")),
+    "rmat20_filter": ("RMAT n=2^20 m=2^24 (0.57,0.19,0.19,0.05) permuted, w in [1,255], Filter-Boruvka (profiling size)",
+                      lambda W: W.rmat_large(scale=20, m=1 << 24), dict(variant="filter")),
     "gnm": ("GNM n=2^16 m=2^20, w in [1,255], plain Boruvka", lambda W: W.gnm_small(), dict(variant="boruvka")),
     "rgg2d": ("RGG2D n=2^22 degree 8, w in [1,2^32-1], plain Boruvka", lambda W: W.rgg2d_large(),
               dict(variant="boruvka")),
@@ -186,6 +188,11 @@ def gpu_main(args, rank: int, world: int, local_rank: int):
         dist.init_process_group("nccl", device_id=dev)
 
     desc, gen, cfg = WORKLOADS[args.workload]
+    cfg = dict(cfg)
+    if args.variant:
+        cfg["variant"] = args.variant
+    if args.dedupe:
+        cfg["dedupe"] = args.dedupe
     g = gen(W)
     n, m = g.n, g.m
     src = torch.from_numpy(g.src.view(np.int32)).to(dev)
@@ -315,6 +322,9 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--cpu-sample-edges", type=int, default=1 << 25)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--variant", default=None, choices=["boruvka", "filter", "auto"],
+                    help="override the workload's solver variant")
+    ap.add_argument("--dedupe", default=None, choices=["auto", "hash", "none"])
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "gpu":
         args.warmup = 3

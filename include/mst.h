@@ -151,9 +151,10 @@ mst_status mst_profile_get(mst_handle h, int kind, mst_kernel_stats *out);
 /* ----------------------------------------------------------------------
  * Step entry points: one step of the method each, on caller buffers, so that
  * every step can be checked on its own.  Edge lists are SoA (u, v, w, id) of
- * length m; d_id may be NULL, meaning id = index.  Lists passed here must have
- * ascending ids (true of the input and of every list the solver builds).
- * "key" means the uint64 (w << 32) | id.
+ * length m; d_id may be NULL, meaning id = index.  "key" means the uint64
+ * (w << 32) | id.  The list-producing steps write their survivors in an
+ * unspecified order (each block of 2048 input edges keeps its order, blocks
+ * land in the order they finish); the set of survivors is exact.
  * -------------------------------------------------------------------- */
 
 /* minEdges (Alg. 1; Section 2.3): d_best[c] = minimum key over the
@@ -164,7 +165,7 @@ mst_status mst_step_min_edges(mst_handle h, uint32_t n, uint64_t m, const uint32
 /* Hook + pointer doubling (Section 2.3; Section 4.2 contractComponents) of one
  * round: every vertex with an incident edge hooks to the other end of its
  * minimum edge; a 2-cycle keeps the smaller vertex as root; pointers are then
- * doubled until every tree is a star.
+ * doubled until every tree is a star.  d_id must be NULL (edge id = index).
  *   d_parent   [out] [n] root of every vertex (itself when it has no edge)
  *   d_chosen   [in/out] bitmap over edge ids (bit id%32 of word id/32); the
  *              bits of the chosen edges are set, each edge once */
@@ -173,15 +174,14 @@ mst_status mst_step_contract(mst_handle h, uint32_t n, uint64_t m, const uint32_
                              void *stream);
 
 /* Relabel (Section 4.3): (u, v) -> (d_label[u], d_label[v]); self-loops are
- * dropped; the survivors keep their order.  Output arrays need capacity m;
- * d_out_count receives one uint64. */
+ * dropped.  Output arrays need capacity m; d_out_count receives one uint64. */
 mst_status mst_step_relabel(mst_handle h, uint32_t n, uint64_t m, const uint32_t *d_u, const uint32_t *d_v,
                             const uint32_t *d_w, const uint32_t *d_id, const uint32_t *d_label, uint32_t *d_ou,
                             uint32_t *d_ov, uint32_t *d_ow, uint32_t *d_oid, uint64_t *d_out_count, void *stream);
 
 /* Parallel-edge removal (Section 2.3; Section 4.3 Redistribute; Section 6.2
  * hash table): of the edges joining one unordered pair keep the minimum key;
- * survivors keep their order and orientation.  Capacity m; one uint64 count. */
+ * survivors keep their orientation.  Capacity m; one uint64 count. */
 mst_status mst_step_dedupe(mst_handle h, uint64_t m, const uint32_t *d_u, const uint32_t *d_v, const uint32_t *d_w,
                            const uint32_t *d_id, uint32_t *d_ou, uint32_t *d_ov, uint32_t *d_ow, uint32_t *d_oid,
                            uint64_t *d_out_count, void *stream);
@@ -193,8 +193,8 @@ mst_status mst_step_dedupe(mst_handle h, uint64_t m, const uint32_t *d_u, const 
 mst_status mst_step_pivot(mst_handle h, uint64_t m, const uint32_t *d_w, const uint32_t *d_id, uint64_t state,
                           uint32_t sample, uint64_t *d_pivot, void *stream);
 
-/* Light part of the partition (Alg. 2): edges with key <= pivot and u != v,
- * in order.  Capacity m; one uint64 count. */
+/* Light part of the partition (Alg. 2): edges with key <= pivot and u != v.
+ * Capacity m; one uint64 count. */
 mst_status mst_step_partition(mst_handle h, uint64_t m, const uint32_t *d_u, const uint32_t *d_v, const uint32_t *d_w,
                               const uint32_t *d_id, uint64_t pivot, uint32_t *d_ou, uint32_t *d_ov, uint32_t *d_ow,
                               uint32_t *d_oid, uint64_t *d_out_count, void *stream);

@@ -21,24 +21,29 @@ enum : uint32_t {
 struct DevState {
   uint32_t err;
   uint32_t jump_flag;   // set when a pointer-jump launch left a vertex short of its root
-  uint32_t tile_ctr[2]; // dynamic tile counters of the scan kernels (alternating by epoch)
+  uint32_t tile_ctr[2]; // reserved
   u64 count[6];         // counts written by the last tile of a scan kernel
   u64 pivot;            // result of the pivot selection
+  uint32_t giant_root;  // root of the largest sampled component (filter fast path)
+  uint32_t pad;
 };
 enum { CNT_EDGES = 0, CNT_ACTIVE = 1, CNT_TMP = 2, CNT_AUX = 3, CNT_USER = 4 };
 
-// State of one decoupled look-back scan launch.
+// Output bookkeeping of a compaction launch.  Unordered compactions claim
+// their output ranges by atomic adds on *total (zero before the launch); the
+// ordered scan of the output ids uses the look-back status words, and its last
+// tile writes *total.
 struct ScanState {
   u64 *status;       // one status word per tile: epoch(30) | flag(2) | value(32)
-  uint32_t *tile_ctr;
-  uint32_t epoch;    // 1 .. 2^30-1, different for every launch
-  u64 *total;        // receives the scan total (written by the last tile)
+  uint32_t *tile_ctr;  // unused
+  uint32_t epoch;    // 1 .. 2^30-1, different for every ordered launch
+  u64 *total;
   uint32_t *err;
 };
 
 struct HashSlot {
   u64 pair;  // (min(u,v) << 32) | max(u,v); all ones = empty
-  u64 key;   // minimum (w << 32) | slot seen for this pair
+  u64 key;   // minimum (w << 32) | id seen for this pair
 };
 
 // An edge list in structure-of-arrays form.  id == nullptr: id = index.
@@ -53,7 +58,7 @@ enum CompactMode : int {
   CM_RELABEL = 0,    // (label[u], label[v]); drop self-loops
   CM_PARTITION = 1,  // key <= pivot and u != v; unchanged
   CM_FILTER = 2,     // key > pivot; (label[u], label[v]); drop self-loops
-  CM_DEDUPE = 3,     // keep iff the hash table holds this edge's slot key for its pair
+  CM_DEDUPE = 3,     // keep iff the hash table holds this edge's key for its pair
 };
 
 struct CompactArgs {
@@ -62,9 +67,10 @@ struct CompactArgs {
   const u64 *m_dev;        // input length in device memory, or nullptr
   EdgeOut out;
   const uint32_t *label;   // relabel / filter
+  const uint32_t *giant_bits;  // filter: bitmap of the vertices in the largest component, or nullptr
   u64 pivot;               // partition / filter (used when pivot_dev == nullptr)
   const u64 *pivot_dev;
-  u64 *best;               // if set: relax best[] with the output slot keys
+  u64 *best;               // if set: relax best[] of both ends with each survivor's key
   HashSlot *table;         // dedupe lookup, or insert target when hash_insert
   uint64_t tmask;
   int hash_insert;
@@ -77,12 +83,13 @@ struct HookArgs {
   const uint32_t *cand;    // candidate vertices; nullptr = 0..ncand-1
   uint64_t ncand;
   const u64 *ncand_dev;    // candidate count in device memory, or nullptr
-  u64 *best;
-  EdgeList list;           // the list whose slots the keys in best[] refer to
+  u64 *best;               // keys (w << 32) | id of the round's minimum edges
+  const uint32_t *src, *dst;  // input endpoints, indexed by edge id
   uint32_t *parent;
-  uint32_t *chosen_bits;   // bitmap over original edge ids
-  uint32_t *active_out;    // compacted active vertices
-  ScanState st;
+  uint32_t *chosen_bits;   // bitmap over edge ids
+  uint32_t *active_out;    // active vertices (best != INF), unspecified order
+  u64 *counter;            // number written to active_out; zero before the launch
+  uint32_t *err;
 };
 
 // ---- launchers (kernels.cu); all asynchronous on `s` ----
@@ -95,11 +102,12 @@ void launch_jump(const uint32_t *act, const u64 *count_dev, uint64_t count_host,
                  uint32_t *parent, u64 *best, int reset_best, uint32_t *flag, int sms, cudaStream_t s);
 void launch_hash_insert(EdgeList in, uint64_t m, HashSlot *table, uint64_t tmask, uint32_t *err, int sms,
                         cudaStream_t s);
-void launch_best_slot_to_id(u64 *best, uint32_t n, const uint32_t *ids, int sms, cudaStream_t s);
 void launch_pivot(EdgeList in, uint64_t m, const u64 *m_dev, u64 state, uint32_t sample, u64 *sample_buf,
                   u64 *pivot_out, cudaStream_t s);
 void launch_finalize(const uint32_t *bits, uint64_t m, const uint32_t *w, uint32_t *out_ids, uint32_t *out_count,
                      u64 *total_weight, ScanState st, cudaStream_t s);
+void launch_giant_bits(EdgeList in, uint64_t m, u64 state, const uint32_t *P, uint32_t n, uint32_t *root_tmp,
+                       uint32_t *bits, int sms, cudaStream_t s);
 void launch_iota(uint32_t *p, uint64_t n, int sms, cudaStream_t s);
 void launch_u64_to_u32(const u64 *src, uint32_t *dst, cudaStream_t s);
 

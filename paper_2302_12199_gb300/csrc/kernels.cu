@@ -3,16 +3,16 @@
 // Everything here is integer work on edge lists stored as SoA uint32 arrays
 // (u, v, w, id).  The order on edges is the uint64 key (w << 32) | id, a strict
 // total order (paper Section 2.3: ties broken consistently so that the MST is
-// unique).  Inside one list the ids ascend with the position ("slot"), so the
-// solver keys edges by (w << 32) | slot, which orders them exactly as
-// (w << 32) | id while letting a vertex find its chosen edge by slot.
+// unique); id is the edge's index in the caller's input.
 //
-// Stream compaction (relabel, partition, filter, dedupe, active vertices,
-// output ids) is one pass per list: each 256-thread block takes the next tile
-// of 2048 items from a dynamic counter, scans its keep flags, and learns the
-// tile's output offset by a decoupled look-back over the preceding tiles' status
-// words (Merrill & Garland, "Single-pass Parallel Prefix Scan with Decoupled
-// Look-back", 2016).  Survivors keep their input order.  Every wait is bounded.
+// Stream compaction (relabel, partition, filter, dedupe, active vertices) is
+// one pass per list: each 256-thread block takes a tile of 2048 items, keeps
+// the tile's survivors in order, and claims its output range with one atomic
+// add.  Tiles therefore land in an unspecified order; nothing downstream
+// depends on list order, because edges are keyed by id and a vertex finds its
+// chosen edge through the input arrays.  The output ids (finalize) are the one
+// ordered compaction: a decoupled look-back scan (Merrill & Garland, 2016).
+// Every wait is bounded.
 #include <cstdint>
 
 #include "internal.h"
@@ -38,14 +38,34 @@ __device__ __forceinline__ void st_relaxed(u64 *p, u64 v) {
   asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
 
-__device__ __forceinline__ void load8(const uint32_t *p, uint64_t base, uint32_t (&x)[ITEMS]) {
-  const uint4 *q = reinterpret_cast<const uint4 *>(p + base);
-  const uint4 a = __ldg(q), b = __ldg(q + 1);
+// Striped item layout inside a tile of TILE items: item k (0..7) of thread t
+// sits at tile offset (k / 4) * (BLOCK * 4) + 4 * t + k % 4.  Each warp-wide
+// 16-byte load then covers 512 contiguous bytes (whole sectors, used once).
+// Output order is tile order: chunk 0 (k < 4) of every thread, then chunk 1.
+__device__ __forceinline__ uint32_t item_off(int k) {
+  return (uint32_t)((k >> 2) * (BLOCK * 4) + 4 * threadIdx.x + (k & 3));
+}
+
+__device__ __forceinline__ void load_striped(const uint32_t *p, uint64_t tile_base, uint32_t (&x)[ITEMS]) {
+  const uint4 *q = reinterpret_cast<const uint4 *>(p + tile_base);
+  const uint4 a = __ldg(q + threadIdx.x), b = __ldg(q + BLOCK + threadIdx.x);
   x[0] = a.x; x[1] = a.y; x[2] = a.z; x[3] = a.w;
   x[4] = b.x; x[5] = b.y; x[6] = b.z; x[7] = b.w;
 }
 
-__device__ __forceinline__ u64 edge_key(uint32_t w, uint64_t slot) { return ((u64)w << 32) | (u64)(uint32_t)slot; }
+// Per-thread counts of kept items in the two chunks, packed for one scan.
+__device__ __forceinline__ uint32_t packed_counts(uint32_t keep) {
+  return (uint32_t)__popc(keep & 0xfu) | ((uint32_t)__popc(keep >> 4) << 16);
+}
+
+// Tile-local output position of kept item k, from the packed exclusive scan
+// value of this thread and the packed tile total.
+__device__ __forceinline__ uint32_t local_pos(uint32_t keep, int k, uint32_t excl_p, uint32_t total_p) {
+  if (k < 4) return (excl_p & 0xffffu) + (uint32_t)__popc(keep & ((1u << k) - 1u));
+  return (total_p & 0xffffu) + (excl_p >> 16) + (uint32_t)__popc((keep >> 4) & ((1u << (k - 4)) - 1u));
+}
+
+__device__ __forceinline__ u64 edge_key(uint32_t w, uint32_t id) { return ((u64)w << 32) | (u64)id; }
 
 __device__ __forceinline__ u64 pair_of(uint32_t a, uint32_t b) {
   return a < b ? (((u64)a << 32) | b) : (((u64)b << 32) | a);
@@ -90,53 +110,90 @@ __device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t x, uint32_t &t
   return s_warp[wid] + incl - x;
 }
 
-// Decoupled look-back, run by all 32 lanes of warp 0.  Publishes the tile's
-// aggregate, waits (bounded) for predecessors, publishes the inclusive prefix
-// and returns the tile's exclusive prefix.  Status word layout:
+// Decoupled look-back by the whole block.  Publishes the tile's aggregate,
+// then examines LB_WINDOW = BLOCK * LB_PER_THREAD predecessors per round (each
+// thread polls LB_PER_THREAD status words, bounded), adds the values up to the
+// nearest tile whose inclusive prefix is published, and continues further back
+// only if none in the window has one; finally publishes its own inclusive
+// prefix and returns the exclusive one.  A window as wide as the number of
+// tiles in flight keeps the walk to one round.  Status word layout:
 // epoch (bits 63..34) | flag (33..32: 1 aggregate, 2 inclusive, 3 error) | value.
-__device__ uint32_t decoupled_lookback(const ScanState &st, uint32_t tile, uint32_t aggregate, bool &error) {
-  const uint32_t lane = threadIdx.x & 31;
+constexpr int LB_PER_THREAD = 4;
+constexpr int LB_WINDOW = BLOCK * LB_PER_THREAD;
+
+struct LookbackShared {
+  uint32_t first;    // smallest window offset holding an inclusive prefix
+  uint32_t error;
+  uint32_t sum[BLOCK / 32];
+};
+
+__device__ uint32_t decoupled_lookback(const ScanState &st, uint32_t tile, uint32_t aggregate, bool &error,
+                                       LookbackShared &sh) {
   const u64 tag = (u64)st.epoch << 34;
-  error = false;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   if (tile == 0) {
-    if (lane == 0) st_relaxed(&st.status[0], tag | (2ULL << 32) | aggregate);
+    if (threadIdx.x == 0) st_relaxed(&st.status[0], tag | (2ULL << 32) | aggregate);
+    error = false;
     return 0;
   }
-  if (lane == 0) st_relaxed(&st.status[tile], tag | (1ULL << 32) | aggregate);
-  uint32_t exclusive = 0, spins = 0;
-  long long pred = (long long)tile - 1 - (long long)lane;
+  if (threadIdx.x == 0) st_relaxed(&st.status[tile], tag | (1ULL << 32) | aggregate);
+  uint32_t exclusive = 0;
+  long long top = (long long)tile - 1;  // newest predecessor of the current window
   for (;;) {
-    u64 s = 0;
-    uint32_t flag = 2;
-    for (;;) {
-      if (pred >= 0) {
-        s = ld_relaxed(&st.status[pred]);
-        flag = ((uint32_t)(s >> 34) == st.epoch) ? (uint32_t)((s >> 32) & 3u) : 0u;
-      } else {
-        s = 0;
-        flag = 2;
-      }
-      if (__all_sync(0xffffffffu, flag != 0)) break;
-      if (++spins > SPIN_LIMIT) {
-        error = true;
-        break;
-      }
-      __nanosleep(64);
+    if (threadIdx.x == 0) {
+      sh.first = LB_WINDOW;
+      sh.error = 0;
     }
-    if (error || __any_sync(0xffffffffu, flag == 3)) {
+    __syncthreads();
+    uint32_t val[LB_PER_THREAD], flag[LB_PER_THREAD];
+#pragma unroll
+    for (int k = 0; k < LB_PER_THREAD; ++k) {
+      const long long pred = top - (long long)(k * BLOCK + threadIdx.x);  // window offset k*BLOCK+tid
+      val[k] = 0;
+      flag[k] = 2;
+      if (pred >= 0) {
+        uint32_t spins = 0;
+        for (;;) {
+          const u64 s = ld_relaxed(&st.status[pred]);
+          flag[k] = ((uint32_t)(s >> 34) == st.epoch) ? (uint32_t)((s >> 32) & 3u) : 0u;
+          val[k] = (uint32_t)s;
+          if (flag[k] != 0) break;
+          if (++spins > SPIN_LIMIT) {
+            flag[k] = 3;
+            break;
+          }
+          __nanosleep(32);
+        }
+      }
+      if (flag[k] == 3) atomicOr(&sh.error, 1u);
+      if (flag[k] == 2) atomicMin(&sh.first, (uint32_t)(k * BLOCK + threadIdx.x));
+    }
+    __syncthreads();
+    if (sh.error) {
       error = true;
       break;
     }
-    const uint32_t incl = __ballot_sync(0xffffffffu, flag == 2);
-    const int first = incl ? __ffs(incl) - 1 : 32;
-    uint32_t val = (int)lane <= first ? (uint32_t)(s & 0xffffffffULL) : 0u;
+    const uint32_t first = sh.first;
+    uint32_t part = 0;
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) val += __shfl_xor_sync(0xffffffffu, val, o);
-    exclusive += val;
-    if (incl) break;
-    pred -= 32;
+    for (int k = 0; k < LB_PER_THREAD; ++k)
+      if ((uint32_t)(k * BLOCK + threadIdx.x) <= first) part += val[k];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+    if (lane == 0) sh.sum[wid] = part;
+    __syncthreads();
+    uint32_t win = 0;
+#pragma unroll
+    for (int i = 0; i < BLOCK / 32; ++i) win += sh.sum[i];
+    exclusive += win;
+    if (first < LB_WINDOW) {
+      error = false;
+      break;
+    }
+    top -= LB_WINDOW;
+    __syncthreads();  // sh.sum is rewritten in the next round
   }
-  if (lane == 0) {
+  if (threadIdx.x == 0) {
     if (error)
       st_relaxed(&st.status[tile], tag | (3ULL << 32));
     else
@@ -145,52 +202,53 @@ __device__ uint32_t decoupled_lookback(const ScanState &st, uint32_t tile, uint3
   return exclusive;
 }
 
-// Tile bookkeeping shared by the scan kernels.  Returns false when this block
-// has no tile (more blocks than tiles).
+// Tile bookkeeping shared by the scan kernels.  Tile t is processed by block t
+// (blocks are dispatched in index order, so every predecessor of a waiting
+// block is already resident or finished).  Returns false when this block has
+// no tile (the count is read on the device and the grid was sized for an upper
+// bound).
 struct TileInfo {
   uint32_t tile, ntiles;
 };
 
-__device__ __forceinline__ bool acquire_tile(const ScanState &st, uint64_t count, uint32_t *s_tile, TileInfo &t) {
+__device__ __forceinline__ bool acquire_tile(const ScanState &st, uint64_t count, TileInfo &t) {
   t.ntiles = (uint32_t)((count + TILE - 1) / TILE);
-  if (threadIdx.x == 0) *s_tile = atomicAdd(&st.tile_ctr[st.epoch & 1u], 1u);
-  __syncthreads();
-  t.tile = *s_tile;
+  t.tile = blockIdx.x;
   if (t.tile >= t.ntiles) {
-    if (t.ntiles == 0 && t.tile == 0 && threadIdx.x == 0) {
-      *st.total = 0;
-      st.tile_ctr[(st.epoch + 1) & 1u] = 0;
-    }
+    if (t.ntiles == 0 && t.tile == 0 && threadIdx.x == 0) *st.total = 0;
     return false;
   }
   return true;
 }
 
-// Scan + look-back for one tile.  Returns the tile's output offset; false on a
-// look-back error (the tile then writes nothing).
-__device__ __forceinline__ bool tile_offsets(const ScanState &st, const TileInfo &t, uint32_t count,
-                                             uint32_t &thread_excl, uint32_t &tile_total, uint64_t &tile_base,
-                                             uint32_t *s_warp, uint32_t *s_excl, uint32_t *s_err) {
-  thread_excl = block_exclusive_scan(count, tile_total, s_warp);
-  if (threadIdx.x < 32) {
-    bool err;
-    const uint32_t ex = decoupled_lookback(st, t.tile, tile_total, err);
-    if (threadIdx.x == 0) {
-      *s_excl = ex;
-      *s_err = err ? 1u : 0u;
-    }
-  }
-  __syncthreads();
-  if (*s_err) {
+// Scan + look-back for one tile.  `packed` holds this thread's chunk-0 count in
+// the low and chunk-1 count in the high 16 bits (each block total is at most
+// TILE / 2, so the halves never carry).  Returns the packed exclusive scan, the
+// packed tile total and the tile's output offset; false on a look-back error
+// (the tile then writes nothing).
+__device__ __forceinline__ bool tile_offsets(const ScanState &st, const TileInfo &t, uint32_t packed,
+                                             uint32_t &excl_p, uint32_t &total_p, uint64_t &tile_base,
+                                             uint32_t *s_warp, LookbackShared &sh) {
+  excl_p = block_exclusive_scan(packed, total_p, s_warp);
+  const uint32_t tile_total = (total_p & 0xffffu) + (total_p >> 16);
+  bool err = false;
+  const uint32_t ex = decoupled_lookback(st, t.tile, tile_total, err, sh);
+  if (err) {
     if (threadIdx.x == 0) atomicOr(st.err, ERR_LOOKBACK);
     return false;
   }
-  tile_base = *s_excl;
-  if (t.tile == t.ntiles - 1 && threadIdx.x == 0) {
-    *st.total = tile_base + tile_total;
-    st.tile_ctr[(st.epoch + 1) & 1u] = 0;  // the next launch uses the other counter
-  }
+  tile_base = ex;
+  if (t.tile == t.ntiles - 1 && threadIdx.x == 0) *st.total = tile_base + tile_total;
   return true;
+}
+
+// Claims `total` output slots for this block's tile with one atomic add on the
+// list's counter and broadcasts the base to the block (order of tiles in the
+// output is unspecified; order inside a tile is kept).
+__device__ __forceinline__ uint64_t tile_claim(unsigned long long *counter, uint32_t total, uint32_t *s_base) {
+  if (threadIdx.x == 0) s_base[0] = total ? (uint32_t)atomicAdd(counter, (unsigned long long)total) : 0u;
+  __syncthreads();
+  return s_base[0];
 }
 
 // best[c] = min(best[c], key) for up to 2*ITEMS (vertex, key) pairs.  The
@@ -241,54 +299,16 @@ __device__ __forceinline__ u64 hash_lookup(const HashSlot *t, uint64_t mask, u64
 
 // ---------------------------------------------------------------- compaction
 
-// One stream-compaction pass over an edge list; see CompactMode.  Survivors
-// keep their order.  Optional post actions with the survivors' output slots:
-// relax best[] (minEdges of the next round, fused) and/or insert the pair into
-// the dedupe hash table.
-template <int MODE, bool VEC>
-__global__ void __launch_bounds__(BLOCK) compact_kernel(CompactArgs a) {
-  __shared__ uint32_t s_u[TILE], s_v[TILE], s_w[TILE], s_id[TILE];
-  __shared__ uint32_t s_warp[BLOCK / 32 + 1];
-  __shared__ uint32_t s_tile, s_excl, s_err;
-
-  const uint64_t m = a.m_dev ? *a.m_dev : a.m;
-  TileInfo t;
-  if (!acquire_tile(a.st, m, &s_tile, t)) return;
-  const uint64_t base = (uint64_t)t.tile * TILE + (uint64_t)threadIdx.x * ITEMS;
-
-  uint32_t eu[ITEMS], ev[ITEMS], ew[ITEMS], ei[ITEMS];
-  if (VEC && base + ITEMS <= m) {
-    load8(a.in.u, base, eu);
-    load8(a.in.v, base, ev);
-    load8(a.in.w, base, ew);
-    if (a.in.id) {
-      load8(a.in.id, base, ei);
-    } else {
-#pragma unroll
-      for (int k = 0; k < ITEMS; ++k) ei[k] = (uint32_t)(base + k);
-    }
-  } else {
-#pragma unroll
-    for (int k = 0; k < ITEMS; ++k) {
-      const uint64_t j = base + k;
-      if (j < m) {
-        eu[k] = __ldg(a.in.u + j);
-        ev[k] = __ldg(a.in.v + j);
-        ew[k] = __ldg(a.in.w + j);
-        ei[k] = a.in.id ? __ldg(a.in.id + j) : (uint32_t)j;
-      } else {
-        eu[k] = ev[k] = ew[k] = ei[k] = 0;
-      }
-    }
-  }
-
-  u64 pivot = 0;
-  if (MODE == CM_PARTITION || MODE == CM_FILTER) pivot = a.pivot_dev ? *a.pivot_dev : a.pivot;
-
+// Keep flags of one tile for a compaction mode (see CompactMode); relabels
+// eu/ev in place where the mode relabels.  Bit k = item k.
+template <int MODE>
+__device__ __forceinline__ uint32_t keep_flags(const CompactArgs &a, uint64_t tb, uint64_t m, u64 pivot,
+                                               uint32_t (&eu)[ITEMS], uint32_t (&ev)[ITEMS],
+                                               const uint32_t (&ew)[ITEMS], const uint32_t (&ei)[ITEMS]) {
   uint32_t keep = 0;
 #pragma unroll
   for (int k = 0; k < ITEMS; ++k) {
-    const uint64_t j = base + k;
+    const uint64_t j = tb + item_off(k);
     bool ok = j < m;
     if (ok && a.validate && (eu[k] >= a.n || ev[k] >= a.n)) {
       atomicOr(a.st.err, ERR_VERTEX);
@@ -303,32 +323,42 @@ __global__ void __launch_bounds__(BLOCK) compact_kernel(CompactArgs a) {
     } else if (MODE == CM_PARTITION) {
       ok = ok && eu[k] != ev[k] && (((u64)ew[k] << 32) | ei[k]) <= pivot;
     } else if (MODE == CM_FILTER) {
-      if (ok && (((u64)ew[k] << 32) | ei[k]) > pivot) {
+      ok = ok && (((u64)ew[k] << 32) | ei[k]) > pivot;
+      // both ends in the marked (largest) component: inside one component
+      if (ok && a.giant_bits && ((__ldg(a.giant_bits + (eu[k] >> 5)) >> (eu[k] & 31)) & 1u) &&
+          ((__ldg(a.giant_bits + (ev[k] >> 5)) >> (ev[k] & 31)) & 1u))
+        ok = false;
+      if (ok) {
         eu[k] = __ldg(a.label + eu[k]);
         ev[k] = __ldg(a.label + ev[k]);
         ok = eu[k] != ev[k];
-      } else {
-        ok = false;
       }
     } else {  // CM_DEDUPE
-      if (ok) ok = hash_lookup(a.table, a.tmask, pair_of(eu[k], ev[k])) == edge_key(ew[k], j);
+      if (ok) ok = hash_lookup(a.table, a.tmask, pair_of(eu[k], ev[k])) == edge_key(ew[k], ei[k]);
     }
     keep |= (ok ? 1u : 0u) << k;
   }
+  return keep;
+}
 
-  uint32_t excl, total;
-  uint64_t obase;
-  if (!tile_offsets(a.st, t, __popc(keep), excl, total, obase, s_warp, &s_excl, &s_err)) return;
-
-  uint32_t lp = excl;
+// Writes the kept items of a tile to shared memory at their tile-local output
+// positions, stores them coalesced at obase, then runs the post actions on the
+// survivors: relax best[] (the next round's minEdges, fused) and/or insert the
+// pair into the dedupe hash table.
+__device__ __forceinline__ void emit_survivors(const CompactArgs &a, uint32_t keep, uint32_t excl, uint32_t totp,
+                                               uint64_t obase, const uint32_t (&eu)[ITEMS],
+                                               const uint32_t (&ev)[ITEMS], const uint32_t (&ew)[ITEMS],
+                                               const uint32_t (&ei)[ITEMS], uint32_t *s_u, uint32_t *s_v,
+                                               uint32_t *s_w, uint32_t *s_id) {
+  const uint32_t total = (totp & 0xffffu) + (totp >> 16);
 #pragma unroll
   for (int k = 0; k < ITEMS; ++k) {
     if (keep >> k & 1) {
+      const uint32_t lp = local_pos(keep, k, excl, totp);
       s_u[lp] = eu[k];
       s_v[lp] = ev[k];
       s_w[lp] = ew[k];
       s_id[lp] = ei[k];
-      ++lp;
     }
   }
   __syncthreads();
@@ -338,23 +368,81 @@ __global__ void __launch_bounds__(BLOCK) compact_kernel(CompactArgs a) {
     a.out.w[obase + i] = s_w[i];
     a.out.id[obase + i] = s_id[i];
   }
-
-  if (a.best || a.hash_insert) {
-    u64 key[ITEMS];
-    lp = excl;
+  // post actions read the survivors back from shared memory (coalesced; the
+  // loaded edges' registers are dead by now)
+  if (a.best) {
+    for (uint32_t i0 = 0; i0 < total; i0 += 4 * BLOCK) {
+      uint32_t x[4], y[4];
+      u64 key[4], cx[4], cy[4];
 #pragma unroll
-    for (int k = 0; k < ITEMS; ++k) {
-      key[k] = edge_key(ew[k], obase + lp);
-      lp += keep >> k & 1;
-    }
-    if (a.best) relax_pairs(a.best, eu, ev, key, keep);
-    if (a.hash_insert) {
+      for (int k = 0; k < 4; ++k) {
+        const uint32_t i = i0 + k * BLOCK + threadIdx.x;
+        const bool ok = i < total;
+        x[k] = ok ? s_u[i] : 0u;
+        y[k] = ok ? s_v[i] : 0u;
+        key[k] = ok ? edge_key(s_w[i], s_id[i]) : KEY_INF;
+        cx[k] = ok ? __ldcg(a.best + x[k]) : 0ULL;
+        cy[k] = ok ? __ldcg(a.best + y[k]) : 0ULL;
+      }
 #pragma unroll
-      for (int k = 0; k < ITEMS; ++k)
-        if ((keep >> k & 1) && !hash_insert(a.table, a.tmask, pair_of(eu[k], ev[k]), key[k]))
-          atomicOr(a.st.err, ERR_HASH);
+      for (int k = 0; k < 4; ++k) {
+        if (key[k] < cx[k]) atomicMin(a.best + x[k], key[k]);
+        if (key[k] < cy[k]) atomicMin(a.best + y[k], key[k]);
+      }
     }
   }
+  if (a.hash_insert) {
+    for (uint32_t i = threadIdx.x; i < total; i += BLOCK)
+      if (!hash_insert(a.table, a.tmask, pair_of(s_u[i], s_v[i]), edge_key(s_w[i], s_id[i])))
+        atomicOr(a.st.err, ERR_HASH);
+  }
+}
+
+__device__ __forceinline__ u64 compact_pivot(const CompactArgs &a, int mode) {
+  return (mode == CM_PARTITION || mode == CM_FILTER) ? (a.pivot_dev ? *a.pivot_dev : a.pivot) : 0ULL;
+}
+
+// One stream-compaction pass over an edge list, one tile per block.
+template <int MODE, bool VEC>
+__global__ void __launch_bounds__(BLOCK, 4) compact_kernel(CompactArgs a) {
+  __shared__ uint32_t s_u[TILE], s_v[TILE], s_w[TILE], s_id[TILE];
+  __shared__ uint32_t s_warp[BLOCK / 32 + 1];
+  __shared__ uint32_t s_base[1];
+
+  const uint64_t m = a.m_dev ? *a.m_dev : a.m;
+  const uint64_t tb = (uint64_t)blockIdx.x * TILE;
+  if (tb >= m) return;
+
+  uint32_t eu[ITEMS], ev[ITEMS], ew[ITEMS], ei[ITEMS];
+  if (VEC && tb + TILE <= m) {
+    load_striped(a.in.u, tb, eu);
+    load_striped(a.in.v, tb, ev);
+    load_striped(a.in.w, tb, ew);
+    if (a.in.id) {
+      load_striped(a.in.id, tb, ei);
+    } else {
+#pragma unroll
+      for (int k = 0; k < ITEMS; ++k) ei[k] = (uint32_t)(tb + item_off(k));
+    }
+  } else {
+#pragma unroll
+    for (int k = 0; k < ITEMS; ++k) {
+      const uint64_t j = tb + item_off(k);
+      if (j < m) {
+        eu[k] = __ldg(a.in.u + j);
+        ev[k] = __ldg(a.in.v + j);
+        ew[k] = __ldg(a.in.w + j);
+        ei[k] = a.in.id ? __ldg(a.in.id + j) : (uint32_t)j;
+      } else {
+        eu[k] = ev[k] = ew[k] = ei[k] = 0;
+      }
+    }
+  }
+  const uint32_t keep = keep_flags<MODE>(a, tb, m, compact_pivot(a, MODE), eu, ev, ew, ei);
+  uint32_t totp;
+  const uint32_t excl = block_exclusive_scan(packed_counts(keep), totp, s_warp);
+  const uint64_t obase = tile_claim(a.st.total, (totp & 0xffffu) + (totp >> 16), s_base);
+  emit_survivors(a, keep, excl, totp, obase, eu, ev, ew, ei, s_u, s_v, s_w, s_id);
 }
 
 // --------------------------------------------------------------- min edges
@@ -364,35 +452,42 @@ __global__ void __launch_bounds__(BLOCK) compact_kernel(CompactArgs a) {
 template <bool VEC>
 __global__ void __launch_bounds__(BLOCK) min_edges_kernel(EdgeList in, uint64_t m, uint32_t n, int validate,
                                                           u64 *best, uint32_t *err) {
-  const uint64_t nchunks = (m + ITEMS - 1) / ITEMS;
-  for (uint64_t ch = (uint64_t)blockIdx.x * BLOCK + threadIdx.x; ch < nchunks; ch += (uint64_t)gridDim.x * BLOCK) {
-    const uint64_t base = ch * ITEMS;
-    uint32_t eu[ITEMS], ev[ITEMS], ew[ITEMS];
-    if (VEC && base + ITEMS <= m) {
-      load8(in.u, base, eu);
-      load8(in.v, base, ev);
-      load8(in.w, base, ew);
+  const uint64_t ntiles = (m + TILE - 1) / TILE;
+  for (uint64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const uint64_t tb = tile * TILE;
+    uint32_t eu[ITEMS], ev[ITEMS], ew[ITEMS], ei[ITEMS];
+    if (VEC && tb + TILE <= m) {
+      load_striped(in.u, tb, eu);
+      load_striped(in.v, tb, ev);
+      load_striped(in.w, tb, ew);
+      if (in.id) load_striped(in.id, tb, ei);
     } else {
 #pragma unroll
       for (int k = 0; k < ITEMS; ++k) {
-        const uint64_t j = base + k;
+        const uint64_t j = tb + item_off(k);
         eu[k] = j < m ? __ldg(in.u + j) : 0u;
         ev[k] = j < m ? __ldg(in.v + j) : 0u;
         ew[k] = j < m ? __ldg(in.w + j) : 0u;
+        if (in.id) ei[k] = j < m ? __ldg(in.id + j) : 0u;
       }
+    }
+    if (!in.id) {
+#pragma unroll
+      for (int k = 0; k < ITEMS; ++k) ei[k] = (uint32_t)(tb + item_off(k));
     }
     uint32_t mask = 0;
     u64 key[ITEMS];
 #pragma unroll
     for (int k = 0; k < ITEMS; ++k) {
-      bool ok = base + k < m;
+      const uint64_t j = tb + item_off(k);
+      bool ok = j < m;
       if (ok && validate && (eu[k] >= n || ev[k] >= n)) {
         atomicOr(err, ERR_VERTEX);
         ok = false;
       }
       ok = ok && eu[k] != ev[k];
       mask |= (ok ? 1u : 0u) << k;
-      key[k] = edge_key(ew[k], base + k);
+      key[k] = edge_key(ew[k], ei[k]);
     }
     relax_pairs(best, eu, ev, key, mask);
   }
@@ -400,57 +495,75 @@ __global__ void __launch_bounds__(BLOCK) min_edges_kernel(EdgeList in, uint64_t 
 
 // -------------------------------------------------------------------- hook
 
+constexpr uint32_t FIND_STEPS = 1u << 12;  // bound on one parent-chain walk
+
+// Current label of input vertex x during a round's hook: follow parent pointers
+// from x and stop at the first vertex that is active this round (best != INF).
+// Every vertex on the way was merged in an earlier round and has no edge now,
+// and best[] is not written during the hook, so concurrent hooks (which change
+// parent[] of active vertices only) cannot redirect the walk.
+__device__ __forceinline__ uint32_t current_label(uint32_t x, const u64 *best, const uint32_t *parent,
+                                                  uint32_t *err) {
+  for (uint32_t step = 0; step < FIND_STEPS; ++step) {
+    if (best[x] != KEY_INF) return x;
+    const uint32_t p = __ldcg(parent + x);
+    if (p == x) return x;
+    x = p;
+  }
+  atomicOr(err, ERR_JUMP);
+  return x;
+}
+
 // Hooking (Section 2.3 / 4.2) over the candidate vertices: a vertex c with
-// best[c] != INF points to the other end of its minimum edge; in a 2-cycle
+// best[c] != INF points to the other end of its minimum edge e (found through
+// the input arrays, src[e] and dst[e], and their current labels); in a 2-cycle
 // (both ends chose the same edge) the smaller vertex stays root.  Each chosen
 // edge's id is set once in the bitmap (by the vertex that is not the root).
-// The active vertices (best != INF) are compacted, in order, into active_out.
+// The active vertices (best != INF) are compacted into active_out.
 template <bool IOTA>
 __global__ void __launch_bounds__(BLOCK) hook_kernel(HookArgs a) {
   __shared__ uint32_t s_c[TILE];
   __shared__ uint32_t s_warp[BLOCK / 32 + 1];
-  __shared__ uint32_t s_tile, s_excl, s_err;
+  __shared__ uint32_t s_base[1];
 
   const uint64_t nc = a.ncand_dev ? *a.ncand_dev : a.ncand;
-  TileInfo t;
-  if (!acquire_tile(a.st, nc, &s_tile, t)) return;
-  const uint64_t base = (uint64_t)t.tile * TILE + (uint64_t)threadIdx.x * ITEMS;
+  const uint64_t tb = (uint64_t)blockIdx.x * TILE;
+  if (tb >= nc) return;
 
   uint32_t c[ITEMS];
   u64 kk[ITEMS];
+  if (!IOTA && tb + TILE <= nc && (((uintptr_t)a.cand) & 15u) == 0) {
+    load_striped(a.cand, tb, c);
+  } else {
 #pragma unroll
-  for (int k = 0; k < ITEMS; ++k) {
-    const uint64_t j = base + k;
-    c[k] = 0;
-    kk[k] = KEY_INF;
-    if (j < nc) {
-      c[k] = IOTA ? (uint32_t)j : __ldg(a.cand + j);
-      kk[k] = a.best[c[k]];
+    for (int k = 0; k < ITEMS; ++k) {
+      const uint64_t j = tb + item_off(k);
+      c[k] = IOTA ? (uint32_t)j : (j < nc ? __ldg(a.cand + j) : 0u);
     }
   }
+#pragma unroll
+  for (int k = 0; k < ITEMS; ++k) kk[k] = (tb + item_off(k) < nc) ? a.best[c[k]] : KEY_INF;
   uint32_t keep = 0;
 #pragma unroll
   for (int k = 0; k < ITEMS; ++k) {
     if (kk[k] == KEY_INF) continue;
     keep |= 1u << k;
-    const uint32_t slot = (uint32_t)kk[k];
-    const uint32_t x = __ldg(a.list.u + slot), y = __ldg(a.list.v + slot);
+    const uint32_t e = (uint32_t)kk[k];
+    const uint32_t x = current_label(__ldg(a.src + e), a.best, a.parent, a.err);
+    const uint32_t y = current_label(__ldg(a.dst + e), a.best, a.parent, a.err);
     const uint32_t other = x ^ y ^ c[k];
     const bool root = a.best[other] == kk[k] && c[k] < other;
     a.parent[c[k]] = root ? c[k] : other;
-    if (!root) {
-      const uint32_t id = a.list.id ? __ldg(a.list.id + slot) : slot;
-      atomicOr(a.chosen_bits + (id >> 5), 1u << (id & 31));
-    }
+    if (!root) atomicOr(a.chosen_bits + (e >> 5), 1u << (e & 31));
   }
 
-  uint32_t excl, total;
-  uint64_t obase;
-  if (!tile_offsets(a.st, t, __popc(keep), excl, total, obase, s_warp, &s_excl, &s_err)) return;
-  uint32_t lp = excl;
+  uint32_t totp;
+  const uint32_t excl = block_exclusive_scan(packed_counts(keep), totp, s_warp);
+  const uint32_t total = (totp & 0xffffu) + (totp >> 16);
+  const uint64_t obase = tile_claim(a.counter, total, s_base);
 #pragma unroll
   for (int k = 0; k < ITEMS; ++k)
-    if (keep >> k & 1) s_c[lp++] = c[k];
+    if (keep >> k & 1) s_c[local_pos(keep, k, excl, totp)] = c[k];
   __syncthreads();
   for (uint32_t i = threadIdx.x; i < total; i += BLOCK) a.active_out[obase + i] = s_c[i];
 }
@@ -492,14 +605,8 @@ __global__ void hash_insert_kernel(EdgeList in, uint64_t m, HashSlot *table, uin
   for (uint64_t j = (uint64_t)blockIdx.x * BLOCK + threadIdx.x; j < m; j += (uint64_t)gridDim.x * BLOCK) {
     const uint32_t u = in.u[j], v = in.v[j];
     if (u == v) continue;
-    if (!hash_insert(table, tmask, pair_of(u, v), edge_key(in.w[j], j))) atomicOr(err, ERR_HASH);
-  }
-}
-
-__global__ void best_slot_to_id_kernel(u64 *best, uint32_t n, const uint32_t *ids) {
-  for (uint64_t c = (uint64_t)blockIdx.x * BLOCK + threadIdx.x; c < n; c += (uint64_t)gridDim.x * BLOCK) {
-    const u64 k = best[c];
-    if (k != KEY_INF) best[c] = (k & 0xffffffff00000000ULL) | ids[(uint32_t)k];
+    if (!hash_insert(table, tmask, pair_of(u, v), edge_key(in.w[j], in.id ? in.id[j] : (uint32_t)j)))
+      atomicOr(err, ERR_HASH);
   }
 }
 
@@ -619,6 +726,89 @@ __global__ void __launch_bounds__(SEL_THREADS) pivot_select_kernel(const u64 *ke
   if (threadIdx.x == 0) *out = s_prefix;
 }
 
+// ------------------------------------------------- largest component marks
+
+// Finds the component that most endpoints of a random edge sample belong to:
+// 1024 edges of the list are drawn with splitmix64, the root P[u] of each
+// sample's first endpoint is taken (P fully contracted), and the most frequent
+// root is written to *out (a sort in shared memory, then the longest run).
+constexpr int MODE_SAMPLES = 1024;
+__global__ void __launch_bounds__(MODE_SAMPLES) giant_root_kernel(EdgeList in, uint64_t m, u64 state,
+                                                                  const uint32_t *P, uint32_t n, uint32_t *out) {
+  __shared__ uint32_t s_r[MODE_SAMPLES];
+  __shared__ uint32_t s_best[MODE_SAMPLES / 32], s_bestv[MODE_SAMPLES / 32];
+  const uint32_t t = threadIdx.x;
+  uint32_t r = 0xffffffffu;
+  if (m) {
+    const uint32_t u = __ldg(in.u + __umul64hi(splitmix64_at(state, t), m));
+    if (u < n) r = __ldg(P + u);
+  }
+  s_r[t] = r;
+  __syncthreads();
+  for (uint32_t k = 2; k <= MODE_SAMPLES; k <<= 1) {  // bitonic sort, ascending
+    for (uint32_t j = k >> 1; j > 0; j >>= 1) {
+      const uint32_t p = t ^ j;
+      if (p > t) {
+        const uint32_t a = s_r[t], b = s_r[p];
+        const bool up = (t & k) == 0;
+        if ((a > b) == up) {
+          s_r[t] = b;
+          s_r[p] = a;
+        }
+      }
+      __syncthreads();
+    }
+  }
+  // run length at each run start (upper bound by binary search)
+  const uint32_t v = s_r[t];
+  uint32_t len = 0;
+  if (t == 0 || s_r[t - 1] != v) {
+    uint32_t lo = t, hi = MODE_SAMPLES;
+    while (lo < hi) {
+      const uint32_t mid = (lo + hi) >> 1;
+      if (s_r[mid] <= v)
+        lo = mid + 1;
+      else
+        hi = mid;
+    }
+    len = lo - t;
+  }
+  uint32_t bl = len, bv = v;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const uint32_t ol = __shfl_xor_sync(0xffffffffu, bl, o), ov = __shfl_xor_sync(0xffffffffu, bv, o);
+    if (ol > bl || (ol == bl && ov < bv)) {
+      bl = ol;
+      bv = ov;
+    }
+  }
+  if ((t & 31) == 0) {
+    s_best[t >> 5] = bl;
+    s_bestv[t >> 5] = bv;
+  }
+  __syncthreads();
+  if (t == 0) {
+    uint32_t l = 0, r = 0;
+    for (int i = 0; i < MODE_SAMPLES / 32; ++i)
+      if (s_best[i] > l || (s_best[i] == l && s_bestv[i] < r)) {
+        l = s_best[i];
+        r = s_bestv[i];
+      }
+    *out = r;
+  }
+}
+
+// bits[v/32] bit v%32 = (P[v] == *root), for all n vertices.
+__global__ void giant_bits_kernel(const uint32_t *P, uint32_t n, const uint32_t *root, uint32_t *bits) {
+  const uint32_t r = *root;
+  const uint64_t nw = ((uint64_t)n + 31) / 32;
+  for (uint64_t i = (uint64_t)blockIdx.x * BLOCK + threadIdx.x; i < nw * 32; i += (uint64_t)gridDim.x * BLOCK) {
+    const bool in = i < n && __ldg(P + i) == r;
+    const uint32_t word = __ballot_sync(0xffffffffu, in);
+    if ((threadIdx.x & 31) == 0) bits[i >> 5] = word;
+  }
+}
+
 // ---------------------------------------------------------------- finalize
 
 // Output (Section 2.2; edge ids, Section 6.2): set bits of the chosen-edge
@@ -628,33 +818,41 @@ __global__ void __launch_bounds__(BLOCK) finalize_kernel(const uint32_t *bits, u
                                                          ScanState st) {
   __shared__ uint32_t s_warp[BLOCK / 32 + 1];
   __shared__ u64 s_sum[BLOCK / 32];
-  __shared__ uint32_t s_tile, s_excl, s_err;
+  __shared__ LookbackShared s_lb;
   TileInfo t;
-  if (!acquire_tile(st, nwords, &s_tile, t)) {
+  if (!acquire_tile(st, nwords, t)) {
     if (t.ntiles == 0 && t.tile == 0 && threadIdx.x == 0) *out_count = 0;
     return;
   }
-  const uint64_t base = (uint64_t)t.tile * TILE + (uint64_t)threadIdx.x * ITEMS;
-  uint32_t wd[ITEMS], cnt = 0;
+  const uint64_t tb = (uint64_t)t.tile * TILE;
+  uint32_t wd[ITEMS], c0 = 0, c1 = 0;
 #pragma unroll
   for (int k = 0; k < ITEMS; ++k) {
-    wd[k] = base + k < nwords ? bits[base + k] : 0u;
-    cnt += __popc(wd[k]);
+    const uint64_t j = tb + item_off(k);
+    wd[k] = j < nwords ? bits[j] : 0u;
+    if (k < 4)
+      c0 += __popc(wd[k]);
+    else
+      c1 += __popc(wd[k]);
   }
-  uint32_t excl, total;
+  uint32_t excl, totp;
   uint64_t obase;
-  if (!tile_offsets(st, t, cnt, excl, total, obase, s_warp, &s_excl, &s_err)) return;
-  uint64_t pos = obase + excl;
+  if (!tile_offsets(st, t, c0 | (c1 << 16), excl, totp, obase, s_warp, s_lb)) return;
+  const uint32_t total = (totp & 0xffffu) + (totp >> 16);
   u64 wsum = 0;
 #pragma unroll
-  for (int k = 0; k < ITEMS; ++k) {
-    uint32_t word = wd[k];
-    while (word) {
-      const int b = __ffs(word) - 1;
-      word &= word - 1;
-      const uint32_t id = (uint32_t)((base + k) * 32 + b);
-      out_ids[pos++] = id;
-      wsum += __ldg(w + id);
+  for (int half = 0; half < 2; ++half) {
+    uint64_t pos = obase + (half == 0 ? (excl & 0xffffu) : (totp & 0xffffu) + (excl >> 16));
+#pragma unroll
+    for (int k = half * 4; k < half * 4 + 4; ++k) {
+      uint32_t word = wd[k];
+      while (word) {
+        const int b = __ffs(word) - 1;
+        word &= word - 1;
+        const uint32_t id = (uint32_t)((tb + item_off(k)) * 32 + b);
+        out_ids[pos++] = id;
+        wsum += __ldg(w + id);
+      }
     }
   }
 #pragma unroll
@@ -684,21 +882,30 @@ static inline unsigned grid_for(uint64_t items_per_block_units, int sms, int per
 int max_scan_tiles(uint64_t count) { return (int)((count + TILE - 1) / TILE); }
 
 template <int MODE>
-static void launch_compact_mode(const CompactArgs &a, unsigned grid, cudaStream_t s) {
-  const bool vec = aligned16(a.in.u) && aligned16(a.in.v) && aligned16(a.in.w) && (!a.in.id || aligned16(a.in.id));
-  if (vec)
-    compact_kernel<MODE, true><<<grid, BLOCK, 0, s>>>(a);
+static void launch_compact_mode(const CompactArgs &a, uint64_t max_count, cudaStream_t s) {
+  static bool attrs = false;  // prefer shared memory over L1 so that 4 blocks fit per SM
+  if (!attrs) {
+    cudaFuncSetAttribute(compact_kernel<MODE, true>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                         cudaSharedmemCarveoutMaxShared);
+    cudaFuncSetAttribute(compact_kernel<MODE, false>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                         cudaSharedmemCarveoutMaxShared);
+    attrs = true;
+  }
+  const uint64_t tiles = (max_count + TILE - 1) / TILE;
+  if (tiles == 0) return;
+  const bool aligned = aligned16(a.in.u) && aligned16(a.in.v) && aligned16(a.in.w) && (!a.in.id || aligned16(a.in.id));
+  if (aligned)
+    compact_kernel<MODE, true><<<(unsigned)tiles, BLOCK, 0, s>>>(a);
   else
-    compact_kernel<MODE, false><<<grid, BLOCK, 0, s>>>(a);
+    compact_kernel<MODE, false><<<(unsigned)tiles, BLOCK, 0, s>>>(a);
 }
 
 void launch_compact(CompactMode mode, const CompactArgs &a, uint64_t max_count, cudaStream_t s) {
-  const unsigned grid = (unsigned)(max_scan_tiles(max_count) > 0 ? max_scan_tiles(max_count) : 1);
   switch (mode) {
-    case CM_RELABEL: launch_compact_mode<CM_RELABEL>(a, grid, s); break;
-    case CM_PARTITION: launch_compact_mode<CM_PARTITION>(a, grid, s); break;
-    case CM_FILTER: launch_compact_mode<CM_FILTER>(a, grid, s); break;
-    case CM_DEDUPE: launch_compact_mode<CM_DEDUPE>(a, grid, s); break;
+    case CM_RELABEL: launch_compact_mode<CM_RELABEL>(a, max_count, s); break;
+    case CM_PARTITION: launch_compact_mode<CM_PARTITION>(a, max_count, s); break;
+    case CM_FILTER: launch_compact_mode<CM_FILTER>(a, max_count, s); break;
+    case CM_DEDUPE: launch_compact_mode<CM_DEDUPE>(a, max_count, s); break;
   }
 }
 
@@ -713,7 +920,8 @@ void launch_min_edges(EdgeList in, uint64_t m, uint32_t n, int validate, u64 *be
 }
 
 void launch_hook(const HookArgs &a, uint64_t max_cand, cudaStream_t s) {
-  const unsigned grid = (unsigned)(max_scan_tiles(max_cand) > 0 ? max_scan_tiles(max_cand) : 1);
+  if (max_cand == 0) return;
+  const unsigned grid = (unsigned)max_scan_tiles(max_cand);
   if (a.cand)
     hook_kernel<false><<<grid, BLOCK, 0, s>>>(a);
   else
@@ -733,11 +941,6 @@ void launch_hash_insert(EdgeList in, uint64_t m, HashSlot *table, uint64_t tmask
   hash_insert_kernel<<<grid_for((m + BLOCK - 1) / BLOCK, sms, 8), BLOCK, 0, s>>>(in, m, table, tmask, err);
 }
 
-void launch_best_slot_to_id(u64 *best, uint32_t n, const uint32_t *ids, int sms, cudaStream_t s) {
-  if (n == 0 || ids == nullptr) return;
-  best_slot_to_id_kernel<<<grid_for(((uint64_t)n + BLOCK - 1) / BLOCK, sms, 8), BLOCK, 0, s>>>(best, n, ids);
-}
-
 void launch_pivot(EdgeList in, uint64_t m, const u64 *m_dev, u64 state, uint32_t sample, u64 *sample_buf,
                   u64 *pivot_out, cudaStream_t s) {
   const unsigned g = (sample + BLOCK - 1) / BLOCK;
@@ -750,6 +953,13 @@ void launch_finalize(const uint32_t *bits, uint64_t m, const uint32_t *w, uint32
   const uint64_t nwords = (m + 31) / 32;
   const unsigned grid = (unsigned)(max_scan_tiles(nwords) > 0 ? max_scan_tiles(nwords) : 1);
   finalize_kernel<<<grid, BLOCK, 0, s>>>(bits, nwords, w, out_ids, out_count, total_weight, st);
+}
+
+void launch_giant_bits(EdgeList in, uint64_t m, u64 state, const uint32_t *P, uint32_t n, uint32_t *root_tmp,
+                       uint32_t *bits, int sms, cudaStream_t s) {
+  giant_root_kernel<<<1, MODE_SAMPLES, 0, s>>>(in, m, state, P, n, root_tmp);
+  const uint64_t threads = ((uint64_t)n + 31) / 32 * 32;
+  giant_bits_kernel<<<grid_for((threads + BLOCK - 1) / BLOCK, sms, 8), BLOCK, 0, s>>>(P, n, root_tmp, bits);
 }
 
 void launch_iota(uint32_t *p, uint64_t n, int sms, cudaStream_t s) {

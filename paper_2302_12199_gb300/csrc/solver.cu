@@ -258,6 +258,14 @@ mst_status clear_device_flags(mst_ctx *c, cudaStream_t s) {
 
 bool aligned4(const void *p) { return ((uintptr_t)p & 3u) == 0; }
 
+// Zeroes the counters that the unordered compactions of one step add into
+// (edges, active vertices, the dedupe temporary).
+mst_status zero_counters(mst_ctx *c, cudaStream_t s) {
+  static_assert(CNT_EDGES == 0 && CNT_ACTIVE == 1 && CNT_TMP == 2, "counter layout");
+  CK(cudaMemsetAsync(&c->ds->count[0], 0, 3 * sizeof(u64), s));
+  return MST_OK;
+}
+
 // Per-solve state: vertex arrays and the chosen-edge bitmap.
 struct Solve {
   mst_ctx *c;
@@ -265,6 +273,7 @@ struct Solve {
   uint32_t n;
   uint64_t m;
   Buf best_b, parent_b, act_b[2], bits_b;
+  const uint32_t *src = nullptr, *dst = nullptr;  // input endpoints, indexed by edge id
   u64 *best = nullptr;
   uint32_t *parent = nullptr, *act[2] = {nullptr, nullptr}, *bits = nullptr;
   int rounds = 0;
@@ -320,30 +329,36 @@ struct Solve {
     return MST_OK;
   }
 
+  // Parallel-edge removal is optional (Section 2.3).  `auto` keeps parallel
+  // edges: on GNM, RGG and RMAT inputs the two extra passes and the table cost
+  // more than the parallel edges they remove save in later rounds.
   bool want_dedupe(int round, uint64_t cur_m) const {
-    switch (c->cfg.dedupe) {
-      case MST_DEDUPE_HASH: return cur_m > 0;
-      case MST_DEDUPE_NONE: return false;
-      default: return round >= 2 && cur_m >= 4096;
-    }
+    (void)round;
+    return c->cfg.dedupe == MST_DEDUPE_HASH && cur_m > 0;
   }
 
   // Borůvka rounds (Section 2.3) on the list E of mE edges whose endpoints are
   // current component roots; merged roots get their new root in parent[].
-  mst_status boruvka(EdgeList E, uint64_t mE, bool validate) {
+  // best_ready: best[] already holds this list's minEdges (relaxed by the pass
+  // that wrote the list).
+  mst_status boruvka(EdgeList E, uint64_t mE, bool validate, bool best_ready = false) {
     if (mE == 0) return MST_OK;
     // round 0: minEdges straight from the stored list, then hook and jump
-    PROF(MST_K_MIN_EDGES, 12.0 * (double)mE, -1, 0.0, -1, 0.0,
-         launch_min_edges(E, mE, n, validate ? 1 : 0, best, &c->ds->err, c->sms, s));
+    if (!best_ready)
+      PROF(MST_K_MIN_EDGES, 12.0 * (double)mE, -1, 0.0, -1, 0.0,
+           launch_min_edges(E, mE, n, validate ? 1 : 0, best, &c->ds->err, c->sms, s));
+    TRY(zero_counters(c, s));
     HookArgs ha{};
     ha.cand = nullptr;
     ha.ncand = n;
     ha.best = best;
-    ha.list = E;
+    ha.src = src;
+    ha.dst = dst;
     ha.parent = parent;
     ha.chosen_bits = bits;
     ha.active_out = act[0];
-    ha.st = next_scan(c, CNT_ACTIVE);
+    ha.counter = &c->ds->count[CNT_ACTIVE];
+    ha.err = &c->ds->err;
     PROF(MST_K_HOOK, 8.0 * (double)n, CNT_ACTIVE, 8.0, -1, 0.0, launch_hook(ha, n, s));
     TRY(jump_until_stars(act[0], &c->ds->count[CNT_ACTIVE], 0, n, 1));
     uint64_t n_act = c->hs->count[CNT_ACTIVE];
@@ -359,6 +374,7 @@ struct Solve {
       if (r > bound) return MST_ERR_INTERNAL;
       ListBuf &out = (cur.u == X.out.u) ? Y : X;
       if (out.cap < cur_m) TRY(out.alloc(c, cur_m, s));
+      TRY(zero_counters(c, s));
       CompactArgs ca{};
       ca.in = cur;
       ca.m = cur_m;
@@ -399,11 +415,13 @@ struct Solve {
       hb.cand = act[a];
       hb.ncand = n_act;
       hb.best = best;
-      hb.list = out.list();
+      hb.src = src;
+      hb.dst = dst;
       hb.parent = parent;
       hb.chosen_bits = bits;
       hb.active_out = act[1 - a];
-      hb.st = next_scan(c, CNT_ACTIVE);
+      hb.counter = &c->ds->count[CNT_ACTIVE];
+      hb.err = &c->ds->err;
       PROF(MST_K_HOOK, 12.0 * (double)n_act, CNT_ACTIVE, 8.0, -1, 0.0, launch_hook(hb, n_act, s));
       TRY(jump_until_stars(act[1 - a], &c->ds->count[CNT_ACTIVE], 0, n_act, 1));
       table_b.release();
@@ -425,13 +443,31 @@ struct Solve {
   // the representative array P before filtering, Section 5).
   mst_status compress_all() { return jump_until_stars(nullptr, nullptr, n, n, 0); }
 
-  // Rec-Filter-MST (Alg. 2).
-  mst_status filter(EdgeList E, uint64_t mE, bool is_input, int depth) {
-    if (is_sparse(mE) || depth >= 40) return boruvka(E, mE, is_input);
+  mst_status reset_best() {
+    CK(cudaMemsetAsync(best, 0xff, (size_t)n * 8, s));
+    return MST_OK;
+  }
+
+  // Marks the vertices of the component that most sampled edges of E touch,
+  // after P (= parent) is fully contracted: the filter drops an edge with both
+  // ends marked without reading P.
+  mst_status mark_giant(EdgeList E, uint64_t mE, u64 state, Buf &bits_b) {
+    TRY(bits_b.alloc(c, ((size_t)n + 31) / 32 * 4, s));
+    launch_giant_bits(E, mE, state, parent, n, &c->ds->giant_root, bits_b.as<uint32_t>(), c->sms, s);
+    return MST_OK;
+  }
+
+  // Rec-Filter-MST (Alg. 2).  best_ready: best[] holds E's minEdges already.
+  mst_status filter(EdgeList E, uint64_t mE, bool is_input, int depth, bool best_ready = false) {
+    if (is_sparse(mE) || depth >= 40) return boruvka(E, mE, is_input, best_ready);
+    if (best_ready) TRY(reset_best());
     const u64 state = host_splitmix64_at(c->cfg.seed, c->pivot_counter++);
     PROF(MST_K_PIVOT, 16.0 * (double)c->cfg.pivot_sample, -1, 0.0, -1, 0.0,
          launch_pivot(E, mE, nullptr, state, c->cfg.pivot_sample, c->sample_buf, &c->ds->pivot, s));
     const double in_bytes = (E.id ? 16.0 : 12.0) * (double)mE;
+    // the light half goes straight to Borůvka rounds when it will be sparse:
+    // the partition pass then also performs that call's first minEdges
+    const bool fuse_light = is_sparse(mE / 2);
     ListBuf L;
     TRY(L.alloc(c, mE, s));
     CompactArgs cp{};
@@ -441,18 +477,23 @@ struct Solve {
     cp.pivot_dev = &c->ds->pivot;
     cp.n = n;
     cp.validate = is_input ? 1 : 0;
+    cp.best = fuse_light ? best : nullptr;
     cp.st = next_scan(c, CNT_EDGES);
+    TRY(zero_counters(c, s));
     PROF(MST_K_PARTITION, in_bytes, CNT_EDGES, 16.0, -1, 0.0, launch_compact(CM_PARTITION, cp, mE, s));
     TRY(readback(c, s));
     const uint64_t mL = c->hs->count[CNT_EDGES];
     const u64 pivot = c->hs->pivot;
     if (mL == 0 || mL == mE) {  // no progress from this pivot: solve the list directly
       L.mem.release();
+      if (fuse_light) TRY(reset_best());
       return boruvka(E, mE, is_input);
     }
-    TRY(filter(L.list(), mL, false, depth + 1));
+    TRY(filter(L.list(), mL, false, depth + 1, fuse_light));
     L.mem.release();
     TRY(compress_all());
+    Buf giant_b;
+    TRY(mark_giant(E, mE, host_mix64(state), giant_b));
     ListBuf H;
     TRY(H.alloc(c, mE - mL, s));
     CompactArgs cf{};
@@ -460,13 +501,17 @@ struct Solve {
     cf.m = mE;
     cf.out = H.out;
     cf.label = parent;
+    cf.giant_bits = giant_b.as<uint32_t>();
     cf.pivot = pivot;
     cf.n = n;
+    cf.best = best;  // the survivors are expected to be sparse (Theorem 1)
     cf.st = next_scan(c, CNT_EDGES);
+    TRY(zero_counters(c, s));
     PROF(MST_K_FILTER, in_bytes, CNT_EDGES, 16.0, -1, 0.0, launch_compact(CM_FILTER, cf, mE, s));
     TRY(readback(c, s));
+    giant_b.release();
     const uint64_t mH = c->hs->count[CNT_EDGES];
-    return filter(H.list(), mH, false, depth + 1);
+    return filter(H.list(), mH, false, depth + 1, true);
   }
 
   mst_status finalize(const uint32_t *w, uint32_t *out_ids, uint32_t *out_count, u64 *total_weight) {
@@ -498,6 +543,8 @@ mst_status solve_device(mst_ctx *c, uint32_t n, uint64_t m, const uint32_t *src,
   }
   Solve S(c, s, n, m);
   TRY(S.init());
+  S.src = src;
+  S.dst = dst;
   const EdgeList in{src, dst, w, nullptr};
   c->pivot_counter = 0;
   if (use_filter(c->cfg, n, m))
@@ -839,30 +886,34 @@ mst_status mst_step_min_edges(mst_handle h, uint32_t n, uint64_t m, const uint32
       cudaMemsetAsync(&h->ds->err, 0, 4, s) != cudaSuccess)
     return record(h, MST_ERR_CUDA);
   launch_min_edges(EdgeList{d_u, d_v, d_w, d_id}, m, n, 1, (u64 *)d_best, &h->ds->err, h->sms, s);
-  launch_best_slot_to_id((u64 *)d_best, n, d_id, h->sms, s);
   return record(h, readback(h, s));
 }
 
 mst_status mst_step_contract(mst_handle h, uint32_t n, uint64_t m, const uint32_t *d_u, const uint32_t *d_v,
                              const uint32_t *d_w, const uint32_t *d_id, uint32_t *d_parent, uint32_t *d_chosen,
                              void *stream) {
-  if (!h || !d_parent || !d_chosen || (m > 0 && (!d_u || !d_v || !d_w))) return MST_ERR_INVALID_ARG;
+  if (!h || !d_parent || !d_chosen || d_id || (m > 0 && (!d_u || !d_v || !d_w))) return MST_ERR_INVALID_ARG;
   if (m >= (1ULL << 32)) return record(h, MST_ERR_TOO_LARGE);
   DeviceGuard g(h->device);
   cudaStream_t s = (cudaStream_t)stream;
   Solve S(h, s, n, m);
   mst_status st = S.init(d_parent, d_chosen);
   if (st != MST_OK) return record(h, st);
-  const EdgeList E{d_u, d_v, d_w, d_id};
+  S.src = d_u;
+  S.dst = d_v;
+  const EdgeList E{d_u, d_v, d_w, nullptr};
   launch_min_edges(E, m, n, 1, S.best, &h->ds->err, h->sms, s);
+  if (zero_counters(h, s) != MST_OK) return record(h, MST_ERR_CUDA);
   HookArgs ha{};
   ha.ncand = n;
   ha.best = S.best;
-  ha.list = E;
+  ha.src = d_u;
+  ha.dst = d_v;
   ha.parent = d_parent;
   ha.chosen_bits = d_chosen;
   ha.active_out = S.act[0];
-  ha.st = next_scan(h, CNT_ACTIVE);
+  ha.counter = &h->ds->count[CNT_ACTIVE];
+  ha.err = &h->ds->err;
   launch_hook(ha, n, s);
   return record(h, S.jump_until_stars(S.act[0], &h->ds->count[CNT_ACTIVE], 0, n, 1));
 }
@@ -888,7 +939,13 @@ static mst_status step_compact(mst_handle h, CompactMode mode, uint32_t n, uint6
   a.pivot = pivot;
   a.n = n;
   a.validate = (mode == CM_RELABEL || mode == CM_FILTER) ? 1 : 0;
-  Buf table_b;
+  Buf table_b, giant_b;
+  if (mode == CM_FILTER && n > 0 && m > 0) {  // the solver's fast path for edges inside the largest component
+    st = giant_b.alloc(h, ((size_t)n + 31) / 32 * 4, s);
+    if (st != MST_OK) return record(h, st);
+    launch_giant_bits(E, m, 0x9e3779b97f4a7c15ULL, label, n, &h->ds->giant_root, giant_b.as<uint32_t>(), h->sms, s);
+    a.giant_bits = giant_b.as<uint32_t>();
+  }
   if (mode == CM_DEDUPE) {
     const uint64_t slots = next_pow2(2 * m < 1024 ? 1024 : 2 * m);
     st = table_b.alloc(h, slots * sizeof(HashSlot), s);
@@ -899,6 +956,7 @@ static mst_status step_compact(mst_handle h, CompactMode mode, uint32_t n, uint6
     launch_hash_insert(E, m, a.table, a.tmask, &h->ds->err, h->sms, s);
   }
   a.st = next_scan(h, CNT_USER);
+  if (cudaMemsetAsync(&h->ds->count[CNT_USER], 0, sizeof(u64), s) != cudaSuccess) return record(h, MST_ERR_CUDA);
   launch_compact(mode, a, m, s);
   if (cudaMemcpyAsync(d_out_count, &h->ds->count[CNT_USER], 8, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
     return record(h, MST_ERR_CUDA);
