@@ -25,7 +25,7 @@ struct DevState {
   u64 count[6];         // counts written by the last tile of a scan kernel
   u64 pivot;            // result of the pivot selection
   uint32_t giant_root;  // root of the largest sampled component (filter fast path)
-  uint32_t pad;
+  uint32_t max_w;       // largest input weight (key layout)
 };
 enum { CNT_EDGES = 0, CNT_ACTIVE = 1, CNT_TMP = 2, CNT_AUX = 3, CNT_USER = 4 };
 
@@ -44,6 +44,19 @@ struct ScanState {
 struct HashSlot {
   u64 pair;  // (min(u,v) << 32) | max(u,v); all ones = empty
   u64 key;   // minimum (w << 32) | id seen for this pair
+};
+
+// Layout of the uint64 relaxation key of a solve.  Edges are ordered by
+// (w, id).  When the weight, the edge id and a vertex id fit into 64 bits
+// together (vbits + idbits + bits(max w) <= 64), the key is
+//   w << (idbits + vbits) | id << vbits | other,
+// where `other` is the far end of the edge as seen from the relaxed vertex, so
+// the hook reads the chosen neighbour straight from the key.  Otherwise the
+// key is w << 32 | id and the hook finds the neighbour through the input
+// arrays.  Either way the minimum key of a vertex is its (w, id)-lightest edge.
+struct KeyLayout {
+  int packed;
+  int vbits, idbits;
 };
 
 // An edge list in structure-of-arrays form.  id == nullptr: id = index.
@@ -71,6 +84,7 @@ struct CompactArgs {
   u64 pivot;               // partition / filter (used when pivot_dev == nullptr)
   const u64 *pivot_dev;
   u64 *best;               // if set: relax best[] of both ends with each survivor's key
+  KeyLayout kl;
   HashSlot *table;         // dedupe lookup, or insert target when hash_insert
   uint64_t tmask;
   int hash_insert;
@@ -83,8 +97,9 @@ struct HookArgs {
   const uint32_t *cand;    // candidate vertices; nullptr = 0..ncand-1
   uint64_t ncand;
   const u64 *ncand_dev;    // candidate count in device memory, or nullptr
-  u64 *best;               // keys (w << 32) | id of the round's minimum edges
-  const uint32_t *src, *dst;  // input endpoints, indexed by edge id
+  u64 *best;               // keys (see KeyLayout) of the round's minimum edges
+  KeyLayout kl;
+  const uint32_t *src, *dst;  // input endpoints, indexed by edge id (unpacked keys)
   uint32_t *parent;
   uint32_t *chosen_bits;   // bitmap over edge ids
   uint32_t *active_out;    // active vertices (best != INF), unspecified order
@@ -95,8 +110,9 @@ struct HookArgs {
 // ---- launchers (kernels.cu); all asynchronous on `s` ----
 int max_scan_tiles(uint64_t count);
 void launch_compact(CompactMode mode, const CompactArgs &a, uint64_t max_count, cudaStream_t s);
-void launch_min_edges(EdgeList in, uint64_t m, uint32_t n, int validate, u64 *best, uint32_t *err, int sms,
-                      cudaStream_t s);
+void launch_min_edges(EdgeList in, uint64_t m, uint32_t n, int validate, KeyLayout kl, u64 *best, uint32_t *err,
+                      int sms, cudaStream_t s);
+void launch_max_weight(const uint32_t *w, uint64_t m, uint32_t *out, int sms, cudaStream_t s);
 void launch_hook(const HookArgs &a, uint64_t max_cand, cudaStream_t s);
 void launch_jump(const uint32_t *act, const u64 *count_dev, uint64_t count_host, uint64_t max_count,
                  uint32_t *parent, u64 *best, int reset_best, uint32_t *flag, int sms, cudaStream_t s);

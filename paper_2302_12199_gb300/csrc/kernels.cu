@@ -67,6 +67,18 @@ __device__ __forceinline__ uint32_t local_pos(uint32_t keep, int k, uint32_t exc
 
 __device__ __forceinline__ u64 edge_key(uint32_t w, uint32_t id) { return ((u64)w << 32) | (u64)id; }
 
+// Relaxation key of an edge as seen from one end (see KeyLayout).
+__device__ __forceinline__ u64 relax_key(const KeyLayout &kl, uint32_t w, uint32_t id, uint32_t other) {
+  return kl.packed ? (((u64)w << (kl.idbits + kl.vbits)) | ((u64)id << kl.vbits) | (u64)other) : edge_key(w, id);
+}
+__device__ __forceinline__ uint32_t key_edge_id(const KeyLayout &kl, u64 key) {
+  return kl.packed ? (uint32_t)((key >> kl.vbits) & ((1ULL << kl.idbits) - 1)) : (uint32_t)key;
+}
+// Do two keys name the same edge (the 2-cycle test)?
+__device__ __forceinline__ bool same_edge(const KeyLayout &kl, u64 a, u64 b) {
+  return kl.packed ? (a >> kl.vbits) == (b >> kl.vbits) : a == b;
+}
+
 __device__ __forceinline__ u64 pair_of(uint32_t a, uint32_t b) {
   return a < b ? (((u64)a << 32) | b) : (((u64)b << 32) | a);
 }
@@ -252,20 +264,22 @@ __device__ __forceinline__ uint64_t tile_claim(unsigned long long *counter, uint
 }
 
 // best[c] = min(best[c], key) for up to 2*ITEMS (vertex, key) pairs.  The
-// current value is read first (from L2) and the atomic is skipped when it
-// cannot lower it; the atomic's result is unused, so it compiles to a reduction.
+// current value is read first and the atomic is skipped when it cannot lower
+// it.  The read may be served from L1 and be stale, which only costs an extra
+// atomic (values only decrease); it keeps hub vertices from turning every edge
+// into an L2 access.  The atomic's result is unused, so it is a reduction.
 __device__ __forceinline__ void relax_pairs(u64 *best, const uint32_t (&a)[ITEMS], const uint32_t (&b)[ITEMS],
-                                            const u64 (&key)[ITEMS], uint32_t mask) {
+                                            const u64 (&key)[ITEMS], const u64 (&keyb)[ITEMS], uint32_t mask) {
   u64 ca[ITEMS], cb[ITEMS];
 #pragma unroll
   for (int k = 0; k < ITEMS; ++k) {
-    ca[k] = (mask >> k & 1) ? __ldcg(best + a[k]) : 0ULL;
-    cb[k] = (mask >> k & 1) ? __ldcg(best + b[k]) : 0ULL;
+    ca[k] = (mask >> k & 1) ? __ldca(best + a[k]) : 0ULL;
+    cb[k] = (mask >> k & 1) ? __ldca(best + b[k]) : 0ULL;
   }
 #pragma unroll
   for (int k = 0; k < ITEMS; ++k) {
     if (key[k] < ca[k]) atomicMin(best + a[k], key[k]);
-    if (key[k] < cb[k]) atomicMin(best + b[k], key[k]);
+    if (keyb[k] < cb[k]) atomicMin(best + b[k], keyb[k]);
   }
 }
 
@@ -373,21 +387,22 @@ __device__ __forceinline__ void emit_survivors(const CompactArgs &a, uint32_t ke
   if (a.best) {
     for (uint32_t i0 = 0; i0 < total; i0 += 4 * BLOCK) {
       uint32_t x[4], y[4];
-      u64 key[4], cx[4], cy[4];
+      u64 kx[4], ky[4], cx[4], cy[4];
 #pragma unroll
       for (int k = 0; k < 4; ++k) {
         const uint32_t i = i0 + k * BLOCK + threadIdx.x;
         const bool ok = i < total;
         x[k] = ok ? s_u[i] : 0u;
         y[k] = ok ? s_v[i] : 0u;
-        key[k] = ok ? edge_key(s_w[i], s_id[i]) : KEY_INF;
-        cx[k] = ok ? __ldcg(a.best + x[k]) : 0ULL;
-        cy[k] = ok ? __ldcg(a.best + y[k]) : 0ULL;
+        kx[k] = ok ? relax_key(a.kl, s_w[i], s_id[i], y[k]) : KEY_INF;
+        ky[k] = ok ? relax_key(a.kl, s_w[i], s_id[i], x[k]) : KEY_INF;
+        cx[k] = ok ? __ldca(a.best + x[k]) : 0ULL;
+        cy[k] = ok ? __ldca(a.best + y[k]) : 0ULL;
       }
 #pragma unroll
       for (int k = 0; k < 4; ++k) {
-        if (key[k] < cx[k]) atomicMin(a.best + x[k], key[k]);
-        if (key[k] < cy[k]) atomicMin(a.best + y[k], key[k]);
+        if (kx[k] < cx[k]) atomicMin(a.best + x[k], kx[k]);
+        if (ky[k] < cy[k]) atomicMin(a.best + y[k], ky[k]);
       }
     }
   }
@@ -451,7 +466,7 @@ __global__ void __launch_bounds__(BLOCK, 4) compact_kernel(CompactArgs a) {
 // built by partition/filter): best[c] = min slot key over incident edges.
 template <bool VEC>
 __global__ void __launch_bounds__(BLOCK) min_edges_kernel(EdgeList in, uint64_t m, uint32_t n, int validate,
-                                                          u64 *best, uint32_t *err) {
+                                                          KeyLayout kl, u64 *best, uint32_t *err) {
   const uint64_t ntiles = (m + TILE - 1) / TILE;
   for (uint64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     const uint64_t tb = tile * TILE;
@@ -476,7 +491,7 @@ __global__ void __launch_bounds__(BLOCK) min_edges_kernel(EdgeList in, uint64_t 
       for (int k = 0; k < ITEMS; ++k) ei[k] = (uint32_t)(tb + item_off(k));
     }
     uint32_t mask = 0;
-    u64 key[ITEMS];
+    u64 key[ITEMS], keyb[ITEMS];
 #pragma unroll
     for (int k = 0; k < ITEMS; ++k) {
       const uint64_t j = tb + item_off(k);
@@ -487,9 +502,10 @@ __global__ void __launch_bounds__(BLOCK) min_edges_kernel(EdgeList in, uint64_t 
       }
       ok = ok && eu[k] != ev[k];
       mask |= (ok ? 1u : 0u) << k;
-      key[k] = edge_key(ew[k], ei[k]);
+      key[k] = relax_key(kl, ew[k], ei[k], ev[k]);
+      keyb[k] = relax_key(kl, ew[k], ei[k], eu[k]);
     }
-    relax_pairs(best, eu, ev, key, mask);
+    relax_pairs(best, eu, ev, key, keyb, mask);
   }
 }
 
@@ -497,29 +513,22 @@ __global__ void __launch_bounds__(BLOCK) min_edges_kernel(EdgeList in, uint64_t 
 
 constexpr uint32_t FIND_STEPS = 1u << 12;  // bound on one parent-chain walk
 
-// Current label of input vertex x during a round's hook: follow parent pointers
-// from x and stop at the first vertex that is active this round (best != INF).
-// Every vertex on the way was merged in an earlier round and has no edge now,
-// and best[] is not written during the hook, so concurrent hooks (which change
-// parent[] of active vertices only) cannot redirect the walk.
-__device__ __forceinline__ uint32_t current_label(uint32_t x, const u64 *best, const uint32_t *parent,
-                                                  uint32_t *err) {
-  for (uint32_t step = 0; step < FIND_STEPS; ++step) {
-    if (best[x] != KEY_INF) return x;
-    const uint32_t p = __ldcg(parent + x);
-    if (p == x) return x;
-    x = p;
-  }
-  atomicOr(err, ERR_JUMP);
-  return x;
-}
-
 // Hooking (Section 2.3 / 4.2) over the candidate vertices: a vertex c with
-// best[c] != INF points to the other end of its minimum edge e (found through
-// the input arrays, src[e] and dst[e], and their current labels); in a 2-cycle
+// best[c] != INF points to the other end of its minimum edge e; in a 2-cycle
 // (both ends chose the same edge) the smaller vertex stays root.  Each chosen
 // edge's id is set once in the bitmap (by the vertex that is not the root).
 // The active vertices (best != INF) are compacted into active_out.
+//
+// The ends of e are found through the input arrays: src[e] and dst[e] are
+// input vertices, and their current labels are reached by following parent
+// pointers until the first vertex that is active this round (best != INF).
+// Every vertex passed on the way was merged in an earlier round and has no edge
+// now, and best[] is not written during the hook, so the hooks of other threads
+// (which only change parent[] of active vertices) cannot redirect a walk.  All
+// 2 * ITEMS walks of a thread advance in lockstep, so each step costs one round
+// of independent loads.  The start vertex of a walk longer than one step is
+// then pointed at its label directly (a concurrent walker sees either pointer,
+// both on the same path).
 template <bool IOTA>
 __global__ void __launch_bounds__(BLOCK) hook_kernel(HookArgs a) {
   __shared__ uint32_t s_c[TILE];
@@ -544,17 +553,69 @@ __global__ void __launch_bounds__(BLOCK) hook_kernel(HookArgs a) {
 #pragma unroll
   for (int k = 0; k < ITEMS; ++k) kk[k] = (tb + item_off(k) < nc) ? a.best[c[k]] : KEY_INF;
   uint32_t keep = 0;
+  if (a.kl.packed) {  // the chosen neighbour is in the key
+#pragma unroll
+    for (int k = 0; k < ITEMS; ++k) {
+      if (kk[k] == KEY_INF) continue;
+      keep |= 1u << k;
+      const uint32_t e = key_edge_id(a.kl, kk[k]);
+      const uint32_t other = (uint32_t)(kk[k] & ((1ULL << a.kl.vbits) - 1));
+      const bool root = same_edge(a.kl, a.best[other], kk[k]) && c[k] < other;
+      a.parent[c[k]] = root ? c[k] : other;
+      if (!root) atomicOr(a.chosen_bits + (e >> 5), 1u << (e & 31));
+    }
+  } else {
+  uint32_t start[2 * ITEMS], cur[2 * ITEMS];
 #pragma unroll
   for (int k = 0; k < ITEMS; ++k) {
-    if (kk[k] == KEY_INF) continue;
-    keep |= 1u << k;
+    keep |= (kk[k] != KEY_INF ? 1u : 0u) << k;
     const uint32_t e = (uint32_t)kk[k];
-    const uint32_t x = current_label(__ldg(a.src + e), a.best, a.parent, a.err);
-    const uint32_t y = current_label(__ldg(a.dst + e), a.best, a.parent, a.err);
-    const uint32_t other = x ^ y ^ c[k];
+    start[2 * k] = kk[k] != KEY_INF ? __ldg(a.src + e) : c[k];
+    start[2 * k + 1] = kk[k] != KEY_INF ? __ldg(a.dst + e) : c[k];
+  }
+  // lockstep walks to the current labels
+  uint32_t pending = 0;
+#pragma unroll
+  for (int i = 0; i < 2 * ITEMS; ++i) {
+    cur[i] = start[i];
+    pending |= ((keep >> (i >> 1)) & 1u) << i;
+  }
+  uint32_t steps = 0;
+  while (pending) {
+    if (++steps > FIND_STEPS) {
+      atomicOr(a.err, ERR_JUMP);
+      break;
+    }
+    u64 bv[2 * ITEMS];
+    uint32_t pv[2 * ITEMS];
+#pragma unroll
+    for (int i = 0; i < 2 * ITEMS; ++i) {
+      bv[i] = (pending >> i & 1) ? a.best[cur[i]] : 0ULL;
+      pv[i] = (pending >> i & 1) ? __ldcg(a.parent + cur[i]) : 0u;
+    }
+#pragma unroll
+    for (int i = 0; i < 2 * ITEMS; ++i) {
+      if (!(pending >> i & 1)) continue;
+      if (bv[i] != KEY_INF || pv[i] == cur[i])
+        pending &= ~(1u << i);
+      else
+        cur[i] = pv[i];
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < ITEMS; ++k) {
+    if (!(keep >> k & 1)) continue;
+    const uint32_t e = (uint32_t)kk[k];
+    const uint32_t other = cur[2 * k] ^ cur[2 * k + 1] ^ c[k];
     const bool root = a.best[other] == kk[k] && c[k] < other;
     a.parent[c[k]] = root ? c[k] : other;
     if (!root) atomicOr(a.chosen_bits + (e >> 5), 1u << (e & 31));
+  }
+  // shortcut the walked start vertices to their labels
+#pragma unroll
+  for (int i = 0; i < 2 * ITEMS; ++i)
+    if ((keep >> (i >> 1) & 1) && cur[i] != start[i] && __ldcg(a.parent + start[i]) != cur[i])
+      __stcg(a.parent + start[i], cur[i]);
   }
 
   uint32_t totp;
@@ -608,6 +669,15 @@ __global__ void hash_insert_kernel(EdgeList in, uint64_t m, HashSlot *table, uin
     if (!hash_insert(table, tmask, pair_of(u, v), edge_key(in.w[j], in.id ? in.id[j] : (uint32_t)j)))
       atomicOr(err, ERR_HASH);
   }
+}
+
+__global__ void max_weight_kernel(const uint32_t *w, uint64_t m, uint32_t *out) {
+  uint32_t mx = 0;
+  for (uint64_t i = (uint64_t)blockIdx.x * BLOCK + threadIdx.x; i < m; i += (uint64_t)gridDim.x * BLOCK)
+    mx = max(mx, __ldcs(w + i));
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if ((threadIdx.x & 31) == 0 && mx) atomicMax(out, mx);
 }
 
 __global__ void iota_kernel(uint32_t *p, uint64_t n) {
@@ -909,14 +979,19 @@ void launch_compact(CompactMode mode, const CompactArgs &a, uint64_t max_count, 
   }
 }
 
-void launch_min_edges(EdgeList in, uint64_t m, uint32_t n, int validate, u64 *best, uint32_t *err, int sms,
-                      cudaStream_t s) {
+void launch_min_edges(EdgeList in, uint64_t m, uint32_t n, int validate, KeyLayout kl, u64 *best, uint32_t *err,
+                      int sms, cudaStream_t s) {
   if (m == 0) return;
   const unsigned grid = grid_for((m + (uint64_t)TILE - 1) / TILE, sms, 8);
-  if (aligned16(in.u) && aligned16(in.v) && aligned16(in.w))
-    min_edges_kernel<true><<<grid, BLOCK, 0, s>>>(in, m, n, validate, best, err);
+  if (aligned16(in.u) && aligned16(in.v) && aligned16(in.w) && (!in.id || aligned16(in.id)))
+    min_edges_kernel<true><<<grid, BLOCK, 0, s>>>(in, m, n, validate, kl, best, err);
   else
-    min_edges_kernel<false><<<grid, BLOCK, 0, s>>>(in, m, n, validate, best, err);
+    min_edges_kernel<false><<<grid, BLOCK, 0, s>>>(in, m, n, validate, kl, best, err);
+}
+
+void launch_max_weight(const uint32_t *w, uint64_t m, uint32_t *out, int sms, cudaStream_t s) {
+  if (m == 0) return;
+  max_weight_kernel<<<grid_for((m + BLOCK - 1) / BLOCK, sms, 4), BLOCK, 0, s>>>(w, m, out);
 }
 
 void launch_hook(const HookArgs &a, uint64_t max_cand, cudaStream_t s) {

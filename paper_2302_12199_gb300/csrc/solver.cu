@@ -274,6 +274,7 @@ struct Solve {
   uint64_t m;
   Buf best_b, parent_b, act_b[2], bits_b;
   const uint32_t *src = nullptr, *dst = nullptr;  // input endpoints, indexed by edge id
+  KeyLayout kl{0, 0, 0};  // unpacked unless choose_layout() packs
   u64 *best = nullptr;
   uint32_t *parent = nullptr, *act[2] = {nullptr, nullptr}, *bits = nullptr;
   int rounds = 0;
@@ -305,6 +306,21 @@ struct Solve {
     }
     TRY(ensure_status(c, (uint64_t)n > m ? (uint64_t)n : m, s));
     TRY(clear_device_flags(c, s));
+    return MST_OK;
+  }
+
+  // Picks the relaxation key layout (KeyLayout): the far end of the edge goes
+  // into the key when the largest weight, the edge ids and the vertex ids fit
+  // into 63 bits together (the top bit stays clear, so no key equals INF).
+  mst_status choose_layout(const uint32_t *w) {
+    CK(cudaMemsetAsync(&c->ds->max_w, 0, sizeof(uint32_t), s));
+    launch_max_weight(w, m, &c->ds->max_w, c->sms, s);
+    TRY(readback(c, s));
+    const int vb = n > 1 ? 64 - __builtin_clzll((unsigned long long)(n - 1)) : 1;
+    const int ib = m > 1 ? 64 - __builtin_clzll((unsigned long long)(m - 1)) : 1;
+    const uint32_t mw = c->hs->max_w;
+    const int wb = mw ? 32 - __builtin_clz(mw) : 0;
+    kl = KeyLayout{wb + ib + vb <= 63 ? 1 : 0, vb, ib};
     return MST_OK;
   }
 
@@ -346,12 +362,13 @@ struct Solve {
     // round 0: minEdges straight from the stored list, then hook and jump
     if (!best_ready)
       PROF(MST_K_MIN_EDGES, 12.0 * (double)mE, -1, 0.0, -1, 0.0,
-           launch_min_edges(E, mE, n, validate ? 1 : 0, best, &c->ds->err, c->sms, s));
+           launch_min_edges(E, mE, n, validate ? 1 : 0, kl, best, &c->ds->err, c->sms, s));
     TRY(zero_counters(c, s));
     HookArgs ha{};
     ha.cand = nullptr;
     ha.ncand = n;
     ha.best = best;
+    ha.kl = kl;
     ha.src = src;
     ha.dst = dst;
     ha.parent = parent;
@@ -381,6 +398,7 @@ struct Solve {
       ca.out = out.out;
       ca.label = parent;
       ca.n = n;
+      ca.kl = kl;
       const double in_bytes = (cur.id ? 16.0 : 12.0) * (double)cur_m;
       if (!want_dedupe(r, cur_m)) {
         ca.best = best;
@@ -407,6 +425,7 @@ struct Solve {
         cd.table = ca.table;
         cd.tmask = ca.tmask;
         cd.best = best;
+        cd.kl = kl;
         cd.n = n;
         cd.st = next_scan(c, CNT_EDGES);
         PROF(MST_K_DEDUPE, 0.0, CNT_TMP, 16.0, CNT_EDGES, 16.0, launch_compact(CM_DEDUPE, cd, cur_m, s));
@@ -415,6 +434,7 @@ struct Solve {
       hb.cand = act[a];
       hb.ncand = n_act;
       hb.best = best;
+      hb.kl = kl;
       hb.src = src;
       hb.dst = dst;
       hb.parent = parent;
@@ -478,6 +498,7 @@ struct Solve {
     cp.n = n;
     cp.validate = is_input ? 1 : 0;
     cp.best = fuse_light ? best : nullptr;
+    cp.kl = kl;
     cp.st = next_scan(c, CNT_EDGES);
     TRY(zero_counters(c, s));
     PROF(MST_K_PARTITION, in_bytes, CNT_EDGES, 16.0, -1, 0.0, launch_compact(CM_PARTITION, cp, mE, s));
@@ -505,6 +526,7 @@ struct Solve {
     cf.pivot = pivot;
     cf.n = n;
     cf.best = best;  // the survivors are expected to be sparse (Theorem 1)
+    cf.kl = kl;
     cf.st = next_scan(c, CNT_EDGES);
     TRY(zero_counters(c, s));
     PROF(MST_K_FILTER, in_bytes, CNT_EDGES, 16.0, -1, 0.0, launch_compact(CM_FILTER, cf, mE, s));
@@ -545,6 +567,7 @@ mst_status solve_device(mst_ctx *c, uint32_t n, uint64_t m, const uint32_t *src,
   TRY(S.init());
   S.src = src;
   S.dst = dst;
+  TRY(S.choose_layout(w));
   const EdgeList in{src, dst, w, nullptr};
   c->pivot_counter = 0;
   if (use_filter(c->cfg, n, m))
@@ -885,7 +908,7 @@ mst_status mst_step_min_edges(mst_handle h, uint32_t n, uint64_t m, const uint32
   if (cudaMemsetAsync(d_best, 0xff, (size_t)n * 8, s) != cudaSuccess ||
       cudaMemsetAsync(&h->ds->err, 0, 4, s) != cudaSuccess)
     return record(h, MST_ERR_CUDA);
-  launch_min_edges(EdgeList{d_u, d_v, d_w, d_id}, m, n, 1, (u64 *)d_best, &h->ds->err, h->sms, s);
+  launch_min_edges(EdgeList{d_u, d_v, d_w, d_id}, m, n, 1, KeyLayout{0, 0, 0}, (u64 *)d_best, &h->ds->err, h->sms, s);
   return record(h, readback(h, s));
 }
 
@@ -902,11 +925,12 @@ mst_status mst_step_contract(mst_handle h, uint32_t n, uint64_t m, const uint32_
   S.src = d_u;
   S.dst = d_v;
   const EdgeList E{d_u, d_v, d_w, nullptr};
-  launch_min_edges(E, m, n, 1, S.best, &h->ds->err, h->sms, s);
+  launch_min_edges(E, m, n, 1, S.kl, S.best, &h->ds->err, h->sms, s);
   if (zero_counters(h, s) != MST_OK) return record(h, MST_ERR_CUDA);
   HookArgs ha{};
   ha.ncand = n;
   ha.best = S.best;
+  ha.kl = S.kl;
   ha.src = d_u;
   ha.dst = d_v;
   ha.parent = d_parent;
