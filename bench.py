@@ -193,6 +193,10 @@ def gpu_main(args, rank: int, world: int, local_rank: int):
         cfg["variant"] = args.variant
     if args.dedupe:
         cfg["dedupe"] = args.dedupe
+    if args.filter_max_avg_degree is not None:
+        cfg["filter_max_avg_degree"] = args.filter_max_avg_degree
+    if args.filter_min_edges is not None:
+        cfg["filter_min_edges"] = args.filter_min_edges
     g = gen(W)
     n, m = g.n, g.m
     src = torch.from_numpy(g.src.view(np.int32)).to(dev)
@@ -325,6 +329,8 @@ def main():
     ap.add_argument("--variant", default=None, choices=["boruvka", "filter", "auto"],
                     help="override the workload's solver variant")
     ap.add_argument("--dedupe", default=None, choices=["auto", "hash", "none"])
+    ap.add_argument("--filter-max-avg-degree", type=float, default=None)
+    ap.add_argument("--filter-min-edges", type=int, default=None)
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "gpu":
         args.warmup = 3

@@ -90,6 +90,7 @@ struct CompactArgs {
   int hash_insert;
   uint32_t n;              // vertex count, for validation
   int validate;            // check u, v < n (sets ERR_VERTEX, skips the edge)
+  uint32_t *max_w;         // if set: atomicMax of every input weight (key layout)
   ScanState st;
 };
 
@@ -120,6 +121,12 @@ void launch_hash_insert(EdgeList in, uint64_t m, HashSlot *table, uint64_t tmask
                         cudaStream_t s);
 void launch_pivot(EdgeList in, uint64_t m, const u64 *m_dev, u64 state, uint32_t sample, u64 *sample_buf,
                   u64 *pivot_out, cudaStream_t s);
+// Pivot selection by a cooperative multi-block radix select (same result as
+// launch_pivot); `scratch` holds pivot_scratch_bytes().  False if the
+// cooperative launch was refused.
+size_t pivot_scratch_bytes();
+bool launch_pivot_coop(EdgeList in, uint64_t m, u64 state, uint32_t sample, u64 *keys, void *scratch,
+                       u64 *pivot_out, cudaStream_t s);
 void launch_finalize(const uint32_t *bits, uint64_t m, const uint32_t *w, uint32_t *out_ids, uint32_t *out_count,
                      u64 *total_weight, ScanState st, cudaStream_t s);
 void launch_giant_bits(EdgeList in, uint64_t m, u64 state, const uint32_t *P, uint32_t n, uint32_t *root_tmp,

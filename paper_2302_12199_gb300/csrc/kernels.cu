@@ -15,6 +15,8 @@
 // Every wait is bounded.
 #include <cstdint>
 
+#include <cooperative_groups.h>
+
 #include "internal.h"
 
 namespace mstgpu {
@@ -337,20 +339,42 @@ __device__ __forceinline__ uint32_t keep_flags(const CompactArgs &a, uint64_t tb
     } else if (MODE == CM_PARTITION) {
       ok = ok && eu[k] != ev[k] && (((u64)ew[k] << 32) | ei[k]) <= pivot;
     } else if (MODE == CM_FILTER) {
-      ok = ok && (((u64)ew[k] << 32) | ei[k]) > pivot;
-      // both ends in the marked (largest) component: inside one component
-      if (ok && a.giant_bits && ((__ldg(a.giant_bits + (eu[k] >> 5)) >> (eu[k] & 31)) & 1u) &&
-          ((__ldg(a.giant_bits + (ev[k] >> 5)) >> (ev[k] & 31)) & 1u))
-        ok = false;
-      if (ok) {
-        eu[k] = __ldg(a.label + eu[k]);
-        ev[k] = __ldg(a.label + ev[k]);
-        ok = eu[k] != ev[k];
-      }
+      ok = ok && (((u64)ew[k] << 32) | ei[k]) > pivot;  // heavy; resolved below for all items at once
     } else {  // CM_DEDUPE
       if (ok) ok = hash_lookup(a.table, a.tmask, pair_of(eu[k], ev[k])) == edge_key(ew[k], ei[k]);
     }
     keep |= (ok ? 1u : 0u) << k;
+  }
+  if (MODE == CM_FILTER) {
+    // Heavy edges with both ends in the marked (largest) component lie inside
+    // one component.  The bitmap words of all items are loaded together, then
+    // the labels of the remaining items, so that each thread has one round of
+    // independent loads in flight per step.
+    if (a.giant_bits) {
+      uint32_t bu[ITEMS], bv[ITEMS];
+#pragma unroll
+      for (int k = 0; k < ITEMS; ++k) {
+        const bool h = keep >> k & 1;
+        bu[k] = h ? __ldg(a.giant_bits + (eu[k] >> 5)) : 0u;
+        bv[k] = h ? __ldg(a.giant_bits + (ev[k] >> 5)) : 0u;
+      }
+#pragma unroll
+      for (int k = 0; k < ITEMS; ++k)
+        if ((bu[k] >> (eu[k] & 31)) & (bv[k] >> (ev[k] & 31)) & 1u) keep &= ~(1u << k);
+    }
+    uint32_t lu[ITEMS], lv[ITEMS];
+#pragma unroll
+    for (int k = 0; k < ITEMS; ++k) {
+      const bool h = keep >> k & 1;
+      lu[k] = h ? __ldg(a.label + eu[k]) : 0u;
+      lv[k] = h ? __ldg(a.label + ev[k]) : 0u;
+    }
+#pragma unroll
+    for (int k = 0; k < ITEMS; ++k) {
+      eu[k] = lu[k];
+      ev[k] = lv[k];
+      if (lu[k] == lv[k]) keep &= ~(1u << k);
+    }
   }
   return keep;
 }
@@ -454,6 +478,14 @@ __global__ void __launch_bounds__(BLOCK, 4) compact_kernel(CompactArgs a) {
     }
   }
   const uint32_t keep = keep_flags<MODE>(a, tb, m, compact_pivot(a, MODE), eu, ev, ew, ei);
+  if (a.max_w) {  // largest weight of the input, folded into this pass
+    uint32_t mx = 0;
+#pragma unroll
+    for (int k = 0; k < ITEMS; ++k) mx = max(mx, tb + item_off(k) < m ? ew[k] : 0u);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if ((threadIdx.x & 31) == 0 && mx > __ldca(a.max_w)) atomicMax(a.max_w, mx);  // rarely true after a few tiles
+  }
   uint32_t totp;
   const uint32_t excl = block_exclusive_scan(packed_counts(keep), totp, s_warp);
   const uint64_t obase = tile_claim(a.st.total, (totp & 0xffffu) + (totp >> 16), s_base);
@@ -671,10 +703,23 @@ __global__ void hash_insert_kernel(EdgeList in, uint64_t m, HashSlot *table, uin
   }
 }
 
-__global__ void max_weight_kernel(const uint32_t *w, uint64_t m, uint32_t *out) {
+__global__ void __launch_bounds__(BLOCK) max_weight_kernel(const uint32_t *w, uint64_t m, uint32_t *out) {
   uint32_t mx = 0;
-  for (uint64_t i = (uint64_t)blockIdx.x * BLOCK + threadIdx.x; i < m; i += (uint64_t)gridDim.x * BLOCK)
-    mx = max(mx, __ldcs(w + i));
+  const uint64_t nv = ((uintptr_t)w & 15u) ? 0 : m / 4;  // 16-byte vectors
+  const uint4 *w4 = reinterpret_cast<const uint4 *>(w);
+  const uint64_t stride = (uint64_t)gridDim.x * BLOCK;
+  uint64_t i = (uint64_t)blockIdx.x * BLOCK + threadIdx.x;
+  for (; i + 3 * stride < nv; i += 4 * stride) {
+    const uint4 a = __ldcs(w4 + i), b = __ldcs(w4 + i + stride), c = __ldcs(w4 + i + 2 * stride),
+                d = __ldcs(w4 + i + 3 * stride);
+    mx = max(mx, max(max(max(a.x, a.y), max(a.z, a.w)), max(max(b.x, b.y), max(b.z, b.w))));
+    mx = max(mx, max(max(max(c.x, c.y), max(c.z, c.w)), max(max(d.x, d.y), max(d.z, d.w))));
+  }
+  for (; i < nv; i += stride) {
+    const uint4 a = __ldcs(w4 + i);
+    mx = max(mx, max(max(a.x, a.y), max(a.z, a.w)));
+  }
+  for (uint64_t j = nv * 4 + (uint64_t)blockIdx.x * BLOCK + threadIdx.x; j < m; j += stride) mx = max(mx, w[j]);
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
   if ((threadIdx.x & 31) == 0 && mx) atomicMax(out, mx);
@@ -794,6 +839,137 @@ __global__ void __launch_bounds__(SEL_THREADS) pivot_select_kernel(const u64 *ke
     __syncthreads();
   }
   if (threadIdx.x == 0) *out = s_prefix;
+}
+
+// The same selection spread over PSEL_BLOCKS blocks of a cooperative launch:
+// every thread draws its samples, then each pass histograms the next 12 bits
+// (below the bits shared by all candidates) in shared memory, adds the block's
+// bins to a global histogram, and after a grid-wide barrier every block reads
+// the histogram and fixes the same digit.  The first pass starts below the
+// bits that the sample's minimum and maximum share.
+constexpr int PSEL_BLOCKS = 64, PSEL_THREADS = 1024, PSEL_BITS = 12, PSEL_BINS = 1 << PSEL_BITS;
+
+struct PivotScratch {
+  u64 min, max;
+  uint32_t hist[2][PSEL_BINS];
+};
+
+__global__ void __launch_bounds__(PSEL_THREADS) pivot_coop_kernel(EdgeList in, uint64_t m, u64 state,
+                                                                 uint32_t sample, u64 *keys, PivotScratch *ps,
+                                                                 u64 *out) {
+  namespace cg = cooperative_groups;
+  cg::grid_group grid = cg::this_grid();
+  __shared__ uint32_t s_hist[PSEL_BINS];
+  __shared__ u64 s_prefix, s_mask;
+  __shared__ uint32_t s_rank, s_scan[PSEL_THREADS / 32 + 1];
+  const uint32_t nthreads = PSEL_BLOCKS * PSEL_THREADS;
+  const uint32_t tid = blockIdx.x * PSEL_THREADS + threadIdx.x;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+
+  if (blockIdx.x == 0) {
+    for (int i = threadIdx.x; i < 2 * PSEL_BINS; i += PSEL_THREADS) (&ps->hist[0][0])[i] = 0;
+    if (threadIdx.x == 0) {
+      ps->min = KEY_INF;
+      ps->max = 0;
+    }
+  }
+  grid.sync();
+  // draw the samples; track the minimum and maximum key
+  u64 mn = KEY_INF, mx = 0;
+  for (uint32_t i = tid; i < sample; i += nthreads) {
+    u64 k = KEY_INF;
+    if (m) {
+      const uint64_t j = __umul64hi(splitmix64_at(state, i), m);
+      k = ((u64)__ldg(in.w + j) << 32) | (u64)(in.id ? __ldg(in.id + j) : (uint32_t)j);
+    }
+    keys[i] = k;
+    mn = k < mn ? k : mn;
+    mx = k > mx ? k : mx;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const u64 a = __shfl_xor_sync(0xffffffffu, mn, o), b = __shfl_xor_sync(0xffffffffu, mx, o);
+    mn = a < mn ? a : mn;
+    mx = b > mx ? b : mx;
+  }
+  if (lane == 0) {
+    atomicMin(&ps->min, mn);
+    atomicMax(&ps->max, mx);
+  }
+  grid.sync();
+  mn = *(volatile u64 *)&ps->min;
+  mx = *(volatile u64 *)&ps->max;
+  if (mn == mx || sample == 0) {
+    if (tid == 0) *out = mn;
+    return;
+  }
+  int low = 63 - __clzll((long long)(mn ^ mx)) + 1 - PSEL_BITS;  // lowest bit of the first digit
+  if (threadIdx.x == 0) {
+    const int top = low + PSEL_BITS;  // bits >= top are shared by every key
+    s_mask = top >= 64 ? 0ULL : ~((1ULL << top) - 1ULL);
+    s_prefix = mn & s_mask;
+    s_rank = sample / 2;
+  }
+  __syncthreads();
+  for (int pass = 0;; ++pass) {
+    const int shift = low < 0 ? 0 : low;
+    const int width = low < 0 ? PSEL_BITS + low : PSEL_BITS;
+    const uint32_t dmask = (1u << width) - 1u;
+    for (int i = threadIdx.x; i < PSEL_BINS; i += PSEL_THREADS) s_hist[i] = 0;
+    __syncthreads();
+    const u64 prefix = s_prefix, mask = s_mask;
+    for (uint32_t i = tid; i < sample; i += nthreads) {
+      const u64 k = keys[i];
+      if ((k & mask) == prefix) atomicAdd(&s_hist[(uint32_t)(k >> shift) & dmask], 1u);
+    }
+    __syncthreads();
+    uint32_t *gh = ps->hist[pass & 1];
+    for (int i = threadIdx.x; i < PSEL_BINS; i += PSEL_THREADS)
+      if (s_hist[i]) atomicAdd(gh + i, s_hist[i]);
+    grid.sync();
+    // every block: find the digit holding the current rank (4 bins per thread)
+    uint32_t c4[4], sum = 0;
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      c4[b] = *(volatile uint32_t *)(gh + threadIdx.x * 4 + b);
+      sum += c4[b];
+    }
+    uint32_t incl = sum;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += y;
+    }
+    if (lane == 31) s_scan[wid] = incl;
+    __syncthreads();
+    if (wid == 0) {
+      const uint32_t v = lane < PSEL_THREADS / 32 ? s_scan[lane] : 0u;
+      uint32_t wi = v;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, wi, o);
+        if (lane >= o) wi += y;
+      }
+      if (lane < PSEL_THREADS / 32) s_scan[lane] = wi - v;
+    }
+    __syncthreads();
+    const uint32_t before = s_scan[wid] + incl - sum, rank = s_rank;
+    if (before <= rank && rank < before + sum) {  // exactly one thread
+      uint32_t below = before;
+      int b = 0;
+      while (below + c4[b] <= rank) below += c4[b++];
+      s_prefix = prefix | ((u64)(threadIdx.x * 4 + b) << shift);
+      s_mask = mask | ((u64)dmask << shift);
+      s_rank = rank - below;
+    }
+    if (blockIdx.x == 0)  // the other histogram is reused by the next pass
+      for (int i = threadIdx.x; i < PSEL_BINS; i += PSEL_THREADS) ps->hist[(pass + 1) & 1][i] = 0;
+    __syncthreads();
+    if (shift == 0) break;
+    low -= PSEL_BITS;
+    grid.sync();
+  }
+  if (tid == 0) *out = s_prefix;
 }
 
 // ------------------------------------------------- largest component marks
@@ -991,7 +1167,7 @@ void launch_min_edges(EdgeList in, uint64_t m, uint32_t n, int validate, KeyLayo
 
 void launch_max_weight(const uint32_t *w, uint64_t m, uint32_t *out, int sms, cudaStream_t s) {
   if (m == 0) return;
-  max_weight_kernel<<<grid_for((m + BLOCK - 1) / BLOCK, sms, 4), BLOCK, 0, s>>>(w, m, out);
+  max_weight_kernel<<<grid_for((m / 4 + BLOCK - 1) / BLOCK, sms, 8), BLOCK, 0, s>>>(w, m, out);
 }
 
 void launch_hook(const HookArgs &a, uint64_t max_cand, cudaStream_t s) {
@@ -1021,6 +1197,19 @@ void launch_pivot(EdgeList in, uint64_t m, const u64 *m_dev, u64 state, uint32_t
   const unsigned g = (sample + BLOCK - 1) / BLOCK;
   pivot_sample_kernel<<<g > 0 ? g : 1, BLOCK, 0, s>>>(in, m, m_dev, state, sample, sample_buf);
   pivot_select_kernel<<<1, SEL_THREADS, 0, s>>>(sample_buf, sample, pivot_out);
+}
+
+size_t pivot_scratch_bytes() { return sizeof(PivotScratch); }
+
+bool launch_pivot_coop(EdgeList in, uint64_t m, u64 state, uint32_t sample, u64 *keys, void *scratch,
+                       u64 *pivot_out, cudaStream_t s) {
+  PivotScratch *ps = static_cast<PivotScratch *>(scratch);
+  void *args[] = {&in, &m, &state, &sample, &keys, &ps, &pivot_out};
+  if (cudaLaunchCooperativeKernel((const void *)pivot_coop_kernel, dim3(PSEL_BLOCKS), dim3(PSEL_THREADS), args, 0, s) ==
+      cudaSuccess)
+    return true;
+  cudaGetLastError();
+  return false;
 }
 
 void launch_finalize(const uint32_t *bits, uint64_t m, const uint32_t *w, uint32_t *out_ids, uint32_t *out_count,

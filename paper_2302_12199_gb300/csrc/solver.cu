@@ -31,6 +31,7 @@ struct mst_ctx {
   uint32_t epoch = 0;
   u64 *sample_buf = nullptr;
   uint32_t sample_cap = 0;
+  void *pivot_scratch = nullptr;  // histograms of the multi-block pivot selection
   uint64_t pivot_counter = 0;
   // per-kernel-class event timing (mst_profile_enable)
   struct ProfRec {
@@ -274,7 +275,9 @@ struct Solve {
   uint64_t m;
   Buf best_b, parent_b, act_b[2], bits_b;
   const uint32_t *src = nullptr, *dst = nullptr;  // input endpoints, indexed by edge id
+  const uint32_t *w_in = nullptr;                 // input weights
   KeyLayout kl{0, 0, 0};  // unpacked unless choose_layout() packs
+  bool layout_set = false;
   u64 *best = nullptr;
   uint32_t *parent = nullptr, *act[2] = {nullptr, nullptr}, *bits = nullptr;
   int rounds = 0;
@@ -316,12 +319,17 @@ struct Solve {
     CK(cudaMemsetAsync(&c->ds->max_w, 0, sizeof(uint32_t), s));
     launch_max_weight(w, m, &c->ds->max_w, c->sms, s);
     TRY(readback(c, s));
+    set_layout();
+    return MST_OK;
+  }
+  // From the largest weight in hs->max_w (read back by the caller).
+  void set_layout() {
+    layout_set = true;
     const int vb = n > 1 ? 64 - __builtin_clzll((unsigned long long)(n - 1)) : 1;
     const int ib = m > 1 ? 64 - __builtin_clzll((unsigned long long)(m - 1)) : 1;
     const uint32_t mw = c->hs->max_w;
     const int wb = mw ? 32 - __builtin_clz(mw) : 0;
     kl = KeyLayout{wb + ib + vb <= 63 ? 1 : 0, vb, ib};
-    return MST_OK;
   }
 
   // Pointer jumping over the listed vertices (act == nullptr: all n) until
@@ -359,6 +367,7 @@ struct Solve {
   // that wrote the list).
   mst_status boruvka(EdgeList E, uint64_t mE, bool validate, bool best_ready = false) {
     if (mE == 0) return MST_OK;
+    if (!layout_set) TRY(choose_layout(w_in ? w_in : E.w));
     // round 0: minEdges straight from the stored list, then hook and jump
     if (!best_ready)
       PROF(MST_K_MIN_EDGES, 12.0 * (double)mE, -1, 0.0, -1, 0.0,
@@ -483,7 +492,9 @@ struct Solve {
     if (best_ready) TRY(reset_best());
     const u64 state = host_splitmix64_at(c->cfg.seed, c->pivot_counter++);
     PROF(MST_K_PIVOT, 16.0 * (double)c->cfg.pivot_sample, -1, 0.0, -1, 0.0,
-         launch_pivot(E, mE, nullptr, state, c->cfg.pivot_sample, c->sample_buf, &c->ds->pivot, s));
+         if (!launch_pivot_coop(E, mE, state, c->cfg.pivot_sample, c->sample_buf, c->pivot_scratch, &c->ds->pivot,
+                                s)) launch_pivot(E, mE, nullptr, state, c->cfg.pivot_sample, c->sample_buf,
+                                                 &c->ds->pivot, s));
     const double in_bytes = (E.id ? 16.0 : 12.0) * (double)mE;
     // the light half goes straight to Borůvka rounds when it will be sparse:
     // the partition pass then also performs that call's first minEdges
@@ -497,12 +508,20 @@ struct Solve {
     cp.pivot_dev = &c->ds->pivot;
     cp.n = n;
     cp.validate = is_input ? 1 : 0;
+    if (!layout_set) {
+      if (fuse_light) TRY(choose_layout(w_in));  // the pass below relaxes already
+      else {
+        CK(cudaMemsetAsync(&c->ds->max_w, 0, sizeof(uint32_t), s));
+        cp.max_w = &c->ds->max_w;
+      }
+    }
     cp.best = fuse_light ? best : nullptr;
     cp.kl = kl;
     cp.st = next_scan(c, CNT_EDGES);
     TRY(zero_counters(c, s));
     PROF(MST_K_PARTITION, in_bytes, CNT_EDGES, 16.0, -1, 0.0, launch_compact(CM_PARTITION, cp, mE, s));
     TRY(readback(c, s));
+    if (cp.max_w && is_input) set_layout();
     const uint64_t mL = c->hs->count[CNT_EDGES];
     const u64 pivot = c->hs->pivot;
     if (mL == 0 || mL == mE) {  // no progress from this pivot: solve the list directly
@@ -567,7 +586,7 @@ mst_status solve_device(mst_ctx *c, uint32_t n, uint64_t m, const uint32_t *src,
   TRY(S.init());
   S.src = src;
   S.dst = dst;
-  TRY(S.choose_layout(w));
+  S.w_in = w;
   const EdgeList in{src, dst, w, nullptr};
   c->pivot_counter = 0;
   if (use_filter(c->cfg, n, m))
@@ -684,7 +703,7 @@ void mst_config_default(mst_config *cfg) {
   cfg->pivot_sample = 1u << 16;
   cfg->seed = 0x2302121990ULL;
   cfg->filter_min_edges = 1ULL << 20;
-  cfg->filter_max_avg_degree = 4.0f;
+  cfg->filter_max_avg_degree = 1.0f;  // measured optimum on GB300 (the paper uses 4 on its cluster)
 }
 
 const char *mst_status_string(mst_status s) {
@@ -732,6 +751,7 @@ mst_status mst_create(mst_handle *out, const mst_config *cfg) {
   ok = ok && cudaMemset(c->ds, 0, sizeof(DevState)) == cudaSuccess;
   ok = ok && cudaMallocHost(&c->hs, sizeof(DevState)) == cudaSuccess;
   ok = ok && ensure_sample(c) == MST_OK;
+  ok = ok && cudaMalloc(&c->pivot_scratch, pivot_scratch_bytes()) == cudaSuccess;
   ok = ok && cudaDeviceSynchronize() == cudaSuccess;
   if (!ok) {
     cudaGetLastError();
@@ -751,6 +771,7 @@ void mst_destroy(mst_handle h) {
     if (h->hs) cudaFreeHost(h->hs);
     if (h->status) cudaFree(h->status);
     if (h->sample_buf) cudaFree(h->sample_buf);
+    if (h->pivot_scratch) cudaFree(h->pivot_scratch);
     if (h->pool) cudaMemPoolDestroy(h->pool);
     for (auto &r : h->prof_pending) {
       h->ev_pool.push_back(r.a);
@@ -1034,7 +1055,9 @@ mst_status mst_step_pivot(mst_handle h, uint64_t m, const uint32_t *d_w, const u
   Buf sb;
   mst_status st = sb.alloc(h, (size_t)sample * 8, s);
   if (st != MST_OK) return record(h, st);
-  launch_pivot(EdgeList{nullptr, nullptr, d_w, d_id}, m, nullptr, state, sample, sb.as<u64>(), (u64 *)d_pivot, s);
+  const EdgeList E{nullptr, nullptr, d_w, d_id};
+  if (!launch_pivot_coop(E, m, state, sample, sb.as<u64>(), h->pivot_scratch, (u64 *)d_pivot, s))
+    launch_pivot(E, m, nullptr, state, sample, sb.as<u64>(), (u64 *)d_pivot, s);
   if (cudaStreamSynchronize(s) != cudaSuccess) return record(h, MST_ERR_CUDA);
   return record(h, MST_OK);
 }

@@ -26,7 +26,7 @@ def test_default_config(lib):
     lib.mst_config_default(ctypes.byref(cfg))
     assert cfg.variant == 0 and cfg.dedupe == 0
     assert cfg.pivot_sample == 1 << 16
-    assert cfg.filter_max_avg_degree == 4.0
+    assert cfg.filter_max_avg_degree == 1.0
 
 
 def test_status_strings(lib):
