@@ -492,6 +492,168 @@ __global__ void __launch_bounds__(BLOCK, 4) compact_kernel(CompactArgs a) {
   emit_survivors(a, keep, excl, totp, obase, eu, ev, ew, ei, s_u, s_v, s_w, s_id);
 }
 
+// ------------------------------------------------ TMA-pipelined compaction
+
+// The persistent form of compact_kernel for long lists: block b of G handles
+// tiles b, b + G, b + 2G, ...  Full tiles arrive in a ring of TMA_STAGES
+// shared-memory stages by bulk copies (cp.async.bulk, one per array, completion
+// counted on the stage's mbarrier), issued TMA_STAGES tiles ahead; a stage is
+// refilled as soon as its items are in registers.  So HBM keeps streaming the
+// next tiles while the block waits on the current tile's label / bitmap
+// gathers, scans it and stores it.  Blocks never wait for each other.
+constexpr int TMA_STAGES = 1;
+constexpr uint32_t MBAR_SPIN_LIMIT = 1u << 24;
+
+struct __align__(16) EdgeStage {
+  uint32_t u[TILE], v[TILE], w[TILE], id[TILE];
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(u64 *bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(u64 *bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(u64 *bar, uint32_t parity) {
+  uint32_t done;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(done)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return done != 0;
+}
+
+// Bounded wait for phase `parity` of a stage barrier; false if it never came.
+__device__ __forceinline__ bool mbar_wait_bounded(u64 *bar, uint32_t parity) {
+  for (uint32_t i = 0; i < MBAR_SPIN_LIMIT; ++i)
+    if (mbar_try_wait(bar, parity)) return true;
+  return false;
+}
+
+__device__ __forceinline__ void bulk_load(void *dst, const void *src, uint32_t bytes, u64 *bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_u32(dst)),
+               "l"(src), "r"(bytes), "r"(smem_u32(bar))
+               : "memory");
+}
+
+// Issues the bulk copies of full tile `tile` into stage `st` (one thread).
+__device__ __forceinline__ void issue_tile(const CompactArgs &a, uint64_t tile, EdgeStage *st, u64 *bar) {
+  const uint32_t bytes = TILE * 4;
+  const uint64_t off = tile * TILE;
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // order the stage's earlier generic reads
+  mbar_arrive_expect_tx(bar, (a.in.id ? 4u : 3u) * bytes);
+  bulk_load(st->u, a.in.u + off, bytes, bar);
+  bulk_load(st->v, a.in.v + off, bytes, bar);
+  bulk_load(st->w, a.in.w + off, bytes, bar);
+  if (a.in.id) bulk_load(st->id, a.in.id + off, bytes, bar);
+}
+
+__device__ __forceinline__ void read_striped_smem(const uint32_t *p, uint32_t (&x)[ITEMS]) {
+  const uint4 *q = reinterpret_cast<const uint4 *>(p);
+  const uint4 lo = q[threadIdx.x], hi = q[BLOCK + threadIdx.x];
+  x[0] = lo.x; x[1] = lo.y; x[2] = lo.z; x[3] = lo.w;
+  x[4] = hi.x; x[5] = hi.y; x[6] = hi.z; x[7] = hi.w;
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(BLOCK, 3 * 256 / BLOCK) compact_tma_kernel(CompactArgs a) {
+  extern __shared__ __align__(128) unsigned char smem_dyn[];
+  EdgeStage *stage = reinterpret_cast<EdgeStage *>(smem_dyn);  // TMA_STAGES input stages + 1 output stage
+  EdgeStage *out = stage + TMA_STAGES;
+  __shared__ __align__(8) u64 mbar[TMA_STAGES];
+  __shared__ uint32_t s_warp[BLOCK / 32 + 1];
+  __shared__ uint32_t s_base[1];
+  __shared__ uint32_t s_abort;
+
+  const uint64_t m = a.m_dev ? *a.m_dev : a.m;
+  const uint64_t ntiles = (m + TILE - 1) / TILE, nfull = m / TILE;
+  const uint64_t G = gridDim.x;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < TMA_STAGES; ++s) mbar_init(&mbar[s], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    s_abort = 0;
+    for (int s = 0; s < TMA_STAGES; ++s) {
+      const uint64_t tile = blockIdx.x + (uint64_t)s * G;
+      if (tile < nfull) issue_tile(a, tile, &stage[s], &mbar[s]);
+    }
+  }
+  __syncthreads();
+  const u64 pivot = compact_pivot(a, MODE);
+  uint64_t it = 0;
+  for (;; ++it) {
+    const uint64_t tile = blockIdx.x + it * G;
+    if (tile >= ntiles) break;
+    const int si = (int)(it % TMA_STAGES);
+    EdgeStage *st = &stage[si];
+    const uint64_t tb = tile * TILE;
+    uint32_t eu[ITEMS], ev[ITEMS], ew[ITEMS], ei[ITEMS];
+    if (tile < nfull) {
+      if (!mbar_wait_bounded(&mbar[si], (uint32_t)((it / TMA_STAGES) & 1))) atomicOr(&s_abort, 1u);
+      __syncthreads();
+      if (s_abort) break;
+      read_striped_smem(st->u, eu);
+      read_striped_smem(st->v, ev);
+      read_striped_smem(st->w, ew);
+      if (a.in.id) {
+        read_striped_smem(st->id, ei);
+      } else {
+#pragma unroll
+        for (int k = 0; k < ITEMS; ++k) ei[k] = (uint32_t)(tb + item_off(k));
+      }
+      __syncthreads();  // the stage is consumed: refill it with the tile TMA_STAGES ahead
+      if (threadIdx.x == 0) {
+        const uint64_t next = tile + (uint64_t)TMA_STAGES * G;
+        if (next < nfull) issue_tile(a, next, st, &mbar[si]);
+      }
+    } else {  // the partial last tile: plain loads
+#pragma unroll
+      for (int k = 0; k < ITEMS; ++k) {
+        const uint64_t j = tb + item_off(k);
+        if (j < m) {
+          eu[k] = __ldg(a.in.u + j);
+          ev[k] = __ldg(a.in.v + j);
+          ew[k] = __ldg(a.in.w + j);
+          ei[k] = a.in.id ? __ldg(a.in.id + j) : (uint32_t)j;
+        } else {
+          eu[k] = ev[k] = ew[k] = ei[k] = 0;
+        }
+      }
+    }
+    const uint32_t keep = keep_flags<MODE>(a, tb, m, pivot, eu, ev, ew, ei);
+    if (a.max_w) {
+      uint32_t mx = 0;
+#pragma unroll
+      for (int k = 0; k < ITEMS; ++k) mx = max(mx, tb + item_off(k) < m ? ew[k] : 0u);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+      if ((threadIdx.x & 31) == 0 && mx > __ldca(a.max_w)) atomicMax(a.max_w, mx);
+    }
+    uint32_t totp;
+    const uint32_t excl = block_exclusive_scan(packed_counts(keep), totp, s_warp);
+    const uint64_t obase = tile_claim(a.st.total, (totp & 0xffffu) + (totp >> 16), s_base);
+    emit_survivors(a, keep, excl, totp, obase, eu, ev, ew, ei, out->u, out->v, out->w, out->id);
+    __syncthreads();  // the output stage is reused by the next tile
+  }
+  // On an abort, wait (bounded) for the copies this block still has in flight
+  // before its shared memory goes away.
+  __syncthreads();
+  if (s_abort && threadIdx.x == 0) {
+    for (uint64_t k = it; k < it + TMA_STAGES; ++k) {
+      const uint64_t tile = blockIdx.x + k * G;
+      if (tile < nfull) mbar_wait_bounded(&mbar[k % TMA_STAGES], (uint32_t)((k / TMA_STAGES) & 1));
+    }
+  }
+}
+
 // --------------------------------------------------------------- min edges
 
 // minEdges of a round that starts from a stored list (the input, or a list
@@ -1129,17 +1291,29 @@ int max_scan_tiles(uint64_t count) { return (int)((count + TILE - 1) / TILE); }
 
 template <int MODE>
 static void launch_compact_mode(const CompactArgs &a, uint64_t max_count, cudaStream_t s) {
-  static bool attrs = false;  // prefer shared memory over L1 so that 4 blocks fit per SM
-  if (!attrs) {
+  static int attrs = 0, tma_blocks = 0;
+  const size_t tma_smem = sizeof(EdgeStage) * (TMA_STAGES + 1);
+  if (!attrs) {  // prefer shared memory over L1; size the persistent grid
     cudaFuncSetAttribute(compact_kernel<MODE, true>, cudaFuncAttributePreferredSharedMemoryCarveout,
                          cudaSharedmemCarveoutMaxShared);
     cudaFuncSetAttribute(compact_kernel<MODE, false>, cudaFuncAttributePreferredSharedMemoryCarveout,
                          cudaSharedmemCarveoutMaxShared);
-    attrs = true;
+    cudaFuncSetAttribute(compact_tma_kernel<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tma_smem);
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, compact_tma_kernel<MODE>, BLOCK, tma_smem);
+    cudaGetLastError();
+    tma_blocks = sms * per_sm;
+    attrs = 1;
   }
   const uint64_t tiles = (max_count + TILE - 1) / TILE;
   if (tiles == 0) return;
   const bool aligned = aligned16(a.in.u) && aligned16(a.in.v) && aligned16(a.in.w) && (!a.in.id || aligned16(a.in.id));
+  if (aligned && tma_blocks > 0 && tiles >= (uint64_t)tma_blocks * TMA_STAGES) {
+    compact_tma_kernel<MODE><<<(unsigned)tma_blocks, BLOCK, tma_smem, s>>>(a);
+    return;
+  }
   if (aligned)
     compact_kernel<MODE, true><<<(unsigned)tiles, BLOCK, 0, s>>>(a);
   else
