@@ -56,8 +56,9 @@ typedef struct {
   int device;                  /* CUDA device ordinal */
   int variant;                 /* MST_VARIANT_*: Borůvka (Alg. 1 rounds) or Filter-Borůvka (Alg. 2) */
   int dedupe;                  /* MST_DEDUPE_*: parallel-edge removal between rounds (Section 2.3, optional) */
-  int tile_contract;           /* -1 auto, 0 off, 1 on: local contraction before the rounds (Section 4.1) */
-  uint32_t tile_vertices;      /* vertices per tile for local contraction */
+  int tile_contract;           /* -1 auto (when >= 10% of sampled edges are local), 0 off, 1 on: local
+                                  contraction on vertex-range tiles before the rounds (Section 4.1) */
+  uint32_t tile_vertices;      /* vertices per tile for local contraction, 32..4096 */
   uint32_t pivot_sample;       /* edges sampled per pivot selection (Alg. 2 PivotSelection) */
   uint64_t seed;               /* seed of the pivot sampling stream */
   uint64_t filter_min_edges;   /* isSparse: lists shorter than this are not partitioned */
@@ -135,6 +136,7 @@ enum {
   MST_K_PARTITION,      /* light/heavy partition */
   MST_K_FILTER,         /* filtering of heavy edges */
   MST_K_FINALIZE,       /* bitmap -> ascending ids + weight */
+  MST_K_TILE,           /* tile-local contraction (count, bucket, contract) */
   MST_K_COUNT
 };
 typedef struct {
@@ -207,6 +209,19 @@ mst_status mst_step_partition(mst_handle h, uint64_t m, const uint32_t *d_u, con
 mst_status mst_step_filter(mst_handle h, uint32_t n, uint64_t m, const uint32_t *d_u, const uint32_t *d_v,
                            const uint32_t *d_w, const uint32_t *d_id, uint64_t pivot, uint32_t *d_P, uint32_t *d_ou,
                            uint32_t *d_ov, uint32_t *d_ow, uint32_t *d_oid, uint64_t *d_out_count, void *stream);
+
+/* Local preprocessing (Section 4.1) with vertex-range tiles in place of PEs:
+ * vertex x is in tile x / tile_vertices (32..4096); an edge with both ends in
+ * one tile is local.  Borůvka rounds run on each tile's local edges, and a
+ * component is contracted along its lightest local edge only if that edge is
+ * lighter than every cut edge incident to the component; rounds repeat until
+ * no component contracts.
+ *   d_parent  [out] [n] tile root of every vertex
+ *   d_chosen  [in/out] bitmap over edge ids; bits of contracted edges are set
+ * Input as mst_solve (validated; MST_ERR_VERTEX_RANGE on a bad id). */
+mst_status mst_step_tile_contract(mst_handle h, uint32_t n, uint64_t m, const uint32_t *d_src, const uint32_t *d_dst,
+                                  const uint32_t *d_w, uint32_t tile_vertices, uint32_t *d_parent, uint32_t *d_chosen,
+                                  void *stream);
 
 /* Output step (Section 2.2 output; Section 6.2 edge ids): the set bits of the
  * bitmap d_chosen over ids 0..m-1 become ascending ids in d_msf_ids, their

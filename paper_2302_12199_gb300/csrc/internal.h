@@ -26,6 +26,8 @@ struct DevState {
   u64 pivot;            // result of the pivot selection
   uint32_t giant_root;  // root of the largest sampled component (filter fast path)
   uint32_t max_w;       // largest input weight (key layout)
+  uint32_t local_samples;  // sampled local edges (automatic tile contraction)
+  uint32_t pad;
 };
 enum { CNT_EDGES = 0, CNT_ACTIVE = 1, CNT_TMP = 2, CNT_AUX = 3, CNT_USER = 4 };
 
@@ -131,6 +133,17 @@ void launch_finalize(const uint32_t *bits, uint64_t m, const uint32_t *w, uint32
                      u64 *total_weight, ScanState st, cudaStream_t s);
 void launch_giant_bits(EdgeList in, uint64_t m, u64 state, const uint32_t *P, uint32_t n, uint32_t *root_tmp,
                        uint32_t *bits, int sms, cudaStream_t s);
+// tile-local contraction (Section 4.1)
+void launch_tile_count(EdgeList in, uint64_t m, uint32_t n, uint32_t B, u64 *cutmin, uint32_t *count,
+                       u64 *local_total, uint32_t *max_w, uint32_t *err, int sms, cudaStream_t s);
+void launch_tile_scan(const uint32_t *count, uint32_t ntiles, u64 *offsets, cudaStream_t s);
+void launch_tile_scatter(EdgeList in, uint64_t m, uint32_t n, uint32_t B, const u64 *offsets, uint32_t *fill,
+                         uint32_t *b_ends, uint32_t *b_w, uint32_t *b_id, int sms, cudaStream_t s);
+bool launch_tile_contract(uint32_t n, uint32_t B, const u64 *cutmin, const u64 *offsets, const uint32_t *b_ends,
+                          const uint32_t *b_w, const uint32_t *b_id, uint32_t *parent, uint32_t *bits, uint32_t *err,
+                          cudaStream_t s);
+void launch_tile_sample(EdgeList in, uint64_t m, uint32_t n, uint32_t B, u64 state, uint32_t samples,
+                        uint32_t *local_count, cudaStream_t s);
 void launch_iota(uint32_t *p, uint64_t n, int sms, cudaStream_t s);
 void launch_u64_to_u32(const u64 *src, uint32_t *dst, cudaStream_t s);
 

@@ -81,6 +81,8 @@ __device__ __forceinline__ bool same_edge(const KeyLayout &kl, u64 a, u64 b) {
   return kl.packed ? (a >> kl.vbits) == (b >> kl.vbits) : a == b;
 }
 
+__device__ __forceinline__ bool aligned16_dev(const void *p) { return ((uintptr_t)p & 15u) == 0; }
+
 __device__ __forceinline__ u64 pair_of(uint32_t a, uint32_t b) {
   return a < b ? (((u64)a << 32) | b) : (((u64)b << 32) | a);
 }
@@ -1134,6 +1136,276 @@ __global__ void __launch_bounds__(PSEL_THREADS) pivot_coop_kernel(EdgeList in, u
   if (tid == 0) *out = s_prefix;
 }
 
+// ---------------------------------------------------- tile-local contraction
+
+// Local preprocessing (Section 4.1) with vertex-range tiles standing in for the
+// paper's PEs: vertex x belongs to tile x / B; an edge is local when both ends
+// are in one tile, a cut edge otherwise.
+
+// Pass over the input: vertex-range check, per-vertex minimum key over incident
+// cut edges (cutmin), number of local edges per tile, total local edges, and
+// the largest weight (key layout).  Local-edge counts are aggregated per warp.
+__global__ void __launch_bounds__(BLOCK) tile_count_kernel(EdgeList in, uint64_t m, uint32_t n, uint32_t B,
+                                                           u64 *cutmin, uint32_t *count, u64 *local_total,
+                                                           uint32_t *max_w, uint32_t *err) {
+  const uint64_t ntiles = (m + TILE - 1) / TILE;
+  uint32_t nlocal = 0, mx = 0;
+  for (uint64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const uint64_t tb = tile * TILE;
+    uint32_t eu[ITEMS], ev[ITEMS], ew[ITEMS];
+    if (tb + TILE <= m && aligned16_dev(in.u) && aligned16_dev(in.v) && aligned16_dev(in.w)) {
+      load_striped(in.u, tb, eu);
+      load_striped(in.v, tb, ev);
+      load_striped(in.w, tb, ew);
+    } else {
+#pragma unroll
+      for (int k = 0; k < ITEMS; ++k) {
+        const uint64_t j = tb + item_off(k);
+        eu[k] = j < m ? __ldg(in.u + j) : 0u;
+        ev[k] = j < m ? __ldg(in.v + j) : 0u;
+        ew[k] = j < m ? __ldg(in.w + j) : 0u;
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < ITEMS; ++k) {
+      const uint64_t j = tb + item_off(k);
+      bool ok = j < m;
+      if (ok && (eu[k] >= n || ev[k] >= n)) {
+        atomicOr(err, ERR_VERTEX);
+        ok = false;
+      }
+      if (ok) mx = max(mx, ew[k]);
+      ok = ok && eu[k] != ev[k];
+      const uint32_t tu = eu[k] / B, tv = ev[k] / B;
+      const bool local = ok && tu == tv;
+      const uint32_t peers = __match_any_sync(0xffffffffu, local ? tu : 0xffffffffu);
+      if (local && (threadIdx.x & 31) == (unsigned)(__ffs(peers) - 1)) atomicAdd(count + tu, (uint32_t)__popc(peers));
+      nlocal += local ? 1u : 0u;
+      if (ok && !local) {
+        const u64 key = edge_key(ew[k], (uint32_t)j);
+        if (key < __ldca(cutmin + eu[k])) atomicMin(cutmin + eu[k], key);
+        if (key < __ldca(cutmin + ev[k])) atomicMin(cutmin + ev[k], key);
+      }
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    nlocal += __shfl_xor_sync(0xffffffffu, nlocal, o);
+    mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  }
+  if ((threadIdx.x & 31) == 0) {
+    if (nlocal) atomicAdd(local_total, (u64)nlocal);
+    if (mx > __ldca(max_w)) atomicMax(max_w, mx);
+  }
+}
+
+// Exclusive scan of the per-tile counts into offsets[0..ntiles] (one block).
+__global__ void __launch_bounds__(1024) tile_scan_kernel(const uint32_t *count, uint32_t ntiles, u64 *offsets) {
+  __shared__ u64 s_w[33];
+  __shared__ u64 s_carry;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (threadIdx.x == 0) s_carry = 0;
+  __syncthreads();
+  for (uint32_t base = 0; base < ntiles; base += 1024) {
+    const uint32_t i = base + threadIdx.x;
+    const u64 x = i < ntiles ? count[i] : 0;
+    u64 incl = x;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const u64 y = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += y;
+    }
+    if (lane == 31) s_w[wid] = incl;
+    __syncthreads();
+    if (wid == 0) {
+      const u64 v = s_w[lane];
+      u64 wi = v;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const u64 y = __shfl_up_sync(0xffffffffu, wi, o);
+        if (lane >= o) wi += y;
+      }
+      s_w[lane] = wi - v;
+      if (lane == 31) s_w[32] = wi;
+    }
+    __syncthreads();
+    const u64 carry = s_carry;
+    if (i < ntiles) offsets[i] = carry + s_w[wid] + incl - x;
+    __syncthreads();
+    if (threadIdx.x == 0) s_carry = carry + s_w[32];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) offsets[ntiles] = s_carry;
+}
+
+// Scatters the local edges into per-tile buckets: packed tile-local ends
+// (u | v << 16), weight and id.  Order inside a bucket is unspecified.
+__global__ void __launch_bounds__(BLOCK) tile_scatter_kernel(EdgeList in, uint64_t m, uint32_t n, uint32_t B,
+                                                             const u64 *offsets, uint32_t *fill, uint32_t *b_ends,
+                                                             uint32_t *b_w, uint32_t *b_id) {
+  const uint64_t ntiles = (m + TILE - 1) / TILE;
+  for (uint64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const uint64_t tb = tile * TILE;
+    uint32_t eu[ITEMS], ev[ITEMS], ew[ITEMS];
+    if (tb + TILE <= m && aligned16_dev(in.u) && aligned16_dev(in.v) && aligned16_dev(in.w)) {
+      load_striped(in.u, tb, eu);
+      load_striped(in.v, tb, ev);
+      load_striped(in.w, tb, ew);
+    } else {
+#pragma unroll
+      for (int k = 0; k < ITEMS; ++k) {
+        const uint64_t j = tb + item_off(k);
+        eu[k] = j < m ? __ldg(in.u + j) : 0u;
+        ev[k] = j < m ? __ldg(in.v + j) : 0u;
+        ew[k] = j < m ? __ldg(in.w + j) : 0u;
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < ITEMS; ++k) {
+      const uint64_t j = tb + item_off(k);
+      const bool ok = j < m && eu[k] < n && ev[k] < n && eu[k] != ev[k];
+      const uint32_t tu = eu[k] / B, tv = ev[k] / B;
+      const bool local = ok && tu == tv;
+      const uint32_t peers = __match_any_sync(0xffffffffu, local ? tu : 0xffffffffu);
+      const int leader = __ffs(peers) - 1;
+      uint32_t pos = 0;
+      if (local && (threadIdx.x & 31) == (unsigned)leader) pos = atomicAdd(fill + tu, (uint32_t)__popc(peers));
+      pos = __shfl_sync(0xffffffffu, pos, leader);
+      if (local) {
+        const u64 at = offsets[tu] + pos + __popc(peers & ((1u << (threadIdx.x & 31)) - 1u));
+        b_ends[at] = (eu[k] - tu * B) | ((ev[k] - tu * B) << 16);
+        b_w[at] = ew[k];
+        b_id[at] = (uint32_t)j;
+      }
+    }
+  }
+}
+
+// One block per tile: synchronous Borůvka rounds on the tile's local edges in
+// shared memory.  A component hooks along its lightest local edge only when
+// that edge is lighter than every cut edge incident to the component (then it
+// is the component's lightest edge overall, an MSF edge by the cut property);
+// 2-cycles keep the smaller vertex as root.  Rounds repeat until no component
+// hooks.  Writes the tile root of every vertex to parent[] and sets the bits
+// of the contracted edges.  A tile whose edges exceed the shared-memory
+// capacity runs the same rounds reading its bucket from global memory.
+constexpr int TC_THREADS = 512;
+__global__ void __launch_bounds__(TC_THREADS) tile_contract_kernel(uint32_t n, uint32_t B, const u64 *cutmin,
+                                                                    const u64 *offsets, const uint32_t *b_ends,
+                                                                    const uint32_t *b_w, const uint32_t *b_id,
+                                                                    uint32_t edge_cap, uint32_t *parent,
+                                                                    uint32_t *bits, uint32_t *err) {
+  extern __shared__ __align__(16) unsigned char smem_dyn[];
+  u64 *best = reinterpret_cast<u64 *>(smem_dyn);  // [B]
+  u64 *comp = best + B;                           // [B] component cut minimum (valid at roots)
+  u64 *skey = comp + B;                           // [edge_cap]
+  uint32_t *lab = reinterpret_cast<uint32_t *>(skey + edge_cap);  // [B]
+  uint32_t *hook = lab + B;                                        // [B]
+  uint32_t *other = hook + B;                                      // [B]
+  uint32_t *sends = other + B;                                     // [edge_cap]
+  __shared__ uint32_t s_any;
+
+  const uint32_t t = blockIdx.x;
+  const uint64_t vbase = (uint64_t)t * B;
+  const uint32_t nv = (uint32_t)min((uint64_t)B, (uint64_t)n - vbase);
+  const u64 e0 = offsets[t];
+  const uint32_t ne = (uint32_t)(offsets[t + 1] - e0);
+  const bool in_smem = ne <= edge_cap;
+  for (uint32_t x = threadIdx.x; x < nv; x += TC_THREADS) {
+    lab[x] = x;
+    comp[x] = cutmin[vbase + x];
+  }
+  if (in_smem) {
+    for (uint32_t e = threadIdx.x; e < ne; e += TC_THREADS) {
+      sends[e] = b_ends[e0 + e];
+      skey[e] = edge_key(b_w[e0 + e], b_id[e0 + e]);
+    }
+  }
+  __syncthreads();
+  for (uint32_t round = 0; round <= nv; ++round) {
+    for (uint32_t c = threadIdx.x; c < nv; c += TC_THREADS) best[c] = KEY_INF;
+    if (threadIdx.x == 0) s_any = 0;
+    __syncthreads();
+    for (uint32_t e = threadIdx.x; e < ne; e += TC_THREADS) {  // lightest local edge per component
+      const uint32_t pe = in_smem ? sends[e] : b_ends[e0 + e];
+      const u64 k = in_smem ? skey[e] : edge_key(b_w[e0 + e], b_id[e0 + e]);
+      const uint32_t a = lab[pe & 0xffffu], b = lab[pe >> 16];
+      if (a != b) {
+        atomicMin(best + a, k);
+        atomicMin(best + b, k);
+      }
+    }
+    __syncthreads();
+    for (uint32_t c = threadIdx.x; c < nv; c += TC_THREADS)  // hook only below every incident cut edge
+      if (lab[c] != c || !(best[c] < comp[c])) best[c] = KEY_INF;
+    __syncthreads();
+    for (uint32_t e = threadIdx.x; e < ne; e += TC_THREADS) {  // far end of each hooking component's edge
+      const uint32_t pe = in_smem ? sends[e] : b_ends[e0 + e];
+      const u64 k = in_smem ? skey[e] : edge_key(b_w[e0 + e], b_id[e0 + e]);
+      const uint32_t a = lab[pe & 0xffffu], b = lab[pe >> 16];
+      if (a != b) {
+        if (best[a] == k) other[a] = b;
+        if (best[b] == k) other[b] = a;
+      }
+    }
+    __syncthreads();
+    for (uint32_t c = threadIdx.x; c < nv; c += TC_THREADS) {
+      hook[c] = c;
+      if (best[c] != KEY_INF) {
+        const uint32_t o = other[c];
+        const bool root = best[o] == best[c] && c < o;
+        if (!root) {
+          hook[c] = o;
+          const uint32_t id = (uint32_t)best[c];
+          atomicOr(bits + (id >> 5), 1u << (id & 31));
+          s_any = 1;
+        }
+      }
+    }
+    __syncthreads();
+    if (!s_any) break;
+    // pointer doubling among this round's roots (at most log2(nv) + 1 steps)
+    for (int it = 0; it < 32; ++it) {
+      __syncthreads();
+      if (threadIdx.x == 0) s_any = 0;
+      __syncthreads();
+      for (uint32_t c = threadIdx.x; c < nv; c += TC_THREADS) {
+        if (lab[c] != c) continue;
+        const uint32_t h = hook[c], hh = hook[h];
+        if (hh != h) {
+          hook[c] = hh;
+          s_any = 1;
+        }
+      }
+      __syncthreads();
+      if (!s_any) break;
+      if (it == 31 && threadIdx.x == 0) atomicOr(err, ERR_JUMP);
+    }
+    // merge the cut minima into the new roots, then relabel the vertices
+    for (uint32_t c = threadIdx.x; c < nv; c += TC_THREADS)
+      if (lab[c] == c && hook[c] != c) atomicMin(comp + hook[c], comp[c]);
+    __syncthreads();
+    for (uint32_t x = threadIdx.x; x < nv; x += TC_THREADS) lab[x] = hook[lab[x]];
+    __syncthreads();
+  }
+  for (uint32_t x = threadIdx.x; x < nv; x += TC_THREADS) parent[vbase + x] = (uint32_t)(vbase + lab[x]);
+}
+
+// Fraction estimate for the automatic switch: counts how many of `samples`
+// random edges (splitmix64) are local.
+__global__ void tile_sample_kernel(EdgeList in, uint64_t m, uint32_t n, uint32_t B, u64 state, uint32_t samples,
+                                   uint32_t *local_count) {
+  uint32_t c = 0;
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < samples; i += gridDim.x * blockDim.x) {
+    const uint64_t j = __umul64hi(splitmix64_at(state, i), m);
+    const uint32_t u = __ldg(in.u + j), v = __ldg(in.v + j);
+    c += (u < n && v < n && u != v && u / B == v / B) ? 1u : 0u;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+  if ((threadIdx.x & 31) == 0 && c) atomicAdd(local_count, c);
+}
+
 // ------------------------------------------------- largest component marks
 
 // Finds the component that most endpoints of a random edge sample belong to:
@@ -1398,6 +1670,51 @@ void launch_giant_bits(EdgeList in, uint64_t m, u64 state, const uint32_t *P, ui
   giant_root_kernel<<<1, MODE_SAMPLES, 0, s>>>(in, m, state, P, n, root_tmp);
   const uint64_t threads = ((uint64_t)n + 31) / 32 * 32;
   giant_bits_kernel<<<grid_for((threads + BLOCK - 1) / BLOCK, sms, 8), BLOCK, 0, s>>>(P, n, root_tmp, bits);
+}
+
+void launch_tile_count(EdgeList in, uint64_t m, uint32_t n, uint32_t B, u64 *cutmin, uint32_t *count,
+                       u64 *local_total, uint32_t *max_w, uint32_t *err, int sms, cudaStream_t s) {
+  if (m == 0) return;
+  tile_count_kernel<<<grid_for((m + TILE - 1) / TILE, sms, 8), BLOCK, 0, s>>>(in, m, n, B, cutmin, count,
+                                                                              local_total, max_w, err);
+}
+
+void launch_tile_scan(const uint32_t *count, uint32_t ntiles, u64 *offsets, cudaStream_t s) {
+  tile_scan_kernel<<<1, 1024, 0, s>>>(count, ntiles, offsets);
+}
+
+void launch_tile_scatter(EdgeList in, uint64_t m, uint32_t n, uint32_t B, const u64 *offsets, uint32_t *fill,
+                         uint32_t *b_ends, uint32_t *b_w, uint32_t *b_id, int sms, cudaStream_t s) {
+  if (m == 0) return;
+  tile_scatter_kernel<<<grid_for((m + TILE - 1) / TILE, sms, 8), BLOCK, 0, s>>>(in, m, n, B, offsets, fill, b_ends,
+                                                                                b_w, b_id);
+}
+
+bool launch_tile_contract(uint32_t n, uint32_t B, const u64 *cutmin, const u64 *offsets, const uint32_t *b_ends,
+                          const uint32_t *b_w, const uint32_t *b_id, uint32_t *parent, uint32_t *bits, uint32_t *err,
+                          cudaStream_t s) {
+  static int smem_max = 0;
+  if (!smem_max) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    smem_max -= 2048;  // static shared memory and slack
+    cudaFuncSetAttribute(tile_contract_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_max);
+  }
+  const size_t vbytes = (size_t)B * (8 + 8 + 4 + 4 + 4);
+  if ((size_t)smem_max <= vbytes) return false;
+  const uint32_t cap = (uint32_t)(((size_t)smem_max - vbytes) / 12);
+  const size_t bytes = vbytes + (size_t)cap * 12;
+  const uint32_t ntiles = (uint32_t)(((uint64_t)n + B - 1) / B);
+  tile_contract_kernel<<<ntiles, TC_THREADS, bytes, s>>>(n, B, cutmin, offsets, b_ends, b_w, b_id, cap, parent, bits,
+                                                         err);
+  return true;
+}
+
+void launch_tile_sample(EdgeList in, uint64_t m, uint32_t n, uint32_t B, u64 state, uint32_t samples,
+                        uint32_t *local_count, cudaStream_t s) {
+  if (m == 0) return;
+  tile_sample_kernel<<<(samples + 255) / 256, 256, 0, s>>>(in, m, n, B, state, samples, local_count);
 }
 
 void launch_iota(uint32_t *p, uint64_t n, int sms, cudaStream_t s) {

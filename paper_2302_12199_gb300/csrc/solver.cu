@@ -464,6 +464,72 @@ struct Solve {
     return MST_OK;
   }
 
+  // Local preprocessing (Section 4.1) on vertex-range tiles.  When applied,
+  // parent[] holds every vertex's tile root, the contracted edges are marked,
+  // and the input relabelled by those roots (internal edges dropped) is left in
+  // `out` (fused with the first minEdges when relax is set).  `auto` (-1)
+  // applies it only if at least 10% of the edges are local (Section 6.2),
+  // estimated from a sample first.
+  mst_status tile_preprocess(const uint32_t *w, bool relax, ListBuf &out, uint64_t &m_out, bool &applied) {
+    applied = false;
+    const uint32_t B = c->cfg.tile_vertices;
+    const EdgeList in{src, dst, w, nullptr};
+    if (c->cfg.tile_contract == 0 || m == 0) return MST_OK;
+    if (c->cfg.tile_contract < 0) {
+      CK(cudaMemsetAsync(&c->ds->local_samples, 0, sizeof(uint32_t), s));
+      launch_tile_sample(in, m, n, B, 0x51ced0ULL, 4096, &c->ds->local_samples, s);
+      TRY(readback(c, s));
+      if (c->hs->local_samples < 410) return MST_OK;  // < 10% of 4096 samples local
+    }
+    const uint32_t ntiles = (uint32_t)(((uint64_t)n + B - 1) / B);
+    Buf cut_b, cnt_b, off_b, fill_b, bucket_b;
+    TRY(cut_b.alloc(c, (size_t)n * 8, s));
+    TRY(cnt_b.alloc(c, (size_t)ntiles * 4, s));
+    TRY(off_b.alloc(c, ((size_t)ntiles + 1) * 8, s));
+    TRY(fill_b.alloc(c, (size_t)ntiles * 4, s));
+    CK(cudaMemsetAsync(cut_b.p, 0xff, (size_t)n * 8, s));
+    CK(cudaMemsetAsync(cnt_b.p, 0, (size_t)ntiles * 4, s));
+    CK(cudaMemsetAsync(fill_b.p, 0, (size_t)ntiles * 4, s));
+    CK(cudaMemsetAsync(&c->ds->count[CNT_AUX], 0, sizeof(u64), s));
+    CK(cudaMemsetAsync(&c->ds->max_w, 0, sizeof(uint32_t), s));
+    PROF(MST_K_TILE, 12.0 * (double)m + 8.0 * (double)n, -1, 0.0, -1, 0.0,
+         launch_tile_count(in, m, n, B, cut_b.as<u64>(), cnt_b.as<uint32_t>(), &c->ds->count[CNT_AUX],
+                           &c->ds->max_w, &c->ds->err, c->sms, s));
+    TRY(readback(c, s));
+    if (!layout_set) set_layout();
+    const uint64_t nlocal = c->hs->count[CNT_AUX];
+    if (c->cfg.tile_contract < 0 && nlocal * 10 < m) return MST_OK;
+    PROF(MST_K_TILE, 12.0 * (double)ntiles, -1, 0.0, -1, 0.0, launch_tile_scan(cnt_b.as<uint32_t>(), ntiles, off_b.as<u64>(), s));
+    const uint64_t stride = round_up(nlocal * 4 + 16, 256);
+    TRY(bucket_b.alloc(c, stride * 3, s));
+    char *bb = bucket_b.as<char>();
+    PROF(MST_K_TILE, 12.0 * (double)m + 12.0 * (double)nlocal, -1, 0.0, -1, 0.0,
+         launch_tile_scatter(in, m, n, B, off_b.as<u64>(), fill_b.as<uint32_t>(), (uint32_t *)bb,
+                             (uint32_t *)(bb + stride), (uint32_t *)(bb + 2 * stride), c->sms, s));
+    bool launched = false;
+    PROF(MST_K_TILE, 12.0 * (double)nlocal + 12.0 * (double)n, -1, 0.0, -1, 0.0,
+         launched = launch_tile_contract(n, B, cut_b.as<u64>(), off_b.as<u64>(), (uint32_t *)bb,
+                                         (uint32_t *)(bb + stride), (uint32_t *)(bb + 2 * stride), parent, bits,
+                                         &c->ds->err, s));
+    if (!launched) return MST_ERR_INVALID_ARG;  // tile too large for shared memory
+    TRY(out.alloc(c, m, s));
+    TRY(zero_counters(c, s));
+    CompactArgs ca{};
+    ca.in = in;
+    ca.m = m;
+    ca.out = out.out;
+    ca.label = parent;
+    ca.n = n;
+    ca.kl = kl;
+    ca.best = relax ? best : nullptr;
+    ca.st = next_scan(c, CNT_EDGES);
+    PROF(MST_K_RELABEL_MIN, 12.0 * (double)m, CNT_EDGES, 16.0, -1, 0.0, launch_compact(CM_RELABEL, ca, m, s));
+    TRY(readback(c, s));
+    m_out = c->hs->count[CNT_EDGES];
+    applied = true;
+    return MST_OK;
+  }
+
   bool is_sparse(uint64_t mE) const {
     return mE < c->cfg.filter_min_edges || 2.0 * (double)mE <= (double)c->cfg.filter_max_avg_degree * (double)n;
   }
@@ -589,10 +655,21 @@ mst_status solve_device(mst_ctx *c, uint32_t n, uint64_t m, const uint32_t *src,
   S.w_in = w;
   const EdgeList in{src, dst, w, nullptr};
   c->pivot_counter = 0;
-  if (use_filter(c->cfg, n, m))
+  const bool filt = use_filter(c->cfg, n, m);
+  ListBuf local;
+  uint64_t m_local = 0;
+  bool applied = false;
+  TRY(S.tile_preprocess(w, !filt, local, m_local, applied));
+  if (applied) {  // continue on the contracted graph (ids already validated)
+    if (filt)
+      TRY(S.filter(local.list(), m_local, false, 0));
+    else
+      TRY(S.boruvka(local.list(), m_local, false, true));
+  } else if (filt) {
     TRY(S.filter(in, m, true, 0));
-  else
+  } else {
     TRY(S.boruvka(in, m, true));
+  }
   return S.finalize(w, out_ids, out_count, total_weight);
 }
 
@@ -602,6 +679,8 @@ mst_status validate_cfg(const mst_config *cfg) {
     return MST_ERR_INVALID_ARG;
   if (cfg->pivot_sample == 0 || cfg->pivot_sample > (1u << 24)) return MST_ERR_INVALID_ARG;
   if (!(cfg->filter_max_avg_degree > 0.0f)) return MST_ERR_INVALID_ARG;
+  if (cfg->tile_contract < -1 || cfg->tile_contract > 1) return MST_ERR_INVALID_ARG;
+  if (cfg->tile_vertices < 32 || cfg->tile_vertices > 4096) return MST_ERR_INVALID_ARG;
   return MST_OK;
 }
 
@@ -698,8 +777,8 @@ void mst_config_default(mst_config *cfg) {
   cfg->device = 0;
   cfg->variant = MST_VARIANT_BORUVKA;
   cfg->dedupe = MST_DEDUPE_AUTO;
-  cfg->tile_contract = 0;
-  cfg->tile_vertices = 4096;
+  cfg->tile_contract = -1;
+  cfg->tile_vertices = 2048;
   cfg->pivot_sample = 1u << 16;
   cfg->seed = 0x2302121990ULL;
   cfg->filter_min_edges = 1ULL << 20;
@@ -1060,6 +1139,36 @@ mst_status mst_step_pivot(mst_handle h, uint64_t m, const uint32_t *d_w, const u
     launch_pivot(E, m, nullptr, state, sample, sb.as<u64>(), (u64 *)d_pivot, s);
   if (cudaStreamSynchronize(s) != cudaSuccess) return record(h, MST_ERR_CUDA);
   return record(h, MST_OK);
+}
+
+mst_status mst_step_tile_contract(mst_handle h, uint32_t n, uint64_t m, const uint32_t *d_src, const uint32_t *d_dst,
+                                  const uint32_t *d_w, uint32_t tile_vertices, uint32_t *d_parent, uint32_t *d_chosen,
+                                  void *stream) {
+  if (!h || !d_parent || !d_chosen || (m > 0 && (!d_src || !d_dst || !d_w))) return MST_ERR_INVALID_ARG;
+  if (tile_vertices < 32 || tile_vertices > 4096) return record(h, MST_ERR_INVALID_ARG);
+  if (m >= (1ULL << 32)) return record(h, MST_ERR_TOO_LARGE);
+  DeviceGuard g(h->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  const mst_config saved = h->cfg;
+  h->cfg.tile_contract = 1;
+  h->cfg.tile_vertices = tile_vertices;
+  mst_status st;
+  {
+    Solve S(h, s, n, m);
+    st = S.init(d_parent, d_chosen);
+    if (st == MST_OK) {
+      S.src = d_src;
+      S.dst = d_dst;
+      S.w_in = d_w;
+      ListBuf out;
+      uint64_t mo = 0;
+      bool applied = false;
+      st = S.tile_preprocess(d_w, false, out, mo, applied);
+      if (st == MST_OK && cudaStreamSynchronize(s) != cudaSuccess) st = MST_ERR_CUDA;
+    }
+  }
+  h->cfg = saved;
+  return record(h, st);
 }
 
 mst_status mst_step_finalize(mst_handle h, uint64_t m, const uint32_t *d_chosen, const uint32_t *d_w,

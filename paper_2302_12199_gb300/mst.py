@@ -31,7 +31,8 @@ class MstError(RuntimeError):
         super().__init__(f"{where}: {STATUS_NAMES.get(status, status)}")
 
 
-KERNEL_CLASSES = ["min_edges", "relabel_min", "hook", "jump", "dedupe", "pivot", "partition", "filter", "finalize"]
+KERNEL_CLASSES = ["min_edges", "relabel_min", "hook", "jump", "dedupe", "pivot", "partition", "filter", "finalize",
+                  "tile"]
 
 
 class KernelStats(ctypes.Structure):
@@ -67,6 +68,7 @@ _SIGNATURES = {
     "mst_step_partition": (_I, [_P, _U64, _P, _P, _P, _P, _U64, _P, _P, _P, _P, _P, _P]),
     "mst_step_filter": (_I, [_P, _U32, _U64, _P, _P, _P, _P, _U64, _P, _P, _P, _P, _P, _P, _P]),
     "mst_step_finalize": (_I, [_P, _U64, _P, _P, _P, _P, _P, _P]),
+    "mst_step_tile_contract": (_I, [_P, _U32, _U64, _P, _P, _P, _U32, _P, _P, _P]),
     "mst_profile_enable": (_I, [_P, _I]),
     "mst_profile_get": (_I, [_P, _I, ctypes.POINTER(KernelStats)]),
     "mst_pivot_noalloc": (_I, [_U64, _P, _P, _U64, _U32, _P, _P]),
@@ -329,6 +331,14 @@ class Solver:
                "mst_step_filter")
         k = int(cnt.item())
         return ou[:k], ov[:k], ow[:k], oi[:k]
+
+    def tile_contract(self, n, src, dst, w, tile_vertices: int, stream=None):
+        m = self._list(src, dst, w, None)
+        parent = torch.empty(max(n, 1), dtype=torch.int32, device=self.device)
+        chosen = torch.zeros((m + 32) // 32, dtype=torch.int32, device=self.device)
+        _check(self.lib.mst_step_tile_contract(self.h, n, m, _ptr(src), _ptr(dst), _ptr(w), tile_vertices,
+                                               _ptr(parent), _ptr(chosen), _stream(stream)), "mst_step_tile_contract")
+        return parent[:n], chosen
 
     def finalize(self, m, chosen, w, stream=None):
         ids = torch.empty(max(m, 1), dtype=torch.int32, device=self.device)

@@ -17,13 +17,16 @@ from tests.golden import fixtures
 pytestmark = pytest.mark.gpu
 
 CONFIGS = [
-    dict(variant="boruvka", dedupe="none"),
+    dict(variant="boruvka", dedupe="none", tile_contract=0),
     dict(variant="boruvka", dedupe="hash"),
     dict(variant="boruvka", dedupe="auto"),
     dict(variant="filter", dedupe="auto", filter_min_edges=1 << 10, pivot_sample=4096),
-    dict(variant="filter", dedupe="none", filter_min_edges=1 << 12),
+    dict(variant="filter", dedupe="none", filter_min_edges=1 << 12, filter_max_avg_degree=4.0, tile_contract=0),
+    dict(variant="boruvka", tile_contract=1, tile_vertices=512),
+    dict(variant="filter", tile_contract=1, tile_vertices=256, filter_min_edges=1 << 10, pivot_sample=4096),
 ]
-CONFIG_IDS = ["boruvka-none", "boruvka-hash", "boruvka-auto", "filter-auto", "filter-none"]
+CONFIG_IDS = ["boruvka-none", "boruvka-hash", "boruvka-auto", "filter-auto", "filter-deg4", "boruvka-tile",
+              "filter-tile"]
 
 
 @pytest.fixture(scope="module")
@@ -289,3 +292,29 @@ def test_step_finalize(step_solver, dev):
     ids, tot = f.to_host()
     assert np.array_equal(ids, chosen_ids)
     assert tot == int(w[chosen_ids].astype(np.uint64).sum())
+
+
+@pytest.mark.parametrize("case", ["rgg2", "rgg3", "gnm", "dense_tile"])
+def test_step_tile_contract(step_solver, dev, case):
+    g, tile = {
+        "rgg2": lambda: (W.rgg(2, 1 << 15, 8.0, 41), 512),
+        "rgg3": lambda: (W.rgg(3, 1 << 14, 8.0, 42), 2048),
+        "gnm": lambda: (W.gnm(3000, 30000, 43), 256),
+        # one tile holding far more local edges than fit in shared memory
+        "dense_tile": lambda: (W.gnm(4096, 120000, 44), 4096),
+    }[case]()
+    parent, chosen = step_solver.tile_contract(g.n, *list_on_dev(dev, g.src, g.dst, g.w), tile_vertices=tile)
+    label, con = S.local_contract(g.n, g.src, g.dst, g.w, tile)
+    assert np.array_equal(host(parent), label)
+    got = np.nonzero(np.unpackbits(host(chosen).view(np.uint8), bitorder="little"))[0]
+    assert np.array_equal(got, con)
+
+
+def test_tile_contraction_on_and_off_agree(dev):
+    g = W.rgg(2, 1 << 16, 8.0, 45)
+    kid, ktot = oracle.kruskal(g.n, g.src, g.dst, g.w)
+    for tc in (0, 1, -1):
+        s = Solver(0, tile_contract=tc, tile_vertices=1024)
+        ids, tot = gpu_msf(s, g.n, g.src, g.dst, g.w, dev)
+        s.close()
+        assert np.array_equal(ids, kid) and tot == ktot, tc
