@@ -47,6 +47,8 @@ WORKLOADS = {
               dict(variant="boruvka")),
     "rgg3d": ("RGG3D n=2^21 degree 8, w in [1,2^32-1], plain Boruvka", lambda W: W.rgg3d_large(),
               dict(variant="boruvka")),
+    "rgg2d_small": ("RGG2D n=2^20 degree 8, w in [1,2^32-1], plain Boruvka (profiling size)",
+                    lambda W: W.rgg(2, 1 << 20, 8.0), dict(variant="boruvka")),
 }
 
 
@@ -197,6 +199,10 @@ def gpu_main(args, rank: int, world: int, local_rank: int):
         cfg["filter_max_avg_degree"] = args.filter_max_avg_degree
     if args.filter_min_edges is not None:
         cfg["filter_min_edges"] = args.filter_min_edges
+    if args.tile_contract is not None:
+        cfg["tile_contract"] = args.tile_contract
+    if args.tile_vertices is not None:
+        cfg["tile_vertices"] = args.tile_vertices
     g = gen(W)
     n, m = g.n, g.m
     src = torch.from_numpy(g.src.view(np.int32)).to(dev)
@@ -331,6 +337,8 @@ def main():
     ap.add_argument("--dedupe", default=None, choices=["auto", "hash", "none"])
     ap.add_argument("--filter-max-avg-degree", type=float, default=None)
     ap.add_argument("--filter-min-edges", type=int, default=None)
+    ap.add_argument("--tile-contract", type=int, default=None, choices=[-1, 0, 1])
+    ap.add_argument("--tile-vertices", type=int, default=None)
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "gpu":
         args.warmup = 3

@@ -93,6 +93,7 @@ struct CompactArgs {
   uint32_t n;              // vertex count, for validation
   int validate;            // check u, v < n (sets ERR_VERTEX, skips the edge)
   uint32_t *max_w;         // if set: atomicMax of every input weight (key layout)
+  uint32_t *cur_u, *cur_v; // if set: cur_u[id], cur_v[id] = the survivor's written ends
   ScanState st;
 };
 
@@ -102,7 +103,8 @@ struct HookArgs {
   const u64 *ncand_dev;    // candidate count in device memory, or nullptr
   u64 *best;               // keys (see KeyLayout) of the round's minimum edges
   KeyLayout kl;
-  const uint32_t *src, *dst;  // input endpoints, indexed by edge id (unpacked keys)
+  const uint32_t *src, *dst;  // ends of each edge by id (unpacked keys): the input arrays,
+                              // or the ends recorded when the current list was written
   uint32_t *parent;
   uint32_t *chosen_bits;   // bitmap over edge ids
   uint32_t *active_out;    // active vertices (best != INF), unspecified order

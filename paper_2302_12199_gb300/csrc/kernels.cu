@@ -408,6 +408,12 @@ __device__ __forceinline__ void emit_survivors(const CompactArgs &a, uint32_t ke
     a.out.w[obase + i] = s_w[i];
     a.out.id[obase + i] = s_id[i];
   }
+  if (a.cur_u) {  // ends by id, for the hook of the round that relaxes this list
+    for (uint32_t i = threadIdx.x; i < total; i += BLOCK) {
+      a.cur_u[s_id[i]] = s_u[i];
+      a.cur_v[s_id[i]] = s_v[i];
+    }
+  }
   // post actions read the survivors back from shared memory (coalesced; the
   // loaded edges' registers are dead by now)
   if (a.best) {
@@ -1142,6 +1148,19 @@ __global__ void __launch_bounds__(PSEL_THREADS) pivot_coop_kernel(EdgeList in, u
 // paper's PEs: vertex x belongs to tile x / B; an edge is local when both ends
 // are in one tile, a cut edge otherwise.
 
+// Runs of equal keys among the lanes of a warp (key 0xffffffff = no item):
+// returns the lane mask of this lane's run and the run's first lane.  Inputs
+// grouped by tile give long runs, so one atomic per run serves the whole run.
+__device__ __forceinline__ uint32_t warp_run(uint32_t key, int &head_lane) {
+  const int lane = threadIdx.x & 31;
+  const uint32_t prev = __shfl_up_sync(0xffffffffu, key, 1);
+  const uint32_t heads = __ballot_sync(0xffffffffu, lane == 0 || prev != key);
+  head_lane = 31 - __clz(heads & (0xffffffffu >> (31 - lane)));   // last head at or below this lane
+  const uint32_t above = heads & ~(0xffffffffu >> (31 - lane));    // heads above this lane
+  const int next = above ? __ffs(above) - 1 : 32;
+  return (next >= 32 ? 0xffffffffu : ((1u << next) - 1u)) & ~((1u << head_lane) - 1u);
+}
+
 // Pass over the input: vertex-range check, per-vertex minimum key over incident
 // cut edges (cutmin), number of local edges per tile, total local edges, and
 // the largest weight (key layout).  Local-edge counts are aggregated per warp.
@@ -1178,8 +1197,9 @@ __global__ void __launch_bounds__(BLOCK) tile_count_kernel(EdgeList in, uint64_t
       ok = ok && eu[k] != ev[k];
       const uint32_t tu = eu[k] / B, tv = ev[k] / B;
       const bool local = ok && tu == tv;
-      const uint32_t peers = __match_any_sync(0xffffffffu, local ? tu : 0xffffffffu);
-      if (local && (threadIdx.x & 31) == (unsigned)(__ffs(peers) - 1)) atomicAdd(count + tu, (uint32_t)__popc(peers));
+      int head;
+      const uint32_t run = warp_run(local ? tu : 0xffffffffu, head);
+      if (local && (threadIdx.x & 31) == (unsigned)head) atomicAdd(count + tu, (uint32_t)__popc(run));
       nlocal += local ? 1u : 0u;
       if (ok && !local) {
         const u64 key = edge_key(ew[k], (uint32_t)j);
@@ -1266,13 +1286,13 @@ __global__ void __launch_bounds__(BLOCK) tile_scatter_kernel(EdgeList in, uint64
       const bool ok = j < m && eu[k] < n && ev[k] < n && eu[k] != ev[k];
       const uint32_t tu = eu[k] / B, tv = ev[k] / B;
       const bool local = ok && tu == tv;
-      const uint32_t peers = __match_any_sync(0xffffffffu, local ? tu : 0xffffffffu);
-      const int leader = __ffs(peers) - 1;
+      int head;
+      const uint32_t run = warp_run(local ? tu : 0xffffffffu, head);
       uint32_t pos = 0;
-      if (local && (threadIdx.x & 31) == (unsigned)leader) pos = atomicAdd(fill + tu, (uint32_t)__popc(peers));
-      pos = __shfl_sync(0xffffffffu, pos, leader);
+      if (local && (threadIdx.x & 31) == (unsigned)head) pos = atomicAdd(fill + tu, (uint32_t)__popc(run));
+      pos = __shfl_sync(0xffffffffu, pos, head);
       if (local) {
-        const u64 at = offsets[tu] + pos + __popc(peers & ((1u << (threadIdx.x & 31)) - 1u));
+        const u64 at = offsets[tu] + pos + ((threadIdx.x & 31) - (uint32_t)head);
         b_ends[at] = (eu[k] - tu * B) | ((ev[k] - tu * B) << 16);
         b_w[at] = ew[k];
         b_id[at] = (uint32_t)j;
@@ -1303,33 +1323,38 @@ __global__ void __launch_bounds__(TC_THREADS) tile_contract_kernel(uint32_t n, u
   uint32_t *hook = lab + B;                                        // [B]
   uint32_t *other = hook + B;                                      // [B]
   uint32_t *sends = other + B;                                     // [edge_cap]
-  __shared__ uint32_t s_any;
+  __shared__ uint32_t s_any, s_ne, s_warp[TC_THREADS / 32 + 1];
 
   const uint32_t t = blockIdx.x;
   const uint64_t vbase = (uint64_t)t * B;
   const uint32_t nv = (uint32_t)min((uint64_t)B, (uint64_t)n - vbase);
   const u64 e0 = offsets[t];
-  const uint32_t ne = (uint32_t)(offsets[t + 1] - e0);
-  const bool in_smem = ne <= edge_cap;
+  const uint32_t ne0 = (uint32_t)(offsets[t + 1] - e0);
+  // In shared memory the edges hold their current component labels and are
+  // compacted after every round (edges inside a component are dropped); from
+  // global memory they are read as input ends and mapped through lab[].
+  const bool in_smem = ne0 <= edge_cap;
   for (uint32_t x = threadIdx.x; x < nv; x += TC_THREADS) {
     lab[x] = x;
     comp[x] = cutmin[vbase + x];
   }
   if (in_smem) {
-    for (uint32_t e = threadIdx.x; e < ne; e += TC_THREADS) {
+    for (uint32_t e = threadIdx.x; e < ne0; e += TC_THREADS) {
       sends[e] = b_ends[e0 + e];
       skey[e] = edge_key(b_w[e0 + e], b_id[e0 + e]);
     }
   }
+  if (threadIdx.x == 0) s_ne = ne0;
   __syncthreads();
   for (uint32_t round = 0; round <= nv; ++round) {
+    const uint32_t ne = s_ne;
     for (uint32_t c = threadIdx.x; c < nv; c += TC_THREADS) best[c] = KEY_INF;
     if (threadIdx.x == 0) s_any = 0;
     __syncthreads();
     for (uint32_t e = threadIdx.x; e < ne; e += TC_THREADS) {  // lightest local edge per component
       const uint32_t pe = in_smem ? sends[e] : b_ends[e0 + e];
       const u64 k = in_smem ? skey[e] : edge_key(b_w[e0 + e], b_id[e0 + e]);
-      const uint32_t a = lab[pe & 0xffffu], b = lab[pe >> 16];
+      const uint32_t a = in_smem ? (pe & 0xffffu) : lab[pe & 0xffffu], b = in_smem ? (pe >> 16) : lab[pe >> 16];
       if (a != b) {
         atomicMin(best + a, k);
         atomicMin(best + b, k);
@@ -1342,7 +1367,7 @@ __global__ void __launch_bounds__(TC_THREADS) tile_contract_kernel(uint32_t n, u
     for (uint32_t e = threadIdx.x; e < ne; e += TC_THREADS) {  // far end of each hooking component's edge
       const uint32_t pe = in_smem ? sends[e] : b_ends[e0 + e];
       const u64 k = in_smem ? skey[e] : edge_key(b_w[e0 + e], b_id[e0 + e]);
-      const uint32_t a = lab[pe & 0xffffu], b = lab[pe >> 16];
+      const uint32_t a = in_smem ? (pe & 0xffffu) : lab[pe & 0xffffu], b = in_smem ? (pe >> 16) : lab[pe >> 16];
       if (a != b) {
         if (best[a] == k) other[a] = b;
         if (best[b] == k) other[b] = a;
@@ -1386,6 +1411,44 @@ __global__ void __launch_bounds__(TC_THREADS) tile_contract_kernel(uint32_t n, u
       if (lab[c] == c && hook[c] != c) atomicMin(comp + hook[c], comp[c]);
     __syncthreads();
     for (uint32_t x = threadIdx.x; x < nv; x += TC_THREADS) lab[x] = hook[lab[x]];
+    if (in_smem) {  // relabel the edges to the new roots and keep those between components
+      uint32_t out = 0;
+      for (uint32_t base = 0; base < ne; base += TC_THREADS) {
+        const uint32_t e = base + threadIdx.x;
+        uint32_t pe = 0;
+        u64 k = 0;
+        bool keep = false;
+        if (e < ne) {
+          pe = sends[e];
+          k = skey[e];
+          const uint32_t a = hook[pe & 0xffffu], b = hook[pe >> 16];
+          pe = a | (b << 16);
+          keep = a != b;
+        }
+        const uint32_t bal = __ballot_sync(0xffffffffu, keep);
+        const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+        if (lane == 0) s_warp[wid] = __popc(bal);
+        __syncthreads();  // every thread has read its edge of this chunk
+        if (threadIdx.x == 0) {
+          uint32_t acc = 0;
+          for (int i = 0; i < TC_THREADS / 32; ++i) {
+            const uint32_t c = s_warp[i];
+            s_warp[i] = acc;
+            acc += c;
+          }
+          s_warp[TC_THREADS / 32] = acc;
+        }
+        __syncthreads();
+        if (keep) {
+          const uint32_t pos = out + s_warp[wid] + __popc(bal & ((1u << lane) - 1u));
+          sends[pos] = pe;
+          skey[pos] = k;
+        }
+        out += s_warp[TC_THREADS / 32];
+        __syncthreads();
+      }
+      if (threadIdx.x == 0) s_ne = out;
+    }
     __syncthreads();
   }
   for (uint32_t x = threadIdx.x; x < nv; x += TC_THREADS) parent[vbase + x] = (uint32_t)(vbase + lab[x]);
@@ -1693,15 +1756,19 @@ void launch_tile_scatter(EdgeList in, uint64_t m, uint32_t n, uint32_t B, const 
 bool launch_tile_contract(uint32_t n, uint32_t B, const u64 *cutmin, const u64 *offsets, const uint32_t *b_ends,
                           const uint32_t *b_w, const uint32_t *b_id, uint32_t *parent, uint32_t *bits, uint32_t *err,
                           cudaStream_t s) {
-  static int smem_max = 0;
-  if (!smem_max) {
-    int dev = 0;
+  static int smem_full = 0, smem_half = 0;
+  if (!smem_full) {
+    int dev = 0, optin = 0, per_sm = 0;
     cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-    smem_max -= 2048;  // static shared memory and slack
-    cudaFuncSetAttribute(tile_contract_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_max);
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+    smem_full = optin - 2048;  // static shared memory and slack
+    smem_half = min(optin, per_sm / 2) - 2048;
+    cudaFuncSetAttribute(tile_contract_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_full);
   }
   const size_t vbytes = (size_t)B * (8 + 8 + 4 + 4 + 4);
+  // two tiles per SM when the vertex arrays leave room for edges, else one
+  const int smem_max = vbytes + 12 * 2048 <= (size_t)smem_half ? smem_half : smem_full;
   if ((size_t)smem_max <= vbytes) return false;
   const uint32_t cap = (uint32_t)(((size_t)smem_max - vbytes) / 12);
   const size_t bytes = vbytes + (size_t)cap * 12;

@@ -278,6 +278,22 @@ struct Solve {
   const uint32_t *w_in = nullptr;                 // input weights
   KeyLayout kl{0, 0, 0};  // unpacked unless choose_layout() packs
   bool layout_set = false;
+  // unpacked keys: ends of each edge by id as written with the current list
+  Buf cur_b;
+  uint32_t *cur_u = nullptr, *cur_v = nullptr;
+  mst_status cur_alloc() {
+    if (kl.packed || cur_u) return MST_OK;
+    const uint64_t stride = round_up(m * 4 + 16, 256);
+    TRY(cur_b.alloc(c, stride * 2, s));
+    cur_u = cur_b.as<uint32_t>();
+    cur_v = (uint32_t *)((char *)cur_b.p + stride);
+    return MST_OK;
+  }
+  // Sets the recording of ends by id on a pass that writes a list (unpacked keys).
+  void record_ends(CompactArgs &a) const {
+    a.cur_u = (layout_set && !kl.packed) ? cur_u : nullptr;
+    a.cur_v = (layout_set && !kl.packed) ? cur_v : nullptr;
+  }
   u64 *best = nullptr;
   uint32_t *parent = nullptr, *act[2] = {nullptr, nullptr}, *bits = nullptr;
   int rounds = 0;
@@ -320,7 +336,7 @@ struct Solve {
     launch_max_weight(w, m, &c->ds->max_w, c->sms, s);
     TRY(readback(c, s));
     set_layout();
-    return MST_OK;
+    return cur_alloc();
   }
   // From the largest weight in hs->max_w (read back by the caller).
   void set_layout() {
@@ -365,7 +381,9 @@ struct Solve {
   // current component roots; merged roots get their new root in parent[].
   // best_ready: best[] already holds this list's minEdges (relaxed by the pass
   // that wrote the list).
-  mst_status boruvka(EdgeList E, uint64_t mE, bool validate, bool best_ready = false) {
+  // ends_rec: cur_u/cur_v hold E's ends by id (written with E); otherwise the
+  // hook of the first round walks from the input ends.
+  mst_status boruvka(EdgeList E, uint64_t mE, bool validate, bool best_ready = false, bool ends_rec = false) {
     if (mE == 0) return MST_OK;
     if (!layout_set) TRY(choose_layout(w_in ? w_in : E.w));
     // round 0: minEdges straight from the stored list, then hook and jump
@@ -378,8 +396,9 @@ struct Solve {
     ha.ncand = n;
     ha.best = best;
     ha.kl = kl;
-    ha.src = src;
-    ha.dst = dst;
+    const bool rec = ends_rec && cur_u;  // ends recorded with the list, or walk from the input
+    ha.src = rec ? cur_u : src;
+    ha.dst = rec ? cur_v : dst;
     ha.parent = parent;
     ha.chosen_bits = bits;
     ha.active_out = act[0];
@@ -411,6 +430,7 @@ struct Solve {
       const double in_bytes = (cur.id ? 16.0 : 12.0) * (double)cur_m;
       if (!want_dedupe(r, cur_m)) {
         ca.best = best;
+        record_ends(ca);
         ca.st = next_scan(c, CNT_EDGES);
         PROF(MST_K_RELABEL_MIN, in_bytes, CNT_EDGES, 16.0, -1, 0.0, launch_compact(CM_RELABEL, ca, cur_m, s));
       } else {
@@ -435,6 +455,7 @@ struct Solve {
         cd.tmask = ca.tmask;
         cd.best = best;
         cd.kl = kl;
+        record_ends(cd);
         cd.n = n;
         cd.st = next_scan(c, CNT_EDGES);
         PROF(MST_K_DEDUPE, 0.0, CNT_TMP, 16.0, CNT_EDGES, 16.0, launch_compact(CM_DEDUPE, cd, cur_m, s));
@@ -444,8 +465,8 @@ struct Solve {
       hb.ncand = n_act;
       hb.best = best;
       hb.kl = kl;
-      hb.src = src;
-      hb.dst = dst;
+      hb.src = cur_u ? cur_u : src;
+      hb.dst = cur_v ? cur_v : dst;
       hb.parent = parent;
       hb.chosen_bits = bits;
       hb.active_out = act[1 - a];
@@ -497,6 +518,7 @@ struct Solve {
                            &c->ds->max_w, &c->ds->err, c->sms, s));
     TRY(readback(c, s));
     if (!layout_set) set_layout();
+    TRY(cur_alloc());
     const uint64_t nlocal = c->hs->count[CNT_AUX];
     if (c->cfg.tile_contract < 0 && nlocal * 10 < m) return MST_OK;
     PROF(MST_K_TILE, 12.0 * (double)ntiles, -1, 0.0, -1, 0.0, launch_tile_scan(cnt_b.as<uint32_t>(), ntiles, off_b.as<u64>(), s));
@@ -522,6 +544,7 @@ struct Solve {
     ca.n = n;
     ca.kl = kl;
     ca.best = relax ? best : nullptr;
+    record_ends(ca);
     ca.st = next_scan(c, CNT_EDGES);
     PROF(MST_K_RELABEL_MIN, 12.0 * (double)m, CNT_EDGES, 16.0, -1, 0.0, launch_compact(CM_RELABEL, ca, m, s));
     TRY(readback(c, s));
@@ -553,8 +576,9 @@ struct Solve {
   }
 
   // Rec-Filter-MST (Alg. 2).  best_ready: best[] holds E's minEdges already.
-  mst_status filter(EdgeList E, uint64_t mE, bool is_input, int depth, bool best_ready = false) {
-    if (is_sparse(mE) || depth >= 40) return boruvka(E, mE, is_input, best_ready);
+  mst_status filter(EdgeList E, uint64_t mE, bool is_input, int depth, bool best_ready = false,
+                    bool ends_rec = false) {
+    if (is_sparse(mE) || depth >= 40) return boruvka(E, mE, is_input, best_ready, ends_rec);
     if (best_ready) TRY(reset_best());
     const u64 state = host_splitmix64_at(c->cfg.seed, c->pivot_counter++);
     PROF(MST_K_PIVOT, 16.0 * (double)c->cfg.pivot_sample, -1, 0.0, -1, 0.0,
@@ -583,19 +607,23 @@ struct Solve {
     }
     cp.best = fuse_light ? best : nullptr;
     cp.kl = kl;
+    record_ends(cp);
     cp.st = next_scan(c, CNT_EDGES);
     TRY(zero_counters(c, s));
     PROF(MST_K_PARTITION, in_bytes, CNT_EDGES, 16.0, -1, 0.0, launch_compact(CM_PARTITION, cp, mE, s));
     TRY(readback(c, s));
-    if (cp.max_w && is_input) set_layout();
+    if (cp.max_w && is_input) {
+      set_layout();
+      TRY(cur_alloc());
+    }
     const uint64_t mL = c->hs->count[CNT_EDGES];
     const u64 pivot = c->hs->pivot;
     if (mL == 0 || mL == mE) {  // no progress from this pivot: solve the list directly
       L.mem.release();
       if (fuse_light) TRY(reset_best());
-      return boruvka(E, mE, is_input);
+      return boruvka(E, mE, is_input, false, ends_rec);
     }
-    TRY(filter(L.list(), mL, false, depth + 1, fuse_light));
+    TRY(filter(L.list(), mL, false, depth + 1, fuse_light, cp.cur_u != nullptr));
     L.mem.release();
     TRY(compress_all());
     Buf giant_b;
@@ -612,13 +640,14 @@ struct Solve {
     cf.n = n;
     cf.best = best;  // the survivors are expected to be sparse (Theorem 1)
     cf.kl = kl;
+    record_ends(cf);
     cf.st = next_scan(c, CNT_EDGES);
     TRY(zero_counters(c, s));
     PROF(MST_K_FILTER, in_bytes, CNT_EDGES, 16.0, -1, 0.0, launch_compact(CM_FILTER, cf, mE, s));
     TRY(readback(c, s));
     giant_b.release();
     const uint64_t mH = c->hs->count[CNT_EDGES];
-    return filter(H.list(), mH, false, depth + 1, true);
+    return filter(H.list(), mH, false, depth + 1, true, cf.cur_u != nullptr);
   }
 
   mst_status finalize(const uint32_t *w, uint32_t *out_ids, uint32_t *out_count, u64 *total_weight) {
@@ -662,9 +691,9 @@ mst_status solve_device(mst_ctx *c, uint32_t n, uint64_t m, const uint32_t *src,
   TRY(S.tile_preprocess(w, !filt, local, m_local, applied));
   if (applied) {  // continue on the contracted graph (ids already validated)
     if (filt)
-      TRY(S.filter(local.list(), m_local, false, 0));
+      TRY(S.filter(local.list(), m_local, false, 0, false, true));
     else
-      TRY(S.boruvka(local.list(), m_local, false, true));
+      TRY(S.boruvka(local.list(), m_local, false, true, true));
   } else if (filt) {
     TRY(S.filter(in, m, true, 0));
   } else {
@@ -778,7 +807,7 @@ void mst_config_default(mst_config *cfg) {
   cfg->variant = MST_VARIANT_BORUVKA;
   cfg->dedupe = MST_DEDUPE_AUTO;
   cfg->tile_contract = -1;
-  cfg->tile_vertices = 2048;
+  cfg->tile_vertices = 1024;
   cfg->pivot_sample = 1u << 16;
   cfg->seed = 0x2302121990ULL;
   cfg->filter_min_edges = 1ULL << 20;

@@ -197,10 +197,11 @@ void gen_rmat(int scale, uint64_t n, uint64_t m, double a, double b, double c, i
 /* ---------------------------------------------------------------------- RGG */
 
 /* Points uniform in [0,1)^dim with f32 coordinates (24 random mantissa bits).
- * Vertices are numbered in grid-cell order (cells of side >= r, row-major),
- * which gives ids the spatial locality of KaGen's partition.  Every pair at
- * Euclidean distance < r becomes one undirected edge (u < v), emitted in
- * ascending u.  Returns the number of edges; with src == NULL only counts. */
+ * Vertices are numbered cell by cell (cells of side >= r), the cells taken in
+ * Morton (Z) order, so that a range of consecutive ids covers a compact square
+ * (cube) of the domain, like the spatial partition KaGen gives each PE.  Every
+ * pair at Euclidean distance < r becomes one undirected edge (u < v), emitted
+ * in ascending u.  Returns the number of edges; with src == NULL only counts. */
 static float coord(uint64_t s, uint64_t i) { return (float)((double)(sm_at(s, i) >> 40) * (1.0 / 16777216.0)); }
 
 typedef struct {
@@ -208,7 +209,8 @@ typedef struct {
   uint64_t n, G, ncell;
   double r2;
   float *x, *y, *z;      /* by new id */
-  uint64_t *cell_start;  /* ncell + 1 */
+  uint64_t *cell_start;  /* [ncell] first new id of each (row-major) cell */
+  uint64_t *cell_end;    /* [ncell] one past its last */
 } rgg_t;
 
 static uint64_t cell_of(const rgg_t *g, double x, double y, double z) {
@@ -220,6 +222,26 @@ static uint64_t cell_of(const rgg_t *g, double x, double y, double z) {
     if (cz >= g->G) cz = g->G - 1;
   }
   return (cz * g->G + cy) * g->G + cx;
+}
+
+/* Morton code: bit b of coordinate k goes to bit b*dim + k. */
+static uint64_t morton(uint64_t cx, uint64_t cy, uint64_t cz, int dim) {
+  uint64_t code = 0;
+  for (int b = 0; b < 21; ++b) {
+    code |= ((cx >> b) & 1ULL) << (b * dim);
+    code |= ((cy >> b) & 1ULL) << (b * dim + 1);
+    if (dim == 3) code |= ((cz >> b) & 1ULL) << (b * dim + 2);
+  }
+  return code;
+}
+
+typedef struct {
+  uint64_t code, cell;
+} cell_key_t;
+
+static int cmp_cell_key(const void *a, const void *b) {
+  const cell_key_t *x = (const cell_key_t *)a, *y = (const cell_key_t *)b;
+  return x->code < y->code ? -1 : (x->code > y->code ? 1 : 0);
 }
 
 static int rgg_build(rgg_t *g, int dim, uint64_t n, double r, uint64_t seed) {
@@ -236,7 +258,9 @@ static int rgg_build(rgg_t *g, int dim, uint64_t n, double r, uint64_t seed) {
   float *x0 = (float *)malloc(n * sizeof(float)), *y0 = (float *)malloc(n * sizeof(float));
   float *z0 = dim == 3 ? (float *)malloc(n * sizeof(float)) : NULL;
   uint64_t *cell = (uint64_t *)malloc(n * sizeof(uint64_t));
-  g->cell_start = (uint64_t *)calloc(g->ncell + 1, sizeof(uint64_t));
+  uint64_t *cnt = (uint64_t *)calloc(g->ncell, sizeof(uint64_t));
+  g->cell_start = (uint64_t *)malloc(g->ncell * sizeof(uint64_t));
+  g->cell_end = (uint64_t *)malloc(g->ncell * sizeof(uint64_t));
   g->x = (float *)malloc(n * sizeof(float));
   g->y = (float *)malloc(n * sizeof(float));
   g->z = dim == 3 ? (float *)malloc(n * sizeof(float)) : NULL;
@@ -245,18 +269,33 @@ static int rgg_build(rgg_t *g, int dim, uint64_t n, double r, uint64_t seed) {
     y0[i] = coord(sy, i);
     if (dim == 3) z0[i] = coord(sz, i);
     cell[i] = cell_of(g, x0[i], y0[i], dim == 3 ? z0[i] : 0.0);
-    g->cell_start[cell[i] + 1]++;
+    cnt[cell[i]]++;
   }
-  for (uint64_t c = 0; c < g->ncell; ++c) g->cell_start[c + 1] += g->cell_start[c];
+  /* cells in Morton order; each cell's points get a contiguous id range */
+  cell_key_t *keys = (cell_key_t *)malloc(g->ncell * sizeof(cell_key_t));
+  for (uint64_t c = 0; c < g->ncell; ++c) {
+    keys[c].code = morton(c % G, (c / G) % G, c / (G * G), dim);
+    keys[c].cell = c;
+  }
+  qsort(keys, g->ncell, sizeof(cell_key_t), cmp_cell_key);
+  uint64_t next = 0;
+  for (uint64_t k = 0; k < g->ncell; ++k) {
+    const uint64_t c = keys[k].cell;
+    g->cell_start[c] = next;
+    next += cnt[c];
+    g->cell_end[c] = next;
+  }
+  free(keys);
   uint64_t *fill = (uint64_t *)malloc(g->ncell * sizeof(uint64_t));
   memcpy(fill, g->cell_start, g->ncell * sizeof(uint64_t));
-  for (uint64_t i = 0; i < n; ++i) { /* stable counting sort by cell */
+  for (uint64_t i = 0; i < n; ++i) { /* stable within each cell */
     uint64_t id = fill[cell[i]]++;
     g->x[id] = x0[i];
     g->y[id] = y0[i];
     if (dim == 3) g->z[id] = z0[i];
   }
   free(fill);
+  free(cnt);
   free(cell);
   free(x0);
   free(y0);
@@ -269,6 +308,7 @@ static void rgg_free(rgg_t *g) {
   free(g->y);
   free(g->z);
   free(g->cell_start);
+  free(g->cell_end);
 }
 
 static uint64_t rgg_edges(const rgg_t *g, uint32_t *src, uint32_t *dst) {
@@ -284,7 +324,7 @@ static uint64_t rgg_edges(const rgg_t *g, uint32_t *src, uint32_t *dst) {
           int64_t nx = cx + dx, ny = cy + dy, nz = cz + dz;
           if (nx < 0 || ny < 0 || nz < 0 || nx >= (int64_t)G || ny >= (int64_t)G || nz >= (int64_t)G) continue;
           uint64_t nc = ((uint64_t)nz * G + (uint64_t)ny) * G + (uint64_t)nx;
-          for (uint64_t q = g->cell_start[nc]; q < g->cell_start[nc + 1]; ++q) {
+          for (uint64_t q = g->cell_start[nc]; q < g->cell_end[nc]; ++q) {
             if (q <= p) continue;
             double ddx = px - (double)g->x[q], ddy = py - (double)g->y[q];
             double d2 = ddx * ddx + ddy * ddy;
