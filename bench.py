@@ -42,6 +42,8 @@ WORKLOADS = {
                      lambda W: W.rmat_large(), dict(variant="boruvka")),
     "rmat20_filter": ("RMAT n=2^20 m=2^24 (0.57,0.19,0.19,0.05) permuted, w in [1,255], Filter-Boruvka (profiling size)",
                       lambda W: W.rmat_large(scale=20, m=1 << 24), dict(variant="filter")),
+    "rmat22_filter": ("RMAT n=2^22 m=2^26 (0.57,0.19,0.19,0.05) permuted, w in [1,255], Filter-Boruvka (profiling size)",
+                      lambda W: W.rmat_large(scale=22, m=1 << 26), dict(variant="filter")),
     "gnm": ("GNM n=2^16 m=2^20, w in [1,255], plain Boruvka", lambda W: W.gnm_small(), dict(variant="boruvka")),
     "rgg2d": ("RGG2D n=2^22 degree 8, w in [1,2^32-1], plain Boruvka", lambda W: W.rgg2d_large(),
               dict(variant="boruvka")),

@@ -56,8 +56,10 @@ typedef struct {
   int device;                  /* CUDA device ordinal */
   int variant;                 /* MST_VARIANT_*: Borůvka (Alg. 1 rounds) or Filter-Borůvka (Alg. 2) */
   int dedupe;                  /* MST_DEDUPE_*: parallel-edge removal between rounds (Section 2.3, optional) */
-  int tile_contract;           /* -1 auto (when >= 10% of sampled edges are local), 0 off, 1 on: local
-                                  contraction on vertex-range tiles before the rounds (Section 4.1) */
+  int tile_contract;           /* 0 off (default), 1 on, -1 auto (on when >= 10% of sampled edges are
+                                  local): local contraction on vertex-range tiles before the rounds
+                                  (Section 4.1).  Off by default: on one GPU its passes cost more than
+                                  the global rounds they save, even on geometric graphs */
   uint32_t tile_vertices;      /* vertices per tile for local contraction, 32..4096 */
   uint32_t pivot_sample;       /* edges sampled per pivot selection (Alg. 2 PivotSelection) */
   uint64_t seed;               /* seed of the pivot sampling stream */

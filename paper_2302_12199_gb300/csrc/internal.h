@@ -29,7 +29,7 @@ struct DevState {
   uint32_t local_samples;  // sampled local edges (automatic tile contraction)
   uint32_t pad;
 };
-enum { CNT_EDGES = 0, CNT_ACTIVE = 1, CNT_TMP = 2, CNT_AUX = 3, CNT_USER = 4 };
+enum { CNT_EDGES = 0, CNT_ACTIVE = 1, CNT_TMP = 2, CNT_AUX = 3, CNT_USER = 4, CNT_CUT = 5 };
 
 // Output bookkeeping of a compaction launch.  Unordered compactions claim
 // their output ranges by atomic adds on *total (zero before the launch); the
@@ -140,10 +140,11 @@ void launch_tile_count(EdgeList in, uint64_t m, uint32_t n, uint32_t B, u64 *cut
                        u64 *local_total, uint32_t *max_w, uint32_t *err, int sms, cudaStream_t s);
 void launch_tile_scan(const uint32_t *count, uint32_t ntiles, u64 *offsets, cudaStream_t s);
 void launch_tile_scatter(EdgeList in, uint64_t m, uint32_t n, uint32_t B, const u64 *offsets, uint32_t *fill,
-                         uint32_t *b_ends, uint32_t *b_w, uint32_t *b_id, int sms, cudaStream_t s);
-bool launch_tile_contract(uint32_t n, uint32_t B, const u64 *cutmin, const u64 *offsets, const uint32_t *b_ends,
-                          const uint32_t *b_w, const uint32_t *b_id, uint32_t *parent, uint32_t *bits, uint32_t *err,
-                          cudaStream_t s);
+                         uint32_t *b_ends, uint32_t *b_w, uint32_t *b_id, EdgeOut cut, u64 *cut_fill, int sms,
+                         cudaStream_t s);
+bool launch_tile_contract(uint32_t n, uint32_t B, uint64_t nlocal, const u64 *cutmin, const u64 *offsets,
+                          const uint32_t *b_ends, const uint32_t *b_w, const uint32_t *b_id, uint32_t *parent,
+                          uint32_t *bits, EdgeOut rest, u64 *rest_fill, uint32_t *err, cudaStream_t s);
 void launch_tile_sample(EdgeList in, uint64_t m, uint32_t n, uint32_t B, u64 state, uint32_t samples,
                         uint32_t *local_count, cudaStream_t s);
 void launch_iota(uint32_t *p, uint64_t n, int sms, cudaStream_t s);

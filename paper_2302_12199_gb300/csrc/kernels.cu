@@ -1259,10 +1259,15 @@ __global__ void __launch_bounds__(1024) tile_scan_kernel(const uint32_t *count, 
 }
 
 // Scatters the local edges into per-tile buckets: packed tile-local ends
-// (u | v << 16), weight and id.  Order inside a bucket is unspecified.
+// (u | v << 16), weight and id.  Order inside a bucket is unspecified.  The
+// cut edges (ends in different tiles) go to an edge list with their input ids,
+// in unspecified order; *cut_fill counts them (zero before the launch).
 __global__ void __launch_bounds__(BLOCK) tile_scatter_kernel(EdgeList in, uint64_t m, uint32_t n, uint32_t B,
                                                              const u64 *offsets, uint32_t *fill, uint32_t *b_ends,
-                                                             uint32_t *b_w, uint32_t *b_id) {
+                                                             uint32_t *b_w, uint32_t *b_id, EdgeOut cut,
+                                                             u64 *cut_fill) {
+  __shared__ uint32_t s_warp[BLOCK / 32 + 1];
+  __shared__ u64 s_base;
   const uint64_t ntiles = (m + TILE - 1) / TILE;
   for (uint64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     const uint64_t tb = tile * TILE;
@@ -1280,12 +1285,14 @@ __global__ void __launch_bounds__(BLOCK) tile_scatter_kernel(EdgeList in, uint64
         ew[k] = j < m ? __ldg(in.w + j) : 0u;
       }
     }
+    uint32_t is_cut = 0;
 #pragma unroll
     for (int k = 0; k < ITEMS; ++k) {
       const uint64_t j = tb + item_off(k);
       const bool ok = j < m && eu[k] < n && ev[k] < n && eu[k] != ev[k];
       const uint32_t tu = eu[k] / B, tv = ev[k] / B;
       const bool local = ok && tu == tv;
+      if (ok && !local) is_cut |= 1u << k;
       int head;
       const uint32_t run = warp_run(local ? tu : 0xffffffffu, head);
       uint32_t pos = 0;
@@ -1298,6 +1305,23 @@ __global__ void __launch_bounds__(BLOCK) tile_scatter_kernel(EdgeList in, uint64
         b_id[at] = (uint32_t)j;
       }
     }
+    // one claim per tile for its cut edges
+    uint32_t total;
+    uint32_t at = block_exclusive_scan((uint32_t)__popc(is_cut), total, s_warp);
+    if (threadIdx.x == 0) s_base = total ? atomicAdd(cut_fill, (u64)total) : 0;
+    __syncthreads();
+    const u64 base = s_base;
+#pragma unroll
+    for (int k = 0; k < ITEMS; ++k) {
+      if (is_cut >> k & 1u) {
+        cut.u[base + at] = eu[k];
+        cut.v[base + at] = ev[k];
+        cut.w[base + at] = ew[k];
+        cut.id[base + at] = (uint32_t)(tb + item_off(k));
+        ++at;
+      }
+    }
+    __syncthreads();  // s_base and s_warp are reused by the next tile
   }
 }
 
@@ -1310,12 +1334,41 @@ __global__ void __launch_bounds__(BLOCK) tile_scatter_kernel(EdgeList in, uint64
 // of the contracted edges.  A tile whose edges exceed the shared-memory
 // capacity runs the same rounds reading its bucket from global memory.
 constexpr int TC_THREADS = 512;
+constexpr int TC_EPT = 16;  // edges per thread in the in-place compaction (capacity TC_EPT * TC_THREADS)
+
+__device__ __forceinline__ uint32_t tc_exclusive_scan(uint32_t x, uint32_t &total, uint32_t *s_warp) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  uint32_t incl = x;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += y;
+  }
+  if (lane == 31) s_warp[wid] = incl;
+  __syncthreads();
+  if (wid == 0) {
+    const uint32_t wv = lane < TC_THREADS / 32 ? s_warp[lane] : 0u;
+    uint32_t wi = wv;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, wi, o);
+      if (lane >= o) wi += y;
+    }
+    if (lane < TC_THREADS / 32) s_warp[lane] = wi - wv;
+    if (lane == TC_THREADS / 32 - 1) s_warp[TC_THREADS / 32] = wi;
+  }
+  __syncthreads();
+  total = s_warp[TC_THREADS / 32];
+  return s_warp[wid] + incl - x;
+}
+
 __global__ void __launch_bounds__(TC_THREADS) tile_contract_kernel(uint32_t n, uint32_t B, const u64 *cutmin,
                                                                     const u64 *offsets, const uint32_t *b_ends,
                                                                     const uint32_t *b_w, const uint32_t *b_id,
                                                                     uint32_t edge_cap, uint32_t *parent,
-                                                                    uint32_t *bits, uint32_t *err) {
-  extern __shared__ __align__(16) unsigned char smem_dyn[];
+                                                                    uint32_t *bits, EdgeOut rest, u64 *rest_fill,
+                                                                    uint32_t *err) {
+  extern __shared__ __align__(128) unsigned char smem_dyn[];
   u64 *best = reinterpret_cast<u64 *>(smem_dyn);  // [B]
   u64 *comp = best + B;                           // [B] component cut minimum (valid at roots)
   u64 *skey = comp + B;                           // [edge_cap]
@@ -1324,15 +1377,16 @@ __global__ void __launch_bounds__(TC_THREADS) tile_contract_kernel(uint32_t n, u
   uint32_t *other = hook + B;                                      // [B]
   uint32_t *sends = other + B;                                     // [edge_cap]
   __shared__ uint32_t s_any, s_ne, s_warp[TC_THREADS / 32 + 1];
+  __shared__ u64 s_base;
 
   const uint32_t t = blockIdx.x;
   const uint64_t vbase = (uint64_t)t * B;
   const uint32_t nv = (uint32_t)min((uint64_t)B, (uint64_t)n - vbase);
   const u64 e0 = offsets[t];
   const uint32_t ne0 = (uint32_t)(offsets[t + 1] - e0);
-  // In shared memory the edges hold their current component labels and are
-  // compacted after every round (edges inside a component are dropped); from
-  // global memory they are read as input ends and mapped through lab[].
+  // In shared memory the edges hold the labels of their ends' components and
+  // are compacted after every round (edges inside a component are dropped);
+  // from global memory they are read as input ends and mapped through lab[].
   const bool in_smem = ne0 <= edge_cap;
   for (uint32_t x = threadIdx.x; x < nv; x += TC_THREADS) {
     lab[x] = x;
@@ -1356,8 +1410,8 @@ __global__ void __launch_bounds__(TC_THREADS) tile_contract_kernel(uint32_t n, u
       const u64 k = in_smem ? skey[e] : edge_key(b_w[e0 + e], b_id[e0 + e]);
       const uint32_t a = in_smem ? (pe & 0xffffu) : lab[pe & 0xffffu], b = in_smem ? (pe >> 16) : lab[pe >> 16];
       if (a != b) {
-        atomicMin(best + a, k);
-        atomicMin(best + b, k);
+        if (k < best[a]) atomicMin(best + a, k);
+        if (k < best[b]) atomicMin(best + b, k);
       }
     }
     __syncthreads();
@@ -1389,69 +1443,103 @@ __global__ void __launch_bounds__(TC_THREADS) tile_contract_kernel(uint32_t n, u
     }
     __syncthreads();
     if (!s_any) break;
-    // pointer doubling among this round's roots (at most log2(nv) + 1 steps)
-    for (int it = 0; it < 32; ++it) {
-      __syncthreads();
-      if (threadIdx.x == 0) s_any = 0;
-      __syncthreads();
-      for (uint32_t c = threadIdx.x; c < nv; c += TC_THREADS) {
-        if (lab[c] != c) continue;
-        const uint32_t h = hook[c], hh = hook[h];
-        if (hh != h) {
-          hook[c] = hh;
-          s_any = 1;
-        }
+    // every component of the last round follows its hooks to the new root
+    // (the hooks form a forest: at most nv steps)
+    for (uint32_t c = threadIdx.x; c < nv; c += TC_THREADS) {
+      if (lab[c] != c) continue;
+      uint32_t r = c;
+      for (uint32_t step = 0; step <= nv; ++step) {
+        const uint32_t h = hook[r];
+        if (h == r) break;
+        r = h;
+        if (step == nv) atomicOr(err, ERR_JUMP);
       }
-      __syncthreads();
-      if (!s_any) break;
-      if (it == 31 && threadIdx.x == 0) atomicOr(err, ERR_JUMP);
+      other[c] = r;
     }
-    // merge the cut minima into the new roots, then relabel the vertices
-    for (uint32_t c = threadIdx.x; c < nv; c += TC_THREADS)
-      if (lab[c] == c && hook[c] != c) atomicMin(comp + hook[c], comp[c]);
     __syncthreads();
-    for (uint32_t x = threadIdx.x; x < nv; x += TC_THREADS) lab[x] = hook[lab[x]];
+    // merge the cut minima into the new roots, relabel the vertices
+    for (uint32_t c = threadIdx.x; c < nv; c += TC_THREADS) {
+      const uint32_t l = lab[c];
+      const uint32_t r = other[l];
+      if (l == c && r != c) atomicMin(comp + r, comp[c]);
+      lab[c] = r;
+    }
     if (in_smem) {  // relabel the edges to the new roots and keep those between components
-      uint32_t out = 0;
-      for (uint32_t base = 0; base < ne; base += TC_THREADS) {
-        const uint32_t e = base + threadIdx.x;
-        uint32_t pe = 0;
-        u64 k = 0;
-        bool keep = false;
+      uint32_t pe[TC_EPT];
+      u64 k[TC_EPT];
+      uint32_t keep = 0, cnt = 0;
+#pragma unroll
+      for (int i = 0; i < TC_EPT; ++i) {
+        const uint32_t e = threadIdx.x + (uint32_t)i * TC_THREADS;
+        pe[i] = 0;
+        k[i] = 0;
         if (e < ne) {
-          pe = sends[e];
-          k = skey[e];
-          const uint32_t a = hook[pe & 0xffffu], b = hook[pe >> 16];
-          pe = a | (b << 16);
-          keep = a != b;
-        }
-        const uint32_t bal = __ballot_sync(0xffffffffu, keep);
-        const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-        if (lane == 0) s_warp[wid] = __popc(bal);
-        __syncthreads();  // every thread has read its edge of this chunk
-        if (threadIdx.x == 0) {
-          uint32_t acc = 0;
-          for (int i = 0; i < TC_THREADS / 32; ++i) {
-            const uint32_t c = s_warp[i];
-            s_warp[i] = acc;
-            acc += c;
+          const uint32_t x = sends[e];
+          const uint32_t a = other[x & 0xffffu], b = other[x >> 16];
+          pe[i] = a | (b << 16);
+          k[i] = skey[e];
+          if (a != b) {
+            keep |= 1u << i;
+            ++cnt;
           }
-          s_warp[TC_THREADS / 32] = acc;
         }
-        __syncthreads();
-        if (keep) {
-          const uint32_t pos = out + s_warp[wid] + __popc(bal & ((1u << lane) - 1u));
-          sends[pos] = pe;
-          skey[pos] = k;
-        }
-        out += s_warp[TC_THREADS / 32];
-        __syncthreads();
       }
-      if (threadIdx.x == 0) s_ne = out;
+      uint32_t total;
+      uint32_t pos = tc_exclusive_scan(cnt, total, s_warp);  // all reads precede its barriers
+#pragma unroll
+      for (int i = 0; i < TC_EPT; ++i) {
+        if (keep >> i & 1u) {
+          sends[pos] = pe[i];
+          skey[pos] = k[i];
+          ++pos;
+        }
+      }
+      if (threadIdx.x == 0) s_ne = total;
     }
     __syncthreads();
   }
   for (uint32_t x = threadIdx.x; x < nv; x += TC_THREADS) parent[vbase + x] = (uint32_t)(vbase + lab[x]);
+  // The local edges left between different components of the tile join the
+  // cut edges in the contracted graph, with their ends at the tile roots.
+  if (in_smem) {
+    const uint32_t ne = s_ne;
+    if (threadIdx.x == 0) s_base = ne ? atomicAdd(rest_fill, (u64)ne) : 0;
+    __syncthreads();
+    const u64 base = s_base;
+    for (uint32_t e = threadIdx.x; e < ne; e += TC_THREADS) {
+      const uint32_t pe = sends[e];
+      const u64 k = skey[e];
+      rest.u[base + e] = (uint32_t)(vbase + (pe & 0xffffu));
+      rest.v[base + e] = (uint32_t)(vbase + (pe >> 16));
+      rest.w[base + e] = (uint32_t)(k >> 32);
+      rest.id[base + e] = (uint32_t)k;
+    }
+  } else {
+    const int lane = threadIdx.x & 31;
+    for (uint32_t b0 = 0; b0 < ne0; b0 += TC_THREADS) {
+      const uint32_t e = b0 + threadIdx.x;
+      uint32_t a = 0, b = 0;
+      if (e < ne0) {
+        const uint32_t pe = b_ends[e0 + e];
+        a = lab[pe & 0xffffu];
+        b = lab[pe >> 16];
+      }
+      const bool keep = e < ne0 && a != b;
+      const uint32_t kb = __ballot_sync(0xffffffffu, keep);
+      if (!kb) continue;
+      const int lead = __ffs(kb) - 1;
+      u64 base = 0;
+      if (lane == lead) base = atomicAdd(rest_fill, (u64)__popc(kb));
+      base = __shfl_sync(0xffffffffu, base, lead);
+      if (keep) {
+        const u64 at = base + __popc(kb & ((1u << lane) - 1u));
+        rest.u[at] = (uint32_t)(vbase + a);
+        rest.v[at] = (uint32_t)(vbase + b);
+        rest.w[at] = b_w[e0 + e];
+        rest.id[at] = b_id[e0 + e];
+      }
+    }
+  }
 }
 
 // Fraction estimate for the automatic switch: counts how many of `samples`
@@ -1747,34 +1835,37 @@ void launch_tile_scan(const uint32_t *count, uint32_t ntiles, u64 *offsets, cuda
 }
 
 void launch_tile_scatter(EdgeList in, uint64_t m, uint32_t n, uint32_t B, const u64 *offsets, uint32_t *fill,
-                         uint32_t *b_ends, uint32_t *b_w, uint32_t *b_id, int sms, cudaStream_t s) {
+                         uint32_t *b_ends, uint32_t *b_w, uint32_t *b_id, EdgeOut cut, u64 *cut_fill, int sms,
+                         cudaStream_t s) {
   if (m == 0) return;
   tile_scatter_kernel<<<grid_for((m + TILE - 1) / TILE, sms, 8), BLOCK, 0, s>>>(in, m, n, B, offsets, fill, b_ends,
-                                                                                b_w, b_id);
+                                                                                b_w, b_id, cut, cut_fill);
 }
 
-bool launch_tile_contract(uint32_t n, uint32_t B, const u64 *cutmin, const u64 *offsets, const uint32_t *b_ends,
-                          const uint32_t *b_w, const uint32_t *b_id, uint32_t *parent, uint32_t *bits, uint32_t *err,
-                          cudaStream_t s) {
-  static int smem_full = 0, smem_half = 0;
+bool launch_tile_contract(uint32_t n, uint32_t B, uint64_t nlocal, const u64 *cutmin, const u64 *offsets,
+                          const uint32_t *b_ends, const uint32_t *b_w, const uint32_t *b_id, uint32_t *parent,
+                          uint32_t *bits, EdgeOut rest, u64 *rest_fill, uint32_t *err, cudaStream_t s) {
+  static int smem_full = 0;
   if (!smem_full) {
-    int dev = 0, optin = 0, per_sm = 0;
+    int dev = 0, optin = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-    cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
     smem_full = optin - 2048;  // static shared memory and slack
-    smem_half = min(optin, per_sm / 2) - 2048;
     cudaFuncSetAttribute(tile_contract_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_full);
   }
   const size_t vbytes = (size_t)B * (8 + 8 + 4 + 4 + 4);
-  // two tiles per SM when the vertex arrays leave room for edges, else one
-  const int smem_max = vbytes + 12 * 2048 <= (size_t)smem_half ? smem_half : smem_full;
-  if ((size_t)smem_max <= vbytes) return false;
-  const uint32_t cap = (uint32_t)(((size_t)smem_max - vbytes) / 12);
-  const size_t bytes = vbytes + (size_t)cap * 12;
+  if ((size_t)smem_full <= vbytes) return false;
   const uint32_t ntiles = (uint32_t)(((uint64_t)n + B - 1) / B);
-  tile_contract_kernel<<<ntiles, TC_THREADS, bytes, s>>>(n, B, cutmin, offsets, b_ends, b_w, b_id, cap, parent, bits,
-                                                         err);
+  // Edge capacity: a quarter above the mean bucket (so more tiles share an
+  // SM), at most what the in-place compaction holds and the block can get.
+  // Larger buckets run from global memory.
+  uint64_t want = nlocal / ntiles;
+  want = ((want + want / 4 + 256) + 31) / 32 * 32;
+  uint64_t cap = min(want, (uint64_t)TC_EPT * TC_THREADS);
+  cap = min(cap, ((size_t)smem_full - vbytes) / 12);
+  const size_t bytes = vbytes + (size_t)cap * 12;
+  tile_contract_kernel<<<ntiles, TC_THREADS, bytes, s>>>(n, B, cutmin, offsets, b_ends, b_w, b_id, (uint32_t)cap,
+                                                         parent, bits, rest, rest_fill, err);
   return true;
 }
 

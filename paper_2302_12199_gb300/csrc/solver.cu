@@ -525,20 +525,29 @@ struct Solve {
     const uint64_t stride = round_up(nlocal * 4 + 16, 256);
     TRY(bucket_b.alloc(c, stride * 3, s));
     char *bb = bucket_b.as<char>();
-    PROF(MST_K_TILE, 12.0 * (double)m + 12.0 * (double)nlocal, -1, 0.0, -1, 0.0,
+    // the cut edges (written by the scatter) and the local edges that remain
+    // between tile components (appended by the contraction)
+    const uint64_t mcut = m;
+    ListBuf cutl;
+    TRY(cutl.alloc(c, mcut, s));
+    CK(cudaMemsetAsync(&c->ds->count[CNT_CUT], 0, sizeof(u64), s));
+    PROF(MST_K_TILE, 12.0 * (double)m + 12.0 * (double)nlocal + 16.0 * (double)(m - nlocal), -1, 0.0, -1, 0.0,
          launch_tile_scatter(in, m, n, B, off_b.as<u64>(), fill_b.as<uint32_t>(), (uint32_t *)bb,
-                             (uint32_t *)(bb + stride), (uint32_t *)(bb + 2 * stride), c->sms, s));
+                             (uint32_t *)(bb + stride), (uint32_t *)(bb + 2 * stride), cutl.out,
+                             &c->ds->count[CNT_CUT], c->sms, s));
     bool launched = false;
     PROF(MST_K_TILE, 12.0 * (double)nlocal + 12.0 * (double)n, -1, 0.0, -1, 0.0,
-         launched = launch_tile_contract(n, B, cut_b.as<u64>(), off_b.as<u64>(), (uint32_t *)bb,
+         launched = launch_tile_contract(n, B, nlocal, cut_b.as<u64>(), off_b.as<u64>(), (uint32_t *)bb,
                                          (uint32_t *)(bb + stride), (uint32_t *)(bb + 2 * stride), parent, bits,
-                                         &c->ds->err, s));
+                                         cutl.out, &c->ds->count[CNT_CUT], &c->ds->err, s));
     if (!launched) return MST_ERR_INVALID_ARG;  // tile too large for shared memory
-    TRY(out.alloc(c, m, s));
+    // the cut edges, relabelled to the tile roots, are the contracted graph
+    TRY(out.alloc(c, mcut, s));
     TRY(zero_counters(c, s));
     CompactArgs ca{};
-    ca.in = in;
-    ca.m = m;
+    ca.in = cutl.list();
+    ca.m = mcut;
+    ca.m_dev = &c->ds->count[CNT_CUT];
     ca.out = out.out;
     ca.label = parent;
     ca.n = n;
@@ -546,7 +555,7 @@ struct Solve {
     ca.best = relax ? best : nullptr;
     record_ends(ca);
     ca.st = next_scan(c, CNT_EDGES);
-    PROF(MST_K_RELABEL_MIN, 12.0 * (double)m, CNT_EDGES, 16.0, -1, 0.0, launch_compact(CM_RELABEL, ca, m, s));
+    PROF(MST_K_RELABEL_MIN, 0.0, CNT_CUT, 16.0, CNT_EDGES, 16.0, launch_compact(CM_RELABEL, ca, mcut, s));
     TRY(readback(c, s));
     m_out = c->hs->count[CNT_EDGES];
     applied = true;
@@ -806,7 +815,7 @@ void mst_config_default(mst_config *cfg) {
   cfg->device = 0;
   cfg->variant = MST_VARIANT_BORUVKA;
   cfg->dedupe = MST_DEDUPE_AUTO;
-  cfg->tile_contract = -1;
+  cfg->tile_contract = 0;
   cfg->tile_vertices = 1024;
   cfg->pivot_sample = 1u << 16;
   cfg->seed = 0x2302121990ULL;

@@ -27,6 +27,7 @@ def test_default_config(lib):
     assert cfg.variant == 0 and cfg.dedupe == 0
     assert cfg.pivot_sample == 1 << 16
     assert cfg.filter_max_avg_degree == 1.0
+    assert cfg.tile_contract == 0 and cfg.tile_vertices == 1024
 
 
 def test_status_strings(lib):

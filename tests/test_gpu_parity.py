@@ -18,9 +18,9 @@ pytestmark = pytest.mark.gpu
 
 CONFIGS = [
     dict(variant="boruvka", dedupe="none", tile_contract=0),
-    dict(variant="boruvka", dedupe="hash"),
+    dict(variant="boruvka", dedupe="hash", tile_contract=-1),
     dict(variant="boruvka", dedupe="auto"),
-    dict(variant="filter", dedupe="auto", filter_min_edges=1 << 10, pivot_sample=4096),
+    dict(variant="filter", dedupe="auto", filter_min_edges=1 << 10, pivot_sample=4096, tile_contract=-1),
     dict(variant="filter", dedupe="none", filter_min_edges=1 << 12, filter_max_avg_degree=4.0, tile_contract=0),
     dict(variant="boruvka", tile_contract=1, tile_vertices=512),
     dict(variant="filter", tile_contract=1, tile_vertices=256, filter_min_edges=1 << 10, pivot_sample=4096),
@@ -279,6 +279,42 @@ def test_step_partition_and_filter(step_solver, dev):
     out = step_solver.filter(g.n, *list_on_dev(dev, g.src, g.dst, g.w, ids), pivot=pv, P=Pd)
     assert_same_list(out, S.filter_heavy(g.src, g.dst, g.w, ids, pv, P))
     assert np.array_equal(host(Pd), S.roots(P))
+
+
+def light_fixed_point(n, src, dst, w, ids, pv):
+    """P after Borůvka rounds on the light part (the state a filter step sees)."""
+    P = np.arange(n, dtype=np.uint32)
+    uu, vv, ww, ii = S.partition_light(src, dst, w, ids, pv)
+    while uu.size:
+        r, _, (uu, vv, ww, ii) = S.boruvka_round(n, uu, vv, ww, ii)
+        moved = r != np.arange(n, dtype=np.uint32)
+        P[moved] = r[moved]
+    return P
+
+
+@pytest.mark.parametrize("with_ids", [True, False])
+def test_step_filter_long_list(step_solver, dev, with_ids):
+    """Lists long enough for the persistent two-stage filter (over 2^21 items,
+    ragged last tile), with a giant component in P."""
+    g = W.gnm(1 << 18, 3_000_001, 42)
+    ids = (np.random.default_rng(42).permutation(g.m)).astype(np.uint32) if with_ids else None
+    eids = ids if with_ids else np.arange(g.m, dtype=np.uint32)
+    pv = int(S.pivot(g.w, eids, 321, 1 << 16))
+    P = light_fixed_point(g.n, g.src, g.dst, g.w, eids, pv)
+    Pd = to_dev(P, dev)
+    out = step_solver.filter(g.n, *list_on_dev(dev, g.src, g.dst, g.w), to_dev(ids, dev) if with_ids else None,
+                             pivot=pv, P=Pd)
+    assert_same_list(out, S.filter_heavy(g.src, g.dst, g.w, eids, pv, P))
+
+
+def test_filter_solve_long_lists(dev):
+    """Whole Filter-Borůvka solves whose filter passes run on lists of millions of edges."""
+    s = Solver(0, variant="filter")
+    try:
+        for g in (W.rmat(18, (1 << 22) + 5, 43), W.gnm(1 << 17, 3_000_017, 44)):
+            assert_same_forest(s, g.n, g.src, g.dst, g.w, dev, "filter-long")
+    finally:
+        s.close()
 
 
 def test_step_finalize(step_solver, dev):
