@@ -54,6 +54,48 @@ WORKLOADS = {
 }
 
 
+# DRAM traffic of the dominant kernel, from one single-pass ncu capture of the
+# default workload (dram__bytes_read.sum + dram__bytes_write.sum over the
+# filter launches of one timed solve, divided by the algorithmic bytes the
+# library's profiler counted for them).  A launch's traffic is taken as that
+# ratio times its algorithmic bytes.  The ratio holds only for the kernel source it was measured
+# on: when the source region below hashes differently, traffic is reported as
+# null until it is captured again.
+TRAFFIC = {
+    "class": "filter",
+    "kernel": "compact_tma_kernel<CM_FILTER>",
+    "dram_per_algorithmic_byte": 1.352,
+    "source_sha256": "e81fd73b978bfb7a9fb715fd2278456775c2b34e408c08143cdbebdbb6a8b039",
+    "summary": "profiles/filter_compaction_rmat.md",
+}
+TRAFFIC_SOURCE = ("paper_2302_12199_gb300/csrc/kernels.cu",
+                  "__device__ __forceinline__ uint32_t keep_flags",
+                  "// --------------------------------------------------------------- min edges")
+
+
+def traffic_source_digest():
+    import hashlib
+    path, start, end = TRAFFIC_SOURCE
+    try:
+        with open(os.path.join(ROOT, path)) as f:
+            text = f.read()
+        i, j = text.index(start), text.index(end)
+    except (OSError, ValueError):
+        return None
+    return hashlib.sha256(text[i:j].encode()).hexdigest()
+
+
+def nvtx_mark(torch, what: str) -> None:
+    """Opens or closes the NVTX range "timed" (no-op where NVTX is missing)."""
+    try:
+        if what == "push":
+            torch.cuda.nvtx.range_push("timed")
+        else:
+            torch.cuda.nvtx.range_pop()
+    except Exception:
+        pass
+
+
 def host_cores() -> int:
     try:
         return len(os.sched_getaffinity(0))
@@ -232,10 +274,12 @@ def gpu_main(args, rank: int, world: int, local_rank: int):
     time.sleep(0.3)
     solver.profile(True)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    nvtx_mark(torch, "push")  # lets a profiler capture the timed solves only
     e0.record(stream)
     for _ in range(args.steps):
         solver.solve(n, src, dst, w, out=out)
     e1.record(stream)
+    nvtx_mark(torch, "pop")
     torch.cuda.synchronize(dev)
     solver.profile(False)
     if dist:
@@ -286,13 +330,20 @@ def gpu_main(args, rank: int, world: int, local_rank: int):
         all_bytes += kbytes
         if nl:
             kernels[name] = {"launches_per_step": nl / args.steps, "ms_per_step": kms / args.steps,
+                             "bytes_per_step": kbytes / args.steps,
                              "GBps": (kbytes / (kms / 1e3) / 1e9) if kms > 0 else None}
     dom = max(stats, key=lambda k: stats[k][1])
     nl, kms, kbytes = stats[dom]
     achieved = kbytes / (kms / 1e3) / 1e9
+    traffic = None
+    if (dom == TRAFFIC["class"] and TRAFFIC["dram_per_algorithmic_byte"] and nl
+            and traffic_source_digest() == TRAFFIC["source_sha256"]):
+        traffic = TRAFFIC["dram_per_algorithmic_byte"] * kbytes / nl
     roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                 "frac": achieved / peaks["hbm_gbs"], "peak_source": peaks["source"],
-                "traffic": None, "time_share": kms / ms if ms > 0 else None}
+                "bytes_per_launch": kbytes / nl if nl else None,
+                "traffic": traffic, "traffic_source": TRAFFIC["summary"] if traffic is not None else None,
+                "time_share": kms / ms if ms > 0 else None}
     effective = all_bytes / args.steps / (ms / args.steps / 1e3) / 1e9
 
     line = {
