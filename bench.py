@@ -189,10 +189,58 @@ def cpu_oracle_rate(g, sample_edges: int, repeats: int = 1) -> tuple[float, floa
     return k / best, best
 
 
+def reference_batched(args):
+    """The oracle (Kruskal, one thread) on the first graphs of the batched mix
+    (or of the served pool), as many as fit in about two seconds per step;
+    reported in graphs/s."""
+    import numpy as np
+    import oracle
+    from paper_2302_12199_gb300 import workloads as W
+    if args.workload == "served":
+        args.graphs = args.pool
+        b = W.mix(args.pool, W.DEFAULT_SEED + 5, log_lo=8, log_hi=20)
+    else:
+        b = W.mix(args.graphs, W.DEFAULT_SEED)
+    off = np.asarray(b.edge_off, dtype=np.int64)
+
+    def step(limit_s=2.0):
+        t0 = time.perf_counter()
+        g = 0
+        while g < args.graphs and time.perf_counter() - t0 < limit_s:
+            lo, hi = off[g], off[g + 1]
+            oracle.kruskal(int(b.n[g]), b.src[lo:hi], b.dst[lo:hi], b.w[lo:hi])
+            g += 1
+        return g, time.perf_counter() - t0
+    for _ in range(args.warmup):
+        step()
+    done, secs = 0, 0.0
+    for _ in range(args.steps):
+        k, dt = step()
+        done += k
+        secs += dt
+    value = done / secs
+    line = {
+        "impl": "reference", "value": value,
+        "metric": ("served graphs/s (Poisson arrivals, continuous batching)" if args.workload == "served"
+                   else "batched graphs/s (one mst_solve_batched call per step)"),
+        "unit": "graphs/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * secs / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "u32", "data": "synthetic", "config": {"workload": args.workload, "graphs": args.graphs},
+        "cpu_baseline": {"value": value, "unit": "graphs/s", "cores": 1, "kind": "oracle",
+                         "sample": f"the first graphs of the {args.graphs}-graph {args.workload} mix, "
+                                                   "~2 s of Kruskal per step"},
+        "e2e": {"value": value, "unit": "graphs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def reference_main(args, rank: int):
     if rank != 0:
         return 0
     from paper_2302_12199_gb300 import workloads as W
+    if args.workload in ("batched", "served"):
+        return reference_batched(args)
     desc, gen, cfg = WORKLOADS[args.workload]
     g = gen(W)
     sample = min(g.m, args.cpu_sample_edges)
@@ -375,13 +423,267 @@ def gpu_main(args, rank: int, world: int, local_rank: int):
     return 0
 
 
+def percentiles(xs, qs=(50, 99, 99.9)):
+    import numpy as np
+    a = np.asarray(xs, dtype=np.float64)
+    return {f"p{q:g}": float(np.percentile(a, q)) for q in qs} if a.size else {}
+
+
+def batched_main(args, rank: int, world: int, local_rank: int):
+    """The batched configuration: G mixed graphs (n log-uniform in [2^8, 2^16];
+    1/3 GNM with average degree in [4,32], 1/3 RGG2D degree 8, 1/3 RMAT degree
+    16; w in [1,255]) solved by one mst_solve_batched call per step, against
+    one mst_solve call per graph (plain Borůvka) on the same GPU."""
+    import numpy as np
+    import torch
+
+    from paper_2302_12199_gb300 import workloads as W
+    from paper_2302_12199_gb300.autotune import autotune, label
+    from paper_2302_12199_gb300.mst import Solver
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    G = args.graphs
+    b = W.mix(G, W.DEFAULT_SEED + rank)
+    n_per = np.asarray(b.n, dtype=np.uint32)
+    off = np.asarray(b.edge_off, dtype=np.uint64)
+    m_tot = int(off[-1])
+    n_tot = int(n_per.astype(np.int64).sum())
+    to_dev = lambda a: torch.from_numpy(a.view(np.int32)).to(dev)
+    src, dst, w = to_dev(b.src), to_dev(b.dst), to_dev(b.w)
+    stream = torch.cuda.current_stream(dev)
+
+    def timed_batch(solver):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        res = solver.solve_batched(n_per, off, src, dst, w)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        return e0.elapsed_time(e1) / 1e3, res
+
+    # autotuned configuration (tile contraction and dedupe strategy, variant)
+    def trial(cfg):
+        s = Solver(local_rank, **cfg)
+        try:
+            return timed_batch(s)[0]
+        finally:
+            s.close()
+    if args.no_autotune:
+        best, tuning = dict(variant="boruvka", dedupe="none", tile_contract=0), []
+    else:
+        best, tuning = autotune(trial, reps=1)
+    solver = Solver(local_rank, **best)
+    for _ in range(args.warmup):
+        timed_batch(solver)
+    ref_ids, ref_off, ref_tot = [t.cpu() for t in solver.solve_batched(n_per, off, src, dst, w)]
+    torch.cuda.synchronize(dev)
+
+    uuid = None
+    try:
+        uuid = "GPU-" + str(torch.cuda.get_device_properties(dev).uuid)
+    except Exception:
+        pass
+    sampler = ClockSampler(uuid)
+    if dist:
+        dist.barrier()
+    sampler.start()
+    time.sleep(0.3)
+    solver.profile(True)
+    lat = []
+    nvtx_mark(torch, "push")
+    for _ in range(args.steps):
+        dt, res = timed_batch(solver)
+        lat.append(dt)
+    nvtx_mark(torch, "pop")
+    solver.profile(False)
+    clocks = sampler.stop()
+    stats = solver.profile_stats()
+    ids, moff, tot = [t.cpu() for t in res]
+    if not (torch.equal(ids, ref_ids) and torch.equal(moff, ref_off) and torch.equal(tot, ref_tot)):
+        raise RuntimeError("timed batched solves returned different forests than the warm-up solve")
+    total_s = sum(lat)
+    if dist:
+        t = torch.tensor([total_s], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_s = float(t.item())
+    value = G * args.steps * world / total_s
+
+    # baseline: one mst_solve per graph, plain Borůvka, same GPU and stream
+    base = Solver(local_rank, variant="boruvka", dedupe="none", tile_contract=0)
+    outs = [base.alloc_forest(int(n_per[g]), int(off[g + 1] - off[g])) for g in range(G)]
+    per = []
+    for rep in range(2):  # the first pass warms the pool allocator
+        per = []
+        torch.cuda.synchronize(dev)
+        t_all = time.perf_counter()
+        for g in range(G):
+            lo, hi = int(off[g]), int(off[g + 1])
+            t0 = time.perf_counter()
+            base.solve(int(n_per[g]), src[lo:hi], dst[lo:hi], w[lo:hi], out=outs[g])
+            torch.cuda.synchronize(dev)
+            per.append(time.perf_counter() - t0)
+        t_all = time.perf_counter() - t_all
+    base_value = G / t_all
+    # the batched forests equal the per-graph ones
+    mismatch = 0
+    moff_np = moff.numpy().astype(np.int64)
+    ids_np = ids.numpy().view(np.uint32)
+    tot_np = tot.numpy().view(np.uint64)
+    for g in range(G):
+        gi, gt = outs[g].to_host()
+        seg = ids_np[moff_np[g]:moff_np[g + 1]]
+        if not (np.array_equal(np.sort(seg), gi) and int(tot_np[g]) == gt):
+            mismatch += 1
+    if mismatch:
+        raise RuntimeError(f"{mismatch} graphs differ between the batched and the per-graph solves")
+    base.close()
+
+    # end to end: pinned host batch -> device, solve, forests back to the host
+    pin = [torch.from_numpy(a.view(np.int32)).pin_memory() for a in (b.src, b.dst, b.w)]
+    e2e_steps = max(1, min(args.steps, args.e2e_steps))
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    d2h = 0
+    for _ in range(e2e_steps):
+        ds, dd, dw = [p.to(dev, non_blocking=True) for p in pin]
+        r_ids, r_off, r_tot = solver.solve_batched(n_per, off, ds, dd, dw)
+        h_ids, h_off, h_tot = r_ids.cpu(), r_off.cpu(), r_tot.cpu()
+        d2h = h_ids.numel() * 4 + h_off.numel() * 8 + h_tot.numel() * 8
+    torch.cuda.synchronize(dev)
+    e2e_s = time.perf_counter() - t0
+    e2e = {"value": G * e2e_steps * world / e2e_s, "unit": "graphs/s", "h2d_bytes_per_step": 12 * m_tot,
+           "d2h_bytes_per_step": d2h, "steps": e2e_steps}
+
+    peaks = measured_peaks()
+    kernels, all_bytes, launches = {}, 0.0, 0
+    for name, (nl, kms, kbytes) in stats.items():
+        launches += nl
+        all_bytes += kbytes
+        if nl:
+            kernels[name] = {"launches_per_step": nl / args.steps, "ms_per_step": kms / args.steps,
+                             "bytes_per_step": kbytes / args.steps,
+                             "GBps": (kbytes / (kms / 1e3) / 1e9) if kms > 0 else None}
+    dom = max(stats, key=lambda k: stats[k][1])
+    nl, kms, kbytes = stats[dom]
+    achieved = kbytes / (kms / 1e3) / 1e9
+    ms = total_s * 1e3
+    line = {
+        "metric": "batched graphs/s (one mst_solve_batched call per step)", "value": value, "unit": "graphs/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+        "config": {"workload": "batched", "graphs": G, "n_total": n_tot, "m_total": m_tot,
+                   "mix": "n log-uniform [2^8,2^16]; 1/3 GNM deg 4-32, 1/3 RGG2D deg 8, 1/3 RMAT deg 16; w in [1,255]",
+                   "autotuned": best, "autotune_trials_s": {k: v for k, v in tuning},
+                   "parallelism": f"replicas{world}" if world > 1 else "single",
+                   "l2": "inputs (12 B/edge) larger than L2, no flush"},
+        "latency_ms": {k: v * 1e3 for k, v in percentiles(lat).items()},
+        "edges_per_s": m_tot * args.steps * world / total_s,
+        "one_launch_per_graph": {"value": base_value, "unit": "graphs/s", "variant": "boruvka",
+                                 "latency_ms": {k: v * 1e3 for k, v in percentiles(per).items()},
+                                 "batched_over_per_graph": value / world / base_value},
+        "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                     "frac": achieved / peaks["hbm_gbs"], "peak_source": peaks["source"], "traffic": None,
+                     "time_share": kms / ms if ms > 0 else None},
+        "effective_bw": {"GBps": all_bytes / total_s / 1e9, "frac": all_bytes / total_s / 1e9 / peaks["hbm_gbs"]},
+        "kernels": kernels,
+        "gpu_launches": launches,
+        "e2e": e2e,
+        "clocks": clocks,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    solver.close()
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+def served_main(args, rank: int, world: int, local_rank: int):
+    """The served configuration: Poisson arrivals of mixed graphs (n log-uniform
+    in [2^8, 2^20], families as in the batched mix) at each offered rate,
+    served by the continuous-batching loop of paper_2302_12199_gb300.serve;
+    graphs/s and latency percentiles per rate, every response compared with the
+    same graph solved alone."""
+    import numpy as np
+    import torch
+
+    from paper_2302_12199_gb300 import workloads as W
+    from paper_2302_12199_gb300.serve import PoolGraph, Server, poisson_arrivals
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    b = W.mix(args.pool, W.DEFAULT_SEED + 5 + rank, log_lo=8, log_hi=20)
+    off = np.asarray(b.edge_off, dtype=np.int64)
+    to_dev = lambda a: torch.from_numpy(np.ascontiguousarray(a).view(np.int32)).to(dev)
+    pool = [PoolGraph(int(b.n[g]), to_dev(b.src[off[g]:off[g + 1]]), to_dev(b.dst[off[g]:off[g + 1]]),
+                      to_dev(b.w[off[g]:off[g + 1]])) for g in range(args.pool)]
+    server = Server(local_rank, slots=args.slots, budget_bytes=int(args.slot_budget_gb * (1 << 30)))
+    expected = {g: server.solve_alone(pool[g]) for g in range(args.pool)}  # each graph solved alone
+    for s in server.slots:  # warm every slot
+        s.solve(pool[:8])
+    uuid = None
+    try:
+        uuid = "GPU-" + str(torch.cuda.get_device_properties(dev).uuid)
+    except Exception:
+        pass
+    sampler = ClockSampler(uuid)
+    sampler.start()
+    time.sleep(0.3)
+    rng = np.random.default_rng(77 + rank)
+    per_rate = []
+    for lg in args.rates:
+        rate = float(1 << lg)
+        seconds = min(args.serve_seconds, args.max_requests / rate)
+        arr = poisson_arrivals(rate, seconds, seed=1000 + lg)
+        picks = rng.integers(0, args.pool, arr.size)
+        st = server.run(pool, picks, arr, expected=expected, rate=rate, seconds=seconds)
+        if st.mismatches:
+            raise RuntimeError(f"{st.mismatches} served responses differ from the graphs solved alone")
+        per_rate.append(st.summary())
+    clocks = sampler.stop()
+    server.close()
+    best = max(per_rate, key=lambda r: r["graphs_per_s"])
+    sizes = np.diff(off)
+    line = {
+        "metric": "served graphs/s (Poisson arrivals, continuous batching)", "value": best["graphs_per_s"],
+        "unit": "graphs/s", "n_gpus": world, "steps": len(per_rate), "warmup": 1,
+        "ms_per_step": None, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
+        "data": "synthetic",
+        "config": {"workload": "served", "pool_graphs": args.pool, "pool_mean_n": float(np.mean(b.n)),
+                   "pool_mean_m": float(np.mean(sizes)),
+                   "mix": "n log-uniform [2^8,2^20]; 1/3 GNM deg 4-32, 1/3 RGG2D deg 8, 1/3 RMAT deg 16; w in [1,255]",
+                   "slots": args.slots, "slot_budget_gb": args.slot_budget_gb,
+                   "payloads": "device-resident request pool, gathered per batch"},
+        "rates": per_rate,
+        "latency_ms_at_best": best["latency_ms"],
+        "clocks": clocks,
+        "e2e": None,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
-    ap.add_argument("--workload", default="rmat_filter", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="rmat_filter", choices=sorted(WORKLOADS) + ["batched", "served"])
+    ap.add_argument("--graphs", type=int, default=4096, help="graphs per batch (--workload batched)")
+    ap.add_argument("--no-autotune", action="store_true", help="batched: skip the configuration autotuner")
+    ap.add_argument("--pool", type=int, default=256, help="served: distinct request graphs")
+    ap.add_argument("--slots", type=int, default=3, help="served: solver slots (batches in flight)")
+    ap.add_argument("--slot-budget-gb", type=float, default=6.0, help="served: device memory per slot's batch")
+    ap.add_argument("--rates", type=lambda t: [int(x) for x in t.split(",")], default=[12, 13, 14, 15, 16],
+                    help="served: log2 of the offered arrival rates (requests/s)")
+    ap.add_argument("--serve-seconds", type=float, default=60.0, help="served: arrival window per rate")
+    ap.add_argument("--max-requests", type=int, default=20000, help="served: cap on requests per rate")
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--cpu-sample-edges", type=int, default=1 << 25)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -400,6 +702,10 @@ def main():
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         return reference_main(args, rank)
+    if args.workload == "batched":
+        return batched_main(args, rank, world, local_rank)
+    if args.workload == "served":
+        return served_main(args, rank, world, local_rank)
     return gpu_main(args, rank, world, local_rank)
 
 

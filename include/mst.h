@@ -87,6 +87,11 @@ const char *mst_status_string(mst_status s);
 /* Status of the last call made with this handle. */
 mst_status mst_get_error(mst_handle h);
 
+/* The CUDA runtime error code (cudaError_t) behind the last MST_ERR_CUDA
+ * returned for this handle, 0 if none; *line (if line != NULL) receives the
+ * library source line of the failing call, 0 if unknown.  For diagnostics. */
+int mst_last_cuda_error(mst_handle h, int *line);
+
 /* Upper bound on the scratch bytes a solve of (n, m) allocates with the given
  * configuration (cfg == NULL: defaults), for admission by memory footprint. */
 uint64_t mst_workspace_bytes(uint32_t n, uint64_t m, const mst_config *cfg);

@@ -1,0 +1,56 @@
+"""Autotuner for the solver configuration of a workload.
+
+The fastest way through a workload depends on its graphs: the Filter-Borůvka
+variant (Alg. 2) pays off on dense, heavy-tailed graphs, parallel-edge removal
+(Section 2.3, optional) on graphs whose contracted rounds keep many parallel
+edges, and tile-local contraction (Section 4.1) only where vertex numbering
+gives locality.  Rather than guess, the autotuner times each candidate
+configuration on the caller's own input and keeps the fastest.  Every
+candidate computes the same forest (the MSF under the (w, id) order is
+unique), so the choice affects time only.
+
+Host logic only: each trial is one call into the CUDA library.
+"""
+from __future__ import annotations
+
+from typing import Callable, Dict, Iterable, List, Tuple
+
+# Candidate configurations (keyword arguments of mst.Solver).
+DEFAULT_CANDIDATES: Tuple[dict, ...] = (
+    dict(variant="boruvka", dedupe="none", tile_contract=0),
+    dict(variant="boruvka", dedupe="hash", tile_contract=0),
+    dict(variant="filter", dedupe="none", tile_contract=0),
+    dict(variant="boruvka", dedupe="none", tile_contract=1),
+)
+
+_cache: Dict[str, dict] = {}
+
+
+def label(cfg: dict) -> str:
+    return ",".join(f"{k}={cfg[k]}" for k in sorted(cfg))
+
+
+def autotune(trial: Callable[[dict], float], candidates: Iterable[dict] = DEFAULT_CANDIDATES, reps: int = 2,
+             key: str | None = None) -> Tuple[dict, List[Tuple[str, float]]]:
+    """Returns (best configuration, [(label, best seconds)] for every candidate).
+
+    trial(cfg) runs one solve of the workload with configuration cfg and
+    returns its duration in seconds (the caller times it on the device).  Each
+    candidate gets one untimed run and `reps` timed runs; its score is the
+    fastest timed run.  With `key`, the choice is remembered for the process
+    and later calls with the same key return it without trials."""
+    if key is not None and key in _cache:
+        return dict(_cache[key]), []
+    results: List[Tuple[str, float]] = []
+    best, best_t = None, float("inf")
+    for cfg in candidates:
+        trial(cfg)
+        t = min(trial(cfg) for _ in range(max(1, reps)))
+        results.append((label(cfg), t))
+        if t < best_t:
+            best, best_t = dict(cfg), t
+    if best is None:
+        raise ValueError("autotune needs at least one candidate")
+    if key is not None:
+        _cache[key] = dict(best)
+    return best, results

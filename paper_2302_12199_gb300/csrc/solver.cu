@@ -22,6 +22,8 @@ struct mst_ctx {
   int device = 0;
   mst_config cfg;
   mst_status last = MST_OK;
+  int last_cuda = 0;         // cudaError_t behind the last MST_ERR_CUDA
+  int last_cuda_line = 0;    // source line of the call that returned it
   int sms = 152;
   cudaMemPool_t pool = nullptr;
   DevState *ds = nullptr;    // device
@@ -51,9 +53,19 @@ namespace {
 
 constexpr int TILE_ITEMS = 2048;
 
-#define CK(call)                                   \
-  do {                                             \
-    if ((call) != cudaSuccess) return MST_ERR_CUDA; \
+// The CUDA error of the call that made the current API call fail (per host
+// thread; record() moves it into the handle).
+thread_local int tl_cuda_error = 0;
+thread_local int tl_cuda_line = 0;
+
+#define CK(call)                                \
+  do {                                          \
+    const cudaError_t _e = (call);              \
+    if (_e != cudaSuccess) {                    \
+      tl_cuda_error = (int)_e;                  \
+      tl_cuda_line = __LINE__;                  \
+      return MST_ERR_CUDA;                      \
+    }                                           \
   } while (0)
 
 #define TRY(expr)                     \
@@ -736,9 +748,23 @@ mst_status ensure_sample(mst_ctx *c) {
 }
 
 mst_status record(mst_ctx *c, mst_status st) {
-  if (st == MST_ERR_CUDA) cudaGetLastError();
+  if (st == MST_ERR_CUDA) {
+    const int e = (int)cudaGetLastError();
+    c->last_cuda = tl_cuda_error ? tl_cuda_error : e;
+    c->last_cuda_line = tl_cuda_error ? tl_cuda_line : 0;
+  }
+  tl_cuda_error = 0;
+  tl_cuda_line = 0;
   c->last = st;
   return st;
+}
+
+// MST_ERR_CUDA from a call checked in place (not through CK).
+mst_status record_cuda(mst_ctx *c, int line) {
+  const int e = (int)cudaGetLastError();
+  tl_cuda_error = e ? e : (int)cudaErrorUnknown;
+  tl_cuda_line = line;
+  return record(c, MST_ERR_CUDA);
 }
 
 // ---------------------------------------------------------------- batched
@@ -910,6 +936,11 @@ mst_status mst_set_config(mst_handle h, const mst_config *cfg) {
 
 mst_status mst_get_error(mst_handle h) { return h ? h->last : MST_ERR_INVALID_ARG; }
 
+int mst_last_cuda_error(mst_handle h, int *line) {
+  if (line) *line = h ? h->last_cuda_line : 0;
+  return h ? h->last_cuda : 0;
+}
+
 mst_status mst_profile_enable(mst_handle h, int enable) {
   if (!h) return MST_ERR_INVALID_ARG;
   h->prof_on = enable != 0;
@@ -969,7 +1000,7 @@ mst_status mst_solve_host(mst_handle h, uint32_t n, uint64_t m, const uint32_t *
     if (cudaMemcpyAsync(d_src, h_src, m * 4, cudaMemcpyHostToDevice, s) != cudaSuccess ||
         cudaMemcpyAsync(d_dst, h_dst, m * 4, cudaMemcpyHostToDevice, s) != cudaSuccess ||
         cudaMemcpyAsync(d_w, h_w, m * 4, cudaMemcpyHostToDevice, s) != cudaSuccess)
-      return record(h, MST_ERR_CUDA);
+      return record_cuda(h, __LINE__);
   }
   st = solve_device(h, n, m, d_src, d_dst, d_w, d_out, d_count, d_total, s);
   if (st != MST_OK) return record(h, st);
@@ -977,11 +1008,11 @@ mst_status mst_solve_host(mst_handle h, uint32_t n, uint64_t m, const uint32_t *
   if (cudaMemcpyAsync(&cnt, d_count, 4, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
       cudaMemcpyAsync(h_total_weight, d_total, 8, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
       cudaStreamSynchronize(s) != cudaSuccess)
-    return record(h, MST_ERR_CUDA);
+    return record_cuda(h, __LINE__);
   *h_msf_count = cnt;
   if (cnt > 0 && (cudaMemcpyAsync(h_msf_ids, d_out, (size_t)cnt * 4, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
                   cudaStreamSynchronize(s) != cudaSuccess))
-    return record(h, MST_ERR_CUDA);
+    return record_cuda(h, __LINE__);
   return record(h, MST_OK);
 }
 
@@ -1011,7 +1042,8 @@ mst_status mst_solve_batched(mst_handle h, uint32_t num_graphs, const uint32_t *
   const uint64_t stride = round_up(m * 4 + 16, 256);
   if (st == MST_OK) st = uni_b.alloc(h, stride * 2, s);
   const uint64_t cap = m < (uint64_t)n ? m : (uint64_t)n;
-  if (st == MST_OK) st = ids_b.alloc(h, cap * 4 + 512, s);
+  // ids, then (256-byte aligned) the forest size, then 256 bytes on, its weight
+  if (st == MST_OK) st = ids_b.alloc(h, round_up(cap * 4, 256) + 512, s);
   if (st != MST_OK) return record(h, st);
   uint64_t *d_eoff = tab_b.as<uint64_t>();
   uint64_t *d_voff = (uint64_t *)((char *)tab_b.p + round_up((num_graphs + 1) * 8, 256));
@@ -1024,14 +1056,15 @@ mst_status mst_solve_batched(mst_handle h, uint32_t num_graphs, const uint32_t *
       cudaMemcpyAsync(d_voff, voff.data(), (num_graphs + 1) * 8, cudaMemcpyHostToDevice, s) != cudaSuccess ||
       cudaMemcpyAsync(d_gn, h_n, num_graphs * 4, cudaMemcpyHostToDevice, s) != cudaSuccess ||
       cudaMemsetAsync(&h->ds->err, 0, 4, s) != cudaSuccess)
-    return record(h, MST_ERR_CUDA);
+    return record_cuda(h, __LINE__);
   batch_offset_kernel<<<num_graphs, 256, 0, s>>>(d_src, d_dst, d_eoff, d_voff, usrc, udst, d_gn, &h->ds->err);
-  if (readback(h, s) != MST_OK) return record(h, h->hs->err & ERR_VERTEX ? MST_ERR_VERTEX_RANGE : MST_ERR_CUDA);
+  st = readback(h, s);
+  if (st != MST_OK) return record(h, st);
   st = solve_device(h, n, m, usrc, udst, d_w, ids, d_count, d_sum, s);
   if (st != MST_OK) return record(h, st);
   batch_split_kernel<<<num_graphs, 256, 0, s>>>(ids, d_count, d_eoff, num_graphs, d_w, d_msf_ids, d_msf_off,
                                                 (u64 *)d_total_weight);
-  if (cudaStreamSynchronize(s) != cudaSuccess) return record(h, MST_ERR_CUDA);
+  if (cudaStreamSynchronize(s) != cudaSuccess) return record_cuda(h, __LINE__);
   return record(h, MST_OK);
 }
 
@@ -1045,7 +1078,7 @@ mst_status mst_step_min_edges(mst_handle h, uint32_t n, uint64_t m, const uint32
   cudaStream_t s = (cudaStream_t)stream;
   if (cudaMemsetAsync(d_best, 0xff, (size_t)n * 8, s) != cudaSuccess ||
       cudaMemsetAsync(&h->ds->err, 0, 4, s) != cudaSuccess)
-    return record(h, MST_ERR_CUDA);
+    return record_cuda(h, __LINE__);
   launch_min_edges(EdgeList{d_u, d_v, d_w, d_id}, m, n, 1, KeyLayout{0, 0, 0}, (u64 *)d_best, &h->ds->err, h->sms, s);
   return record(h, readback(h, s));
 }
@@ -1064,7 +1097,7 @@ mst_status mst_step_contract(mst_handle h, uint32_t n, uint64_t m, const uint32_
   S.dst = d_v;
   const EdgeList E{d_u, d_v, d_w, nullptr};
   launch_min_edges(E, m, n, 1, S.kl, S.best, &h->ds->err, h->sms, s);
-  if (zero_counters(h, s) != MST_OK) return record(h, MST_ERR_CUDA);
+  if (zero_counters(h, s) != MST_OK) return record_cuda(h, __LINE__);
   HookArgs ha{};
   ha.ncand = n;
   ha.best = S.best;
@@ -1091,7 +1124,7 @@ static mst_status step_compact(mst_handle h, CompactMode mode, uint32_t n, uint6
   cudaStream_t s = (cudaStream_t)stream;
   mst_status st = ensure_status(h, m, s);
   if (st != MST_OK) return record(h, st);
-  if (clear_device_flags(h, s) != MST_OK) return record(h, MST_ERR_CUDA);
+  if (clear_device_flags(h, s) != MST_OK) return record_cuda(h, __LINE__);
   const EdgeList E{d_u, d_v, d_w, d_id};
   CompactArgs a{};
   a.in = E;
@@ -1112,16 +1145,16 @@ static mst_status step_compact(mst_handle h, CompactMode mode, uint32_t n, uint6
     const uint64_t slots = next_pow2(2 * m < 1024 ? 1024 : 2 * m);
     st = table_b.alloc(h, slots * sizeof(HashSlot), s);
     if (st != MST_OK) return record(h, st);
-    if (cudaMemsetAsync(table_b.p, 0xff, slots * sizeof(HashSlot), s) != cudaSuccess) return record(h, MST_ERR_CUDA);
+    if (cudaMemsetAsync(table_b.p, 0xff, slots * sizeof(HashSlot), s) != cudaSuccess) return record_cuda(h, __LINE__);
     a.table = table_b.as<HashSlot>();
     a.tmask = slots - 1;
     launch_hash_insert(E, m, a.table, a.tmask, &h->ds->err, h->sms, s);
   }
   a.st = next_scan(h, CNT_USER);
-  if (cudaMemsetAsync(&h->ds->count[CNT_USER], 0, sizeof(u64), s) != cudaSuccess) return record(h, MST_ERR_CUDA);
+  if (cudaMemsetAsync(&h->ds->count[CNT_USER], 0, sizeof(u64), s) != cudaSuccess) return record_cuda(h, __LINE__);
   launch_compact(mode, a, m, s);
   if (cudaMemcpyAsync(d_out_count, &h->ds->count[CNT_USER], 8, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
-    return record(h, MST_ERR_CUDA);
+    return record_cuda(h, __LINE__);
   return record(h, readback(h, s));
 }
 
@@ -1156,7 +1189,7 @@ mst_status mst_step_filter(mst_handle h, uint32_t n, uint64_t m, const uint32_t 
   if (n > 0) {
     Solve S(h, s, n, 0);
     S.parent = d_P;
-    if (clear_device_flags(h, s) != MST_OK) return record(h, MST_ERR_CUDA);
+    if (clear_device_flags(h, s) != MST_OK) return record_cuda(h, __LINE__);
     mst_status st = S.compress_all();
     if (st != MST_OK) return record(h, st);
   }
@@ -1175,7 +1208,7 @@ mst_status mst_step_pivot(mst_handle h, uint64_t m, const uint32_t *d_w, const u
   const EdgeList E{nullptr, nullptr, d_w, d_id};
   if (!launch_pivot_coop(E, m, state, sample, sb.as<u64>(), h->pivot_scratch, (u64 *)d_pivot, s))
     launch_pivot(E, m, nullptr, state, sample, sb.as<u64>(), (u64 *)d_pivot, s);
-  if (cudaStreamSynchronize(s) != cudaSuccess) return record(h, MST_ERR_CUDA);
+  if (cudaStreamSynchronize(s) != cudaSuccess) return record_cuda(h, __LINE__);
   return record(h, MST_OK);
 }
 
@@ -1218,7 +1251,7 @@ mst_status mst_step_finalize(mst_handle h, uint64_t m, const uint32_t *d_chosen,
   mst_status st = ensure_status(h, (m + 31) / 32, s);
   if (st != MST_OK) return record(h, st);
   if (clear_device_flags(h, s) != MST_OK || cudaMemsetAsync(d_total_weight, 0, 8, s) != cudaSuccess)
-    return record(h, MST_ERR_CUDA);
+    return record_cuda(h, __LINE__);
   launch_finalize(d_chosen, m, d_w, d_msf_ids, d_msf_count, (u64 *)d_total_weight, next_scan(h, CNT_AUX), s);
   return record(h, readback(h, s));
 }

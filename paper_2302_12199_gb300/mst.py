@@ -18,6 +18,7 @@ from . import build as _build
 _lib = None
 
 MST_OK = 0
+MST_ERR_CUDA = 5
 STATUS_NAMES = {0: "MST_OK", 1: "MST_ERR_INVALID_ARG", 2: "MST_ERR_VERTEX_RANGE", 3: "MST_ERR_TOO_LARGE",
                 4: "MST_ERR_OOM", 5: "MST_ERR_CUDA", 6: "MST_ERR_INTERNAL", 7: "MST_ERR_NOT_SUPPORTED"}
 VARIANTS = {"boruvka": 0, "filter": 1, "auto": 2}
@@ -56,6 +57,7 @@ _SIGNATURES = {
     "mst_set_config": (_I, [_P, ctypes.POINTER(MstConfig)]),
     "mst_status_string": (ctypes.c_char_p, [_I]),
     "mst_get_error": (_I, [_P]),
+    "mst_last_cuda_error": (_I, [_P, _P]),
     "mst_workspace_bytes": (_U64, [_U32, _U64, ctypes.POINTER(MstConfig)]),
     "mst_solve": (_I, [_P, _U32, _U64, _P, _P, _P, _P, _P, _P, _P]),
     "mst_solve_host": (_I, [_P, _U32, _U64, _P, _P, _P, _P, _P, _P, _P]),
@@ -95,8 +97,12 @@ def load(build_if_missing: bool = True):
     return _lib
 
 
-def _check(st: int, where: str):
+def _check(st: int, where: str, lib=None, h=None):
     if st != MST_OK:
+        if st == MST_ERR_CUDA and lib is not None and h:
+            line = ctypes.c_int(0)
+            code = lib.mst_last_cuda_error(h, ctypes.byref(line))
+            where = f"{where} (cudaError {code} at solver.cu:{line.value})"
         raise MstError(st, where)
 
 
@@ -157,6 +163,9 @@ class Solver:
         _check(self.lib.mst_create(ctypes.byref(h), ctypes.byref(self.cfg)), "mst_create")
         self.h = h
 
+    def _check(self, st: int, where: str):
+        _check(st, where, self.lib, self.h)
+
     def close(self):
         if getattr(self, "h", None):
             self.lib.mst_destroy(self.h)
@@ -175,18 +184,18 @@ class Solver:
             elif k == "dedupe":
                 v = DEDUPE[v] if isinstance(v, str) else v
             setattr(self.cfg, k, v)
-        _check(self.lib.mst_set_config(self.h, ctypes.byref(self.cfg)), "mst_set_config")
+        self._check(self.lib.mst_set_config(self.h, ctypes.byref(self.cfg)), "mst_set_config")
 
     def profile(self, enable: bool = True):
         """Start (and clear) or stop per-kernel-class event timing."""
-        _check(self.lib.mst_profile_enable(self.h, 1 if enable else 0), "mst_profile_enable")
+        self._check(self.lib.mst_profile_enable(self.h, 1 if enable else 0), "mst_profile_enable")
 
     def profile_stats(self) -> dict:
         """{class: (launches, ms, algorithmic bytes)} since profiling was enabled."""
         out = {}
         for k, name in enumerate(KERNEL_CLASSES):
             st = KernelStats()
-            _check(self.lib.mst_profile_get(self.h, k, ctypes.byref(st)), "mst_profile_get")
+            self._check(self.lib.mst_profile_get(self.h, k, ctypes.byref(st)), "mst_profile_get")
             out[name] = (int(st.launches), float(st.ms), float(st.bytes))
         return out
 
@@ -204,7 +213,7 @@ class Solver:
                 raise ValueError("src, dst and w must have equal length")
         if out is None:
             out = self.alloc_forest(n, m)
-        _check(self.lib.mst_solve(self.h, n, m, _ptr(src), _ptr(dst), _ptr(w), _ptr(out.ids), _ptr(out.count),
+        self._check(self.lib.mst_solve(self.h, n, m, _ptr(src), _ptr(dst), _ptr(w), _ptr(out.ids), _ptr(out.count),
                                   _ptr(out.total), _stream(stream)), "mst_solve")
         return out
 
@@ -225,7 +234,7 @@ class Solver:
         ids = np.empty(cap, dtype=np.uint32)
         cnt = ctypes.c_uint32(0)
         tot = ctypes.c_uint64(0)
-        _check(self.lib.mst_solve_host(self.h, n, m, src.ctypes.data_as(_P), dst.ctypes.data_as(_P),
+        self._check(self.lib.mst_solve_host(self.h, n, m, src.ctypes.data_as(_P), dst.ctypes.data_as(_P),
                                        w.ctypes.data_as(_P), ids.ctypes.data_as(_P), ctypes.byref(cnt),
                                        ctypes.byref(tot), _stream(stream)), "mst_solve_host")
         return ids[: cnt.value].copy(), int(tot.value)
@@ -234,7 +243,7 @@ class Solver:
         """mst_solve_host on raw host pointers (e.g. pinned tensors): returns (count, total)."""
         cnt = ctypes.c_uint32(0)
         tot = ctypes.c_uint64(0)
-        _check(self.lib.mst_solve_host(self.h, n, m, _P(src_ptr), _P(dst_ptr), _P(w_ptr), _P(ids_ptr),
+        self._check(self.lib.mst_solve_host(self.h, n, m, _P(src_ptr), _P(dst_ptr), _P(w_ptr), _P(ids_ptr),
                                        ctypes.byref(cnt), ctypes.byref(tot), _stream(stream)), "mst_solve_host")
         return int(cnt.value), int(tot.value)
 
@@ -254,7 +263,7 @@ class Solver:
         msf_off = torch.zeros(G + 1, dtype=torch.int64, device=self.device)
         totals = torch.zeros(max(G, 1), dtype=torch.int64, device=self.device)
         del m
-        _check(self.lib.mst_solve_batched(self.h, G, n_h.ctypes.data_as(_P), off_h.ctypes.data_as(_P), _ptr(src),
+        self._check(self.lib.mst_solve_batched(self.h, G, n_h.ctypes.data_as(_P), off_h.ctypes.data_as(_P), _ptr(src),
                                           _ptr(dst), _ptr(w), _ptr(ids), _ptr(msf_off), _ptr(totals),
                                           _stream(stream)), "mst_solve_batched")
         return ids, msf_off, totals
@@ -277,7 +286,7 @@ class Solver:
     def min_edges(self, n, u, v, w, ids=None, stream=None) -> torch.Tensor:
         m = self._list(u, v, w, ids)
         best = torch.empty(max(n, 1), dtype=torch.int64, device=self.device)
-        _check(self.lib.mst_step_min_edges(self.h, n, m, _ptr(u), _ptr(v), _ptr(w), _ptr(ids), _ptr(best),
+        self._check(self.lib.mst_step_min_edges(self.h, n, m, _ptr(u), _ptr(v), _ptr(w), _ptr(ids), _ptr(best),
                                            _stream(stream)), "mst_step_min_edges")
         return best[:n]
 
@@ -286,14 +295,14 @@ class Solver:
         parent = torch.empty(max(n, 1), dtype=torch.int32, device=self.device)
         nbits = (id_bound if id_bound is not None else m) + 1
         chosen = torch.zeros((nbits + 31) // 32, dtype=torch.int32, device=self.device)
-        _check(self.lib.mst_step_contract(self.h, n, m, _ptr(u), _ptr(v), _ptr(w), _ptr(ids), _ptr(parent),
+        self._check(self.lib.mst_step_contract(self.h, n, m, _ptr(u), _ptr(v), _ptr(w), _ptr(ids), _ptr(parent),
                                           _ptr(chosen), _stream(stream)), "mst_step_contract")
         return parent[:n], chosen
 
     def relabel(self, n, u, v, w, ids, label, stream=None):
         m = self._list(u, v, w, ids)
         (ou, ov, ow, oi), cnt = self._outlist(m)
-        _check(self.lib.mst_step_relabel(self.h, n, m, _ptr(u), _ptr(v), _ptr(w), _ptr(ids), _ptr(label), _ptr(ou),
+        self._check(self.lib.mst_step_relabel(self.h, n, m, _ptr(u), _ptr(v), _ptr(w), _ptr(ids), _ptr(label), _ptr(ou),
                                          _ptr(ov), _ptr(ow), _ptr(oi), _ptr(cnt), _stream(stream)),
                "mst_step_relabel")
         k = int(cnt.item())
@@ -302,7 +311,7 @@ class Solver:
     def dedupe(self, u, v, w, ids, stream=None):
         m = self._list(u, v, w, ids)
         (ou, ov, ow, oi), cnt = self._outlist(m)
-        _check(self.lib.mst_step_dedupe(self.h, m, _ptr(u), _ptr(v), _ptr(w), _ptr(ids), _ptr(ou), _ptr(ov),
+        self._check(self.lib.mst_step_dedupe(self.h, m, _ptr(u), _ptr(v), _ptr(w), _ptr(ids), _ptr(ou), _ptr(ov),
                                         _ptr(ow), _ptr(oi), _ptr(cnt), _stream(stream)), "mst_step_dedupe")
         k = int(cnt.item())
         return ou[:k], ov[:k], ow[:k], oi[:k]
@@ -310,14 +319,14 @@ class Solver:
     def pivot(self, w, ids, state: int, sample: int, stream=None) -> int:
         m = w.numel()
         out = torch.zeros(1, dtype=torch.int64, device=self.device)
-        _check(self.lib.mst_step_pivot(self.h, m, _ptr(w), _ptr(ids), state, sample, _ptr(out), _stream(stream)),
+        self._check(self.lib.mst_step_pivot(self.h, m, _ptr(w), _ptr(ids), state, sample, _ptr(out), _stream(stream)),
                "mst_step_pivot")
         return int(out.item()) & 0xFFFFFFFFFFFFFFFF
 
     def partition(self, u, v, w, ids, pivot: int, stream=None):
         m = self._list(u, v, w, ids)
         (ou, ov, ow, oi), cnt = self._outlist(m)
-        _check(self.lib.mst_step_partition(self.h, m, _ptr(u), _ptr(v), _ptr(w), _ptr(ids), pivot, _ptr(ou),
+        self._check(self.lib.mst_step_partition(self.h, m, _ptr(u), _ptr(v), _ptr(w), _ptr(ids), pivot, _ptr(ou),
                                            _ptr(ov), _ptr(ow), _ptr(oi), _ptr(cnt), _stream(stream)),
                "mst_step_partition")
         k = int(cnt.item())
@@ -326,7 +335,7 @@ class Solver:
     def filter(self, n, u, v, w, ids, pivot: int, P: torch.Tensor, stream=None):
         m = self._list(u, v, w, ids)
         (ou, ov, ow, oi), cnt = self._outlist(m)
-        _check(self.lib.mst_step_filter(self.h, n, m, _ptr(u), _ptr(v), _ptr(w), _ptr(ids), pivot, _ptr(P),
+        self._check(self.lib.mst_step_filter(self.h, n, m, _ptr(u), _ptr(v), _ptr(w), _ptr(ids), pivot, _ptr(P),
                                         _ptr(ou), _ptr(ov), _ptr(ow), _ptr(oi), _ptr(cnt), _stream(stream)),
                "mst_step_filter")
         k = int(cnt.item())
@@ -336,7 +345,7 @@ class Solver:
         m = self._list(src, dst, w, None)
         parent = torch.empty(max(n, 1), dtype=torch.int32, device=self.device)
         chosen = torch.zeros((m + 32) // 32, dtype=torch.int32, device=self.device)
-        _check(self.lib.mst_step_tile_contract(self.h, n, m, _ptr(src), _ptr(dst), _ptr(w), tile_vertices,
+        self._check(self.lib.mst_step_tile_contract(self.h, n, m, _ptr(src), _ptr(dst), _ptr(w), tile_vertices,
                                                _ptr(parent), _ptr(chosen), _stream(stream)), "mst_step_tile_contract")
         return parent[:n], chosen
 
@@ -344,7 +353,7 @@ class Solver:
         ids = torch.empty(max(m, 1), dtype=torch.int32, device=self.device)
         cnt = torch.zeros(1, dtype=torch.int32, device=self.device)
         tot = torch.zeros(1, dtype=torch.int64, device=self.device)
-        _check(self.lib.mst_step_finalize(self.h, m, _ptr(chosen), _ptr(w), _ptr(ids), _ptr(cnt), _ptr(tot),
+        self._check(self.lib.mst_step_finalize(self.h, m, _ptr(chosen), _ptr(w), _ptr(ids), _ptr(cnt), _ptr(tot),
                                           _stream(stream)), "mst_step_finalize")
         return Forest(ids, cnt, tot)
 

@@ -179,10 +179,13 @@ def mix(num_graphs: int, seed: int = DEFAULT_SEED, log_lo: int = 8, log_hi: int 
     np.cumsum(m, out=off[1:])
     total = int(off[-1])
     src, dst, w = _empty(total)
-    nt = _threads(nthreads)
-    for g in range(num_graphs):
+
+    def fill(g):  # graphs are independent: one generator thread each (the C call releases the GIL)
         lo = int(off[g])
-        lib.gen_mix_graph(seed, g, log_lo, log_hi, nt, _p32(src[lo:]), _p32(dst[lo:]), _p32(w[lo:]))
+        lib.gen_mix_graph(seed, g, log_lo, log_hi, 1, _p32(src[lo:]), _p32(dst[lo:]), _p32(w[lo:]))
+    from concurrent.futures import ThreadPoolExecutor
+    with ThreadPoolExecutor(max_workers=_threads(nthreads)) as ex:
+        list(ex.map(fill, range(num_graphs)))
     return Batch(n, off, src, dst, w, kind)
 
 

@@ -1,0 +1,132 @@
+"""GPU: batched and served solves give every graph exactly its own MSF.
+
+The batched call solves the disjoint union of many graphs; the server batches
+requests of different sizes as they arrive and keeps several batches in
+flight.  Each response must equal the oracle's forest of that graph (ids and
+uint64 weight), and the same whether the graph is solved alone or in a mix."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2302_12199_gb300 import workloads as W
+from paper_2302_12199_gb300.mst import Solver
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def dev():
+    assert torch.cuda.is_available(), "a CUDA GPU is required for the gpu tests"
+    return torch.device("cuda", 0)
+
+
+def to_dev(a, dev):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.uint32).view(np.int32)).to(dev)
+
+
+def oracle_answers(b):
+    out = []
+    for g in range(b.num_graphs):
+        gr = b.graph(g)
+        out.append(oracle.kruskal(gr.n, gr.src, gr.dst, gr.w))
+    return out
+
+
+@pytest.mark.parametrize("cfg", [dict(variant="boruvka", dedupe="none"), dict(variant="filter"),
+                                 dict(variant="boruvka", dedupe="hash", tile_contract=1, tile_vertices=256)])
+def test_batched_mix_matches_oracle(dev, cfg):
+    b = W.mix(60, 91, log_lo=6, log_hi=13)
+    exp = oracle_answers(b)
+    s = Solver(0, **cfg)
+    try:
+        ids, moff, tot = s.solve_batched(b.n, b.edge_off, to_dev(b.src, dev), to_dev(b.dst, dev), to_dev(b.w, dev))
+        ids = ids.cpu().numpy().view(np.uint32)
+        moff = moff.cpu().numpy().astype(np.int64)
+        tot = tot.cpu().numpy().view(np.uint64)
+        for g, (kid, ktot) in enumerate(exp):
+            assert np.array_equal(ids[moff[g]:moff[g + 1]], kid), g
+            assert int(tot[g]) == ktot, g
+    finally:
+        s.close()
+
+
+def test_batched_with_empty_and_tiny_graphs(dev):
+    n = np.array([1, 5, 3, 1, 4], dtype=np.uint32)
+    src = np.array([0, 1, 2, 3, 0, 1, 2, 0, 0, 1], dtype=np.uint32)
+    dst = np.array([1, 2, 3, 4, 4, 2, 0, 0, 1, 0], dtype=np.uint32)
+    w = np.array([5, 1, 2, 3, 4, 7, 7, 9, 2, 2], dtype=np.uint32)
+    off = np.array([0, 0, 5, 7, 8, 10], dtype=np.uint64)
+    s = Solver(0)
+    try:
+        ids, moff, tot = s.solve_batched(n, off, to_dev(src, dev), to_dev(dst, dev), to_dev(w, dev))
+        ids = ids.cpu().numpy().view(np.uint32)
+        moff = moff.cpu().numpy().astype(np.int64)
+        tot = tot.cpu().numpy().view(np.uint64)
+        for g in range(5):
+            lo, hi = int(off[g]), int(off[g + 1])
+            kid, ktot = oracle.kruskal(int(n[g]), src[lo:hi], dst[lo:hi], w[lo:hi])
+            assert np.array_equal(ids[moff[g]:moff[g + 1]], kid) and int(tot[g]) == ktot, g
+    finally:
+        s.close()
+
+
+def test_served_responses_alone_and_in_the_mix(dev):
+    from paper_2302_12199_gb300.serve import PoolGraph, Response, Server, poisson_arrivals
+    b = W.mix(24, 92, log_lo=6, log_hi=12)
+    exp = oracle_answers(b)
+    pool = []
+    for g in range(b.num_graphs):
+        gr = b.graph(g)
+        pool.append(PoolGraph(gr.n, to_dev(gr.src, dev), to_dev(gr.dst, dev), to_dev(gr.w, dev)))
+    expected = {g: Response(kid, ktot) for g, (kid, ktot) in enumerate(exp)}
+    # a small budget forces several batches; two slots keep batches in flight together
+    server = Server(0, slots=2, budget_bytes=4 << 20, max_batch=16, stall_seconds=20.0)
+    try:
+        for g in range(len(pool)):  # alone
+            r = server.solve_alone(pool[g])
+            assert np.array_equal(r.ids, expected[g].ids) and r.total == expected[g].total, g
+        arr = poisson_arrivals(20000.0, 0.02, seed=5)
+        picks = np.random.default_rng(6).integers(0, len(pool), arr.size)
+        st = server.run(pool, picks, arr, expected=expected, rate=20000.0, seconds=0.02)  # in the mix
+        assert st.requests == arr.size and st.mismatches == 0
+        assert st.batches >= 2 and sum(st.batch_sizes) == arr.size
+        assert max(st.batch_sizes) <= 16
+        assert np.all(st.latency > 0)
+        # the same server serves a second stream
+        arr2 = poisson_arrivals(5000.0, 0.02, seed=7)
+        picks2 = np.random.default_rng(8).integers(0, len(pool), arr2.size)
+        st2 = server.run(pool, picks2, arr2, expected=expected, rate=5000.0, seconds=0.02)
+        assert st2.requests == arr2.size and st2.mismatches == 0
+        # one request larger than the whole budget is still admitted, alone
+        tiny = Server(0, slots=1, budget_bytes=1, max_batch=8, stall_seconds=20.0)
+        try:
+            st1 = tiny.run(pool, np.arange(6) % len(pool), np.linspace(0, 1e-3, 6), expected=expected)
+            assert st1.mismatches == 0 and st1.batch_sizes == [1] * 6
+        finally:
+            tiny.close()
+    finally:
+        server.close()
+
+
+def test_batched_forest_capacity_residues(dev):
+    """The forest count and weight follow the id array in one allocation: every
+    residue of its capacity modulo 64 ids must keep them inside it."""
+    s = Solver(0)
+    try:
+        for total_n in range(60, 70):
+            n = np.array([total_n // 2, total_n - total_n // 2], dtype=np.uint32)
+            parts = [W.gnm(int(k), 3 * int(k), 100 + total_n + i) for i, k in enumerate(n)]
+            src = np.concatenate([p.src for p in parts])
+            dst = np.concatenate([p.dst for p in parts])
+            w = np.concatenate([p.w for p in parts])
+            off = np.array([0, parts[0].m, parts[0].m + parts[1].m], dtype=np.uint64)
+            ids, moff, tot = s.solve_batched(n, off, to_dev(src, dev), to_dev(dst, dev), to_dev(w, dev))
+            ids = ids.cpu().numpy().view(np.uint32)
+            moff = moff.cpu().numpy().astype(np.int64)
+            tot = tot.cpu().numpy().view(np.uint64)
+            for g, p in enumerate(parts):
+                kid, ktot = oracle.kruskal(p.n, p.src, p.dst, p.w)
+                assert np.array_equal(ids[moff[g]:moff[g + 1]], kid) and int(tot[g]) == ktot, (total_n, g)
+    finally:
+        s.close()
