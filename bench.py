@@ -448,7 +448,7 @@ def batched_main(args, rank: int, world: int, local_rank: int):
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=dev)
     G = args.graphs
-    b = W.mix(G, W.DEFAULT_SEED + rank)
+    b = W.mix(G, W.DEFAULT_SEED + rank, log_hi=args.log_hi)
     n_per = np.asarray(b.n, dtype=np.uint32)
     off = np.asarray(b.edge_off, dtype=np.uint64)
     m_tot = int(off[-1])
@@ -576,7 +576,8 @@ def batched_main(args, rank: int, world: int, local_rank: int):
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
         "config": {"workload": "batched", "graphs": G, "n_total": n_tot, "m_total": m_tot,
-                   "mix": "n log-uniform [2^8,2^16]; 1/3 GNM deg 4-32, 1/3 RGG2D deg 8, 1/3 RMAT deg 16; w in [1,255]",
+                   "mix": f"n log-uniform [2^8,2^{args.log_hi}]; 1/3 GNM deg 4-32, 1/3 RGG2D deg 8, "
+                          "1/3 RMAT deg 16; w in [1,255]",
                    "autotuned": best, "autotune_trials_s": {k: v for k, v in tuning},
                    "parallelism": f"replicas{world}" if world > 1 else "single",
                    "l2": "inputs (12 B/edge) larger than L2, no flush"},
@@ -677,6 +678,7 @@ def main():
     ap.add_argument("--workload", default="rmat_filter", choices=sorted(WORKLOADS) + ["batched", "served"])
     ap.add_argument("--graphs", type=int, default=4096, help="graphs per batch (--workload batched)")
     ap.add_argument("--no-autotune", action="store_true", help="batched: skip the configuration autotuner")
+    ap.add_argument("--log-hi", type=int, default=16, help="batched: graphs have n log-uniform in [2^8, 2^log_hi]")
     ap.add_argument("--pool", type=int, default=256, help="served: distinct request graphs")
     ap.add_argument("--slots", type=int, default=3, help="served: solver slots (batches in flight)")
     ap.add_argument("--slot-budget-gb", type=float, default=6.0, help="served: device memory per slot's batch")

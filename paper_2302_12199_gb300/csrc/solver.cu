@@ -5,6 +5,7 @@
 // Device memory: each handle owns a CUDA memory pool; every solve allocates its
 // scratch from it in stream order and returns it at the end, so repeated solves
 // reuse the same memory without device-wide synchronisation.
+#include <algorithm>
 #include <cstddef>
 #include <cstdint>
 #include <cstring>
@@ -769,13 +770,34 @@ mst_status record_cuda(mst_ctx *c, int line) {
 
 // ---------------------------------------------------------------- batched
 
+// Graph of union position e: the largest g with off[g] <= e (graphs are
+// contiguous ranges of positions; empty graphs are passed over).
+__device__ __forceinline__ uint32_t batch_graph_of(const uint64_t *off, uint32_t G, uint64_t e) {
+  uint32_t lo = 0, hi = G;
+  while (hi - lo > 1) {
+    const uint32_t mid = (lo + hi) / 2;
+    if (off[mid] <= e)
+      lo = mid;
+    else
+      hi = mid;
+  }
+  return lo;
+}
+
+// Union vertex ids: edge e of graph g gets its ends offset by vert_off[g].
+// Each block takes a contiguous chunk of edges (so a thread walks forward
+// through few graphs), independent of how the edges split into graphs.
 __global__ void batch_offset_kernel(const uint32_t *src, const uint32_t *dst, const uint64_t *edge_off,
                                     const uint64_t *vert_off, uint32_t *usrc, uint32_t *udst, const uint32_t *gn,
-                                    uint32_t *err) {
-  const uint32_t g = blockIdx.x;
-  const uint64_t lo = edge_off[g], hi = edge_off[g + 1];
-  const uint32_t vo = (uint32_t)vert_off[g], ng = gn[g];
-  for (uint64_t e = lo + threadIdx.x; e < hi; e += blockDim.x) {
+                                    uint32_t G, uint64_t m, uint32_t *err) {
+  const uint64_t chunk = ((m + gridDim.x - 1) / gridDim.x + blockDim.x - 1) / blockDim.x * blockDim.x;
+  const uint64_t lo = (uint64_t)blockIdx.x * chunk, hi = min(m, lo + chunk);
+  uint64_t e = lo + threadIdx.x;
+  if (e >= hi) return;
+  uint32_t g = batch_graph_of(edge_off, G, e);
+  for (; e < hi; e += blockDim.x) {
+    while (edge_off[g + 1] <= e) ++g;
+    const uint32_t vo = (uint32_t)vert_off[g], ng = gn[g];
     const uint32_t a = src[e], b = dst[e];
     if (a >= ng || b >= ng) atomicOr(err, ERR_VERTEX);
     usrc[e] = a < ng ? a + vo : vo;
@@ -783,49 +805,59 @@ __global__ void batch_offset_kernel(const uint32_t *src, const uint32_t *dst, co
   }
 }
 
-// Splits the ascending union ids by graph: offsets by binary search, local ids
-// and per-graph weight sums.
-__global__ void batch_split_kernel(const uint32_t *ids, const uint32_t *count, const uint64_t *edge_off,
-                                   uint32_t num_graphs, const uint32_t *w, uint32_t *out_ids, uint64_t *msf_off,
-                                   u64 *total_weight) {
-  __shared__ u64 s_sum[32];
-  __shared__ uint64_t s_lo, s_hi;
-  const uint32_t g = blockIdx.x;
+// Segment offsets of the per-graph forests in the ascending union ids:
+// msf_off[g] = number of union ids below edge_off[g] (g = 0..G).
+__global__ void batch_seg_kernel(const uint32_t *ids, const uint32_t *count, const uint64_t *edge_off, uint32_t G,
+                                 uint64_t *msf_off) {
+  const uint32_t g = blockIdx.x * blockDim.x + threadIdx.x;
+  if (g > G) return;
+  const uint64_t target = edge_off[g];
+  uint64_t lo = 0, hi = *count;
+  while (lo < hi) {
+    const uint64_t mid = (lo + hi) / 2;
+    if ((uint64_t)ids[mid] < target)
+      lo = mid + 1;
+    else
+      hi = mid;
+  }
+  msf_off[g] = lo;
+}
+
+// Graph-local ids and per-graph weight sums (total_weight zeroed before).
+// Contiguous chunks per block; a warp adds up the weights of each run of ids
+// of one graph and issues one atomic per run.
+__global__ void batch_split_kernel(const uint32_t *ids, const uint32_t *count, const uint64_t *edge_off, uint32_t G,
+                                   const uint32_t *w, uint32_t *out_ids, u64 *total_weight) {
   const uint64_t k = *count;
-  if (threadIdx.x == 0) {
-    for (int side = 0; side < 2; ++side) {
-      const uint64_t target = edge_off[g + side];
-      uint64_t lo = 0, hi = k;
-      while (lo < hi) {
-        const uint64_t mid = (lo + hi) / 2;
-        if ((uint64_t)ids[mid] < target)
-          lo = mid + 1;
-        else
-          hi = mid;
+  const uint64_t chunk = ((k + gridDim.x - 1) / gridDim.x + blockDim.x - 1) / blockDim.x * blockDim.x;
+  const uint64_t lo = (uint64_t)blockIdx.x * chunk, hi = min(k, lo + chunk);
+  const int lane = threadIdx.x & 31;
+  uint32_t g = 0;
+  bool first = true;
+  for (uint64_t b0 = lo; b0 < hi; b0 += blockDim.x) {  // warp-uniform trip count
+    const uint64_t i = b0 + threadIdx.x;
+    const bool in = i < hi;
+    u64 v = 0;
+    uint32_t gi = 0xffffffffu;
+    if (in) {
+      const uint32_t id = ids[i];
+      if (first) {
+        g = batch_graph_of(edge_off, G, id);
+        first = false;
       }
-      if (side == 0)
-        s_lo = lo;
-      else
-        s_hi = lo;
+      while (edge_off[g + 1] <= id) ++g;
+      out_ids[i] = (uint32_t)((uint64_t)id - edge_off[g]);
+      v = w[id];
+      gi = g;
     }
-    msf_off[g] = s_lo;
-    if (g == num_graphs - 1) msf_off[num_graphs] = s_hi;
-  }
-  __syncthreads();
-  u64 sum = 0;
-  const uint64_t base = edge_off[g];
-  for (uint64_t i = s_lo + threadIdx.x; i < s_hi; i += blockDim.x) {
-    const uint32_t id = ids[i];
-    sum += w[id];
-    out_ids[i] = (uint32_t)((uint64_t)id - base);
-  }
-  for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
-  if ((threadIdx.x & 31) == 0) s_sum[threadIdx.x >> 5] = sum;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    u64 t = 0;
-    for (unsigned i = 0; i < blockDim.x / 32; ++i) t += s_sum[i];
-    total_weight[g] = t;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {  // segmented inclusive sum over runs of equal graph
+      const u64 pv = __shfl_up_sync(0xffffffffu, v, o);
+      const uint32_t pg = __shfl_up_sync(0xffffffffu, gi, o);
+      if (lane >= o && pg == gi) v += pv;
+    }
+    const uint32_t ng = __shfl_down_sync(0xffffffffu, gi, 1);
+    if (in && (lane == 31 || ng != gi)) atomicAdd(total_weight + gi, v);
   }
 }
 
@@ -1057,13 +1089,18 @@ mst_status mst_solve_batched(mst_handle h, uint32_t num_graphs, const uint32_t *
       cudaMemcpyAsync(d_gn, h_n, num_graphs * 4, cudaMemcpyHostToDevice, s) != cudaSuccess ||
       cudaMemsetAsync(&h->ds->err, 0, 4, s) != cudaSuccess)
     return record_cuda(h, __LINE__);
-  batch_offset_kernel<<<num_graphs, 256, 0, s>>>(d_src, d_dst, d_eoff, d_voff, usrc, udst, d_gn, &h->ds->err);
+  const unsigned grid = (unsigned)std::max<uint64_t>(1, std::min<uint64_t>((m + 2047) / 2048, (uint64_t)h->sms * 8));
+  if (m > 0)
+    batch_offset_kernel<<<grid, 256, 0, s>>>(d_src, d_dst, d_eoff, d_voff, usrc, udst, d_gn, num_graphs, m,
+                                             &h->ds->err);
   st = readback(h, s);
   if (st != MST_OK) return record(h, st);
   st = solve_device(h, n, m, usrc, udst, d_w, ids, d_count, d_sum, s);
   if (st != MST_OK) return record(h, st);
-  batch_split_kernel<<<num_graphs, 256, 0, s>>>(ids, d_count, d_eoff, num_graphs, d_w, d_msf_ids, d_msf_off,
-                                                (u64 *)d_total_weight);
+  if (cudaMemsetAsync(d_total_weight, 0, (size_t)num_graphs * 8, s) != cudaSuccess) return record_cuda(h, __LINE__);
+  batch_seg_kernel<<<(num_graphs + 1 + 255) / 256, 256, 0, s>>>(ids, d_count, d_eoff, num_graphs, d_msf_off);
+  const unsigned sgrid = (unsigned)std::max<uint64_t>(1, std::min<uint64_t>((cap + 2047) / 2048, (uint64_t)h->sms * 8));
+  batch_split_kernel<<<sgrid, 256, 0, s>>>(ids, d_count, d_eoff, num_graphs, d_w, d_msf_ids, (u64 *)d_total_weight);
   if (cudaStreamSynchronize(s) != cudaSuccess) return record_cuda(h, __LINE__);
   return record(h, MST_OK);
 }

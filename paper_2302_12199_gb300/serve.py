@@ -61,6 +61,7 @@ class ServeStats:
     batch_sizes: List[int] = field(default_factory=list)
     max_in_flight: int = 0      # most batches on the device at once
     mismatches: int = 0         # responses that differ from the expected ones
+    phases_ms: dict = field(default_factory=dict)  # mean host time per batch by phase
 
     def summary(self) -> dict:
         lat = self.latency * 1e3
@@ -69,7 +70,8 @@ class ServeStats:
                 "graphs_per_s": self.requests / self.wall if self.wall > 0 else 0.0,
                 "latency_ms": pct, "batches": self.batches,
                 "mean_batch": float(np.mean(self.batch_sizes)) if self.batch_sizes else 0.0,
-                "max_batches_in_flight": self.max_in_flight, "mismatches": self.mismatches}
+                "max_batches_in_flight": self.max_in_flight, "mismatches": self.mismatches,
+                "batch_phases_ms": self.phases_ms}
 
 
 def poisson_arrivals(rate: float, seconds: float, seed: int) -> np.ndarray:
@@ -89,6 +91,8 @@ class _Slot:
         self.stream = torch.cuda.Stream(device=self.dev)
         self.cap = 0
         self.bufs = None
+        self.pinned = None
+        self.phases = []  # (gather, solve, copy back) host seconds per batch
         self.busy = False
         self.job = None
         self.cv = threading.Condition()
@@ -108,17 +112,26 @@ class _Slot:
         off = np.zeros(len(graphs) + 1, dtype=np.uint64)
         np.cumsum([g.m for g in graphs], out=off[1:])
         src, dst, w = (b[:m] for b in self.bufs)
+        t0 = time.perf_counter()
         with torch.cuda.stream(self.stream):
-            for g, lo in zip(graphs, off[:-1]):
-                lo, hi = int(lo), int(lo) + g.m
-                src[lo:hi].copy_(g.src, non_blocking=True)
-                dst[lo:hi].copy_(g.dst, non_blocking=True)
-                w[lo:hi].copy_(g.w, non_blocking=True)
+            if m:  # gather the batch: one concatenation per array
+                torch.cat([g.src for g in graphs], out=src)
+                torch.cat([g.dst for g in graphs], out=dst)
+                torch.cat([g.w for g in graphs], out=w)
+            t1 = time.perf_counter()
             ids, moff, tot = self.solver.solve_batched(n_per, off, src, dst, w, stream=self.stream)
-            out = (ids.cpu().numpy().view(np.uint32), moff.cpu().numpy().astype(np.int64),
-                   tot.cpu().numpy().view(np.uint64))
+            t2 = time.perf_counter()
+            moff_h = moff.cpu().numpy().astype(np.int64)
+            k = int(moff_h[-1])  # copy back only the forests, through pinned memory
+            if self.pinned is None or self.pinned.numel() < k:
+                self.pinned = torch.empty(max(k, 1 << 16), dtype=torch.int32, pin_memory=True)
+            self.pinned[:k].copy_(ids[:k], non_blocking=True)
+            tot_h = tot.cpu().numpy().view(np.uint64)
         self.stream.synchronize()
-        return out
+        t3 = time.perf_counter()
+        self.phases.append((t1 - t0, t2 - t1, t3 - t2))
+        # the ids view stays valid until this slot's next solve
+        return self.pinned[:k].numpy().view(np.uint32), moff_h, tot_h
 
     def workspace_bytes(self, n: int, m: int) -> int:
         return self.solver.workspace_bytes(n, m)
@@ -138,7 +151,7 @@ class Server:
                  config: Optional[dict] = None, stall_seconds: float = 60.0, slot_factory=None):
         self.device = device
         self.stall_seconds = float(stall_seconds)
-        self.config = dict(config or dict(variant="boruvka", dedupe="none", tile_contract=0))
+        self.config = dict(config or dict(variant="filter", dedupe="none", tile_contract=0))
         make = slot_factory or (lambda: _Slot(device, self.config))
         self.slots = [make() for _ in range(slots)]
         self.budget = int(budget_bytes)
@@ -165,7 +178,11 @@ class Server:
         foot = {int(p): self.footprint(pool[int(p)]) for p in np.unique(picks)}
         done_at = np.zeros(nreq)
         lock = threading.Lock()
-        state = {"in_flight": 0, "max_in_flight": 0, "mismatches": 0, "batches": 0, "sizes": [], "error": None}
+        state = {"in_flight": 0, "max_in_flight": 0, "mismatches": 0, "batches": 0, "sizes": [], "error": None,
+                 "verify": []}
+        for slot in self.slots:
+            if hasattr(slot, "phases"):
+                slot.phases.clear()
 
         clock0 = [time.perf_counter()]
 
@@ -182,6 +199,7 @@ class Server:
                 try:
                     ids, moff, tot = slot.solve([pool[int(picks[i])] for i in batch])
                     t_done = time.perf_counter() - clock0[0]
+                    tv = time.perf_counter()
                     bad = 0
                     if expected is not None:
                         for k, i in enumerate(batch):
@@ -193,6 +211,7 @@ class Server:
                         for i in batch:
                             done_at[i] = t_done
                         state["mismatches"] += bad
+                        state["verify"].append(time.perf_counter() - tv)
                         state["in_flight"] -= 1
                 except Exception as exc:  # surface the first failure to the scheduler
                     with lock:
@@ -261,9 +280,18 @@ class Server:
             raise state["error"]
         latency = done_at - arrivals
         wall = float(done_at.max()) if nreq else 0.0
+        ph = [p for slot in self.slots for p in getattr(slot, "phases", [])]
+        phases_ms = {}
+        if ph:
+            a = np.asarray(ph) * 1e3
+            phases_ms = {"gather": float(a[:, 0].mean()), "solve": float(a[:, 1].mean()),
+                         "copy_back": float(a[:, 2].mean())}
+        if state["verify"]:
+            phases_ms["verify"] = float(np.mean(state["verify"]) * 1e3)
         return ServeStats(rate=rate, seconds=seconds, requests=nreq, wall=wall, latency=latency,
                           batches=state["batches"], batch_sizes=state["sizes"],
-                          max_in_flight=state["max_in_flight"], mismatches=state["mismatches"])
+                          max_in_flight=state["max_in_flight"], mismatches=state["mismatches"],
+                          phases_ms=phases_ms)
 
     def close(self):
         for s in self.slots:
