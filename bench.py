@@ -295,6 +295,8 @@ def gpu_main(args, rank: int, world: int, local_rank: int):
         cfg["tile_contract"] = args.tile_contract
     if args.tile_vertices is not None:
         cfg["tile_vertices"] = args.tile_vertices
+    if args.base_case is not None:
+        cfg["base_case"] = args.base_case
     g = gen(W)
     n, m = g.n, g.m
     src = torch.from_numpy(g.src.view(np.int32)).to(dev)
@@ -476,6 +478,8 @@ def batched_main(args, rank: int, world: int, local_rank: int):
         best, tuning = dict(variant="boruvka", dedupe="none", tile_contract=0), []
     else:
         best, tuning = autotune(trial, reps=1)
+    if args.base_case is not None:
+        best["base_case"] = args.base_case
     solver = Solver(local_rank, **best)
     for _ in range(args.warmup):
         timed_batch(solver)
@@ -622,7 +626,10 @@ def served_main(args, rank: int, world: int, local_rank: int):
     to_dev = lambda a: torch.from_numpy(np.ascontiguousarray(a).view(np.int32)).to(dev)
     pool = [PoolGraph(int(b.n[g]), to_dev(b.src[off[g]:off[g + 1]]), to_dev(b.dst[off[g]:off[g + 1]]),
                       to_dev(b.w[off[g]:off[g + 1]])) for g in range(args.pool)]
-    server = Server(local_rank, slots=args.slots, budget_bytes=int(args.slot_budget_gb * (1 << 30)))
+    scfg = dict(variant="filter", dedupe="none", tile_contract=0)
+    if args.base_case is not None:
+        scfg["base_case"] = args.base_case
+    server = Server(local_rank, slots=args.slots, budget_bytes=int(args.slot_budget_gb * (1 << 30)), config=scfg)
     expected = {g: server.solve_alone(pool[g]) for g in range(args.pool)}  # each graph solved alone
     for s in server.slots:  # warm every slot
         s.solve(pool[:8])
@@ -696,6 +703,7 @@ def main():
     ap.add_argument("--filter-min-edges", type=int, default=None)
     ap.add_argument("--tile-contract", type=int, default=None, choices=[-1, 0, 1])
     ap.add_argument("--tile-vertices", type=int, default=None)
+    ap.add_argument("--base-case", type=int, default=None, choices=[0, 1])
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "gpu":
         args.warmup = 3

@@ -66,6 +66,10 @@ typedef struct {
   uint64_t filter_min_edges;   /* isSparse: lists shorter than this are not partitioned */
   float filter_max_avg_degree; /* isSparse: stop partitioning at average degree 2m/n <= this (the paper's
                                   Section 6.3 uses 4; the default 1 is the measured optimum on GB300) */
+  int base_case;               /* 1 (default): once a Borůvka call's live components (<= 4096) and
+                                  edges (<= 6144) fit one block's shared memory, finish its rounds in
+                                  one launch (the role of the paper's base case, Section 4.4); 0: run
+                                  every round globally */
 } mst_config;
 
 /* Fills *cfg with the defaults (Borůvka variant, automatic dedupe, pivot sample
@@ -144,6 +148,7 @@ enum {
   MST_K_FILTER,         /* filtering of heavy edges */
   MST_K_FINALIZE,       /* bitmap -> ascending ids + weight */
   MST_K_TILE,           /* tile-local contraction (count, bucket, contract) */
+  MST_K_BASE,           /* single-block base case (the last rounds of a Borůvka call) */
   MST_K_COUNT
 };
 typedef struct {

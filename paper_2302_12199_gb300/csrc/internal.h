@@ -147,6 +147,21 @@ bool launch_tile_contract(uint32_t n, uint32_t B, uint64_t nlocal, const u64 *cu
                           uint32_t *bits, EdgeOut rest, u64 *rest_fill, uint32_t *err, cudaStream_t s);
 void launch_tile_sample(EdgeList in, uint64_t m, uint32_t n, uint32_t B, u64 state, uint32_t samples,
                         uint32_t *local_count, cudaStream_t s);
+// single-block base case: the last rounds of a Borůvka call in one launch
+constexpr uint32_t BASE_MAX_N = 4096;  // live components (16-bit local ends; shared-memory vertex arrays)
+constexpr uint64_t BASE_MAX_M = 6144;  // live edges (fit the tile kernel's shared-memory edge capacity)
+struct BaseScratch {
+  uint32_t *loc;      // [n] local index of each live component (only those entries are written)
+  uint32_t *ends;     // [m] packed local ends
+  u64 *cutmin;        // [BASE_MAX_N] all ones (no cut limit)
+  u64 *offsets;       // [2]
+  uint32_t *plocal;   // [BASE_MAX_N] local root of each live component
+  EdgeOut rest;       // [m] edges left between final components (discarded)
+  u64 *rest_fill;
+};
+// False (nothing launched) when the call does not fit the base case.
+bool launch_base_case(const uint32_t *act, uint32_t n_act, EdgeList cur, uint64_t m, uint32_t *parent, uint32_t *bits,
+                      const BaseScratch &b, uint32_t *err, cudaStream_t s);
 void launch_iota(uint32_t *p, uint64_t n, int sms, cudaStream_t s);
 void launch_u64_to_u32(const u64 *src, uint32_t *dst, cudaStream_t s);
 

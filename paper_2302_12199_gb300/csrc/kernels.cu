@@ -1542,6 +1542,53 @@ __global__ void __launch_bounds__(TC_THREADS) tile_contract_kernel(uint32_t n, u
   }
 }
 
+// ---------------------------------------------------- single-block base case
+
+// Once the live components and edges of a Borůvka call fit in one block's
+// shared memory, the remaining rounds run in one launch of the tile kernel on
+// a single tile with no cut limit (every component hooks along its minimum
+// edge), instead of a few launches and a host readback per round.  The live
+// components get local indices 0..k-1 (their position in the active list).
+__global__ void base_map_kernel(const uint32_t *act, uint32_t n_act, uint32_t *loc, u64 *offsets, uint64_t m) {
+  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n_act) loc[act[i]] = i;
+  if (i == 0) {
+    offsets[0] = 0;
+    offsets[1] = m;
+  }
+}
+
+// Local ends of each list edge through the current roots (parent[] after the
+// last jump points every listed end at its root, which is in the active list).
+__global__ void base_pack_kernel(const uint32_t *u, const uint32_t *v, uint64_t m, const uint32_t *parent,
+                                 const uint32_t *loc, uint32_t *ends) {
+  for (uint64_t e = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m; e += (uint64_t)gridDim.x * blockDim.x)
+    ends[e] = loc[parent[u[e]]] | (loc[parent[v[e]]] << 16);
+}
+
+// New roots back to global ids: a live root takes the global id of its local
+// root; vertices that were already merged keep their parent.
+__global__ void base_unmap_kernel(const uint32_t *act, uint32_t n_act, const uint32_t *plocal, uint32_t *parent) {
+  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n_act) return;
+  const uint32_t g = act[i];
+  if (parent[g] == g) parent[g] = act[plocal[i]];
+}
+
+bool launch_base_case(const uint32_t *act, uint32_t n_act, EdgeList cur, uint64_t m, uint32_t *parent, uint32_t *bits,
+                      const BaseScratch &b, uint32_t *err, cudaStream_t s) {
+  if (n_act == 0 || n_act > BASE_MAX_N || m > BASE_MAX_M || !cur.id) return false;
+  base_map_kernel<<<(n_act + 255) / 256, 256, 0, s>>>(act, n_act, b.loc, b.offsets, m);
+  if (m) base_pack_kernel<<<(unsigned)((m + 255) / 256), 256, 0, s>>>(cur.u, cur.v, m, parent, b.loc, b.ends);
+  cudaMemsetAsync(b.cutmin, 0xff, (size_t)n_act * 8, s);
+  cudaMemsetAsync(b.rest_fill, 0, sizeof(u64), s);
+  if (!launch_tile_contract(n_act, n_act, m, b.cutmin, b.offsets, b.ends, cur.w, cur.id, b.plocal, bits, b.rest,
+                            b.rest_fill, err, s))
+    return false;
+  base_unmap_kernel<<<(n_act + 255) / 256, 256, 0, s>>>(act, n_act, b.plocal, parent);
+  return true;
+}
+
 // Fraction estimate for the automatic switch: counts how many of `samples`
 // random edges (splitmix64) are local.
 __global__ void tile_sample_kernel(EdgeList in, uint64_t m, uint32_t n, uint32_t B, u64 state, uint32_t samples,

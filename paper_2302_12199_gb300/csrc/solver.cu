@@ -430,6 +430,7 @@ struct Solve {
     const int bound = 2 * (ceil_log2(n) + 2);
     for (int r = 1; n_act > 0; ++r) {
       if (r > bound) return MST_ERR_INTERNAL;
+      if (base_case_fits(cur, cur_m, n_act)) return base_case(cur, cur_m, act[a], (uint32_t)n_act);
       ListBuf &out = (cur.u == X.out.u) ? Y : X;
       if (out.cap < cur_m) TRY(out.alloc(c, cur_m, s));
       TRY(zero_counters(c, s));
@@ -496,6 +497,38 @@ struct Solve {
       if (cur_m == 0) break;
     }
     return MST_OK;
+  }
+
+  // The last rounds of a Borůvka call in one block once the live components
+  // and edges fit in its shared memory (the list must carry ids).
+  bool base_case_fits(EdgeList cur, uint64_t cur_m, uint64_t n_act) const {
+    return c->cfg.base_case && cur.id && n_act > 0 && n_act <= BASE_MAX_N && cur_m <= BASE_MAX_M;
+  }
+  mst_status base_case(EdgeList cur, uint64_t cur_m, const uint32_t *act_list, uint32_t n_act) {
+    const size_t a_loc = round_up((size_t)n * 4 + 4, 256), a_ends = round_up(BASE_MAX_M * 4, 256);
+    const size_t a_cut = (size_t)BASE_MAX_N * 8, a_off = 256, a_pl = (size_t)BASE_MAX_N * 4;
+    Buf sb;
+    TRY(sb.alloc(c, a_loc + a_ends + a_cut + a_off + a_pl + 4 * a_ends + 256, s));
+    char *p = sb.as<char>();
+    BaseScratch b{};
+    b.loc = (uint32_t *)p;
+    p += a_loc;
+    b.ends = (uint32_t *)p;
+    p += a_ends;
+    b.cutmin = (u64 *)p;
+    p += a_cut;
+    b.offsets = (u64 *)p;
+    p += a_off;
+    b.plocal = (uint32_t *)p;
+    p += a_pl;
+    b.rest = EdgeOut{(uint32_t *)p, (uint32_t *)(p + a_ends), (uint32_t *)(p + 2 * a_ends), (uint32_t *)(p + 3 * a_ends)};
+    p += 4 * a_ends;
+    b.rest_fill = (u64 *)p;
+    bool launched = false;
+    PROF(MST_K_BASE, 16.0 * (double)cur_m + 28.0 * (double)n_act, -1, 0.0, -1, 0.0,
+         launched = launch_base_case(act_list, n_act, cur, cur_m, parent, bits, b, &c->ds->err, s));
+    if (!launched) return MST_ERR_INTERNAL;
+    return readback(c, s);
   }
 
   // Local preprocessing (Section 4.1) on vertex-range tiles.  When applied,
@@ -731,6 +764,7 @@ mst_status validate_cfg(const mst_config *cfg) {
   if (cfg->pivot_sample == 0 || cfg->pivot_sample > (1u << 24)) return MST_ERR_INVALID_ARG;
   if (!(cfg->filter_max_avg_degree > 0.0f)) return MST_ERR_INVALID_ARG;
   if (cfg->tile_contract < -1 || cfg->tile_contract > 1) return MST_ERR_INVALID_ARG;
+  if (cfg->base_case < 0 || cfg->base_case > 1) return MST_ERR_INVALID_ARG;
   if (cfg->tile_vertices < 32 || cfg->tile_vertices > 4096) return MST_ERR_INVALID_ARG;
   return MST_OK;
 }
@@ -879,6 +913,7 @@ void mst_config_default(mst_config *cfg) {
   cfg->seed = 0x2302121990ULL;
   cfg->filter_min_edges = 1ULL << 20;
   cfg->filter_max_avg_degree = 1.0f;  // measured optimum on GB300 (the paper uses 4 on its cluster)
+  cfg->base_case = 1;
 }
 
 const char *mst_status_string(mst_status s) {

@@ -17,11 +17,12 @@ from tests.golden import fixtures
 pytestmark = pytest.mark.gpu
 
 CONFIGS = [
-    dict(variant="boruvka", dedupe="none", tile_contract=0),
+    dict(variant="boruvka", dedupe="none", tile_contract=0, base_case=0),
     dict(variant="boruvka", dedupe="hash", tile_contract=-1),
     dict(variant="boruvka", dedupe="auto"),
     dict(variant="filter", dedupe="auto", filter_min_edges=1 << 10, pivot_sample=4096, tile_contract=-1),
-    dict(variant="filter", dedupe="none", filter_min_edges=1 << 12, filter_max_avg_degree=4.0, tile_contract=0),
+    dict(variant="filter", dedupe="none", filter_min_edges=1 << 12, filter_max_avg_degree=4.0, tile_contract=0,
+         base_case=0),
     dict(variant="boruvka", tile_contract=1, tile_vertices=512),
     dict(variant="filter", tile_contract=1, tile_vertices=256, filter_min_edges=1 << 10, pivot_sample=4096),
 ]
@@ -354,3 +355,27 @@ def test_tile_contraction_on_and_off_agree(dev):
         ids, tot = gpu_msf(s, g.n, g.src, g.dst, g.w, dev)
         s.close()
         assert np.array_equal(ids, kid) and tot == ktot, tc
+
+
+@pytest.mark.parametrize("family", ["gnm", "rmat", "rgg2", "path", "star"])
+def test_base_case_on_and_off_agree(dev, family):
+    """The single-block base case finishes the last rounds; the forest equals
+    the oracle's with and without it, for both variants."""
+    g = {
+        "gnm": lambda: W.gnm(3000, 20000, 51),
+        "rmat": lambda: W.rmat(13, 60000, 52),
+        "rgg2": lambda: W.rgg(2, 20000, 8.0, 53),
+        "path": lambda: W.Graph(5000, np.arange(4999, dtype=np.uint32), np.arange(1, 5000, dtype=np.uint32),
+                                np.arange(1, 5000, dtype=np.uint32)),
+        "star": lambda: W.Graph(7000, np.zeros(6999, dtype=np.uint32), np.arange(1, 7000, dtype=np.uint32),
+                                (np.arange(6999, dtype=np.uint32) % 7 + 1).astype(np.uint32)),
+    }[family]()
+    kid, ktot = oracle.kruskal(g.n, g.src, g.dst, g.w)
+    for variant in ("boruvka", "filter"):
+        for base in (0, 1):
+            s = Solver(0, variant=variant, base_case=base, filter_min_edges=1 << 10)
+            try:
+                ids, tot = gpu_msf(s, g.n, g.src, g.dst, g.w, dev)
+                assert np.array_equal(ids, kid) and tot == ktot, (variant, base)
+            finally:
+                s.close()
