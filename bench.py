@@ -49,6 +49,10 @@ WORKLOADS = {
               dict(variant="boruvka")),
     "rgg3d": ("RGG3D n=2^21 degree 8, w in [1,2^32-1], plain Boruvka", lambda W: W.rgg3d_large(),
               dict(variant="boruvka")),
+    "grid2d": ("2D grid 2048x2048 (n=2^22, m=8,384,512), w in [1,255], plain Boruvka", lambda W: W.grid2d_large(),
+               dict(variant="boruvka")),
+    "rhg": ("random hyperbolic graph n=2^22, gamma=3, average degree ~16, w in [1,255], plain Boruvka",
+            lambda W: W.rhg_large(), dict(variant="boruvka")),
     "rgg2d_small": ("RGG2D n=2^20 degree 8, w in [1,2^32-1], plain Boruvka (profiling size)",
                     lambda W: W.rgg(2, 1 << 20, 8.0), dict(variant="boruvka")),
 }

@@ -61,6 +61,14 @@ def _load():
         lib.gen_rgg_fill.restype = ctypes.c_uint64
         lib.gen_rgg_fill.argtypes = [ctypes.c_int, ctypes.c_uint64, ctypes.c_double, ctypes.c_uint64, ctypes.c_uint32,
                                      ctypes.c_uint32, _u32p, _u32p, _u32p]
+        lib.gen_grid2d.restype = ctypes.c_uint64
+        lib.gen_grid2d.argtypes = [ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32,
+                                   _u32p, _u32p, _u32p]
+        lib.gen_rhg_radius.restype = ctypes.c_double
+        lib.gen_rhg_radius.argtypes = [ctypes.c_uint64, ctypes.c_double, ctypes.c_double]
+        lib.gen_rhg.restype = ctypes.c_uint64
+        lib.gen_rhg.argtypes = [ctypes.c_uint64, ctypes.c_double, ctypes.c_double, ctypes.c_uint64, ctypes.c_uint32,
+                                ctypes.c_uint32, ctypes.c_int, _u32p, _u32p, _u32p]
         lib.gen_mix_sizes.restype = None
         lib.gen_mix_sizes.argtypes = [ctypes.c_uint64, ctypes.c_uint64, ctypes.c_int, ctypes.c_int, _u32p, _u64p,
                                       _u32p]
@@ -147,6 +155,35 @@ def rgg(dim: int, n: int, deg: float = 8.0, seed: int = DEFAULT_SEED, wmin: int 
     return Graph(n, src, dst, w, f"rgg{dim}d_n{n}")
 
 
+def grid2d(rows: int, cols: int, seed: int = DEFAULT_SEED, wmin: int = 1, wmax: int = 255) -> Graph:
+    """rows x cols 4-neighbour grid (vertex r*cols + c), weights uniform in [wmin, wmax]."""
+    lib = _load()
+    m = int(lib.gen_grid2d(rows, cols, seed, wmin, wmax, None, None, None))
+    src, dst, w = _empty(m)
+    got = int(lib.gen_grid2d(rows, cols, seed, wmin, wmax, _p32(src), _p32(dst), _p32(w)))
+    assert got == m
+    return Graph(rows * cols, src, dst, w, f"grid2d_{rows}x{cols}")
+
+
+def rhg_radius(n: int, deg: float, gamma: float = 3.0) -> float:
+    return float(_load().gen_rhg_radius(n, deg, (gamma - 1.0) / 2.0))
+
+
+def rhg(n: int, deg: float = 16.0, seed: int = DEFAULT_SEED, gamma: float = 3.0, wmin: int = 1, wmax: int = 255,
+        nthreads=None) -> Graph:
+    """Threshold random hyperbolic graph: power-law degrees with exponent gamma,
+    expected average degree about deg, vertices numbered by angle."""
+    lib = _load()
+    alpha = (gamma - 1.0) / 2.0
+    R = rhg_radius(n, deg, gamma)
+    nt = _threads(nthreads)
+    m = int(lib.gen_rhg(n, alpha, R, seed, wmin, wmax, nt, None, None, None))
+    src, dst, w = _empty(m)
+    got = int(lib.gen_rhg(n, alpha, R, seed, wmin, wmax, nt, _p32(src), _p32(dst), _p32(w)))
+    assert got == m
+    return Graph(n, src, dst, w, f"rhg_n{n}_d{deg:g}_g{gamma:g}")
+
+
 @dataclass
 class Batch:
     """Many independent graphs, concatenated; vertex ids are graph-local."""
@@ -193,6 +230,16 @@ def mix(num_graphs: int, seed: int = DEFAULT_SEED, log_lo: int = 8, log_hi: int 
 def gnm_small(seed: int = DEFAULT_SEED) -> Graph:
     """GNM, n = 2^16, m = 2^20, weights uniform in [1,255]."""
     return gnm(1 << 16, 1 << 20, seed)
+
+
+def grid2d_large(seed: int = DEFAULT_SEED) -> Graph:
+    """2D grid 2048 x 2048 (n = 2^22, m ~ 2^23), weights uniform in [1,255]."""
+    return grid2d(2048, 2048, seed)
+
+
+def rhg_large(seed: int = DEFAULT_SEED) -> Graph:
+    """Random hyperbolic graph, n = 2^22, gamma = 3, average degree about 16, weights in [1,255]."""
+    return rhg(1 << 22, 16.0, seed)
 
 
 def rgg2d_large(seed: int = DEFAULT_SEED) -> Graph:

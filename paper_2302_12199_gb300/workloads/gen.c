@@ -1,6 +1,7 @@
 /*
- * Seeded synthetic graph generators: GNM, 2D/3D random geometric (RGG), RMAT and
- * the mixed batches of many small graphs.
+ * Seeded synthetic graph generators: GNM, 2D/3D random geometric (RGG), RMAT,
+ * 2D grids, random hyperbolic graphs (RHG) and the mixed batches of many small
+ * graphs.
  *
  * These stand in for the graph families of the paper's experiments (Section 7,
  * "Instances and Methodology": KaGen GNM / RGG generators and an RMAT generator
@@ -364,6 +365,250 @@ uint64_t gen_rgg_fill(int dim, uint64_t n, double r, uint64_t seed, uint32_t wmi
   uint64_t sw = sub_seed(seed, TAG_W), span = (uint64_t)wmax - wmin + 1;
   for (uint64_t i = 0; i < c; ++i) w[i] = (uint32_t)(wmin + bounded(sm_at(sw, i), span));
   return c;
+}
+
+/* ------------------------------------------------------------------ 2D grid */
+
+/* rows x cols grid, vertex r*cols + c; edges to the right and lower neighbour
+ * (in that order per vertex), rows*(cols-1) + (rows-1)*cols in all; weights
+ * uniform in [wmin, wmax].  Standing in for the paper's 2D-grid family. */
+uint64_t gen_grid2d(uint64_t rows, uint64_t cols, uint64_t seed, uint32_t wmin, uint32_t wmax, uint32_t *src,
+                    uint32_t *dst, uint32_t *w) {
+  const uint64_t m = rows * (cols ? cols - 1 : 0) + (rows ? rows - 1 : 0) * cols;
+  if (!src) return m;
+  const uint64_t sw = sub_seed(seed, TAG_W), span = (uint64_t)wmax - wmin + 1;
+  uint64_t k = 0;
+  for (uint64_t r = 0; r < rows; ++r)
+    for (uint64_t c = 0; c < cols; ++c) {
+      const uint64_t v = r * cols + c;
+      if (c + 1 < cols) {
+        src[k] = (uint32_t)v;
+        dst[k] = (uint32_t)(v + 1);
+        w[k] = (uint32_t)(wmin + bounded(sm_at(sw, k), span));
+        ++k;
+      }
+      if (r + 1 < rows) {
+        src[k] = (uint32_t)v;
+        dst[k] = (uint32_t)(v + cols);
+        w[k] = (uint32_t)(wmin + bounded(sm_at(sw, k), span));
+        ++k;
+      }
+    }
+  return k;
+}
+
+/* ------------------------------------------------- random hyperbolic graph */
+
+/* Threshold random hyperbolic graph in the hyperbolic plane (curvature -1):
+ * n points in a disk of radius R, angle uniform, radius with density
+ * alpha sinh(alpha r) / (cosh(alpha R) - 1) (power-law degrees with exponent
+ * gamma = 2 alpha + 1), an edge between two points closer than R.  Vertices are
+ * numbered in angular order.  Standing in for the paper's RHG family.  Uses
+ * libm (cosh, sinh, acosh, cos): graphs are identical on hosts with the same
+ * libm.  Neighbour search: radial bands of width 1; for a query point, a band
+ * is scanned over the angular window its inner radius allows. */
+typedef struct {
+  uint64_t n;
+  double R, coshR;
+  double *theta, *chr, *shr; /* per vertex (angular order) */
+  int nb;                    /* bands */
+  double *b_lo;              /* inner radius of each band */
+  uint64_t *b_start;         /* band members: positions b_start[j] .. b_start[j+1]-1 in b_idx */
+  uint32_t *b_idx;           /* vertex ids, ascending angle within a band */
+  double *b_theta;
+} rhg_t;
+
+typedef struct {
+  double th;
+  double r;
+} pt_t;
+
+static int cmp_pt(const void *a, const void *b) {
+  const pt_t *x = (const pt_t *)a, *y = (const pt_t *)b;
+  return x->th < y->th ? -1 : x->th > y->th ? 1 : 0;
+}
+
+static void rhg_build(rhg_t *g, uint64_t n, double alpha, double R, uint64_t seed) {
+  const double two_pi = 6.283185307179586476925286766559;
+  g->n = n;
+  g->R = R;
+  g->coshR = cosh(R);
+  pt_t *pts = (pt_t *)malloc(sizeof(pt_t) * (n ? n : 1));
+  const uint64_t s1 = sub_seed(seed, TAG_X), s2 = sub_seed(seed, TAG_Y);
+  const double cmax = cosh(alpha * R) - 1.0;
+  for (uint64_t i = 0; i < n; ++i) {
+    const double u1 = (double)(sm_at(s1, i) >> 11) * (1.0 / 9007199254740992.0);
+    const double u2 = (double)(sm_at(s2, i) >> 11) * (1.0 / 9007199254740992.0);
+    pts[i].th = two_pi * u1;
+    pts[i].r = acosh(1.0 + u2 * cmax) / alpha;
+  }
+  qsort(pts, n, sizeof(pt_t), cmp_pt);
+  g->theta = (double *)malloc(sizeof(double) * (n ? n : 1));
+  g->chr = (double *)malloc(sizeof(double) * (n ? n : 1));
+  g->shr = (double *)malloc(sizeof(double) * (n ? n : 1));
+  for (uint64_t i = 0; i < n; ++i) {
+    g->theta[i] = pts[i].th;
+    g->chr[i] = cosh(pts[i].r);
+    g->shr[i] = sinh(pts[i].r);
+  }
+  /* bands [R-1, R], [R-2, R-1], ..., [0, ...] */
+  g->nb = (int)ceil(R);
+  if (g->nb < 1) g->nb = 1;
+  g->b_lo = (double *)malloc(sizeof(double) * g->nb);
+  for (int j = 0; j < g->nb; ++j) {
+    const double lo = R - (double)(j + 1);
+    g->b_lo[j] = lo > 0.0 ? lo : 0.0;
+  }
+  g->b_start = (uint64_t *)calloc(g->nb + 1, sizeof(uint64_t));
+  int *band = (int *)malloc(sizeof(int) * (n ? n : 1));
+  for (uint64_t i = 0; i < n; ++i) {
+    int j = (int)(R - pts[i].r);
+    if (j < 0) j = 0;
+    if (j >= g->nb) j = g->nb - 1;
+    band[i] = j;
+    g->b_start[j + 1]++;
+  }
+  for (int j = 0; j < g->nb; ++j) g->b_start[j + 1] += g->b_start[j];
+  uint64_t *fill = (uint64_t *)malloc(sizeof(uint64_t) * g->nb);
+  for (int j = 0; j < g->nb; ++j) fill[j] = g->b_start[j];
+  g->b_idx = (uint32_t *)malloc(sizeof(uint32_t) * (n ? n : 1));
+  g->b_theta = (double *)malloc(sizeof(double) * (n ? n : 1));
+  for (uint64_t i = 0; i < n; ++i) { /* ascending angle within each band (vertex order is angular) */
+    const uint64_t at = fill[band[i]]++;
+    g->b_idx[at] = (uint32_t)i;
+    g->b_theta[at] = g->theta[i];
+  }
+  free(fill);
+  free(band);
+  free(pts);
+}
+
+static void rhg_free(rhg_t *g) {
+  free(g->theta);
+  free(g->chr);
+  free(g->shr);
+  free(g->b_lo);
+  free(g->b_start);
+  free(g->b_idx);
+  free(g->b_theta);
+}
+
+static uint64_t lower_theta(const double *a, uint64_t lo, uint64_t hi, double x) {
+  while (lo < hi) {
+    const uint64_t mid = lo + (hi - lo) / 2;
+    if (a[mid] < x)
+      lo = mid + 1;
+    else
+      hi = mid;
+  }
+  return lo;
+}
+
+/* Neighbours q > p of vertex p (each undirected edge once), in band order and
+ * ascending angle within a band; writes them to out (if non-null); returns the count. */
+static uint64_t rhg_neighbours(const rhg_t *g, uint64_t p, uint32_t *out) {
+  const double pi = 3.141592653589793238462643383279, two_pi = 2.0 * pi;
+  const double tp = g->theta[p], chp = g->chr[p], shp = g->shr[p];
+  uint64_t c = 0;
+  for (int j = 0; j < g->nb; ++j) {
+    const uint64_t lo = g->b_start[j], hi = g->b_start[j + 1];
+    if (lo == hi) continue;
+    /* widest angle at which a point of radius >= b_lo[j] can still be closer than R */
+    const double rl = g->b_lo[j];
+    double width = pi;
+    const double sh = shp * sinh(rl);
+    if (sh > 0.0) {
+      const double cth = (chp * cosh(rl) - g->coshR) / sh;
+      if (cth >= 1.0) continue;
+      if (cth > -1.0) width = acos(cth);
+    }
+    /* the window [tp - width, tp + width] on the circle, as at most two ranges */
+    double a0 = tp - width, a1 = tp + width;
+    double ranges[2][2];
+    int nr = 0;
+    if (width >= pi) {
+      ranges[nr][0] = 0.0;
+      ranges[nr][1] = two_pi;
+      ++nr;
+    } else if (a0 < 0.0) {
+      ranges[nr][0] = 0.0, ranges[nr][1] = a1, ++nr;
+      ranges[nr][0] = a0 + two_pi, ranges[nr][1] = two_pi, ++nr;
+    } else if (a1 > two_pi) {
+      ranges[nr][0] = a0, ranges[nr][1] = two_pi, ++nr;
+      ranges[nr][0] = 0.0, ranges[nr][1] = a1 - two_pi, ++nr;
+    } else {
+      ranges[nr][0] = a0, ranges[nr][1] = a1, ++nr;
+    }
+    for (int k = 0; k < nr; ++k) {
+      uint64_t at = lower_theta(g->b_theta, lo, hi, ranges[k][0]);
+      for (; at < hi && g->b_theta[at] <= ranges[k][1]; ++at) {
+        const uint64_t q = g->b_idx[at];
+        if (q <= p) continue;
+        const double dth = fabs(g->theta[q] - tp);
+        const double cd = chp * g->chr[q] - shp * g->shr[q] * cos(dth);
+        if (cd < g->coshR) {
+          if (out) out[c] = (uint32_t)q;
+          ++c;
+        }
+      }
+    }
+  }
+  return c;
+}
+
+typedef struct {
+  const rhg_t *g;
+  uint64_t *count; /* per vertex */
+  const uint64_t *off;
+  uint32_t *src, *dst;
+} rhg_job_t;
+
+static void rhg_count_body(void *p, uint64_t lo, uint64_t hi) {
+  rhg_job_t *j = (rhg_job_t *)p;
+  for (uint64_t v = lo; v < hi; ++v) j->count[v] = rhg_neighbours(j->g, v, NULL);
+}
+
+static void rhg_fill_body(void *p, uint64_t lo, uint64_t hi) {
+  rhg_job_t *j = (rhg_job_t *)p;
+  for (uint64_t v = lo; v < hi; ++v) {
+    const uint64_t o = j->off[v];
+    const uint64_t c = rhg_neighbours(j->g, v, j->dst + o);
+    for (uint64_t k = 0; k < c; ++k) j->src[o + k] = (uint32_t)v;
+  }
+}
+
+/* Radius giving expected average degree deg for alpha (Krioukov et al. 2010,
+ * the large-n form k = xi^2 (2/pi) n e^{-R/2}, xi = alpha / (alpha - 1/2)). */
+double gen_rhg_radius(uint64_t n, double deg, double alpha) {
+  const double pi = 3.141592653589793238462643383279;
+  const double xi = alpha / (alpha - 0.5);
+  return 2.0 * log(xi * xi * 2.0 / pi * (double)n / deg);
+}
+
+/* Two passes as for RGG: with src == NULL returns the edge count only. */
+uint64_t gen_rhg(uint64_t n, double alpha, double R, uint64_t seed, uint32_t wmin, uint32_t wmax, int nthreads,
+                 uint32_t *src, uint32_t *dst, uint32_t *w) {
+  rhg_t g;
+  rhg_build(&g, n, alpha, R, seed);
+  uint64_t *count = (uint64_t *)malloc(sizeof(uint64_t) * (n + 1));
+  rhg_job_t job = {&g, count, NULL, NULL, NULL};
+  parallel_for(n, nthreads, rhg_count_body, &job);
+  uint64_t *off = (uint64_t *)malloc(sizeof(uint64_t) * (n + 1));
+  off[0] = 0;
+  for (uint64_t v = 0; v < n; ++v) off[v + 1] = off[v] + count[v];
+  const uint64_t m = off[n];
+  if (src) {
+    job.off = off;
+    job.src = src;
+    job.dst = dst;
+    parallel_for(n, nthreads, rhg_fill_body, &job);
+    const uint64_t sw = sub_seed(seed, TAG_W), span = (uint64_t)wmax - wmin + 1;
+    for (uint64_t i = 0; i < m; ++i) w[i] = (uint32_t)(wmin + bounded(sm_at(sw, i), span));
+  }
+  free(off);
+  free(count);
+  rhg_free(&g);
+  return m;
 }
 
 /* ------------------------------------------------------------ mixed batches */

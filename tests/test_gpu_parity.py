@@ -79,7 +79,7 @@ def test_tiny_random_multigraphs(solver, dev):
         assert_same_forest(solver, n, src, dst, w, dev, f"n={n} m={m}")
 
 
-@pytest.mark.parametrize("family", ["gnm", "rmat", "rgg2", "rgg3", "forestish", "dense_small"])
+@pytest.mark.parametrize("family", ["gnm", "rmat", "rgg2", "rgg3", "forestish", "dense_small", "grid2d", "rhg"])
 def test_families_several_tiles_ragged(solver, dev, family):
     g = {
         "gnm": lambda: W.gnm(1 << 12, (1 << 16) + 123, 5),
@@ -88,6 +88,8 @@ def test_families_several_tiles_ragged(solver, dev, family):
         "rgg3": lambda: W.rgg(3, 1 << 14, 8.0, 8),
         "forestish": lambda: W.gnm(1 << 15, 9000, 9),
         "dense_small": lambda: W.gnm(300, 40000, 10, wmax=3),
+        "grid2d": lambda: W.grid2d(181, 179, 18),
+        "rhg": lambda: W.rhg(1 << 15, 12.0, 19),
     }[family]()
     assert_same_forest(solver, g.n, g.src, g.dst, g.w, dev, family)
 

@@ -69,9 +69,13 @@ def test_kruskal_equals_brute_force_on_tiny_multigraphs():
 
 # ---------------------------------------------- independent cross-checks
 
-@pytest.mark.parametrize("family", ["gnm", "rmat", "rgg2", "rgg3", "sparse_forest"])
+@pytest.mark.parametrize("family", ["gnm", "rmat", "rgg2", "rgg3", "sparse_forest", "grid2d", "rhg"])
 def test_kruskal_equals_prim(family):
-    if family == "gnm":
+    if family == "grid2d":
+        g = W.grid2d(60, 70, 16)
+    elif family == "rhg":
+        g = W.rhg(4000, 10.0, 17)
+    elif family == "gnm":
         g = W.gnm(3000, 30000, 11)
     elif family == "rmat":
         g = W.rmat(12, 40000, 12)
