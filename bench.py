@@ -301,6 +301,8 @@ def gpu_main(args, rank: int, world: int, local_rank: int):
         cfg["tile_vertices"] = args.tile_vertices
     if args.base_case is not None:
         cfg["base_case"] = args.base_case
+    if args.graph_rounds is not None:
+        cfg["graph_rounds"] = args.graph_rounds
     g = gen(W)
     n, m = g.n, g.m
     src = torch.from_numpy(g.src.view(np.int32)).to(dev)
@@ -484,6 +486,8 @@ def batched_main(args, rank: int, world: int, local_rank: int):
         best, tuning = autotune(trial, reps=1)
     if args.base_case is not None:
         best["base_case"] = args.base_case
+    if args.graph_rounds is not None:
+        best["graph_rounds"] = args.graph_rounds
     solver = Solver(local_rank, **best)
     for _ in range(args.warmup):
         timed_batch(solver)
@@ -633,6 +637,8 @@ def served_main(args, rank: int, world: int, local_rank: int):
     scfg = dict(variant="filter", dedupe="none", tile_contract=0)
     if args.base_case is not None:
         scfg["base_case"] = args.base_case
+    if args.graph_rounds is not None:
+        scfg["graph_rounds"] = args.graph_rounds
     server = Server(local_rank, slots=args.slots, budget_bytes=int(args.slot_budget_gb * (1 << 30)), config=scfg)
     expected = {g: server.solve_alone(pool[g]) for g in range(args.pool)}  # each graph solved alone
     for s in server.slots:  # warm every slot
@@ -708,6 +714,7 @@ def main():
     ap.add_argument("--tile-contract", type=int, default=None, choices=[-1, 0, 1])
     ap.add_argument("--tile-vertices", type=int, default=None)
     ap.add_argument("--base-case", type=int, default=None, choices=[0, 1])
+    ap.add_argument("--graph-rounds", type=int, default=None, choices=[0, 1])
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "gpu":
         args.warmup = 3

@@ -70,6 +70,12 @@ typedef struct {
                                   edges (<= 6144) fit one block's shared memory, finish its rounds in
                                   one launch (the role of the paper's base case, Section 4.4); 0: run
                                   every round globally */
+  int graph_rounds;            /* 1 (default): from the second round of a Borůvka call on, run the
+                                  rounds as one CUDA graph launch whose conditional loop the device
+                                  ends (no host round trip per round); 0: one host readback per round */
+  int graph_jump_launches;     /* pointer-jumping launches per round inside the graph, 1..8, of up to
+                                  256 parent steps each (default 2: chains up to 256^2); a round that
+                                  needs more hands the state back to the host, which finishes the jump */
 } mst_config;
 
 /* Fills *cfg with the defaults (Borůvka variant, automatic dedupe, pivot sample
@@ -149,6 +155,7 @@ enum {
   MST_K_FINALIZE,       /* bitmap -> ascending ids + weight */
   MST_K_TILE,           /* tile-local contraction (count, bucket, contract) */
   MST_K_BASE,           /* single-block base case (the last rounds of a Borůvka call) */
+  MST_K_GRAPH,          /* Borůvka rounds run as one CUDA graph launch (time only; bytes not counted) */
   MST_K_COUNT
 };
 typedef struct {

@@ -119,8 +119,10 @@ void launch_min_edges(EdgeList in, uint64_t m, uint32_t n, int validate, KeyLayo
                       int sms, cudaStream_t s);
 void launch_max_weight(const uint32_t *w, uint64_t m, uint32_t *out, int sms, cudaStream_t s);
 void launch_hook(const HookArgs &a, uint64_t max_cand, cudaStream_t s);
+// max_steps: parent steps per thread and launch (0: the default of 64)
 void launch_jump(const uint32_t *act, const u64 *count_dev, uint64_t count_host, uint64_t max_count,
-                 uint32_t *parent, u64 *best, int reset_best, uint32_t *flag, int sms, cudaStream_t s);
+                 uint32_t *parent, u64 *best, int reset_best, uint32_t *flag, int sms, cudaStream_t s,
+                 uint32_t max_steps = 0);
 void launch_hash_insert(EdgeList in, uint64_t m, HashSlot *table, uint64_t tmask, uint32_t *err, int sms,
                         cudaStream_t s);
 void launch_pivot(EdgeList in, uint64_t m, const u64 *m_dev, u64 state, uint32_t sample, u64 *sample_buf,
@@ -147,6 +149,22 @@ bool launch_tile_contract(uint32_t n, uint32_t B, uint64_t nlocal, const u64 *cu
                           uint32_t *bits, EdgeOut rest, u64 *rest_fill, uint32_t *err, cudaStream_t s);
 void launch_tile_sample(EdgeList in, uint64_t m, uint32_t n, uint32_t B, u64 state, uint32_t samples,
                         uint32_t *local_count, cudaStream_t s);
+// Borůvka rounds as a CUDA graph (device-driven loop): state in device memory.
+enum : uint32_t { ROUNDS_RUNNING = 0xff, ROUNDS_DONE = 0, ROUNDS_BASE = 1, ROUNDS_JUMP = 2, ROUNDS_BOUND = 3 };
+struct GraphRounds {
+  u64 ce[2];      // edges in the list of slot 0 / 1
+  u64 ca[2];      // active vertices of slot 0 / 1
+  u64 saved_ce, saved_ca;  // counts of the slot handed back to the host
+  uint32_t jflag; // the round's last jump launch left a vertex short of its root
+  uint32_t jdummy;  // flag word of the earlier jump launches (not read)
+  uint32_t iter;  // body executions (two rounds each)
+  uint32_t reason, slot;
+};
+void launch_round_init(GraphRounds *g, uint64_t m, uint64_t n_act, cudaStream_t s);
+void launch_round_check(GraphRounds *g, int base_ok, cudaStream_t s);
+void launch_round_cond(GraphRounds *g, cudaGraphConditionalHandle h, int base_ok, uint32_t max_iter, u64 *out_counts,
+                       cudaStream_t s);
+
 // single-block base case: the last rounds of a Borůvka call in one launch
 constexpr uint32_t BASE_MAX_N = 4096;  // live components (16-bit local ends; shared-memory vertex arrays)
 constexpr uint64_t BASE_MAX_M = 6144;  // live edges (fit the tile kernel's shared-memory edge capacity)

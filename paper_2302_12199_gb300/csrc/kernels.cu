@@ -13,6 +13,7 @@
 // chosen edge through the input arrays.  The output ids (finalize) are the one
 // ordered compaction: a decoupled look-back scan (Merrill & Garland, 2016).
 // Every wait is bounded.
+#include <algorithm>
 #include <cstdint>
 
 #include <cooperative_groups.h>
@@ -738,9 +739,8 @@ __global__ void __launch_bounds__(BLOCK) hook_kernel(HookArgs a) {
   __shared__ uint32_t s_base[1];
 
   const uint64_t nc = a.ncand_dev ? *a.ncand_dev : a.ncand;
-  const uint64_t tb = (uint64_t)blockIdx.x * TILE;
-  if (tb >= nc) return;
-
+  for (uint64_t tile = blockIdx.x; tile * TILE < nc; tile += gridDim.x) {  // uniform per block
+  const uint64_t tb = tile * TILE;
   uint32_t c[ITEMS];
   u64 kk[ITEMS];
   if (!IOTA && tb + TILE <= nc && (((uintptr_t)a.cand) & 15u) == 0) {
@@ -829,18 +829,21 @@ __global__ void __launch_bounds__(BLOCK) hook_kernel(HookArgs a) {
     if (keep >> k & 1) s_c[local_pos(keep, k, excl, totp)] = c[k];
   __syncthreads();
   for (uint32_t i = threadIdx.x; i < total; i += BLOCK) a.active_out[obase + i] = s_c[i];
+  __syncthreads();  // s_c, s_warp and s_base are reused by the block's next tile
+  }
 }
 
 // --------------------------------------------------------- pointer jumping
 
 // Pointer doubling toward the roots (Section 4.2): each listed vertex follows
-// parent pointers (reading the other threads' progress) for at most JUMP_STEPS
+// parent pointers (reading the other threads' progress) for at most max_steps
 // steps and stores the furthest ancestor reached; `flag` is set if some vertex
 // did not reach its root, and the host launches again.  Parent values only ever
 // move toward the root, so concurrent reads and writes are benign.  When
 // reset_best is set, best[c] is returned to INF for the next round.
 __global__ void __launch_bounds__(BLOCK) jump_kernel(const uint32_t *act, const u64 *count_dev, uint64_t count_host,
-                                                     uint32_t *parent, u64 *best, int reset_best, uint32_t *flag) {
+                                                     uint32_t *parent, u64 *best, int reset_best, uint32_t *flag,
+                                                     uint32_t max_steps) {
   const uint64_t cnt = count_dev ? *count_dev : count_host;
   for (uint64_t i = (uint64_t)blockIdx.x * BLOCK + threadIdx.x; i < cnt; i += (uint64_t)gridDim.x * BLOCK) {
     const uint32_t c = act ? __ldg(act + i) : (uint32_t)i;
@@ -848,7 +851,7 @@ __global__ void __launch_bounds__(BLOCK) jump_kernel(const uint32_t *act, const 
     uint32_t p = __ldcg(parent + c);
     uint32_t steps = 0;
     bool done = false;
-    while (steps < JUMP_STEPS) {
+    while (steps < max_steps) {
       const uint32_t pp = __ldcg(parent + p);
       if (pp == p) {
         done = true;
@@ -1542,6 +1545,79 @@ __global__ void __launch_bounds__(TC_THREADS) tile_contract_kernel(uint32_t n, u
   }
 }
 
+// ------------------------------------------------- device-driven round loop
+
+// State of the Borůvka rounds run as a CUDA graph: a conditional WHILE node
+// repeats a body of two rounds (lists and active lists alternate between slot
+// 0 and slot 1) while round_cond_kernel sets its condition.  Counts live here,
+// so no round waits for the host.
+__global__ void round_init_kernel(GraphRounds *g, uint64_t m, uint64_t n_act) {
+  g->ce[0] = m;
+  g->ca[0] = n_act;
+  g->ce[1] = g->ca[1] = 0;  // outputs of the first round
+  g->jflag = 0;
+  g->iter = 0;
+  g->reason = ROUNDS_RUNNING;
+  g->slot = 0;
+  g->saved_ce = g->saved_ca = 0;
+}
+
+// After the first round of the body (slot 0 -> 1): stop early (the second
+// round then sees zero counts and does nothing) when the jump did not reach
+// the roots or the base case fits.
+__global__ void round_check_kernel(GraphRounds *g, int base_ok) {
+  if (g->jflag || (base_ok && g->ca[1] > 0 && g->ca[1] <= BASE_MAX_N && g->ce[1] > 0 && g->ce[1] <= BASE_MAX_M)) {
+    g->reason = g->jflag ? ROUNDS_JUMP : ROUNDS_BASE;
+    g->slot = 1;
+    g->saved_ce = g->ce[1];
+    g->saved_ca = g->ca[1];
+    g->ce[1] = g->ca[1] = 0;
+  }
+  g->ce[0] = g->ca[0] = 0;  // outputs of the second round
+  g->jflag = 0;
+}
+
+// After the second round (slot 1 -> 0): decide whether the body runs again,
+// and publish the outcome in the solver's counters (edges, active, info).
+__global__ void round_cond_kernel(GraphRounds *g, cudaGraphConditionalHandle h, int base_ok, uint32_t max_iter,
+                                  u64 *out_counts) {
+  const uint32_t it = ++g->iter;
+  unsigned int go = 0;
+  if (g->reason == ROUNDS_RUNNING) {
+    if (g->jflag) {
+      g->reason = ROUNDS_JUMP;
+    } else if (g->ca[0] == 0 || g->ce[0] == 0) {
+      g->reason = ROUNDS_DONE;
+    } else if (base_ok && g->ca[0] <= BASE_MAX_N && g->ce[0] <= BASE_MAX_M) {
+      g->reason = ROUNDS_BASE;
+    } else if (it >= max_iter) {
+      g->reason = ROUNDS_BOUND;
+    } else {
+      go = 1;
+    }
+    if (!go) {
+      g->slot = 0;
+      g->saved_ce = g->ce[0];
+      g->saved_ca = g->ca[0];
+    }
+  }
+  out_counts[0] = g->saved_ce;
+  out_counts[1] = g->saved_ca;
+  out_counts[2] = (u64)g->reason | ((u64)g->slot << 8) | ((u64)it << 16);
+  g->ce[1] = g->ca[1] = 0;  // outputs of the next body's first round
+  g->jflag = 0;
+  cudaGraphSetConditional(h, go);
+}
+
+void launch_round_init(GraphRounds *g, uint64_t m, uint64_t n_act, cudaStream_t s) {
+  round_init_kernel<<<1, 1, 0, s>>>(g, m, n_act);
+}
+void launch_round_check(GraphRounds *g, int base_ok, cudaStream_t s) { round_check_kernel<<<1, 1, 0, s>>>(g, base_ok); }
+void launch_round_cond(GraphRounds *g, cudaGraphConditionalHandle h, int base_ok, uint32_t max_iter, u64 *out_counts,
+                       cudaStream_t s) {
+  round_cond_kernel<<<1, 1, 0, s>>>(g, h, base_ok, max_iter, out_counts);
+}
+
 // ---------------------------------------------------- single-block base case
 
 // Once the live components and edges of a Borůvka call fit in one block's
@@ -1816,7 +1892,10 @@ void launch_max_weight(const uint32_t *w, uint64_t m, uint32_t *out, int sms, cu
 
 void launch_hook(const HookArgs &a, uint64_t max_cand, cudaStream_t s) {
   if (max_cand == 0) return;
-  const unsigned grid = (unsigned)max_scan_tiles(max_cand);
+  // a count known on the host gets one block per tile; a count in device
+  // memory (up to max_cand) gets a bounded grid that strides over the tiles
+  const unsigned tiles = (unsigned)max_scan_tiles(max_cand);
+  const unsigned grid = a.ncand_dev ? std::min(tiles, 152u * 8u) : tiles;
   if (a.cand)
     hook_kernel<false><<<grid, BLOCK, 0, s>>>(a);
   else
@@ -1824,10 +1903,12 @@ void launch_hook(const HookArgs &a, uint64_t max_cand, cudaStream_t s) {
 }
 
 void launch_jump(const uint32_t *act, const u64 *count_dev, uint64_t count_host, uint64_t max_count,
-                 uint32_t *parent, u64 *best, int reset_best, uint32_t *flag, int sms, cudaStream_t s) {
+                 uint32_t *parent, u64 *best, int reset_best, uint32_t *flag, int sms, cudaStream_t s,
+                 uint32_t max_steps) {
   if (max_count == 0) return;
   const unsigned grid = grid_for((max_count + BLOCK - 1) / BLOCK, sms, 8);
-  jump_kernel<<<grid, BLOCK, 0, s>>>(act, count_dev, count_host, parent, best, reset_best, flag);
+  jump_kernel<<<grid, BLOCK, 0, s>>>(act, count_dev, count_host, parent, best, reset_best, flag,
+                                     max_steps ? max_steps : JUMP_STEPS);
 }
 
 void launch_hash_insert(EdgeList in, uint64_t m, HashSlot *table, uint64_t tmask, uint32_t *err, int sms,

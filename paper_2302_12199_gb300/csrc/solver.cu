@@ -45,6 +45,15 @@ struct mst_ctx {
     double per1, per2;
   };
   bool prof_on = false;
+  cudaStream_t cap_stream = nullptr;  // stream the round graphs are captured on
+  GraphRounds *grounds = nullptr;     // device state of the graph round loop
+  struct RoundGraph {
+    u64 sig;  // every pointer and size the graph was built with
+    cudaGraph_t graph;
+    cudaGraphExec_t exec;
+  };
+  std::vector<RoundGraph> round_graphs;  // most recently used first
+  std::vector<u64> round_sigs_seen;      // shapes met once (a graph is built on the second meeting)
   std::vector<cudaEvent_t> ev_pool;
   std::vector<ProfRec> prof_pending;
   mst_kernel_stats prof[MST_K_COUNT];
@@ -431,6 +440,18 @@ struct Solve {
     for (int r = 1; n_act > 0; ++r) {
       if (r > bound) return MST_ERR_INTERNAL;
       if (base_case_fits(cur, cur_m, n_act)) return base_case(cur, cur_m, act[a], (uint32_t)n_act);
+      if (c->cfg.graph_rounds && cur.u == X.out.u && cur.id && !want_dedupe(r, cur_m)) {
+        bool used = false, done = false;
+        int ran = 0;
+        TRY(graph_rounds(X, Y, cur, cur_m, n_act, a, bound - r, used, done, ran));
+        if (used) {
+          r += ran;
+          rounds += ran;
+          if (done || n_act == 0 || cur_m == 0) return MST_OK;
+          --r;  // the loop's ++r
+          continue;
+        }
+      }
       ListBuf &out = (cur.u == X.out.u) ? Y : X;
       if (out.cap < cur_m) TRY(out.alloc(c, cur_m, s));
       TRY(zero_counters(c, s));
@@ -495,6 +516,167 @@ struct Solve {
       cur_m = c->hs->count[CNT_EDGES];
       ++rounds;
       if (cur_m == 0) break;
+    }
+    return MST_OK;
+  }
+
+  // Rounds of a Borůvka call as one CUDA graph launch (the round loop without
+  // host round trips): a conditional WHILE node repeats a body of two rounds
+  // (list X -> Y, then Y -> X; the active lists alternate the same way) while
+  // the device sees active vertices and edges.  It hands the state back to the
+  // host when the base case fits, when a round's pointer jumping needs more
+  // than the four launches a round holds, or at the round bound.  Counts live
+  // in device memory; nothing in the body waits for the host.
+  mst_status graph_rounds(ListBuf &X, ListBuf &Y, EdgeList &cur, uint64_t &cur_m, uint64_t &n_act, int &a,
+                          int rounds_left, bool &used, bool &done, int &ran) {
+    used = false;
+    done = false;
+    ran = 0;
+    const uint64_t cap = cur_m, nmax = n_act;
+    if (Y.cap < cap) TRY(Y.alloc(c, cap, s));
+    if (!c->grounds) CK(cudaMalloc(&c->grounds, sizeof(GraphRounds)));
+    if (!c->cap_stream) CK(cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
+    GraphRounds *g = c->grounds;
+    const int base_ok = c->cfg.base_case ? 1 : 0;
+    const int jl = c->cfg.graph_jump_launches;
+    const uint32_t max_iter = (uint32_t)(rounds_left > 2 ? rounds_left / 2 : 1);
+    const ListBuf *L[2] = {&X, &Y};
+    uint32_t *A[2] = {act[a], act[1 - a]};
+    // A built graph is reused when every value baked into it is unchanged.
+    u64 sig = 0x2302121990ULL;
+    auto fold = [&](u64 v) { sig = host_mix64(sig ^ (v + 0x9e3779b97f4a7c15ULL)); };
+    for (int i = 0; i < 2; ++i) {
+      fold((u64)L[i]->out.u), fold((u64)L[i]->out.v), fold((u64)L[i]->out.w), fold((u64)L[i]->out.id);
+      fold((u64)A[i]);
+    }
+    const u64 vals[] = {(u64)parent,  (u64)best,    (u64)bits,     (u64)cur_u,  (u64)cur_v,
+                        (u64)src,     (u64)dst,     (u64)c->status, (u64)c->ds,  (u64)g,
+                        (u64)kl.packed, (u64)kl.vbits, (u64)kl.idbits, (u64)n,     (u64)cap,
+                        (u64)nmax,    (u64)jl,      (u64)base_ok,  (u64)max_iter, (u64)c->sms};
+    for (u64 v : vals) fold(v);
+    cudaGraphExec_t exec = nullptr;
+    for (size_t i = 0; i < c->round_graphs.size(); ++i)
+      if (c->round_graphs[i].sig == sig) {
+        const mst_ctx::RoundGraph hit = c->round_graphs[i];
+        c->round_graphs.erase(c->round_graphs.begin() + i);
+        c->round_graphs.insert(c->round_graphs.begin(), hit);
+        exec = hit.exec;
+        break;
+      }
+    if (!exec) {
+      // a graph pays for its capture and instantiation only when its shape
+      // comes back: the first time, the host runs the rounds
+      auto &seen = c->round_sigs_seen;
+      const bool again = std::find(seen.begin(), seen.end(), sig) != seen.end();
+      if (!again) {
+        seen.insert(seen.begin(), sig);
+        if (seen.size() > 64) seen.pop_back();
+        return MST_OK;
+      }
+      TRY(build_round_graph(sig, L, A, cap, nmax, base_ok, jl, max_iter, exec));
+    }
+    used = true;
+    launch_round_init(g, cur_m, n_act, s);
+    PROF(MST_K_GRAPH, 0.0, -1, 0.0, -1, 0.0, CK(cudaGraphLaunch(exec, s)));
+    TRY(readback(c, s));
+    const u64 info = c->hs->count[CNT_TMP];
+    const uint32_t reason = (uint32_t)(info & 0xff), slot = (uint32_t)((info >> 8) & 0xff);
+    ran = 2 * (int)(info >> 16);
+    if (reason == ROUNDS_BOUND || reason == ROUNDS_RUNNING || slot > 1) return MST_ERR_INTERNAL;
+    cur_m = c->hs->count[CNT_EDGES];
+    n_act = c->hs->count[CNT_ACTIVE];
+    cur = L[slot]->list();
+    if (slot == 1) a = 1 - a;
+    if (reason == ROUNDS_DONE) {
+      done = true;
+      return MST_OK;
+    }
+    if (reason == ROUNDS_JUMP) TRY(jump_until_stars(act[a], nullptr, n_act, n_act, 0));
+    return MST_OK;
+  }
+
+  // Captures and instantiates the round graph: a conditional WHILE node whose
+  // body is two rounds (slot 0 -> 1, slot 1 -> 0), each compaction (relabel +
+  // minEdges relaxation), hooking, `jl` pointer-jumping launches and a check;
+  // the body ends with the kernel that sets the loop condition.
+  mst_status build_round_graph(u64 sig, const ListBuf *const L[2], uint32_t *const A[2], uint64_t cap, uint64_t nmax,
+                               int base_ok, int jl, uint32_t max_iter, cudaGraphExec_t &exec_out) {
+    GraphRounds *g = c->grounds;
+    cudaStream_t cs = c->cap_stream;
+    struct Owned {
+      cudaGraph_t graph = nullptr;
+      cudaGraphExec_t exec = nullptr;
+      cudaStream_t capturing = nullptr;
+      ~Owned() {
+        if (capturing) {  // an error during capture: end it so the stream is usable again
+          cudaGraph_t dummy = nullptr;
+          cudaStreamEndCapture(capturing, &dummy);
+          cudaGetLastError();
+        }
+        if (exec) cudaGraphExecDestroy(exec);
+        if (graph) cudaGraphDestroy(graph);
+      }
+    } o;
+    CK(cudaGraphCreate(&o.graph, 0));
+    cudaGraphConditionalHandle h;
+    CK(cudaGraphConditionalHandleCreate(&h, o.graph, 1, cudaGraphCondAssignDefault));
+    cudaGraphNodeParams cp{};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = h;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t node;
+    CK(cudaGraphAddNode(&node, o.graph, nullptr, nullptr, 0, &cp));
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    CK(cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+    o.capturing = cs;
+    for (int half = 0; half < 2; ++half) {
+      const int in = half, out = 1 - half;
+      CompactArgs ca{};
+      ca.in = L[in]->list();
+      ca.m = cap;
+      ca.m_dev = &g->ce[in];
+      ca.out = L[out]->out;
+      ca.label = parent;
+      ca.n = n;
+      ca.kl = kl;
+      ca.best = best;
+      record_ends(ca);
+      ca.st = ScanState{c->status, c->ds->tile_ctr, 0, &g->ce[out], &c->ds->err};
+      launch_compact(CM_RELABEL, ca, cap, cs);
+      HookArgs hb{};
+      hb.cand = A[in];
+      hb.ncand_dev = &g->ca[in];
+      hb.best = best;
+      hb.kl = kl;
+      hb.src = cur_u ? cur_u : src;
+      hb.dst = cur_v ? cur_v : dst;
+      hb.parent = parent;
+      hb.chosen_bits = bits;
+      hb.active_out = A[out];
+      hb.counter = &g->ca[out];
+      hb.err = &c->ds->err;
+      launch_hook(hb, nmax, cs);
+      // pointer jumping: jl launches of up to 256 steps each; only the last
+      // launch reports a vertex short of its root
+      for (int k = 0; k < jl; ++k)
+        launch_jump(A[out], &g->ca[out], 0, nmax, parent, best, k == 0 ? 1 : 0, k == jl - 1 ? &g->jflag : &g->jdummy,
+                    c->sms, cs, 256);
+      if (half == 0) launch_round_check(g, base_ok, cs);
+    }
+    launch_round_cond(g, h, base_ok, max_iter, &c->ds->count[CNT_EDGES], cs);
+    cudaGraph_t captured = nullptr;
+    o.capturing = nullptr;
+    CK(cudaStreamEndCapture(cs, &captured));
+    CK(cudaGraphInstantiate(&o.exec, o.graph, 0));
+    c->round_graphs.insert(c->round_graphs.begin(), mst_ctx::RoundGraph{sig, o.graph, o.exec});
+    exec_out = o.exec;
+    o.graph = nullptr;
+    o.exec = nullptr;
+    while (c->round_graphs.size() > 16) {
+      cudaGraphExecDestroy(c->round_graphs.back().exec);
+      cudaGraphDestroy(c->round_graphs.back().graph);
+      c->round_graphs.pop_back();
     }
     return MST_OK;
   }
@@ -765,6 +947,8 @@ mst_status validate_cfg(const mst_config *cfg) {
   if (!(cfg->filter_max_avg_degree > 0.0f)) return MST_ERR_INVALID_ARG;
   if (cfg->tile_contract < -1 || cfg->tile_contract > 1) return MST_ERR_INVALID_ARG;
   if (cfg->base_case < 0 || cfg->base_case > 1) return MST_ERR_INVALID_ARG;
+  if (cfg->graph_rounds < 0 || cfg->graph_rounds > 1) return MST_ERR_INVALID_ARG;
+  if (cfg->graph_jump_launches < 1 || cfg->graph_jump_launches > 8) return MST_ERR_INVALID_ARG;
   if (cfg->tile_vertices < 32 || cfg->tile_vertices > 4096) return MST_ERR_INVALID_ARG;
   return MST_OK;
 }
@@ -914,6 +1098,8 @@ void mst_config_default(mst_config *cfg) {
   cfg->filter_min_edges = 1ULL << 20;
   cfg->filter_max_avg_degree = 1.0f;  // measured optimum on GB300 (the paper uses 4 on its cluster)
   cfg->base_case = 1;
+  cfg->graph_rounds = 1;
+  cfg->graph_jump_launches = 2;
 }
 
 const char *mst_status_string(mst_status s) {
@@ -982,6 +1168,12 @@ void mst_destroy(mst_handle h) {
     if (h->status) cudaFree(h->status);
     if (h->sample_buf) cudaFree(h->sample_buf);
     if (h->pivot_scratch) cudaFree(h->pivot_scratch);
+    if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+    for (auto &rg : h->round_graphs) {
+      cudaGraphExecDestroy(rg.exec);
+      cudaGraphDestroy(rg.graph);
+    }
+    if (h->grounds) cudaFree(h->grounds);
     if (h->pool) cudaMemPoolDestroy(h->pool);
     for (auto &r : h->prof_pending) {
       h->ev_pool.push_back(r.a);

@@ -33,7 +33,7 @@ class MstError(RuntimeError):
 
 
 KERNEL_CLASSES = ["min_edges", "relabel_min", "hook", "jump", "dedupe", "pivot", "partition", "filter", "finalize",
-                  "tile", "base"]
+                  "tile", "base", "graph"]
 
 
 class KernelStats(ctypes.Structure):
@@ -44,7 +44,8 @@ class MstConfig(ctypes.Structure):
     _fields_ = [("device", ctypes.c_int), ("variant", ctypes.c_int), ("dedupe", ctypes.c_int),
                 ("tile_contract", ctypes.c_int), ("tile_vertices", ctypes.c_uint32),
                 ("pivot_sample", ctypes.c_uint32), ("seed", ctypes.c_uint64), ("filter_min_edges", ctypes.c_uint64),
-                ("filter_max_avg_degree", ctypes.c_float), ("base_case", ctypes.c_int)]
+                ("filter_max_avg_degree", ctypes.c_float), ("base_case", ctypes.c_int),
+                ("graph_rounds", ctypes.c_int), ("graph_jump_launches", ctypes.c_int)]
 
 
 _P = ctypes.c_void_p

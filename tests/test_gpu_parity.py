@@ -17,12 +17,12 @@ from tests.golden import fixtures
 pytestmark = pytest.mark.gpu
 
 CONFIGS = [
-    dict(variant="boruvka", dedupe="none", tile_contract=0, base_case=0),
+    dict(variant="boruvka", dedupe="none", tile_contract=0, base_case=0, graph_rounds=0),
     dict(variant="boruvka", dedupe="hash", tile_contract=-1),
     dict(variant="boruvka", dedupe="auto"),
     dict(variant="filter", dedupe="auto", filter_min_edges=1 << 10, pivot_sample=4096, tile_contract=-1),
     dict(variant="filter", dedupe="none", filter_min_edges=1 << 12, filter_max_avg_degree=4.0, tile_contract=0,
-         base_case=0),
+         base_case=0, graph_rounds=0),
     dict(variant="boruvka", tile_contract=1, tile_vertices=512),
     dict(variant="filter", tile_contract=1, tile_vertices=256, filter_min_edges=1 << 10, pivot_sample=4096),
 ]
@@ -381,3 +381,46 @@ def test_base_case_on_and_off_agree(dev, family):
                 assert np.array_equal(ids, kid) and tot == ktot, (variant, base)
             finally:
                 s.close()
+
+
+def quad_path(k):
+    """A path of k blocks of 4 vertices: inside a block weights 1, 2, 1; between
+    blocks increasing weights.  Round 0 pairs vertices, round 1 makes the
+    blocks, round 2 hooks block i into block i-1: one chain of k-1 blocks."""
+    n = 4 * k
+    src = np.arange(n - 1, dtype=np.uint32)
+    dst = src + 1
+    pos = src % 4
+    w = np.where(pos == 0, 1, np.where(pos == 1, 2, np.where(pos == 2, 1, 3 + src // 4))).astype(np.uint32)
+    return W.Graph(n, src, dst, w)
+
+
+@pytest.mark.parametrize("family", ["gnm", "rmat", "rgg2", "rhg", "quad_path"])
+def test_graph_rounds_on_and_off_agree(dev, family):
+    """Rounds run as a CUDA graph (device-ended loop) give the oracle's forest,
+    also when a round's chain needs more jump launches than the graph holds
+    (one launch here) and the host takes over."""
+    g = {
+        "gnm": lambda: W.gnm(20000, 200000, 61),
+        "rmat": lambda: W.rmat(15, 300000, 62),
+        "rgg2": lambda: W.rgg(2, 50000, 8.0, 63),
+        "rhg": lambda: W.rhg(40000, 10.0, 64),
+        "quad_path": lambda: quad_path(20000),
+    }[family]()
+    kid, ktot = oracle.kruskal(g.n, g.src, g.dst, g.w)
+    src, dst, w = to_dev(g.src, dev), to_dev(g.dst, dev), to_dev(g.w, dev)
+    for cfg in (dict(graph_rounds=0), dict(graph_rounds=1), dict(graph_rounds=1, graph_jump_launches=1),
+                dict(graph_rounds=1, base_case=0), dict(graph_rounds=1, variant="filter", filter_min_edges=1 << 10)):
+        s = Solver(0, **cfg)
+        try:
+            s.profile(True)
+            for rep in range(3):  # a round graph is built when a solve shape comes back
+                ids, tot = s.solve(g.n, src, dst, w).to_host()
+                assert np.array_equal(ids, kid) and tot == ktot, (cfg, rep)
+            graph_launches = s.profile_stats()["graph"][0]
+            if cfg["graph_rounds"] and cfg.get("variant") != "filter":
+                assert graph_launches >= 1, cfg
+            if not cfg["graph_rounds"]:
+                assert graph_launches == 0
+        finally:
+            s.close()
