@@ -303,6 +303,8 @@ def gpu_main(args, rank: int, world: int, local_rank: int):
         cfg["base_case"] = args.base_case
     if args.graph_rounds is not None:
         cfg["graph_rounds"] = args.graph_rounds
+    if args.filter_carry is not None:
+        cfg["filter_carry"] = args.filter_carry
     g = gen(W)
     n, m = g.n, g.m
     src = torch.from_numpy(g.src.view(np.int32)).to(dev)
@@ -715,6 +717,7 @@ def main():
     ap.add_argument("--tile-vertices", type=int, default=None)
     ap.add_argument("--base-case", type=int, default=None, choices=[0, 1])
     ap.add_argument("--graph-rounds", type=int, default=None, choices=[0, 1])
+    ap.add_argument("--filter-carry", type=int, default=None, choices=[0, 1])
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "gpu":
         args.warmup = 3

@@ -76,6 +76,9 @@ typedef struct {
   int graph_jump_launches;     /* pointer-jumping launches per round inside the graph, 1..8, of up to
                                   256 parent steps each (default 2: chains up to 256^2); a round that
                                   needs more hands the state back to the host, which finishes the jump */
+  int filter_carry;            /* Filter-Borůvka: 1 hands a level's filtered heavy edges, when at most
+                                  n/8, back to the level above instead of solving them there (Section
+                                  6.3); 0 (default, measured faster on GB300): every level solves its own */
 } mst_config;
 
 /* Fills *cfg with the defaults (Borůvka variant, automatic dedupe, pivot sample

@@ -813,8 +813,15 @@ struct Solve {
   }
 
   // Rec-Filter-MST (Alg. 2).  best_ready: best[] holds E's minEdges already.
+  // With `carry` (levels below the top), a small set of filtered heavy edges
+  // is not solved at this level but handed back in *carry (Section 6.3: small
+  // filtered sets go back up and join the heavy edges one level up); the
+  // caller appends it to its own filtered edges.  Filtering against a P that
+  // lacks those edges' contractions only keeps more edges, never drops an MSF
+  // edge.
   mst_status filter(EdgeList E, uint64_t mE, bool is_input, int depth, bool best_ready = false,
-                    bool ends_rec = false) {
+                    bool ends_rec = false, ListBuf *carry = nullptr, uint64_t *carry_m = nullptr) {
+    if (carry_m) *carry_m = 0;
     if (is_sparse(mE) || depth >= 40) return boruvka(E, mE, is_input, best_ready, ends_rec);
     if (best_ready) TRY(reset_best());
     const u64 state = host_splitmix64_at(c->cfg.seed, c->pivot_counter++);
@@ -860,13 +867,17 @@ struct Solve {
       if (fuse_light) TRY(reset_best());
       return boruvka(E, mE, is_input, false, ends_rec);
     }
-    TRY(filter(L.list(), mL, false, depth + 1, fuse_light, cp.cur_u != nullptr));
+    ListBuf lcarry;
+    uint64_t lcarry_m = 0;
+    const bool carrying = c->cfg.filter_carry != 0;
+    TRY(filter(L.list(), mL, false, depth + 1, fuse_light, cp.cur_u != nullptr, carrying ? &lcarry : nullptr,
+               carrying ? &lcarry_m : nullptr));
     L.mem.release();
     TRY(compress_all());
     Buf giant_b;
     TRY(mark_giant(E, mE, host_mix64(state), giant_b));
     ListBuf H;
-    TRY(H.alloc(c, mE - mL, s));
+    TRY(H.alloc(c, mE - mL + lcarry_m, s));
     CompactArgs cf{};
     cf.in = E;
     cf.m = mE;
@@ -883,8 +894,28 @@ struct Solve {
     PROF(MST_K_FILTER, in_bytes, CNT_EDGES, 16.0, -1, 0.0, launch_compact(CM_FILTER, cf, mE, s));
     TRY(readback(c, s));
     giant_b.release();
-    const uint64_t mH = c->hs->count[CNT_EDGES];
-    return filter(H.list(), mH, false, depth + 1, true, cf.cur_u != nullptr);
+    uint64_t mH = c->hs->count[CNT_EDGES];
+    bool relaxed = true;  // best[] holds the minEdges of H
+    if (lcarry_m) {       // the light recursion's unsolved edges join H (their ends are current roots)
+      for (int k = 0; k < 4; ++k) {
+        uint32_t *dstp = k == 0 ? H.out.u : k == 1 ? H.out.v : k == 2 ? H.out.w : H.out.id;
+        const uint32_t *srcp = k == 0 ? lcarry.out.u : k == 1 ? lcarry.out.v : k == 2 ? lcarry.out.w : lcarry.out.id;
+        CK(cudaMemcpyAsync(dstp + mH, srcp, lcarry_m * 4, cudaMemcpyDeviceToDevice, s));
+      }
+      mH += lcarry_m;
+      TRY(reset_best());  // minEdges over the union runs again
+      relaxed = false;
+      lcarry.mem.release();
+    }
+    if (carry && mH <= n / 8) {  // small: hand it to the level above
+      *carry_m = mH;
+      std::swap(carry->mem.p, H.mem.p);
+      std::swap(carry->mem.s, H.mem.s);
+      carry->cap = H.cap;
+      carry->out = H.out;
+      return MST_OK;
+    }
+    return filter(H.list(), mH, false, depth + 1, relaxed, cf.cur_u != nullptr);
   }
 
   mst_status finalize(const uint32_t *w, uint32_t *out_ids, uint32_t *out_count, u64 *total_weight) {
@@ -949,6 +980,7 @@ mst_status validate_cfg(const mst_config *cfg) {
   if (cfg->base_case < 0 || cfg->base_case > 1) return MST_ERR_INVALID_ARG;
   if (cfg->graph_rounds < 0 || cfg->graph_rounds > 1) return MST_ERR_INVALID_ARG;
   if (cfg->graph_jump_launches < 1 || cfg->graph_jump_launches > 8) return MST_ERR_INVALID_ARG;
+  if (cfg->filter_carry < 0 || cfg->filter_carry > 1) return MST_ERR_INVALID_ARG;
   if (cfg->tile_vertices < 32 || cfg->tile_vertices > 4096) return MST_ERR_INVALID_ARG;
   return MST_OK;
 }
@@ -1100,6 +1132,7 @@ void mst_config_default(mst_config *cfg) {
   cfg->base_case = 1;
   cfg->graph_rounds = 1;
   cfg->graph_jump_launches = 2;
+  cfg->filter_carry = 0;  // measured slower on GB300 (the merged tail loses the fused minEdges)
 }
 
 const char *mst_status_string(mst_status s) {

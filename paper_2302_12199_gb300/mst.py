@@ -45,7 +45,8 @@ class MstConfig(ctypes.Structure):
                 ("tile_contract", ctypes.c_int), ("tile_vertices", ctypes.c_uint32),
                 ("pivot_sample", ctypes.c_uint32), ("seed", ctypes.c_uint64), ("filter_min_edges", ctypes.c_uint64),
                 ("filter_max_avg_degree", ctypes.c_float), ("base_case", ctypes.c_int),
-                ("graph_rounds", ctypes.c_int), ("graph_jump_launches", ctypes.c_int)]
+                ("graph_rounds", ctypes.c_int), ("graph_jump_launches", ctypes.c_int),
+                ("filter_carry", ctypes.c_int)]
 
 
 _P = ctypes.c_void_p

@@ -424,3 +424,25 @@ def test_graph_rounds_on_and_off_agree(dev, family):
                 assert graph_launches == 0
         finally:
             s.close()
+
+
+@pytest.mark.parametrize("family", ["rmat", "gnm", "rhg", "rgg2"])
+def test_filter_carry_on_and_off_agree(dev, family):
+    """Small filtered sets handed back up the Filter-Borůvka recursion
+    (Section 6.3) give the oracle's forest, as does solving every level's."""
+    g = {
+        "rmat": lambda: W.rmat(17, 1 << 21, 71),
+        "gnm": lambda: W.gnm(1 << 15, 1 << 20, 72),
+        "rhg": lambda: W.rhg(1 << 16, 24.0, 73),
+        "rgg2": lambda: W.rgg(2, 1 << 16, 20.0, 74),
+    }[family]()
+    kid, ktot = oracle.kruskal(g.n, g.src, g.dst, g.w)
+    for carry in (0, 1):
+        for deg in (1.0, 4.0):
+            s = Solver(0, variant="filter", filter_carry=carry, filter_min_edges=1 << 12, filter_max_avg_degree=deg,
+                       pivot_sample=4096)
+            try:
+                ids, tot = gpu_msf(s, g.n, g.src, g.dst, g.w, dev)
+                assert np.array_equal(ids, kid) and tot == ktot, (carry, deg)
+            finally:
+                s.close()
