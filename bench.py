@@ -89,6 +89,23 @@ def traffic_source_digest():
     return hashlib.sha256(text[i:j].encode()).hexdigest()
 
 
+def reduce_scalar(x: float, op: str, dist, device) -> float:
+    """x combined over all ranks by "max" or "sum" (x itself without a process group)."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX if op == "max" else dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def job_rate(units_per_rank: float, seconds: float, world: int, dist, device):
+    """Whole-job rate of `world` replicas that each processed units_per_rank in
+    `seconds`: all units over the slowest rank's time.  Returns (rate, slowest)."""
+    slowest = reduce_scalar(seconds, "max", dist, device)
+    return units_per_rank * world / slowest, slowest
+
+
 def nvtx_mark(torch, what: str) -> None:
     """Opens or closes the NVTX range "timed" (no-op where NVTX is missing)."""
     try:
@@ -349,12 +366,8 @@ def gpu_main(args, rank: int, world: int, local_rank: int):
     if not (np.array_equal(ids, ref_ids) and total == ref_total):
         raise RuntimeError("timed solves returned a different forest than the warm-up solve")
 
-    ms_max = ms
-    if dist:
-        t = torch.tensor([ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_max = float(t.item())
-    value = m * args.steps * world / (ms_max / 1e3)
+    value, slowest_s = job_rate(m * args.steps, ms / 1e3, world, dist, dev)
+    ms_max = slowest_s * 1e3
 
     # end to end through the public API with host buffers: H2D of the inputs
     # from pinned memory and D2H of the forest inside the timed region
@@ -371,12 +384,8 @@ def gpu_main(args, rank: int, world: int, local_rank: int):
         cnt, _tot = solver.solve_host_ptr(n, m, pin[0].data_ptr(), pin[1].data_ptr(), pin[2].data_ptr(),
                                           ids_h.data_ptr())
     torch.cuda.synchronize(dev)
-    e2e_s = time.perf_counter() - t0
-    if dist:
-        t = torch.tensor([e2e_s], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
-    e2e = {"value": m * e2e_steps * world / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 12 * m,
+    e2e_value, e2e_s = job_rate(m * e2e_steps, time.perf_counter() - t0, world, dist, dev)
+    e2e = {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 12 * m,
            "d2h_bytes_per_step": 4 * cnt + 12, "steps": e2e_steps}
 
     peaks = measured_peaks()
@@ -519,12 +528,7 @@ def batched_main(args, rank: int, world: int, local_rank: int):
     ids, moff, tot = [t.cpu() for t in res]
     if not (torch.equal(ids, ref_ids) and torch.equal(moff, ref_off) and torch.equal(tot, ref_tot)):
         raise RuntimeError("timed batched solves returned different forests than the warm-up solve")
-    total_s = sum(lat)
-    if dist:
-        t = torch.tensor([total_s], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_s = float(t.item())
-    value = G * args.steps * world / total_s
+    value, total_s = job_rate(G * args.steps, sum(lat), world, dist, dev)
 
     # baseline: one mst_solve per graph, plain Borůvka, same GPU and stream
     base = Solver(local_rank, variant="boruvka", dedupe="none", tile_contract=0)
@@ -568,8 +572,8 @@ def batched_main(args, rank: int, world: int, local_rank: int):
         h_ids, h_off, h_tot = r_ids.cpu(), r_off.cpu(), r_tot.cpu()
         d2h = h_ids.numel() * 4 + h_off.numel() * 8 + h_tot.numel() * 8
     torch.cuda.synchronize(dev)
-    e2e_s = time.perf_counter() - t0
-    e2e = {"value": G * e2e_steps * world / e2e_s, "unit": "graphs/s", "h2d_bytes_per_step": 12 * m_tot,
+    e2e_value, _ = job_rate(G * e2e_steps, time.perf_counter() - t0, world, dist, dev)
+    e2e = {"value": e2e_value, "unit": "graphs/s", "h2d_bytes_per_step": 12 * m_tot,
            "d2h_bytes_per_step": d2h, "steps": e2e_steps}
 
     peaks = measured_peaks()
