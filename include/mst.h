@@ -79,6 +79,9 @@ typedef struct {
   int filter_carry;            /* Filter-Borůvka: 1 hands a level's filtered heavy edges, when at most
                                   n/8, back to the level above instead of solving them there (Section
                                   6.3); 0 (default, measured faster on GB300): every level solves its own */
+  int filter_split;            /* Filter-Borůvka: 1 filters in two passes (heavy edges outside the giant
+                                  component first, then the label test on that short list); 0 (default):
+                                  one pass */
 } mst_config;
 
 /* Fills *cfg with the defaults (Borůvka variant, automatic dedupe, pivot sample

@@ -74,6 +74,7 @@ enum CompactMode : int {
   CM_PARTITION = 1,  // key <= pivot and u != v; unchanged
   CM_FILTER = 2,     // key > pivot; (label[u], label[v]); drop self-loops
   CM_DEDUPE = 3,     // keep iff the hash table holds this edge's key for its pair
+  CM_HEAVY = 4,      // key > pivot and not both ends in the giant component; unchanged (first filter pass)
 };
 
 struct CompactArgs {

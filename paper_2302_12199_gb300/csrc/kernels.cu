@@ -341,12 +341,24 @@ __device__ __forceinline__ uint32_t keep_flags(const CompactArgs &a, uint64_t tb
       }
     } else if (MODE == CM_PARTITION) {
       ok = ok && eu[k] != ev[k] && (((u64)ew[k] << 32) | ei[k]) <= pivot;
-    } else if (MODE == CM_FILTER) {
+    } else if (MODE == CM_FILTER || MODE == CM_HEAVY) {
       ok = ok && (((u64)ew[k] << 32) | ei[k]) > pivot;  // heavy; resolved below for all items at once
     } else {  // CM_DEDUPE
       if (ok) ok = hash_lookup(a.table, a.tmask, pair_of(eu[k], ev[k])) == edge_key(ew[k], ei[k]);
     }
     keep |= (ok ? 1u : 0u) << k;
+  }
+  if (MODE == CM_HEAVY && a.giant_bits) {  // drop heavy edges inside the giant component; keep the ends
+    uint32_t bu[ITEMS], bv[ITEMS];
+#pragma unroll
+    for (int k = 0; k < ITEMS; ++k) {
+      const bool h = keep >> k & 1;
+      bu[k] = h ? __ldg(a.giant_bits + (eu[k] >> 5)) : 0u;
+      bv[k] = h ? __ldg(a.giant_bits + (ev[k] >> 5)) : 0u;
+    }
+#pragma unroll
+    for (int k = 0; k < ITEMS; ++k)
+      if ((bu[k] >> (eu[k] & 31)) & (bv[k] >> (ev[k] & 31)) & 1u) keep &= ~(1u << k);
   }
   if (MODE == CM_FILTER) {
     // Heavy edges with both ends in the marked (largest) component lie inside
@@ -447,7 +459,8 @@ __device__ __forceinline__ void emit_survivors(const CompactArgs &a, uint32_t ke
 }
 
 __device__ __forceinline__ u64 compact_pivot(const CompactArgs &a, int mode) {
-  return (mode == CM_PARTITION || mode == CM_FILTER) ? (a.pivot_dev ? *a.pivot_dev : a.pivot) : 0ULL;
+  return (mode == CM_PARTITION || mode == CM_FILTER || mode == CM_HEAVY) ? (a.pivot_dev ? *a.pivot_dev : a.pivot)
+                                                                         : 0ULL;
 }
 
 // One stream-compaction pass over an edge list, one tile per block.
@@ -1872,6 +1885,7 @@ void launch_compact(CompactMode mode, const CompactArgs &a, uint64_t max_count, 
     case CM_PARTITION: launch_compact_mode<CM_PARTITION>(a, max_count, s); break;
     case CM_FILTER: launch_compact_mode<CM_FILTER>(a, max_count, s); break;
     case CM_DEDUPE: launch_compact_mode<CM_DEDUPE>(a, max_count, s); break;
+    case CM_HEAVY: launch_compact_mode<CM_HEAVY>(a, max_count, s); break;
   }
 }
 

@@ -891,8 +891,32 @@ struct Solve {
     record_ends(cf);
     cf.st = next_scan(c, CNT_EDGES);
     TRY(zero_counters(c, s));
-    PROF(MST_K_FILTER, in_bytes, CNT_EDGES, 16.0, -1, 0.0, launch_compact(CM_FILTER, cf, mE, s));
+    ListBuf C;
+    if (c->cfg.filter_split) {
+      // two passes: the streaming pass keeps the heavy edges not inside the
+      // giant component (bitmap gathers only), the filter then gathers the
+      // labels for that short list
+      TRY(C.alloc(c, mE - mL, s));
+      CompactArgs ch{};
+      ch.in = E;
+      ch.m = mE;
+      ch.out = C.out;
+      ch.giant_bits = cf.giant_bits;
+      ch.pivot = pivot;
+      ch.n = n;
+      ch.kl = kl;
+      ch.st = next_scan(c, CNT_TMP);
+      PROF(MST_K_FILTER, in_bytes, CNT_TMP, 16.0, -1, 0.0, launch_compact(CM_HEAVY, ch, mE, s));
+      cf.in = C.list();
+      cf.m = mE - mL;
+      cf.m_dev = &c->ds->count[CNT_TMP];
+      cf.giant_bits = nullptr;
+      PROF(MST_K_FILTER, 0.0, CNT_TMP, 16.0, CNT_EDGES, 16.0, launch_compact(CM_FILTER, cf, mE - mL, s));
+    } else {
+      PROF(MST_K_FILTER, in_bytes, CNT_EDGES, 16.0, -1, 0.0, launch_compact(CM_FILTER, cf, mE, s));
+    }
     TRY(readback(c, s));
+    C.mem.release();
     giant_b.release();
     uint64_t mH = c->hs->count[CNT_EDGES];
     bool relaxed = true;  // best[] holds the minEdges of H
@@ -981,6 +1005,7 @@ mst_status validate_cfg(const mst_config *cfg) {
   if (cfg->graph_rounds < 0 || cfg->graph_rounds > 1) return MST_ERR_INVALID_ARG;
   if (cfg->graph_jump_launches < 1 || cfg->graph_jump_launches > 8) return MST_ERR_INVALID_ARG;
   if (cfg->filter_carry < 0 || cfg->filter_carry > 1) return MST_ERR_INVALID_ARG;
+  if (cfg->filter_split < 0 || cfg->filter_split > 1) return MST_ERR_INVALID_ARG;
   if (cfg->tile_vertices < 32 || cfg->tile_vertices > 4096) return MST_ERR_INVALID_ARG;
   return MST_OK;
 }
@@ -1133,6 +1158,7 @@ void mst_config_default(mst_config *cfg) {
   cfg->graph_rounds = 1;
   cfg->graph_jump_launches = 2;
   cfg->filter_carry = 0;  // measured slower on GB300 (the merged tail loses the fused minEdges)
+  cfg->filter_split = 0;
 }
 
 const char *mst_status_string(mst_status s) {

@@ -437,12 +437,12 @@ def test_filter_carry_on_and_off_agree(dev, family):
         "rgg2": lambda: W.rgg(2, 1 << 16, 20.0, 74),
     }[family]()
     kid, ktot = oracle.kruskal(g.n, g.src, g.dst, g.w)
-    for carry in (0, 1):
+    for carry, split in ((0, 0), (1, 0), (0, 1), (1, 1)):
         for deg in (1.0, 4.0):
-            s = Solver(0, variant="filter", filter_carry=carry, filter_min_edges=1 << 12, filter_max_avg_degree=deg,
-                       pivot_sample=4096)
+            s = Solver(0, variant="filter", filter_carry=carry, filter_split=split, filter_min_edges=1 << 12,
+                       filter_max_avg_degree=deg, pivot_sample=4096)
             try:
                 ids, tot = gpu_msf(s, g.n, g.src, g.dst, g.w, dev)
-                assert np.array_equal(ids, kid) and tot == ktot, (carry, deg)
+                assert np.array_equal(ids, kid) and tot == ktot, (carry, split, deg)
             finally:
                 s.close()
