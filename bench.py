@@ -68,8 +68,8 @@ WORKLOADS = {
 TRAFFIC = {
     "class": "filter",
     "kernel": "compact_tma_kernel<CM_FILTER>",
-    "dram_per_algorithmic_byte": 1.352,
-    "source_sha256": "e81fd73b978bfb7a9fb715fd2278456775c2b34e408c08143cdbebdbb6a8b039",
+    "dram_per_algorithmic_byte": 1.354,
+    "source_sha256": "6f730b384a84122742ec9b298f1ff24e57921fcab8966ae0c4d2b6414b44972b",
     "summary": "profiles/filter_compaction_rmat.md",
 }
 TRAFFIC_SOURCE = ("paper_2302_12199_gb300/csrc/kernels.cu",
