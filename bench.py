@@ -716,7 +716,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--variant", default=None, choices=["boruvka", "filter", "auto"],
                     help="override the workload's solver variant")
-    ap.add_argument("--dedupe", default=None, choices=["auto", "hash", "none"])
+    ap.add_argument("--dedupe", default=None, choices=["auto", "sort", "hash", "none"])
     ap.add_argument("--filter-max-avg-degree", type=float, default=None)
     ap.add_argument("--filter-min-edges", type=int, default=None)
     ap.add_argument("--tile-contract", type=int, default=None, choices=[-1, 0, 1])

@@ -50,7 +50,7 @@ typedef enum {
 } mst_status;
 
 enum { MST_VARIANT_BORUVKA = 0, MST_VARIANT_FILTER = 1, MST_VARIANT_AUTO = 2 };
-enum { MST_DEDUPE_AUTO = 0, MST_DEDUPE_HASH = 2, MST_DEDUPE_NONE = 3 };
+enum { MST_DEDUPE_AUTO = 0, MST_DEDUPE_SORT = 1, MST_DEDUPE_HASH = 2, MST_DEDUPE_NONE = 3 };
 
 typedef struct {
   int device;                  /* CUDA device ordinal */

@@ -2,8 +2,8 @@
 
 The fastest way through a workload depends on its graphs: the Filter-Borůvka
 variant (Alg. 2) pays off on dense, heavy-tailed graphs, parallel-edge removal
-(Section 2.3, optional) on graphs whose contracted rounds keep many parallel
-edges, and tile-local contraction (Section 4.1) only where vertex numbering
+(Section 2.3, optional; by hashing or by sorting) on graphs whose contracted
+rounds keep many parallel edges, and tile-local contraction (Section 4.1) only where vertex numbering
 gives locality.  Rather than guess, the autotuner times each candidate
 configuration on the caller's own input and keeps the fastest.  Every
 candidate computes the same forest (the MSF under the (w, id) order is
@@ -19,6 +19,7 @@ from typing import Callable, Dict, Iterable, List, Tuple
 DEFAULT_CANDIDATES: Tuple[dict, ...] = (
     dict(variant="boruvka", dedupe="none", tile_contract=0),
     dict(variant="boruvka", dedupe="hash", tile_contract=0),
+    dict(variant="boruvka", dedupe="sort", tile_contract=0),
     dict(variant="filter", dedupe="none", tile_contract=0),
     dict(variant="boruvka", dedupe="none", tile_contract=1),
 )

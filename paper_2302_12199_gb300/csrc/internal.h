@@ -150,6 +150,19 @@ bool launch_tile_contract(uint32_t n, uint32_t B, uint64_t nlocal, const u64 *cu
                           uint32_t *bits, EdgeOut rest, u64 *rest_fill, uint32_t *err, cudaStream_t s);
 void launch_tile_sample(EdgeList in, uint64_t m, uint32_t n, uint32_t B, u64 state, uint32_t samples,
                         uint32_t *local_count, cudaStream_t s);
+// Stable LSD radix sort of (u64 key, u32 value) pairs over the low `bits` bits;
+// true when the result is in (keys_tmp, vals_tmp).  hist holds radix_hist_bytes().
+size_t radix_hist_bytes(uint64_t m, int sms);
+bool launch_radix_sort(u64 *keys, uint32_t *vals, u64 *keys_tmp, uint32_t *vals_tmp, uint64_t m, int bits,
+                       uint32_t *hist, int sms, cudaStream_t s);
+// Sort-based parallel-edge removal of list T (ends already component labels,
+// no self-loops, ids present): keeps each unordered pair's (w, id)-lightest
+// edge and emits it through `emit` (out, counter, best / ends as a compaction).
+// vbits: bits of a vertex label; wbits, ibits: of a weight and an id.
+size_t sort_dedupe_scratch_bytes(uint64_t m, int sms);
+void launch_sort_dedupe(EdgeList T, uint64_t m, int vbits, int wbits, int ibits, const CompactArgs &emit,
+                        void *scratch, int sms, cudaStream_t s);
+
 // Borůvka rounds as a CUDA graph (device-driven loop): state in device memory.
 enum : uint32_t { ROUNDS_RUNNING = 0xff, ROUNDS_DONE = 0, ROUNDS_BASE = 1, ROUNDS_JUMP = 2, ROUNDS_BOUND = 3 };
 struct GraphRounds {

@@ -1558,6 +1558,256 @@ __global__ void __launch_bounds__(TC_THREADS) tile_contract_kernel(uint32_t n, u
   }
 }
 
+// ---------------------------------------------------------- radix sort
+
+// Stable LSD radix sort of (u64 key, u32 value) pairs, 8-bit digits, for the
+// sort-based parallel-edge removal.  Each of RS_BLOCKS blocks owns one
+// contiguous chunk of the input: per pass it counts its chunk's digits, one
+// block scans the counts (digit-major, so a digit's items from earlier chunks
+// come first), and each block scatters its chunk in input order.  Within a
+// 2048-item tile the items go in eight sub-rounds of 256 consecutive items; a
+// warp ranks equal digits among its lanes with __match_any_sync, and the
+// per-warp counts of a sub-round are scanned in warp order: the result is
+// stable.
+constexpr int RS_BITS = 8, RS_BINS = 1 << RS_BITS, RS_WARPS = BLOCK / 32;
+
+__device__ __forceinline__ void rs_chunk(uint64_t m, uint64_t &lo, uint64_t &hi) {
+  const uint64_t per = ((m + gridDim.x - 1) / gridDim.x + TILE - 1) / TILE * TILE;
+  lo = min(m, (uint64_t)blockIdx.x * per);
+  hi = min(m, lo + per);
+}
+
+__global__ void __launch_bounds__(BLOCK) radix_hist_kernel(const u64 *keys, uint64_t m, int shift, uint32_t *hist) {
+  __shared__ uint32_t sh[RS_BINS];
+  for (int d = threadIdx.x; d < RS_BINS; d += BLOCK) sh[d] = 0;
+  __syncthreads();
+  uint64_t lo, hi;
+  rs_chunk(m, lo, hi);
+  for (uint64_t i = lo + threadIdx.x; i < hi; i += BLOCK) atomicAdd(&sh[(keys[i] >> shift) & (RS_BINS - 1)], 1u);
+  __syncthreads();
+  for (int d = threadIdx.x; d < RS_BINS; d += BLOCK) hist[(uint64_t)d * gridDim.x + blockIdx.x] = sh[d];
+}
+
+// Exclusive scan, in place, of `count` entries (one block of 1024 threads).
+__global__ void __launch_bounds__(1024) radix_scan_kernel(uint32_t *a, uint32_t count) {
+  __shared__ uint32_t s_w[33];
+  const uint32_t per = (count + 1023) / 1024;
+  const uint32_t lo = min(count, threadIdx.x * per), hi = min(count, lo + per);
+  uint32_t sum = 0;
+  for (uint32_t i = lo; i < hi; ++i) sum += a[i];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  uint32_t incl = sum;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += y;
+  }
+  if (lane == 31) s_w[wid] = incl;
+  __syncthreads();
+  if (wid == 0) {
+    const uint32_t v = s_w[lane];
+    uint32_t wi = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, wi, o);
+      if (lane >= o) wi += y;
+    }
+    s_w[lane] = wi - v;
+  }
+  __syncthreads();
+  uint32_t run = s_w[wid] + incl - sum;
+  for (uint32_t i = lo; i < hi; ++i) {
+    const uint32_t x = a[i];
+    a[i] = run;
+    run += x;
+  }
+}
+
+__global__ void __launch_bounds__(BLOCK) radix_scatter_kernel(const u64 *keys, const uint32_t *vals, uint64_t m,
+                                                              int shift, const uint32_t *offsets, u64 *keys_out,
+                                                              uint32_t *vals_out) {
+  __shared__ uint32_t base[RS_BINS];
+  __shared__ uint32_t wc[RS_WARPS][RS_BINS];
+  for (int d = threadIdx.x; d < RS_BINS; d += BLOCK) base[d] = offsets[(uint64_t)d * gridDim.x + blockIdx.x];
+  uint64_t lo, hi;
+  rs_chunk(m, lo, hi);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const uint32_t lt = (1u << lane) - 1u;
+  for (uint64_t tb = lo; tb < hi; tb += BLOCK) {  // one sub-round: BLOCK consecutive items
+    const uint64_t i = tb + threadIdx.x;
+    const bool in = i < hi;
+    const u64 k = in ? keys[i] : 0;
+    const uint32_t val = in ? vals[i] : 0u;
+    const uint32_t d = in ? (uint32_t)((k >> shift) & (RS_BINS - 1)) : (uint32_t)RS_BINS;
+    for (int w = 0; w < RS_WARPS; ++w) wc[w][threadIdx.x & (RS_BINS - 1)] = 0;
+    __syncthreads();
+    const uint32_t peers = __match_any_sync(0xffffffffu, d);
+    const uint32_t rank = __popc(peers & lt);
+    if (in && rank == 0) wc[wid][d] = __popc(peers);
+    __syncthreads();
+    {  // warp-order exclusive offsets of each digit (thread t owns digit t)
+      const int dd = threadIdx.x;
+      uint32_t run = base[dd];
+      for (int w = 0; w < RS_WARPS; ++w) {
+        const uint32_t c = wc[w][dd];
+        wc[w][dd] = run;
+        run += c;
+      }
+      base[dd] = run;
+    }
+    __syncthreads();
+    if (in) {
+      const uint32_t pos = wc[wid][d] + rank;
+      keys_out[pos] = k;
+      vals_out[pos] = val;
+    }
+    __syncthreads();
+  }
+}
+
+// Exclusive scan of the digit counts in three coalesced steps: per-segment
+// sums, a scan of the (few) sums, per-segment scans from their offsets.
+constexpr uint32_t RS_SEG = 4096;
+
+__global__ void __launch_bounds__(BLOCK) rs_seg_sum_kernel(const uint32_t *a, uint32_t count, uint32_t *sums) {
+  __shared__ uint32_t s_w[BLOCK / 32];
+  const uint32_t lo = blockIdx.x * RS_SEG, hi = min(count, lo + RS_SEG);
+  uint32_t x = 0;
+  for (uint32_t i = lo + threadIdx.x; i < hi; i += BLOCK) x += a[i];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+  if ((threadIdx.x & 31) == 0) s_w[threadIdx.x >> 5] = x;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    uint32_t t = 0;
+    for (int w = 0; w < BLOCK / 32; ++w) t += s_w[w];
+    sums[blockIdx.x] = t;
+  }
+}
+
+__global__ void __launch_bounds__(BLOCK) rs_seg_scan_kernel(uint32_t *a, uint32_t count, const uint32_t *offs) {
+  __shared__ uint32_t s_warp[BLOCK / 32 + 1];
+  const uint32_t lo = blockIdx.x * RS_SEG, hi = min(count, lo + RS_SEG);
+  uint32_t carry = offs[blockIdx.x];
+  for (uint32_t b0 = lo; b0 < hi; b0 += BLOCK) {  // uniform trip count
+    const uint32_t i = b0 + threadIdx.x;
+    const uint32_t x = i < hi ? a[i] : 0u;
+    uint32_t total;
+    const uint32_t ex = block_exclusive_scan(x, total, s_warp);
+    if (i < hi) a[i] = carry + ex;
+    carry += total;
+    __syncthreads();  // s_warp is reused by the next chunk
+  }
+}
+
+int radix_blocks(uint64_t m, int sms) {
+  const uint64_t tiles = (m + TILE - 1) / TILE;
+  return (int)std::max<uint64_t>(1, std::min<uint64_t>(tiles, (uint64_t)sms * 4));
+}
+
+size_t radix_hist_bytes(uint64_t m, int sms) {
+  const size_t entries = (size_t)RS_BINS * radix_blocks(m, sms);
+  return (entries + (entries + RS_SEG - 1) / RS_SEG) * sizeof(uint32_t);  // counts, then segment sums
+}
+
+bool launch_radix_sort(u64 *keys, uint32_t *vals, u64 *keys_tmp, uint32_t *vals_tmp, uint64_t m, int bits,
+                       uint32_t *hist, int sms, cudaStream_t s) {
+  if (m == 0) return false;
+  const int nb = radix_blocks(m, sms);
+  const uint32_t entries = (uint32_t)RS_BINS * (uint32_t)nb;
+  bool swapped = false;
+  for (int shift = 0; shift < bits; shift += RS_BITS) {
+    const u64 *ki = swapped ? keys_tmp : keys;
+    const uint32_t *vi = swapped ? vals_tmp : vals;
+    u64 *ko = swapped ? keys : keys_tmp;
+    uint32_t *vo = swapped ? vals : vals_tmp;
+    radix_hist_kernel<<<nb, BLOCK, 0, s>>>(ki, m, shift, hist);
+    const uint32_t nseg = (entries + RS_SEG - 1) / RS_SEG;  // <= 1024: one block scans the segment sums
+    uint32_t *sums = hist + entries;
+    rs_seg_sum_kernel<<<nseg, BLOCK, 0, s>>>(hist, entries, sums);
+    radix_scan_kernel<<<1, 1024, 0, s>>>(sums, nseg);
+    rs_seg_scan_kernel<<<nseg, BLOCK, 0, s>>>(hist, entries, sums);
+    radix_scatter_kernel<<<nb, BLOCK, 0, s>>>(ki, vi, m, shift, hist, ko, vo);
+    swapped = !swapped;
+  }
+  return swapped;
+}
+
+// ------------------------------------------- sort-based parallel-edge removal
+
+// Parallel-edge removal by sorting (Section 2.3; the sort variant of Section
+// 4.3): sort the list by (w, id), then stably by the unordered pair
+// {min(u,v), max(u,v)}; the first edge of every pair run is the pair's lightest.
+__global__ void sd_key_kernel(EdgeList T, uint64_t m, int ib, u64 *keys, uint32_t *vals) {
+  for (uint64_t j = (uint64_t)blockIdx.x * BLOCK + threadIdx.x; j < m; j += (uint64_t)gridDim.x * BLOCK) {
+    keys[j] = ((u64)T.w[j] << ib) | (u64)T.id[j];
+    vals[j] = (uint32_t)j;
+  }
+}
+
+__global__ void sd_pair_kernel(EdgeList T, const uint32_t *idx, uint64_t m, int vb, u64 *keys, uint32_t *vals) {
+  for (uint64_t j = (uint64_t)blockIdx.x * BLOCK + threadIdx.x; j < m; j += (uint64_t)gridDim.x * BLOCK) {
+    const uint32_t i = idx[j];
+    const uint32_t u = T.u[i], v = T.v[i];
+    keys[j] = ((u64)min(u, v) << vb) | (u64)max(u, v);
+    vals[j] = i;
+  }
+}
+
+// Keeps position j of the pair-sorted order when it starts a run, gathers that
+// edge from T and emits it like a compaction (relaxing best[] / recording ends).
+__global__ void __launch_bounds__(BLOCK) sd_emit_kernel(const u64 *pk, const uint32_t *idx, uint64_t m, CompactArgs a) {
+  __shared__ uint32_t s_u[TILE], s_v[TILE], s_w[TILE], s_id[TILE];
+  __shared__ uint32_t s_warp[BLOCK / 32 + 1];
+  __shared__ uint32_t s_base[1];
+  const uint64_t tb = (uint64_t)blockIdx.x * TILE;
+  if (tb >= m) return;
+  uint32_t eu[ITEMS], ev[ITEMS], ew[ITEMS], ei[ITEMS];
+  uint32_t keep = 0;
+#pragma unroll
+  for (int k = 0; k < ITEMS; ++k) {
+    const uint64_t j = tb + item_off(k);
+    const bool head = j < m && (j == 0 || pk[j] != pk[j - 1]);
+    eu[k] = ev[k] = ew[k] = ei[k] = 0;
+    if (head) {
+      const uint32_t i = idx[j];
+      eu[k] = a.in.u[i];
+      ev[k] = a.in.v[i];
+      ew[k] = a.in.w[i];
+      ei[k] = a.in.id[i];
+      if (eu[k] != ev[k]) keep |= 1u << k;  // self-loops are never kept
+    }
+  }
+  uint32_t totp;
+  const uint32_t excl = block_exclusive_scan(packed_counts(keep), totp, s_warp);
+  const uint64_t obase = tile_claim(a.st.total, (totp & 0xffffu) + (totp >> 16), s_base);
+  emit_survivors(a, keep, excl, totp, obase, eu, ev, ew, ei, s_u, s_v, s_w, s_id);
+}
+
+size_t sort_dedupe_scratch_bytes(uint64_t m, int sms) {
+  return 2 * ((m * 8 + 255) / 256 * 256) + 2 * ((m * 4 + 255) / 256 * 256) + radix_hist_bytes(m, sms) + 256;
+}
+
+void launch_sort_dedupe(EdgeList T, uint64_t m, int vbits, int wbits, int ibits, const CompactArgs &emit,
+                        void *scratch, int sms, cudaStream_t s) {
+  if (m == 0) return;
+  char *p = (char *)scratch;
+  const size_t kb = (m * 8 + 255) / 256 * 256, vb = (m * 4 + 255) / 256 * 256;
+  u64 *k0 = (u64 *)p, *k1 = (u64 *)(p + kb);
+  uint32_t *v0 = (uint32_t *)(p + 2 * kb), *v1 = (uint32_t *)(p + 2 * kb + vb);
+  uint32_t *hist = (uint32_t *)(p + 2 * kb + 2 * vb);
+  const unsigned grid = (unsigned)std::max<uint64_t>(1, std::min<uint64_t>((m + BLOCK - 1) / BLOCK, (uint64_t)sms * 8));
+  sd_key_kernel<<<grid, BLOCK, 0, s>>>(T, m, ibits, k0, v0);
+  const bool in1 = launch_radix_sort(k0, v0, k1, v1, m, wbits + ibits, hist, sms, s);
+  u64 *ka = in1 ? k1 : k0, *kb2 = in1 ? k0 : k1;
+  uint32_t *va = in1 ? v1 : v0, *vb2 = in1 ? v0 : v1;
+  sd_pair_kernel<<<grid, BLOCK, 0, s>>>(T, va, m, vbits, kb2, vb2);  // pairs in (w, id) order
+  const bool in2 = launch_radix_sort(kb2, vb2, ka, va, m, 2 * vbits, hist, sms, s);
+  const u64 *pk = in2 ? ka : kb2;
+  const uint32_t *pidx = in2 ? va : vb2;
+  sd_emit_kernel<<<(unsigned)((m + TILE - 1) / TILE), BLOCK, 0, s>>>(pk, pidx, m, emit);
+}
+
 // ------------------------------------------------- device-driven round loop
 
 // State of the Borůvka rounds run as a CUDA graph: a conditional WHILE node

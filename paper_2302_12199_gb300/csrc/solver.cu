@@ -318,6 +318,7 @@ struct Solve {
   }
   u64 *best = nullptr;
   uint32_t *parent = nullptr, *act[2] = {nullptr, nullptr}, *bits = nullptr;
+  int wbits = 32;  // bits of the largest weight (set with the key layout)
   int rounds = 0;
 
   Solve(mst_ctx *c_, cudaStream_t s_, uint32_t n_, uint64_t m_) : c(c_), s(s_), n(n_), m(m_) {}
@@ -367,6 +368,7 @@ struct Solve {
     const int ib = m > 1 ? 64 - __builtin_clzll((unsigned long long)(m - 1)) : 1;
     const uint32_t mw = c->hs->max_w;
     const int wb = mw ? 32 - __builtin_clz(mw) : 0;
+    wbits = wb;
     kl = KeyLayout{wb + ib + vb <= 63 ? 1 : 0, vb, ib};
   }
 
@@ -396,7 +398,7 @@ struct Solve {
   // more than the parallel edges they remove save in later rounds.
   bool want_dedupe(int round, uint64_t cur_m) const {
     (void)round;
-    return c->cfg.dedupe == MST_DEDUPE_HASH && cur_m > 0;
+    return (c->cfg.dedupe == MST_DEDUPE_HASH || c->cfg.dedupe == MST_DEDUPE_SORT) && cur_m > 0;
   }
 
   // Borůvka rounds (Section 2.3) on the list E of mE edges whose endpoints are
@@ -468,6 +470,29 @@ struct Solve {
         record_ends(ca);
         ca.st = next_scan(c, CNT_EDGES);
         PROF(MST_K_RELABEL_MIN, in_bytes, CNT_EDGES, 16.0, -1, 0.0, launch_compact(CM_RELABEL, ca, cur_m, s));
+      } else if (c->cfg.dedupe == MST_DEDUPE_SORT) {
+        // relabel into T, then keep each pair's lightest edge by sorting
+        // (Section 2.3 parallel-edge removal, sort variant) and relax best[]
+        if (T.cap < cur_m) TRY(T.alloc(c, cur_m, s));
+        ca.out = T.out;
+        ca.st = next_scan(c, CNT_TMP);
+        PROF(MST_K_DEDUPE, in_bytes, CNT_TMP, 16.0, -1, 0.0, launch_compact(CM_RELABEL, ca, cur_m, s));
+        TRY(readback(c, s));
+        const uint64_t mT = c->hs->count[CNT_TMP];
+        Buf sd_b;
+        TRY(sd_b.alloc(c, sort_dedupe_scratch_bytes(mT, c->sms), s));
+        CompactArgs cd{};
+        cd.in = T.list();
+        cd.m = mT;
+        cd.out = out.out;
+        cd.best = best;
+        cd.kl = kl;
+        record_ends(cd);
+        cd.n = n;
+        cd.st = next_scan(c, CNT_EDGES);
+        const int passes = (wbits + kl.idbits + 7) / 8 + (2 * kl.vbits + 7) / 8;
+        PROF(MST_K_DEDUPE, (32.0 * passes + 56.0) * (double)mT, CNT_EDGES, 16.0, -1, 0.0,
+             launch_sort_dedupe(T.list(), mT, kl.vbits, wbits, kl.idbits, cd, sd_b.p, c->sms, s));
       } else {
         // relabel into T while inserting every pair into the hash table, then
         // keep each pair's minimum (Section 2.3 parallel-edge removal; the
@@ -996,7 +1021,8 @@ mst_status solve_device(mst_ctx *c, uint32_t n, uint64_t m, const uint32_t *src,
 
 mst_status validate_cfg(const mst_config *cfg) {
   if (cfg->variant < 0 || cfg->variant > 2) return MST_ERR_INVALID_ARG;
-  if (cfg->dedupe != MST_DEDUPE_AUTO && cfg->dedupe != MST_DEDUPE_HASH && cfg->dedupe != MST_DEDUPE_NONE)
+  if (cfg->dedupe != MST_DEDUPE_AUTO && cfg->dedupe != MST_DEDUPE_HASH && cfg->dedupe != MST_DEDUPE_NONE &&
+      cfg->dedupe != MST_DEDUPE_SORT)
     return MST_ERR_INVALID_ARG;
   if (cfg->pivot_sample == 0 || cfg->pivot_sample > (1u << 24)) return MST_ERR_INVALID_ARG;
   if (!(cfg->filter_max_avg_degree > 0.0f)) return MST_ERR_INVALID_ARG;
@@ -1492,8 +1518,38 @@ mst_status mst_step_relabel(mst_handle h, uint32_t n, uint64_t m, const uint32_t
 mst_status mst_step_dedupe(mst_handle h, uint64_t m, const uint32_t *d_u, const uint32_t *d_v, const uint32_t *d_w,
                            const uint32_t *d_id, uint32_t *d_ou, uint32_t *d_ov, uint32_t *d_ow, uint32_t *d_oid,
                            uint64_t *d_out_count, void *stream) {
-  return step_compact(h, CM_DEDUPE, 0, m, d_u, d_v, d_w, d_id, nullptr, 0, d_ou, d_ov, d_ow, d_oid, d_out_count,
-                      stream);
+  if (!h || h->cfg.dedupe != MST_DEDUPE_SORT)
+    return step_compact(h, CM_DEDUPE, 0, m, d_u, d_v, d_w, d_id, nullptr, 0, d_ou, d_ov, d_ow, d_oid, d_out_count,
+                        stream);
+  // sort variant: 32-bit ends, weights and ids, so the pair and (w, id) keys take 64 bits each
+  if (!d_out_count || (m > 0 && (!d_u || !d_v || !d_w || !d_ou || !d_ov || !d_ow || !d_oid)))
+    return record(h, MST_ERR_INVALID_ARG);
+  if (m >= (1ULL << 32)) return record(h, MST_ERR_TOO_LARGE);
+  DeviceGuard g(h->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  if (clear_device_flags(h, s) != MST_OK ||
+      cudaMemsetAsync(&h->ds->count[CNT_USER], 0, sizeof(u64), s) != cudaSuccess)
+    return record_cuda(h, __LINE__);
+  Buf id_b, sd_b;
+  mst_status st = MST_OK;
+  const uint32_t *ids = d_id;
+  if (m > 0 && !ids) {  // implicit ids: the index
+    st = id_b.alloc(h, m * 4, s);
+    if (st != MST_OK) return record(h, st);
+    launch_iota(id_b.as<uint32_t>(), m, h->sms, s);
+    ids = id_b.as<uint32_t>();
+  }
+  st = sd_b.alloc(h, sort_dedupe_scratch_bytes(m, h->sms), s);
+  if (st != MST_OK) return record(h, st);
+  CompactArgs cd{};
+  cd.in = EdgeList{d_u, d_v, d_w, ids};
+  cd.m = m;
+  cd.out = EdgeOut{d_ou, d_ov, d_ow, d_oid};
+  cd.st = next_scan(h, CNT_USER);
+  launch_sort_dedupe(cd.in, m, 32, 32, 32, cd, sd_b.p, h->sms, s);
+  if (cudaMemcpyAsync(d_out_count, &h->ds->count[CNT_USER], 8, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+    return record_cuda(h, __LINE__);
+  return record(h, readback(h, s));
 }
 
 mst_status mst_step_partition(mst_handle h, uint64_t m, const uint32_t *d_u, const uint32_t *d_v, const uint32_t *d_w,

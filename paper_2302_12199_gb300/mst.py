@@ -22,7 +22,7 @@ MST_ERR_CUDA = 5
 STATUS_NAMES = {0: "MST_OK", 1: "MST_ERR_INVALID_ARG", 2: "MST_ERR_VERTEX_RANGE", 3: "MST_ERR_TOO_LARGE",
                 4: "MST_ERR_OOM", 5: "MST_ERR_CUDA", 6: "MST_ERR_INTERNAL", 7: "MST_ERR_NOT_SUPPORTED"}
 VARIANTS = {"boruvka": 0, "filter": 1, "auto": 2}
-DEDUPE = {"auto": 0, "hash": 2, "none": 3}
+DEDUPE = {"auto": 0, "sort": 1, "hash": 2, "none": 3}
 KEY_INF = 0xFFFFFFFFFFFFFFFF
 
 

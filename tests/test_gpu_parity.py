@@ -19,6 +19,7 @@ pytestmark = pytest.mark.gpu
 CONFIGS = [
     dict(variant="boruvka", dedupe="none", tile_contract=0, base_case=0, graph_rounds=0),
     dict(variant="boruvka", dedupe="hash", tile_contract=-1),
+    dict(variant="boruvka", dedupe="sort"),
     dict(variant="boruvka", dedupe="auto"),
     dict(variant="filter", dedupe="auto", filter_min_edges=1 << 10, pivot_sample=4096, tile_contract=-1),
     dict(variant="filter", dedupe="none", filter_min_edges=1 << 12, filter_max_avg_degree=4.0, tile_contract=0,
@@ -26,8 +27,8 @@ CONFIGS = [
     dict(variant="boruvka", tile_contract=1, tile_vertices=512),
     dict(variant="filter", tile_contract=1, tile_vertices=256, filter_min_edges=1 << 10, pivot_sample=4096),
 ]
-CONFIG_IDS = ["boruvka-none", "boruvka-hash", "boruvka-auto", "filter-auto", "filter-deg4", "boruvka-tile",
-              "filter-tile"]
+CONFIG_IDS = ["boruvka-none", "boruvka-hash", "boruvka-sort", "boruvka-auto", "filter-auto", "filter-deg4",
+              "boruvka-tile", "filter-tile"]
 
 
 @pytest.fixture(scope="module")
@@ -252,6 +253,27 @@ def test_step_dedupe(step_solver, dev):
     ids = np.arange(u.size, dtype=np.uint32)
     out = step_solver.dedupe(*list_on_dev(dev, u, v, w, ids))
     assert_same_list(out, S.dedupe(u, v, w, ids))
+
+
+@pytest.mark.parametrize("m,vmax,wmax", [(50_003, 200, 5), (1_500_007, 3000, 40), (70_001, 1 << 22, 1 << 31)])
+def test_step_dedupe_sort(dev, m, vmax, wmax):
+    """The sort variant of parallel-edge removal (stable radix sorts by (w, id)
+    then by pair) keeps each pair's lightest edge, like the oracle."""
+    rng = np.random.default_rng(m)
+    u = rng.integers(0, vmax, m).astype(np.uint32)
+    v = rng.integers(0, vmax, m).astype(np.uint32)
+    keep = u != v
+    u, v = u[keep], v[keep]
+    w = rng.integers(1, wmax, u.size).astype(np.uint32)
+    ids = rng.permutation(u.size).astype(np.uint32) * 3 + 1
+    s = Solver(0, dedupe="sort")
+    try:
+        out = s.dedupe(*list_on_dev(dev, u, v, w, ids))
+        assert_same_list(out, S.dedupe(u, v, w, ids))
+        out0 = s.dedupe(*list_on_dev(dev, u, v, w), None)
+        assert_same_list(out0, S.dedupe(u, v, w, np.arange(u.size, dtype=np.uint32)))
+    finally:
+        s.close()
 
 
 def test_step_pivot(step_solver, dev):
