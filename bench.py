@@ -324,6 +324,8 @@ def gpu_main(args, rank: int, world: int, local_rank: int):
         cfg["filter_carry"] = args.filter_carry
     if args.filter_split is not None:
         cfg["filter_split"] = args.filter_split
+    if args.min_edges_sort is not None:
+        cfg["min_edges_sort"] = args.min_edges_sort
     g = gen(W)
     n, m = g.n, g.m
     src = torch.from_numpy(g.src.view(np.int32)).to(dev)
@@ -725,6 +727,7 @@ def main():
     ap.add_argument("--graph-rounds", type=int, default=None, choices=[0, 1])
     ap.add_argument("--filter-carry", type=int, default=None, choices=[0, 1])
     ap.add_argument("--filter-split", type=int, default=None, choices=[0, 1])
+    ap.add_argument("--min-edges-sort", type=int, default=None, choices=[0, 1])
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "gpu":
         args.warmup = 3

@@ -82,6 +82,9 @@ typedef struct {
   int filter_split;            /* Filter-Borůvka: 1 filters in two passes (heavy edges outside the giant
                                   component first, then the label test on that short list); 0 (default):
                                   one pass */
+  int min_edges_sort;          /* 1: the first minEdges of a Borůvka call sorts both ends of every edge by
+                                  vertex and takes segmented minima (one atomic per vertex run and warp, the
+                                  sorted-edge form of Sections 2.2/4.5); 0 (default): one atomic pass */
 } mst_config;
 
 /* Fills *cfg with the defaults (Borůvka variant, automatic dedupe, pivot sample

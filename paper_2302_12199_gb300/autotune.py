@@ -22,6 +22,7 @@ DEFAULT_CANDIDATES: Tuple[dict, ...] = (
     dict(variant="boruvka", dedupe="sort", tile_contract=0),
     dict(variant="filter", dedupe="none", tile_contract=0),
     dict(variant="boruvka", dedupe="none", tile_contract=1),
+    dict(variant="boruvka", dedupe="none", tile_contract=0, min_edges_sort=1),
 )
 
 _cache: Dict[str, dict] = {}

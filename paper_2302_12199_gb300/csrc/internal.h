@@ -163,6 +163,12 @@ size_t sort_dedupe_scratch_bytes(uint64_t m, int sms);
 void launch_sort_dedupe(EdgeList T, uint64_t m, int vbits, int wbits, int ibits, const CompactArgs &emit,
                         void *scratch, int sms, cudaStream_t s);
 
+// minEdges by sorting both ends of every edge by vertex and taking segmented
+// minima (one atomic per vertex run and warp); false if 2m does not fit 32 bits.
+size_t min_edges_sort_scratch_bytes(uint64_t m, int sms);
+bool launch_min_edges_sort(EdgeList E, uint64_t m, uint32_t n, int validate, KeyLayout kl, u64 *best, uint32_t *err,
+                           void *scratch, int sms, cudaStream_t s);
+
 // Borůvka rounds as a CUDA graph (device-driven loop): state in device memory.
 enum : uint32_t { ROUNDS_RUNNING = 0xff, ROUNDS_DONE = 0, ROUNDS_BASE = 1, ROUNDS_JUMP = 2, ROUNDS_BOUND = 3 };
 struct GraphRounds {

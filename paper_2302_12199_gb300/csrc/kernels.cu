@@ -1808,6 +1808,78 @@ void launch_sort_dedupe(EdgeList T, uint64_t m, int vbits, int wbits, int ibits,
   sd_emit_kernel<<<(unsigned)((m + TILE - 1) / TILE), BLOCK, 0, s>>>(pk, pidx, m, emit);
 }
 
+// ----------------------------------------------- sort-based minEdges
+
+// minEdges as a segmented minimum (the sorted-edge representation of Sections
+// 2.2 and 4.5): both ends of every edge become (vertex, 2j + side) entries,
+// sorted by vertex; each run of equal vertices is reduced by warp-segmented
+// minima with one atomic per run and warp, instead of one per edge end.
+__global__ void me_ends_kernel(EdgeList E, uint64_t m, uint32_t n, int validate, u64 *keys, uint32_t *vals,
+                               uint32_t *err) {
+  for (uint64_t j = (uint64_t)blockIdx.x * BLOCK + threadIdx.x; j < m; j += (uint64_t)gridDim.x * BLOCK) {
+    uint32_t u = E.u[j], v = E.v[j];
+    if (validate && (u >= n || v >= n)) {
+      atomicOr(err, ERR_VERTEX);
+      u = v = 0;  // dropped below as a self-loop
+    }
+    const bool live = u != v;
+    keys[2 * j] = live ? u : n;  // dead entries sort last (key n, above every vertex)
+    keys[2 * j + 1] = live ? v : n;
+    vals[2 * j] = (uint32_t)(2 * j);
+    vals[2 * j + 1] = (uint32_t)(2 * j + 1);
+  }
+}
+
+__global__ void me_segmin_kernel(const u64 *keys, const uint32_t *vals, uint64_t entries, uint32_t n, EdgeList E,
+                                 KeyLayout kl, u64 *best) {
+  const int lane = threadIdx.x & 31;
+  const uint64_t stride = (uint64_t)gridDim.x * BLOCK;
+  for (uint64_t b0 = (uint64_t)blockIdx.x * BLOCK; b0 < entries; b0 += stride) {  // warp-uniform trip count
+    const uint64_t p = b0 + threadIdx.x;
+    uint32_t vtx = 0xffffffffu;
+    u64 rk = KEY_INF;
+    if (p < entries && keys[p] < n) {
+      vtx = (uint32_t)keys[p];
+      const uint32_t e = vals[p] >> 1, side = vals[p] & 1u;
+      const uint32_t other = side ? E.u[e] : E.v[e];
+      rk = relax_key(kl, E.w[e], E.id ? E.id[e] : e, other);
+    }
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {  // segmented minimum over runs of one vertex
+      const u64 pr = __shfl_up_sync(0xffffffffu, rk, o);
+      const uint32_t pv = __shfl_up_sync(0xffffffffu, vtx, o);
+      if (lane >= o && pv == vtx && pr < rk) rk = pr;
+    }
+    const uint32_t nv = __shfl_down_sync(0xffffffffu, vtx, 1);
+    if (vtx != 0xffffffffu && (lane == 31 || nv != vtx) && rk < __ldca(best + vtx)) atomicMin(best + vtx, rk);
+  }
+}
+
+size_t min_edges_sort_scratch_bytes(uint64_t m, int sms) {
+  const uint64_t e = 2 * m;
+  return 2 * ((e * 8 + 255) / 256 * 256) + 2 * ((e * 4 + 255) / 256 * 256) + radix_hist_bytes(e, sms) + 256;
+}
+
+bool launch_min_edges_sort(EdgeList E, uint64_t m, uint32_t n, int validate, KeyLayout kl, u64 *best, uint32_t *err,
+                           void *scratch, int sms, cudaStream_t s) {
+  if (m == 0) return true;
+  if (2 * m >= (1ULL << 32)) return false;  // entry values are 32-bit
+  const uint64_t e = 2 * m;
+  char *p = (char *)scratch;
+  const size_t kb = (e * 8 + 255) / 256 * 256, vb = (e * 4 + 255) / 256 * 256;
+  u64 *k0 = (u64 *)p, *k1 = (u64 *)(p + kb);
+  uint32_t *v0 = (uint32_t *)(p + 2 * kb), *v1 = (uint32_t *)(p + 2 * kb + vb);
+  uint32_t *hist = (uint32_t *)(p + 2 * kb + 2 * vb);
+  const unsigned grid = (unsigned)std::max<uint64_t>(1, std::min<uint64_t>((m + BLOCK - 1) / BLOCK, (uint64_t)sms * 8));
+  me_ends_kernel<<<grid, BLOCK, 0, s>>>(E, m, n, validate, k0, v0, err);
+  int bits = 1;
+  while (bits < 33 && (1ULL << bits) <= (uint64_t)n) ++bits;  // keys 0..n (n: dead entries)
+  const bool in1 = launch_radix_sort(k0, v0, k1, v1, e, bits, hist, sms, s);
+  const unsigned g2 = (unsigned)std::max<uint64_t>(1, std::min<uint64_t>((e + BLOCK - 1) / BLOCK, (uint64_t)sms * 8));
+  me_segmin_kernel<<<g2, BLOCK, 0, s>>>(in1 ? k1 : k0, in1 ? v1 : v0, e, n, E, kl, best);
+  return true;
+}
+
 // ------------------------------------------------- device-driven round loop
 
 // State of the Borůvka rounds run as a CUDA graph: a conditional WHILE node

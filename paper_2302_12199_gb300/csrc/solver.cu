@@ -410,10 +410,22 @@ struct Solve {
   mst_status boruvka(EdgeList E, uint64_t mE, bool validate, bool best_ready = false, bool ends_rec = false) {
     if (mE == 0) return MST_OK;
     if (!layout_set) TRY(choose_layout(w_in ? w_in : E.w));
-    // round 0: minEdges straight from the stored list, then hook and jump
-    if (!best_ready)
-      PROF(MST_K_MIN_EDGES, 12.0 * (double)mE, -1, 0.0, -1, 0.0,
-           launch_min_edges(E, mE, n, validate ? 1 : 0, kl, best, &c->ds->err, c->sms, s));
+    // round 0: minEdges straight from the stored list (atomic minima, or
+    // segmented minima over the ends sorted by vertex), then hook and jump
+    if (!best_ready) {
+      bool done_sorted = false;
+      if (c->cfg.min_edges_sort && 2 * mE < (1ULL << 32)) {
+        Buf me_b;
+        TRY(me_b.alloc(c, min_edges_sort_scratch_bytes(mE, c->sms), s));
+        const double passes = (double)((ceil_log2((uint64_t)n + 1) + 7) / 8);
+        PROF(MST_K_MIN_EDGES, (12.0 + 24.0 + 2.0 * (32.0 * passes + 20.0)) * (double)mE, -1, 0.0, -1, 0.0,
+             done_sorted = launch_min_edges_sort(E, mE, n, validate ? 1 : 0, kl, best, &c->ds->err, me_b.p, c->sms,
+                                                 s));
+      }
+      if (!done_sorted)
+        PROF(MST_K_MIN_EDGES, 12.0 * (double)mE, -1, 0.0, -1, 0.0,
+             launch_min_edges(E, mE, n, validate ? 1 : 0, kl, best, &c->ds->err, c->sms, s));
+    }
     TRY(zero_counters(c, s));
     HookArgs ha{};
     ha.cand = nullptr;
@@ -1032,6 +1044,7 @@ mst_status validate_cfg(const mst_config *cfg) {
   if (cfg->graph_jump_launches < 1 || cfg->graph_jump_launches > 8) return MST_ERR_INVALID_ARG;
   if (cfg->filter_carry < 0 || cfg->filter_carry > 1) return MST_ERR_INVALID_ARG;
   if (cfg->filter_split < 0 || cfg->filter_split > 1) return MST_ERR_INVALID_ARG;
+  if (cfg->min_edges_sort < 0 || cfg->min_edges_sort > 1) return MST_ERR_INVALID_ARG;
   if (cfg->tile_vertices < 32 || cfg->tile_vertices > 4096) return MST_ERR_INVALID_ARG;
   return MST_OK;
 }
@@ -1185,6 +1198,7 @@ void mst_config_default(mst_config *cfg) {
   cfg->graph_jump_launches = 2;
   cfg->filter_carry = 0;  // measured slower on GB300 (the merged tail loses the fused minEdges)
   cfg->filter_split = 0;
+  cfg->min_edges_sort = 0;
 }
 
 const char *mst_status_string(mst_status s) {

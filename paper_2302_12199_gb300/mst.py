@@ -46,7 +46,8 @@ class MstConfig(ctypes.Structure):
                 ("pivot_sample", ctypes.c_uint32), ("seed", ctypes.c_uint64), ("filter_min_edges", ctypes.c_uint64),
                 ("filter_max_avg_degree", ctypes.c_float), ("base_case", ctypes.c_int),
                 ("graph_rounds", ctypes.c_int), ("graph_jump_launches", ctypes.c_int),
-                ("filter_carry", ctypes.c_int), ("filter_split", ctypes.c_int)]
+                ("filter_carry", ctypes.c_int), ("filter_split", ctypes.c_int),
+                ("min_edges_sort", ctypes.c_int)]
 
 
 _P = ctypes.c_void_p

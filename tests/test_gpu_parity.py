@@ -468,3 +468,27 @@ def test_filter_carry_on_and_off_agree(dev, family):
                 assert np.array_equal(ids, kid) and tot == ktot, (carry, split, deg)
             finally:
                 s.close()
+
+
+@pytest.mark.parametrize("family", ["rmat", "gnm", "star", "rgg2", "degenerate"])
+def test_min_edges_sort_on_and_off_agree(dev, family):
+    """minEdges as segmented minima over the edge ends sorted by vertex gives the
+    oracle's forest (hub-heavy RMAT and a star included); the step entry point
+    for minEdges is unchanged and compared elsewhere."""
+    g = {
+        "rmat": lambda: W.rmat(16, (1 << 20) + 3, 81),
+        "gnm": lambda: W.gnm(50000, 400000, 82),
+        "star": lambda: W.Graph(300001, np.zeros(300000, dtype=np.uint32), np.arange(1, 300001, dtype=np.uint32),
+                                (np.arange(300000, dtype=np.uint32) % 97 + 1).astype(np.uint32)),
+        "rgg2": lambda: W.rgg(2, 40000, 8.0, 83),
+        "degenerate": lambda: W.Graph(5, np.array([0, 1, 1, 3, 4], np.uint32), np.array([0, 2, 2, 3, 0], np.uint32),
+                                      np.array([5, 1, 1, 9, 2], np.uint32)),
+    }[family]()
+    kid, ktot = oracle.kruskal(g.n, g.src, g.dst, g.w)
+    for variant in ("boruvka", "filter"):
+        s = Solver(0, variant=variant, min_edges_sort=1, filter_min_edges=1 << 10)
+        try:
+            ids, tot = gpu_msf(s, g.n, g.src, g.dst, g.w, dev)
+            assert np.array_equal(ids, kid) and tot == ktot, variant
+        finally:
+            s.close()
