@@ -120,10 +120,12 @@ void launch_min_edges(EdgeList in, uint64_t m, uint32_t n, int validate, KeyLayo
                       int sms, cudaStream_t s);
 void launch_max_weight(const uint32_t *w, uint64_t m, uint32_t *out, int sms, cudaStream_t s);
 void launch_hook(const HookArgs &a, uint64_t max_cand, cudaStream_t s);
-// max_steps: parent steps per thread and launch (0: the default of 64)
+// max_steps: parent steps per thread and launch (0: the default of 64).
+// gbits (jumps over all vertices only, act == count_dev == nullptr): bit v of
+// the bitmap is set iff v's walk reached the root *groot in this launch.
 void launch_jump(const uint32_t *act, const u64 *count_dev, uint64_t count_host, uint64_t max_count,
                  uint32_t *parent, u64 *best, int reset_best, uint32_t *flag, int sms, cudaStream_t s,
-                 uint32_t max_steps = 0);
+                 uint32_t max_steps = 0, const uint32_t *groot = nullptr, uint32_t *gbits = nullptr);
 void launch_hash_insert(EdgeList in, uint64_t m, HashSlot *table, uint64_t tmask, uint32_t *err, int sms,
                         cudaStream_t s);
 void launch_pivot(EdgeList in, uint64_t m, const u64 *m_dev, u64 state, uint32_t sample, u64 *sample_buf,
@@ -136,6 +138,11 @@ bool launch_pivot_coop(EdgeList in, uint64_t m, u64 state, uint32_t sample, u64 
                        u64 *pivot_out, cudaStream_t s);
 void launch_finalize(const uint32_t *bits, uint64_t m, const uint32_t *w, uint32_t *out_ids, uint32_t *out_count,
                      u64 *total_weight, ScanState st, cudaStream_t s);
+// The giant component's root: the most frequent root among the labels of
+// sampled edge ends (P is walked to the roots); launch_giant_bits also marks
+// its vertices (bit v set iff P[v] is that root; P fully contracted).
+void launch_giant_root(EdgeList in, uint64_t m, u64 state, const uint32_t *P, uint32_t n, uint32_t *root_tmp,
+                       cudaStream_t s);
 void launch_giant_bits(EdgeList in, uint64_t m, u64 state, const uint32_t *P, uint32_t n, uint32_t *root_tmp,
                        uint32_t *bits, int sms, cudaStream_t s);
 // tile-local contraction (Section 4.1)

@@ -852,29 +852,67 @@ __global__ void __launch_bounds__(BLOCK) hook_kernel(HookArgs a) {
 // parent pointers (reading the other threads' progress) for at most max_steps
 // steps and stores the furthest ancestor reached; `flag` is set if some vertex
 // did not reach its root, and the host launches again.  Parent values only ever
-// move toward the root, so concurrent reads and writes are benign.  When
+// move toward the root and no root changes during a jump, so concurrent reads
+// and writes are benign, and so is a stale copy: the step loads go through L1,
+// which keeps the many reads of a large component's root (every walk in that
+// component ends there) off a single L2 slice.  When
 // reset_best is set, best[c] is returned to INF for the next round.
+constexpr int JUMP_ITEMS = 4;                   // vertices per thread, walked in lockstep
+constexpr int JUMP_TILE = BLOCK * JUMP_ITEMS;
+
 __global__ void __launch_bounds__(BLOCK) jump_kernel(const uint32_t *act, const u64 *count_dev, uint64_t count_host,
                                                      uint32_t *parent, u64 *best, int reset_best, uint32_t *flag,
-                                                     uint32_t max_steps) {
+                                                     uint32_t max_steps, const uint32_t *groot, uint32_t *gbits) {
   const uint64_t cnt = count_dev ? *count_dev : count_host;
-  for (uint64_t i = (uint64_t)blockIdx.x * BLOCK + threadIdx.x; i < cnt; i += (uint64_t)gridDim.x * BLOCK) {
-    const uint32_t c = act ? __ldg(act + i) : (uint32_t)i;
-    if (reset_best) best[c] = KEY_INF;
-    uint32_t p = __ldcg(parent + c);
-    uint32_t steps = 0;
-    bool done = false;
-    while (steps < max_steps) {
-      const uint32_t pp = __ldcg(parent + p);
-      if (pp == p) {
-        done = true;
-        break;
-      }
-      p = pp;
-      ++steps;
+  // each thread takes JUMP_ITEMS vertices of a block tile (striped, so the list
+  // and parent[] reads are coalesced) and advances their walks together: every
+  // step issues up to JUMP_ITEMS independent loads instead of one
+  for (uint64_t tb = (uint64_t)blockIdx.x * JUMP_TILE; tb < cnt; tb += (uint64_t)gridDim.x * JUMP_TILE) {
+    uint32_t c[JUMP_ITEMS], p[JUMP_ITEMS];
+    uint32_t live = 0;
+#pragma unroll
+    for (int k = 0; k < JUMP_ITEMS; ++k) {
+      const uint64_t i = tb + (uint64_t)k * BLOCK + threadIdx.x;
+      const bool ok = i < cnt;
+      c[k] = ok ? (act ? __ldg(act + i) : (uint32_t)i) : 0u;
+      live |= (ok ? 1u : 0u) << k;
     }
-    if (!done) atomicOr(flag, 1u);
-    if (steps > 0) __stcg(parent + c, p);
+#pragma unroll
+    for (int k = 0; k < JUMP_ITEMS; ++k) {
+      p[k] = (live >> k & 1) ? __ldcg(parent + c[k]) : 0u;
+      if (reset_best && (live >> k & 1)) best[c[k]] = KEY_INF;
+    }
+    uint32_t pending = live, moved = 0;
+    for (uint32_t steps = 0; pending && steps < max_steps; ++steps) {
+      uint32_t pp[JUMP_ITEMS];
+#pragma unroll
+      for (int k = 0; k < JUMP_ITEMS; ++k) pp[k] = (pending >> k & 1) ? __ldca(parent + p[k]) : 0u;
+#pragma unroll
+      for (int k = 0; k < JUMP_ITEMS; ++k) {
+        if (!(pending >> k & 1)) continue;
+        if (pp[k] == p[k]) {
+          pending &= ~(1u << k);
+        } else {
+          p[k] = pp[k];
+          moved |= 1u << k;
+        }
+      }
+    }
+    if (pending) atomicOr(flag, 1u);
+#pragma unroll
+    for (int k = 0; k < JUMP_ITEMS; ++k)
+      if (moved >> k & 1) __stcg(parent + c[k], p[k]);
+    if (gbits) {  // all vertices (no list): a warp's item k is 32 consecutive vertices, one bitmap word
+      const uint32_t r = *groot;
+      const uint64_t w0 = tb + (threadIdx.x & ~31u);
+#pragma unroll
+      for (int k = 0; k < JUMP_ITEMS; ++k) {
+        const bool in = ((live & ~pending) >> k & 1) && p[k] == r;  // an unfinished walk marks nothing
+        const uint32_t word = __ballot_sync(0xffffffffu, in);
+        const uint64_t v0 = w0 + (uint64_t)k * BLOCK;
+        if ((threadIdx.x & 31) == 0 && v0 < cnt) gbits[v0 >> 5] = word;
+      }
+    }
   }
 }
 
@@ -2030,7 +2068,15 @@ __global__ void __launch_bounds__(MODE_SAMPLES) giant_root_kernel(EdgeList in, u
   uint32_t r = 0xffffffffu;
   if (m) {
     const uint32_t u = __ldg(in.u + __umul64hi(splitmix64_at(state, t), m));
-    if (u < n) r = __ldg(P + u);
+    if (u < n) {  // the label of u: P may still hold chains (bounded walk; a short one only
+                  // picks a non-root, which marks no vertex)
+      r = __ldcg(P + u);
+      for (uint32_t k = 0; k < JUMP_STEPS; ++k) {
+        const uint32_t q = __ldcg(P + r);
+        if (q == r) break;
+        r = q;
+      }
+    }
   }
   s_r[t] = r;
   __syncthreads();
@@ -2240,11 +2286,12 @@ void launch_hook(const HookArgs &a, uint64_t max_cand, cudaStream_t s) {
 
 void launch_jump(const uint32_t *act, const u64 *count_dev, uint64_t count_host, uint64_t max_count,
                  uint32_t *parent, u64 *best, int reset_best, uint32_t *flag, int sms, cudaStream_t s,
-                 uint32_t max_steps) {
+                 uint32_t max_steps, const uint32_t *groot, uint32_t *gbits) {
   if (max_count == 0) return;
-  const unsigned grid = grid_for((max_count + BLOCK - 1) / BLOCK, sms, 8);
+  if (act || count_dev) gbits = nullptr;  // the bitmap needs every vertex in order
+  const unsigned grid = grid_for((max_count + JUMP_TILE - 1) / JUMP_TILE, sms, 8);
   jump_kernel<<<grid, BLOCK, 0, s>>>(act, count_dev, count_host, parent, best, reset_best, flag,
-                                     max_steps ? max_steps : JUMP_STEPS);
+                                     max_steps ? max_steps : JUMP_STEPS, groot, gbits);
 }
 
 void launch_hash_insert(EdgeList in, uint64_t m, HashSlot *table, uint64_t tmask, uint32_t *err, int sms,
@@ -2278,6 +2325,11 @@ void launch_finalize(const uint32_t *bits, uint64_t m, const uint32_t *w, uint32
   const uint64_t nwords = (m + 31) / 32;
   const unsigned grid = (unsigned)(max_scan_tiles(nwords) > 0 ? max_scan_tiles(nwords) : 1);
   finalize_kernel<<<grid, BLOCK, 0, s>>>(bits, nwords, w, out_ids, out_count, total_weight, st);
+}
+
+void launch_giant_root(EdgeList in, uint64_t m, u64 state, const uint32_t *P, uint32_t n, uint32_t *root_tmp,
+                       cudaStream_t s) {
+  giant_root_kernel<<<1, MODE_SAMPLES, 0, s>>>(in, m, state, P, n, root_tmp);
 }
 
 void launch_giant_bits(EdgeList in, uint64_t m, u64 state, const uint32_t *P, uint32_t n, uint32_t *root_tmp,

@@ -375,19 +375,20 @@ struct Solve {
   // Pointer jumping over the listed vertices (act == nullptr: all n) until
   // every one points to its root; the first launch may reset best[].
   mst_status jump_until_stars(const uint32_t *act_list, const u64 *count_dev, uint64_t count_host, uint64_t max_count,
-                              int reset_best) {
+                              int reset_best, const uint32_t *groot = nullptr, uint32_t *gbits = nullptr) {
     CK(cudaMemsetAsync(&c->ds->jump_flag, 0, sizeof(uint32_t), s));
     const int slot = count_dev ? CNT_ACTIVE : -1;
-    const double fixed = count_dev ? 0.0 : 8.0 * (double)count_host;
+    const double fixed = count_dev ? 0.0 : (8.0 + (gbits ? 0.125 : 0.0)) * (double)count_host;
     PROF(MST_K_JUMP, fixed, slot, reset_best ? 20.0 : 12.0, -1, 0.0,
          launch_jump(act_list, count_dev, count_host, max_count, parent, best, reset_best, &c->ds->jump_flag,
-                     c->sms, s));
+                     c->sms, s, 0, groot, gbits));
     TRY(readback(c, s));
     for (int it = 0; c->hs->jump_flag; ++it) {
       if (it > 64) return MST_ERR_INTERNAL;
       CK(cudaMemsetAsync(&c->ds->jump_flag, 0, sizeof(uint32_t), s));
       PROF(MST_K_JUMP, fixed, slot, 12.0, -1, 0.0,
-           launch_jump(act_list, count_dev, count_host, max_count, parent, best, 0, &c->ds->jump_flag, c->sms, s));
+           launch_jump(act_list, count_dev, count_host, max_count, parent, best, 0, &c->ds->jump_flag, c->sms, s,
+                       0, groot, gbits));
       TRY(readback(c, s));
     }
     return MST_OK;
@@ -840,13 +841,14 @@ struct Solve {
     return MST_OK;
   }
 
-  // Marks the vertices of the component that most sampled edges of E touch,
-  // after P (= parent) is fully contracted: the filter drops an edge with both
-  // ends marked without reading P.
-  mst_status mark_giant(EdgeList E, uint64_t mE, u64 state, Buf &bits_b) {
+  // Contracts P fully (as compress_all) and marks the vertices of the
+  // component that most sampled edges of E touch: the filter drops an edge
+  // with both ends marked without reading P.  The sampled ends are walked to
+  // their roots first; the marks are written by the contraction pass itself.
+  mst_status compress_and_mark_giant(EdgeList E, uint64_t mE, u64 state, Buf &bits_b) {
     TRY(bits_b.alloc(c, ((size_t)n + 31) / 32 * 4, s));
-    launch_giant_bits(E, mE, state, parent, n, &c->ds->giant_root, bits_b.as<uint32_t>(), c->sms, s);
-    return MST_OK;
+    launch_giant_root(E, mE, state, parent, n, &c->ds->giant_root, s);
+    return jump_until_stars(nullptr, nullptr, n, n, 0, &c->ds->giant_root, bits_b.as<uint32_t>());
   }
 
   // Rec-Filter-MST (Alg. 2).  best_ready: best[] holds E's minEdges already.
@@ -910,9 +912,8 @@ struct Solve {
     TRY(filter(L.list(), mL, false, depth + 1, fuse_light, cp.cur_u != nullptr, carrying ? &lcarry : nullptr,
                carrying ? &lcarry_m : nullptr));
     L.mem.release();
-    TRY(compress_all());
     Buf giant_b;
-    TRY(mark_giant(E, mE, host_mix64(state), giant_b));
+    TRY(compress_and_mark_giant(E, mE, host_mix64(state), giant_b));
     ListBuf H;
     TRY(H.alloc(c, mE - mL + lcarry_m, s));
     CompactArgs cf{};
