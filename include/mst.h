@@ -233,7 +233,10 @@ mst_status mst_step_partition(mst_handle h, uint64_t m, const uint32_t *d_u, con
 /* Filter (Alg. 2; Section 5): edges with key > pivot, relabelled by the
  * representative array d_P after pointer doubling it to its roots (d_P is
  * updated in place to the roots); edges inside one component are dropped.
- * Capacity m; one uint64 count. */
+ * Capacity m; one uint64 count.  Every d_P[x] must be < n and the pointers
+ * must lead to roots (d_P[r] == r): an entry >= n is MST_ERR_VERTEX_RANGE
+ * (checked before d_P is used; d_P is then unchanged), a cycle longer than one
+ * is MST_ERR_INTERNAL after a bounded number of pointer-jumping launches. */
 mst_status mst_step_filter(mst_handle h, uint32_t n, uint64_t m, const uint32_t *d_u, const uint32_t *d_v,
                            const uint32_t *d_w, const uint32_t *d_id, uint64_t pivot, uint32_t *d_P, uint32_t *d_ou,
                            uint32_t *d_ov, uint32_t *d_ow, uint32_t *d_oid, uint64_t *d_out_count, void *stream);

@@ -126,6 +126,8 @@ void launch_hook(const HookArgs &a, uint64_t max_cand, cudaStream_t s);
 void launch_jump(const uint32_t *act, const u64 *count_dev, uint64_t count_host, uint64_t max_count,
                  uint32_t *parent, u64 *best, int reset_best, uint32_t *flag, int sms, cudaStream_t s,
                  uint32_t max_steps = 0, const uint32_t *groot = nullptr, uint32_t *gbits = nullptr);
+// Sets ERR_VERTEX in *err if some x[i] (i < count) is >= bound.
+void launch_range_check(const uint32_t *x, uint64_t count, uint32_t bound, uint32_t *err, int sms, cudaStream_t s);
 void launch_hash_insert(EdgeList in, uint64_t m, HashSlot *table, uint64_t tmask, uint32_t *err, int sms,
                         cudaStream_t s);
 void launch_pivot(EdgeList in, uint64_t m, const u64 *m_dev, u64 state, uint32_t sample, u64 *sample_buf,

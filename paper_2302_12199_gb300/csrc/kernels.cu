@@ -949,6 +949,14 @@ __global__ void __launch_bounds__(BLOCK) max_weight_kernel(const uint32_t *w, ui
   if ((threadIdx.x & 31) == 0 && mx) atomicMax(out, mx);
 }
 
+// Sets ERR_VERTEX if some x[i] (i < count) is >= bound.
+__global__ void range_check_kernel(const uint32_t *x, uint64_t count, uint32_t bound, uint32_t *err) {
+  bool bad = false;
+  for (uint64_t i = (uint64_t)blockIdx.x * BLOCK + threadIdx.x; i < count; i += (uint64_t)gridDim.x * BLOCK)
+    bad |= __ldcs(x + i) >= bound;
+  if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(err, ERR_VERTEX);
+}
+
 __global__ void iota_kernel(uint32_t *p, uint64_t n) {
   for (uint64_t i = (uint64_t)blockIdx.x * BLOCK + threadIdx.x; i < n; i += (uint64_t)gridDim.x * BLOCK)
     p[i] = (uint32_t)i;
@@ -2068,10 +2076,10 @@ __global__ void __launch_bounds__(MODE_SAMPLES) giant_root_kernel(EdgeList in, u
   uint32_t r = 0xffffffffu;
   if (m) {
     const uint32_t u = __ldg(in.u + __umul64hi(splitmix64_at(state, t), m));
-    if (u < n) {  // the label of u: P may still hold chains (bounded walk; a short one only
-                  // picks a non-root, which marks no vertex)
+    if (u < n) {  // the label of u: P may still hold chains (a bounded walk, inside 0..n-1;
+                  // one cut short only picks a non-root, which marks no vertex)
       r = __ldcg(P + u);
-      for (uint32_t k = 0; k < JUMP_STEPS; ++k) {
+      for (uint32_t k = 0; k < JUMP_STEPS && r < n; ++k) {
         const uint32_t q = __ldcg(P + r);
         if (q == r) break;
         r = q;
@@ -2292,6 +2300,11 @@ void launch_jump(const uint32_t *act, const u64 *count_dev, uint64_t count_host,
   const unsigned grid = grid_for((max_count + JUMP_TILE - 1) / JUMP_TILE, sms, 8);
   jump_kernel<<<grid, BLOCK, 0, s>>>(act, count_dev, count_host, parent, best, reset_best, flag,
                                      max_steps ? max_steps : JUMP_STEPS, groot, gbits);
+}
+
+void launch_range_check(const uint32_t *x, uint64_t count, uint32_t bound, uint32_t *err, int sms, cudaStream_t s) {
+  if (count == 0) return;
+  range_check_kernel<<<grid_for((count + BLOCK - 1) / BLOCK, sms, 8), BLOCK, 0, s>>>(x, count, bound, err);
 }
 
 void launch_hash_insert(EdgeList in, uint64_t m, HashSlot *table, uint64_t tmask, uint32_t *err, int sms,

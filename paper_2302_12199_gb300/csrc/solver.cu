@@ -1584,7 +1584,10 @@ mst_status mst_step_filter(mst_handle h, uint32_t n, uint64_t m, const uint32_t 
     Solve S(h, s, n, 0);
     S.parent = d_P;
     if (clear_device_flags(h, s) != MST_OK) return record_cuda(h, __LINE__);
-    mst_status st = S.compress_all();
+    launch_range_check(d_P, n, n, &h->ds->err, h->sms, s);  // P is walked: every entry must name a vertex
+    mst_status st = readback(h, s);
+    if (st != MST_OK) return record(h, st);
+    st = S.compress_all();
     if (st != MST_OK) return record(h, st);
   }
   return step_compact(h, CM_FILTER, n, m, d_u, d_v, d_w, d_id, d_P, pivot, d_ou, d_ov, d_ow, d_oid, d_out_count,

@@ -332,6 +332,31 @@ def test_step_filter_long_list(step_solver, dev, with_ids):
     assert_same_list(out, S.filter_heavy(g.src, g.dst, g.w, eids, pv, P))
 
 
+def test_step_filter_bad_representatives(step_solver, dev):
+    """A representative array with an entry >= n is refused before it is
+    walked (d_P unchanged); one with a 2-cycle ends in an error after the
+    bounded pointer-jumping launches; the handle stays usable after both."""
+    g = W.gnm(1000, 5000, 47)
+    ids = np.arange(g.m, dtype=np.uint32)
+    pv = int(S.pivot(g.w, ids, 5, 1 << 10))
+    bad = np.arange(g.n, dtype=np.uint32)
+    bad[17] = g.n
+    Pd = to_dev(bad, dev)
+    with pytest.raises(MstError) as e:
+        step_solver.filter(g.n, *list_on_dev(dev, g.src, g.dst, g.w), None, pivot=pv, P=Pd)
+    assert e.value.status == 2
+    assert np.array_equal(host(Pd), bad)
+    cyc = np.arange(g.n, dtype=np.uint32)
+    cyc[3], cyc[4] = 4, 3
+    with pytest.raises(MstError) as e:
+        step_solver.filter(g.n, *list_on_dev(dev, g.src, g.dst, g.w), None, pivot=pv, P=to_dev(cyc, dev))
+    assert e.value.status == 6
+    P = light_fixed_point(g.n, g.src, g.dst, g.w, ids, pv)
+    Pd = to_dev(P, dev)
+    out = step_solver.filter(g.n, *list_on_dev(dev, g.src, g.dst, g.w), None, pivot=pv, P=Pd)
+    assert_same_list(out, S.filter_heavy(g.src, g.dst, g.w, ids, pv, P))
+
+
 def test_filter_solve_long_lists(dev):
     """Whole Filter-Borůvka solves whose filter passes run on lists of millions of edges."""
     s = Solver(0, variant="filter")
