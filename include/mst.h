@@ -85,6 +85,10 @@ typedef struct {
   int min_edges_sort;          /* 1: the first minEdges of a Borůvka call sorts both ends of every edge by
                                   vertex and takes segmented minima (one atomic per vertex run and warp, the
                                   sorted-edge form of Sections 2.2/4.5); 0 (default): one atomic pass */
+  uint32_t jump_steps;         /* parent steps per pointer-jumping launch on the host-driven path,
+                                  1..4096 (default 64); a launch that leaves a walk short is repeated
+                                  (at most 64 more times, then MST_ERR_INTERNAL).  1 makes every launch
+                                  one pointer-doubling step (Section 4.2) */
 } mst_config;
 
 /* Fills *cfg with the defaults (Borůvka variant, automatic dedupe, pivot sample

@@ -374,24 +374,35 @@ struct Solve {
 
   // Pointer jumping over the listed vertices (act == nullptr: all n) until
   // every one points to its root; the first launch may reset best[].
-  mst_status jump_until_stars(const uint32_t *act_list, const u64 *count_dev, uint64_t count_host, uint64_t max_count,
-                              int reset_best, const uint32_t *groot = nullptr, uint32_t *gbits = nullptr) {
+  // One pointer-jumping launch over the list (or all n), with the flag cleared
+  // first; the flag is read back by the caller's next readback.
+  mst_status jump_launch(const uint32_t *act_list, const u64 *count_dev, uint64_t count_host, uint64_t max_count,
+                         int reset_best, const uint32_t *groot = nullptr, uint32_t *gbits = nullptr) {
     CK(cudaMemsetAsync(&c->ds->jump_flag, 0, sizeof(uint32_t), s));
     const int slot = count_dev ? CNT_ACTIVE : -1;
     const double fixed = count_dev ? 0.0 : (8.0 + (gbits ? 0.125 : 0.0)) * (double)count_host;
     PROF(MST_K_JUMP, fixed, slot, reset_best ? 20.0 : 12.0, -1, 0.0,
          launch_jump(act_list, count_dev, count_host, max_count, parent, best, reset_best, &c->ds->jump_flag,
-                     c->sms, s, 0, groot, gbits));
-    TRY(readback(c, s));
+                     c->sms, s, c->cfg.jump_steps, groot, gbits));
+    return MST_OK;
+  }
+
+  // Relaunches (after a readback) while the flag says a walk fell short.
+  mst_status jump_finish(const uint32_t *act_list, const u64 *count_dev, uint64_t count_host, uint64_t max_count,
+                         const uint32_t *groot = nullptr, uint32_t *gbits = nullptr) {
     for (int it = 0; c->hs->jump_flag; ++it) {
       if (it > 64) return MST_ERR_INTERNAL;
-      CK(cudaMemsetAsync(&c->ds->jump_flag, 0, sizeof(uint32_t), s));
-      PROF(MST_K_JUMP, fixed, slot, 12.0, -1, 0.0,
-           launch_jump(act_list, count_dev, count_host, max_count, parent, best, 0, &c->ds->jump_flag, c->sms, s,
-                       0, groot, gbits));
+      TRY(jump_launch(act_list, count_dev, count_host, max_count, 0, groot, gbits));
       TRY(readback(c, s));
     }
     return MST_OK;
+  }
+
+  mst_status jump_until_stars(const uint32_t *act_list, const u64 *count_dev, uint64_t count_host, uint64_t max_count,
+                              int reset_best, const uint32_t *groot = nullptr, uint32_t *gbits = nullptr) {
+    TRY(jump_launch(act_list, count_dev, count_host, max_count, reset_best, groot, gbits));
+    TRY(readback(c, s));
+    return jump_finish(act_list, count_dev, count_host, max_count, groot, gbits);
   }
 
   // Parallel-edge removal is optional (Section 2.3).  `auto` keeps parallel
@@ -841,14 +852,19 @@ struct Solve {
     return MST_OK;
   }
 
-  // Contracts P fully (as compress_all) and marks the vertices of the
-  // component that most sampled edges of E touch: the filter drops an edge
-  // with both ends marked without reading P.  The sampled ends are walked to
-  // their roots first; the marks are written by the contraction pass itself.
-  mst_status compress_and_mark_giant(EdgeList E, uint64_t mE, u64 state, Buf &bits_b) {
+  // Contracts P (as compress_all) and marks the vertices of the component
+  // that most sampled edges of E touch: the filter drops an edge with both
+  // ends marked without reading P.  The sampled ends are walked to their roots
+  // first; the marks are written by the contraction pass itself.  Only the
+  // first launch is issued here: its flag is read back with the filter's
+  // count, and contract_finish completes the rare contraction that needs more.
+  mst_status contract_and_mark_start(EdgeList E, uint64_t mE, u64 state, Buf &bits_b) {
     TRY(bits_b.alloc(c, ((size_t)n + 31) / 32 * 4, s));
     launch_giant_root(E, mE, state, parent, n, &c->ds->giant_root, s);
-    return jump_until_stars(nullptr, nullptr, n, n, 0, &c->ds->giant_root, bits_b.as<uint32_t>());
+    return jump_launch(nullptr, nullptr, n, n, 0, &c->ds->giant_root, bits_b.as<uint32_t>());
+  }
+  mst_status contract_and_mark_finish(Buf &bits_b) {
+    return jump_finish(nullptr, nullptr, n, n, &c->ds->giant_root, bits_b.as<uint32_t>());
   }
 
   // Rec-Filter-MST (Alg. 2).  best_ready: best[] holds E's minEdges already.
@@ -913,7 +929,7 @@ struct Solve {
                carrying ? &lcarry_m : nullptr));
     L.mem.release();
     Buf giant_b;
-    TRY(compress_and_mark_giant(E, mE, host_mix64(state), giant_b));
+    TRY(contract_and_mark_start(E, mE, host_mix64(state), giant_b));
     ListBuf H;
     TRY(H.alloc(c, mE - mL + lcarry_m, s));
     CompactArgs cf{};
@@ -927,33 +943,48 @@ struct Solve {
     cf.best = best;  // the survivors are expected to be sparse (Theorem 1)
     cf.kl = kl;
     record_ends(cf);
-    cf.st = next_scan(c, CNT_EDGES);
     TRY(zero_counters(c, s));
     ListBuf C;
-    if (c->cfg.filter_split) {
-      // two passes: the streaming pass keeps the heavy edges not inside the
-      // giant component (bitmap gathers only), the filter then gathers the
-      // labels for that short list
-      TRY(C.alloc(c, mE - mL, s));
-      CompactArgs ch{};
-      ch.in = E;
-      ch.m = mE;
-      ch.out = C.out;
-      ch.giant_bits = cf.giant_bits;
-      ch.pivot = pivot;
-      ch.n = n;
-      ch.kl = kl;
-      ch.st = next_scan(c, CNT_TMP);
-      PROF(MST_K_FILTER, in_bytes, CNT_TMP, 16.0, -1, 0.0, launch_compact(CM_HEAVY, ch, mE, s));
-      cf.in = C.list();
-      cf.m = mE - mL;
-      cf.m_dev = &c->ds->count[CNT_TMP];
-      cf.giant_bits = nullptr;
-      PROF(MST_K_FILTER, 0.0, CNT_TMP, 16.0, CNT_EDGES, 16.0, launch_compact(CM_FILTER, cf, mE - mL, s));
-    } else {
-      PROF(MST_K_FILTER, in_bytes, CNT_EDGES, 16.0, -1, 0.0, launch_compact(CM_FILTER, cf, mE, s));
+    // The filter runs against P before the contraction's flag is known: a P
+    // that is not fully contracted (labels that are ancestors, not roots) only
+    // keeps more edges, but H's ends must be roots, so in that rare case the
+    // contraction is finished and the pass runs again on fresh minEdges.
+    for (int attempt = 0;; ++attempt) {
+      cf.st = next_scan(c, CNT_EDGES);
+      if (c->cfg.filter_split) {
+        // two passes: the streaming pass keeps the heavy edges not inside the
+        // giant component (bitmap gathers only), the filter then gathers the
+        // labels for that short list
+        TRY(C.alloc(c, mE - mL, s));
+        CompactArgs ch{};
+        ch.in = E;
+        ch.m = mE;
+        ch.out = C.out;
+        ch.giant_bits = cf.giant_bits;
+        ch.pivot = pivot;
+        ch.n = n;
+        ch.kl = kl;
+        ch.st = next_scan(c, CNT_TMP);
+        PROF(MST_K_FILTER, in_bytes, CNT_TMP, 16.0, -1, 0.0, launch_compact(CM_HEAVY, ch, mE, s));
+        cf.in = C.list();
+        cf.m = mE - mL;
+        cf.m_dev = &c->ds->count[CNT_TMP];
+        cf.giant_bits = nullptr;
+        PROF(MST_K_FILTER, 0.0, CNT_TMP, 16.0, CNT_EDGES, 16.0, launch_compact(CM_FILTER, cf, mE - mL, s));
+      } else {
+        PROF(MST_K_FILTER, in_bytes, CNT_EDGES, 16.0, -1, 0.0, launch_compact(CM_FILTER, cf, mE, s));
+      }
+      TRY(readback(c, s));
+      if (!c->hs->jump_flag) break;
+      if (attempt > 0) return MST_ERR_INTERNAL;
+      TRY(contract_and_mark_finish(giant_b));
+      TRY(reset_best());
+      TRY(zero_counters(c, s));
+      cf.in = E;
+      cf.m = mE;
+      cf.m_dev = nullptr;
+      cf.giant_bits = giant_b.as<uint32_t>();
     }
-    TRY(readback(c, s));
     C.mem.release();
     giant_b.release();
     uint64_t mH = c->hs->count[CNT_EDGES];
@@ -1046,6 +1077,7 @@ mst_status validate_cfg(const mst_config *cfg) {
   if (cfg->filter_carry < 0 || cfg->filter_carry > 1) return MST_ERR_INVALID_ARG;
   if (cfg->filter_split < 0 || cfg->filter_split > 1) return MST_ERR_INVALID_ARG;
   if (cfg->min_edges_sort < 0 || cfg->min_edges_sort > 1) return MST_ERR_INVALID_ARG;
+  if (cfg->jump_steps < 1 || cfg->jump_steps > 4096) return MST_ERR_INVALID_ARG;
   if (cfg->tile_vertices < 32 || cfg->tile_vertices > 4096) return MST_ERR_INVALID_ARG;
   return MST_OK;
 }
@@ -1200,6 +1232,7 @@ void mst_config_default(mst_config *cfg) {
   cfg->filter_carry = 0;  // measured slower on GB300 (the merged tail loses the fused minEdges)
   cfg->filter_split = 0;
   cfg->min_edges_sort = 0;
+  cfg->jump_steps = 64;
 }
 
 const char *mst_status_string(mst_status s) {

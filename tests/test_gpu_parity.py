@@ -517,3 +517,34 @@ def test_min_edges_sort_on_and_off_agree(dev, family):
             assert np.array_equal(ids, kid) and tot == ktot, variant
         finally:
             s.close()
+
+
+@pytest.mark.parametrize("family", ["rmat", "gnm", "path", "rgg2"])
+def test_one_step_jumps(dev, family):
+    """With one parent step per pointer-jumping launch (jump_steps = 1, every
+    launch a pointer-doubling step) the host relaunches every jump and, in
+    Filter-Borůvka, finishes each level's contraction of P after the filter
+    pass and filters again: the forest is still the oracle's, with round
+    graphs on and off."""
+    g = {
+        "rmat": lambda: W.rmat(16, (1 << 20) + 3, 91),
+        "gnm": lambda: W.gnm(50000, 400000, 92),
+        "path": lambda: W.Graph(200000, np.arange(199999, dtype=np.uint32), np.arange(1, 200000, dtype=np.uint32),
+                                (np.arange(199999, dtype=np.uint32) % 251 + 1).astype(np.uint32)),
+        "rgg2": lambda: W.rgg(2, 40000, 8.0, 93),
+    }[family]()
+    kid, ktot = oracle.kruskal(g.n, g.src, g.dst, g.w)
+    for variant, graph_rounds in (("boruvka", 1), ("boruvka", 0), ("filter", 1)):
+        s = Solver(0, variant=variant, jump_steps=1, graph_rounds=graph_rounds, filter_min_edges=1 << 10)
+        try:
+            ids, tot = gpu_msf(s, g.n, g.src, g.dst, g.w, dev)
+            assert np.array_equal(ids, kid) and tot == ktot, (variant, graph_rounds)
+        finally:
+            s.close()
+
+
+def test_jump_steps_range(dev):
+    for bad in (0, 4097):
+        with pytest.raises(MstError) as e:
+            Solver(0, jump_steps=bad)
+        assert e.value.status == 1
