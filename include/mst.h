@@ -137,6 +137,29 @@ mst_status mst_solve_host(mst_handle h, uint32_t n, uint64_t m, const uint32_t *
                           const uint32_t *h_w, uint32_t *h_msf_ids, uint32_t *h_msf_count, uint64_t *h_total_weight,
                           void *stream);
 
+/* One graph in HOST memory for mst_solve_host_many: inputs as mst_solve (src,
+ * dst, w: m entries each; page-locked memory copies fastest), results as
+ * mst_solve_host (msf_ids: capacity min(m, max(n-1, 0)), ascending ids). */
+typedef struct {
+  uint32_t n;
+  uint64_t m;
+  const uint32_t *src, *dst, *w;
+  uint32_t *msf_ids;      /* [out] */
+  uint32_t msf_count;     /* [out] */
+  uint64_t total_weight;  /* [out] */
+  mst_status status;      /* [out] this graph's status */
+} mst_host_graph;
+
+/* Solves graphs[0..count-1] in order, each as mst_solve_host, with the copy of
+ * graph i+1's inputs to the device overlapping the solve of graph i (two
+ * device input buffers, a copy stream of the handle; the solves run on
+ * `stream`), so a sequence of host-resident graphs costs about max(copy, solve)
+ * per graph rather than their sum.  Each graph gets its own status; a graph
+ * that fails with MST_ERR_CUDA or MST_ERR_OOM ends the sequence, and the
+ * graphs after it keep status MST_ERR_INTERNAL (not attempted).  Returns
+ * MST_OK if every graph was solved, else the first failing graph's status. */
+mst_status mst_solve_host_many(mst_handle h, uint32_t count, mst_host_graph *graphs, void *stream);
+
 /* Minimum spanning forests of G independent graphs in one solve.  Graph g has
  * d_n[g] vertices (graph-local ids 0..d_n[g]-1) and the edges
  * d_edge_off[g] .. d_edge_off[g+1]-1 of d_src/d_dst/d_w.  The graphs are solved

@@ -46,6 +46,8 @@ struct mst_ctx {
   };
   bool prof_on = false;
   cudaStream_t cap_stream = nullptr;  // stream the round graphs are captured on
+  cudaStream_t copy_stream = nullptr; // input copies of mst_solve_host_many
+  cudaEvent_t in_ready[2] = {nullptr, nullptr}, in_free[2] = {nullptr, nullptr};
   GraphRounds *grounds = nullptr;     // device state of the graph round loop
   struct RoundGraph {
     u64 sig;  // every pointer and size the graph was built with
@@ -1302,6 +1304,11 @@ void mst_destroy(mst_handle h) {
     if (h->sample_buf) cudaFree(h->sample_buf);
     if (h->pivot_scratch) cudaFree(h->pivot_scratch);
     if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+    if (h->copy_stream) cudaStreamDestroy(h->copy_stream);
+    for (int k = 0; k < 2; ++k) {
+      if (h->in_ready[k]) cudaEventDestroy(h->in_ready[k]);
+      if (h->in_free[k]) cudaEventDestroy(h->in_free[k]);
+    }
     for (auto &rg : h->round_graphs) {
       cudaGraphExecDestroy(rg.exec);
       cudaGraphDestroy(rg.graph);
@@ -1406,6 +1413,108 @@ mst_status mst_solve_host(mst_handle h, uint32_t n, uint64_t m, const uint32_t *
                   cudaStreamSynchronize(s) != cudaSuccess))
     return record_cuda(h, __LINE__);
   return record(h, MST_OK);
+}
+
+mst_status mst_solve_host_many(mst_handle h, uint32_t count, mst_host_graph *gs, void *stream) {
+  if (!h) return MST_ERR_INVALID_ARG;
+  if (count == 0) return record(h, MST_OK);
+  if (!gs) return record(h, MST_ERR_INVALID_ARG);
+  uint64_t max_m = 0, max_cap = 0;
+  for (uint32_t i = 0; i < count; ++i) {
+    gs[i].status = MST_ERR_INTERNAL;
+    gs[i].msf_count = 0;
+    gs[i].total_weight = 0;
+  }
+  for (uint32_t i = 0; i < count; ++i) {
+    const mst_host_graph &g = gs[i];
+    if (g.m > 0 && (!g.src || !g.dst || !g.w || !g.msf_ids)) return record(h, gs[i].status = MST_ERR_INVALID_ARG);
+    if (g.m >= (1ULL << 32)) return record(h, gs[i].status = MST_ERR_TOO_LARGE);
+    const uint64_t cap = g.m < (uint64_t)(g.n > 0 ? g.n - 1 : 0) ? g.m : (uint64_t)(g.n > 0 ? g.n - 1 : 0);
+    max_m = std::max(max_m, g.m);
+    max_cap = std::max(max_cap, cap);
+  }
+  DeviceGuard dg(h->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  if (!h->copy_stream && cudaStreamCreateWithFlags(&h->copy_stream, cudaStreamNonBlocking) != cudaSuccess)
+    return record_cuda(h, __LINE__);
+  for (int k = 0; k < 2; ++k) {
+    if (!h->in_ready[k] && cudaEventCreateWithFlags(&h->in_ready[k], cudaEventDisableTiming) != cudaSuccess)
+      return record_cuda(h, __LINE__);
+    if (!h->in_free[k] && cudaEventCreateWithFlags(&h->in_free[k], cudaEventDisableTiming) != cudaSuccess)
+      return record_cuda(h, __LINE__);
+  }
+  const uint64_t stride = round_up(max_m * 4 + 16, 256);
+  Buf in_b[2], out_b;
+  mst_status st = MST_OK;
+  for (int k = 0; k < 2 && st == MST_OK; ++k) st = in_b[k].alloc(h, stride * 3, s);
+  if (st == MST_OK) st = out_b.alloc(h, max_cap * 4 + 256, s);
+  if (st != MST_OK) return record(h, gs[0].status = st);
+  // the buffers come from the stream-ordered pool on s: both count as free
+  // (for the copy stream) once s reaches this point
+  for (int k = 0; k < 2; ++k)
+    if (cudaEventRecord(h->in_free[k], s) != cudaSuccess) return record_cuda(h, __LINE__);
+  uint32_t *d_out = out_b.as<uint32_t>();
+  uint32_t *d_count = (uint32_t *)((char *)d_out + max_cap * 4);
+  u64 *d_total = (u64 *)((char *)d_out + round_up(max_cap * 4 + 4, 8));
+  auto set_of = [&](uint32_t i, int a) { return (uint32_t *)(in_b[i % 2].as<char>() + (size_t)a * stride); };
+  auto issue_copy = [&](uint32_t i) -> bool {
+    const int k = (int)(i % 2);
+    if (cudaStreamWaitEvent(h->copy_stream, h->in_free[k], 0) != cudaSuccess) return false;
+    const mst_host_graph &g = gs[i];
+    if (g.m > 0) {
+      const uint32_t *srcs[3] = {g.src, g.dst, g.w};
+      for (int a = 0; a < 3; ++a)
+        if (cudaMemcpyAsync(set_of(i, a), srcs[a], g.m * 4, cudaMemcpyHostToDevice, h->copy_stream) != cudaSuccess)
+          return false;
+    }
+    return cudaEventRecord(h->in_ready[k], h->copy_stream) == cudaSuccess;
+  };
+  mst_status first = MST_OK;
+  if (!issue_copy(0)) return record_cuda(h, __LINE__);
+  uint32_t i = 0;
+  for (; i < count; ++i) {
+    const int k = (int)(i % 2);
+    if (i + 1 < count && !issue_copy(i + 1)) {  // overlaps the solve below
+      st = record_cuda(h, __LINE__);
+      break;
+    }
+    if (cudaStreamWaitEvent(s, h->in_ready[k], 0) != cudaSuccess) {
+      st = record_cuda(h, __LINE__);
+      break;
+    }
+    mst_host_graph &g = gs[i];
+    st = solve_device(h, g.n, g.m, set_of(i, 0), set_of(i, 1), set_of(i, 2), d_out, d_count, d_total, s);
+    if (cudaEventRecord(h->in_free[k], s) != cudaSuccess) {
+      st = record_cuda(h, __LINE__);
+      break;
+    }
+    if (st == MST_OK) {
+      uint32_t cnt = 0;
+      if (cudaMemcpyAsync(&cnt, d_count, 4, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+          cudaMemcpyAsync(&g.total_weight, d_total, 8, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+          cudaStreamSynchronize(s) != cudaSuccess ||
+          (cnt > 0 && (cudaMemcpyAsync(g.msf_ids, d_out, (size_t)cnt * 4, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+                       cudaStreamSynchronize(s) != cudaSuccess))) {
+        st = record_cuda(h, __LINE__);
+        g.status = st;
+        if (first == MST_OK) first = st;
+        ++i;
+        break;
+      }
+      g.msf_count = cnt;
+    }
+    g.status = st;
+    if (st != MST_OK && first == MST_OK) first = st;
+    if (st == MST_ERR_CUDA || st == MST_ERR_OOM) {
+      ++i;
+      break;
+    }
+  }
+  // a copy issued for a graph that was not solved must finish before the
+  // buffers return to the pool (each event marks the last copy into its buffer)
+  for (int k = 0; k < 2; ++k) cudaStreamWaitEvent(s, h->in_ready[k], 0);
+  if (st == MST_ERR_CUDA && first == MST_OK) first = st;
+  return record(h, first);
 }
 
 mst_status mst_solve_batched(mst_handle h, uint32_t num_graphs, const uint32_t *h_n, const uint64_t *h_edge_off,

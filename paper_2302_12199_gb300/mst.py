@@ -36,6 +36,13 @@ KERNEL_CLASSES = ["min_edges", "relabel_min", "hook", "jump", "dedupe", "pivot",
                   "tile", "base", "graph"]
 
 
+class HostGraph(ctypes.Structure):
+    """mst_host_graph: one graph in host memory for mst_solve_host_many."""
+    _fields_ = [("n", ctypes.c_uint32), ("m", ctypes.c_uint64), ("src", ctypes.c_void_p), ("dst", ctypes.c_void_p),
+                ("w", ctypes.c_void_p), ("msf_ids", ctypes.c_void_p), ("msf_count", ctypes.c_uint32),
+                ("total_weight", ctypes.c_uint64), ("status", ctypes.c_int)]
+
+
 class KernelStats(ctypes.Structure):
     _fields_ = [("launches", ctypes.c_uint64), ("ms", ctypes.c_double), ("bytes", ctypes.c_double)]
 
@@ -65,6 +72,7 @@ _SIGNATURES = {
     "mst_solve": (_I, [_P, _U32, _U64, _P, _P, _P, _P, _P, _P, _P]),
     "mst_solve_host": (_I, [_P, _U32, _U64, _P, _P, _P, _P, _P, _P, _P]),
     "mst_solve_batched": (_I, [_P, _U32, _P, _P, _P, _P, _P, _P, _P, _P, _P]),
+    "mst_solve_host_many": (_I, [_P, _U32, _P, _P]),
     "mst_step_min_edges": (_I, [_P, _U32, _U64, _P, _P, _P, _P, _P, _P]),
     "mst_step_contract": (_I, [_P, _U32, _U64, _P, _P, _P, _P, _P, _P, _P]),
     "mst_step_relabel": (_I, [_P, _U32, _U64, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P]),
@@ -249,6 +257,34 @@ class Solver:
         self._check(self.lib.mst_solve_host(self.h, n, m, _P(src_ptr), _P(dst_ptr), _P(w_ptr), _P(ids_ptr),
                                        ctypes.byref(cnt), ctypes.byref(tot), _stream(stream)), "mst_solve_host")
         return int(cnt.value), int(tot.value)
+
+    def solve_host_many_ptr(self, graphs, stream=None):
+        """mst_solve_host_many on raw host pointers: graphs is a sequence of
+        (n, m, src_ptr, dst_ptr, w_ptr, ids_ptr); returns [(count, total)].
+        Graph i+1's inputs are copied while graph i is solved."""
+        arr = (HostGraph * max(1, len(graphs)))()
+        for i, (n, m, s_p, d_p, w_p, i_p) in enumerate(graphs):
+            arr[i] = HostGraph(n, m, s_p, d_p, w_p, i_p, 0, 0, 0)
+        st = self.lib.mst_solve_host_many(self.h, len(graphs), ctypes.cast(arr, _P), _stream(stream))
+        bad = [(i, arr[i].status) for i in range(len(graphs)) if arr[i].status != MST_OK]
+        if st != MST_OK or bad:
+            self._check(st if st != MST_OK else bad[0][1], f"mst_solve_host_many (graph {bad[0][0] if bad else '?'})")
+        return [(int(arr[i].msf_count), int(arr[i].total_weight)) for i in range(len(graphs))]
+
+    def solve_host_many(self, graphs, stream=None):
+        """mst_solve_host_many on host arrays: graphs is a sequence of (n, src,
+        dst, w); returns [(ids, total)] (ascending ids)."""
+        import numpy as np
+        keep, spec, outs = [], [], []
+        for n, src, dst, w in graphs:
+            arrs = [np.ascontiguousarray(a, dtype=np.uint32) for a in (src, dst, w)]
+            m = arrs[0].size
+            ids = np.empty(max(1, min(m, max(n - 1, 0))), dtype=np.uint32)
+            keep.append(arrs)
+            outs.append(ids)
+            spec.append((n, m, *(a.ctypes.data for a in arrs), ids.ctypes.data))
+        res = self.solve_host_many_ptr(spec, stream)
+        return [(outs[i][:cnt].copy(), tot) for i, (cnt, tot) in enumerate(res)]
 
     def solve_batched(self, n_per_graph, edge_off, src: torch.Tensor, dst: torch.Tensor, w: torch.Tensor,
                       stream=None):

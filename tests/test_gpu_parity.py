@@ -151,6 +151,57 @@ def test_vertex_out_of_range_is_an_error(solver, dev):
     assert_same_forest(solver, 5, src[:2], dst[:2], w[:2], dev, "after error")
 
 
+@pytest.mark.parametrize("variant", ["boruvka", "filter"])
+def test_solve_host_many(dev, variant):
+    """A sequence of host-resident graphs of different sizes (empty ones, one
+    with a bad vertex id, one repeated), each solved while the next one's
+    inputs are copied: every forest is the oracle's, the bad graph alone
+    reports MST_ERR_VERTEX_RANGE, and the handle stays usable."""
+    gs = [W.rmat(14, 200000, 101), W.gnm(3000, 20000, 102), W.Graph(5, *(np.empty(0, np.uint32),) * 3),
+          W.rgg(2, 20000, 8.0, 103), W.Graph(0, *(np.empty(0, np.uint32),) * 3), W.gnm(50000, 400000, 104)]
+    gs.append(gs[0])
+    s = Solver(0, variant=variant, filter_min_edges=1 << 10)
+    try:
+        res = s.solve_host_many([(g.n, g.src, g.dst, g.w) for g in gs])
+        for g, (ids, tot) in zip(gs, res):
+            kid, ktot = oracle.kruskal(g.n, g.src, g.dst, g.w)
+            assert np.array_equal(ids, kid) and tot == ktot
+        bad = W.Graph(4, np.array([0, 1], np.uint32), np.array([1, 9], np.uint32), np.array([3, 4], np.uint32))
+        with pytest.raises(MstError) as e:
+            s.solve_host_many([(g.n, g.src, g.dst, g.w) for g in (gs[1], bad, gs[3])])
+        assert e.value.status == 2
+        ids, tot = s.solve_host_many([(gs[1].n, gs[1].src, gs[1].dst, gs[1].w)])[0]
+        kid, ktot = oracle.kruskal(gs[1].n, gs[1].src, gs[1].dst, gs[1].w)
+        assert np.array_equal(ids, kid) and tot == ktot
+    finally:
+        s.close()
+
+
+def test_solve_host_many_statuses(dev):
+    """Per-graph statuses: a graph with a bad id fails alone, the graphs after
+    it are still solved."""
+    import ctypes
+    from paper_2302_12199_gb300.mst import HostGraph
+    good = W.gnm(2000, 10000, 105)
+    bad = W.Graph(4, np.array([0, 1], np.uint32), np.array([1, 9], np.uint32), np.array([3, 4], np.uint32))
+    s = Solver(0)
+    try:
+        keep = []
+        arr = (HostGraph * 3)()
+        for i, g in enumerate((good, bad, good)):
+            a = [np.ascontiguousarray(x, dtype=np.uint32) for x in (g.src, g.dst, g.w)]
+            ids = np.empty(max(1, min(g.m, g.n - 1)), np.uint32)
+            keep.append((a, ids))
+            arr[i] = HostGraph(g.n, g.m, a[0].ctypes.data, a[1].ctypes.data, a[2].ctypes.data, ids.ctypes.data, 0, 0, 0)
+        st = s.lib.mst_solve_host_many(s.h, 3, ctypes.cast(arr, ctypes.c_void_p), None)
+        assert st == 2 and [arr[i].status for i in range(3)] == [0, 2, 0]
+        kid, ktot = oracle.kruskal(good.n, good.src, good.dst, good.w)
+        for i in (0, 2):
+            assert np.array_equal(keep[i][1][:arr[i].msf_count], kid) and arr[i].total_weight == ktot
+    finally:
+        s.close()
+
+
 def test_solve_host_matches_device(solver, dev):
     g = W.rmat(12, 50000, 12)
     ids, tot = solver.solve_host(g.n, g.src, g.dst, g.w)
