@@ -13,9 +13,10 @@ others run on the GPU start as soon as a slot and memory free up, and their
 work overlaps on the device.
 
 Host logic only: every step of a solve runs in the CUDA library.  Request
-payloads are resident in device memory (a pool of graphs standing in for
-uploaded requests); a batch gathers its graphs' edges into the slot's
-contiguous buffers with device-to-device copies.
+payloads are either resident in device memory (a pool of graphs standing in
+for uploaded requests; a batch gathers its graphs' edges into the slot's
+contiguous buffers with device-to-device copies) or in page-locked host
+memory (a batch copies each graph's edges to the device on the slot's stream).
 """
 from __future__ import annotations
 
@@ -33,9 +34,10 @@ from .mst import Solver
 
 @dataclass
 class PoolGraph:
-    """One request payload: an undirected multigraph resident on the device."""
+    """One request payload: an undirected multigraph on the device or in
+    page-locked host memory."""
     n: int
-    src: torch.Tensor  # int32 (uint32 bits), device
+    src: torch.Tensor  # int32 (uint32 bits), device or pinned host
     dst: torch.Tensor
     w: torch.Tensor
 
@@ -114,10 +116,19 @@ class _Slot:
         src, dst, w = (b[:m] for b in self.bufs)
         t0 = time.perf_counter()
         with torch.cuda.stream(self.stream):
-            if m:  # gather the batch: one concatenation per array
+            if m and graphs[0].src.is_cuda:  # gather the batch: one concatenation per array
                 torch.cat([g.src for g in graphs], out=src)
                 torch.cat([g.dst for g in graphs], out=dst)
                 torch.cat([g.w for g in graphs], out=w)
+            elif m:  # host payloads: copy each graph's arrays in
+                o = 0
+                for g in graphs:
+                    k = g.m
+                    if k:
+                        src[o:o + k].copy_(g.src, non_blocking=True)
+                        dst[o:o + k].copy_(g.dst, non_blocking=True)
+                        w[o:o + k].copy_(g.w, non_blocking=True)
+                    o += k
             t1 = time.perf_counter()
             ids, moff, tot = self.solver.solve_batched(n_per, off, src, dst, w, stream=self.stream)
             t2 = time.perf_counter()

@@ -109,6 +109,31 @@ def test_served_responses_alone_and_in_the_mix(dev):
         server.close()
 
 
+def test_served_host_payloads(dev):
+    """Payloads in page-locked host memory (copied in per batch, empty graphs
+    included) give the same responses as the oracle."""
+    from paper_2302_12199_gb300.serve import PoolGraph, Response, Server, poisson_arrivals
+    b = W.mix(20, 93, log_lo=6, log_hi=12)
+    exp = oracle_answers(b)
+    pin = lambda a: torch.from_numpy(np.ascontiguousarray(a, dtype=np.uint32).view(np.int32)).pin_memory()
+    pool = []
+    for g in range(b.num_graphs):
+        gr = b.graph(g)
+        pool.append(PoolGraph(gr.n, pin(gr.src), pin(gr.dst), pin(gr.w)))
+    empty = np.empty(0, np.uint32)
+    pool.append(PoolGraph(7, pin(empty), pin(empty), pin(empty)))
+    exp.append((empty, 0))
+    expected = {g: Response(kid, ktot) for g, (kid, ktot) in enumerate(exp)}
+    server = Server(0, slots=2, budget_bytes=4 << 20, max_batch=16, stall_seconds=20.0)
+    try:
+        arr = poisson_arrivals(20000.0, 0.02, seed=9)
+        picks = np.random.default_rng(10).integers(0, len(pool), arr.size)
+        st = server.run(pool, picks, arr, expected=expected, rate=20000.0, seconds=0.02)
+        assert st.requests == arr.size and st.mismatches == 0 and st.batches >= 2
+    finally:
+        server.close()
+
+
 def test_batched_forest_capacity_residues(dev):
     """The forest count and weight follow the id array in one allocation: every
     residue of its capacity modulo 64 ids must keep them inside it."""
