@@ -57,3 +57,35 @@ def test_workspace_bytes_grows_with_size(lib):
     assert 0 < a < b < c
     cfg.variant = 1
     assert lib.mst_workspace_bytes(1000, 20000, ctypes.byref(cfg)) > b
+
+
+def test_struct_layouts_match_the_header(tmp_path):
+    """The ctypes mirrors of mst_config, mst_host_graph and mst_kernel_stats have
+    the C compiler's size and field offsets (a mismatch would silently pass
+    wrong values across the boundary)."""
+    import os
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    structs = {"mst_config": mst.MstConfig, "mst_host_graph": mst.HostGraph, "mst_kernel_stats": mst.KernelStats}
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "mst.h"', "int main(void) {"]
+    for cname, py in structs.items():
+        lines.append(f'  printf("{cname} size %zu\\n", sizeof({cname}));')
+        for field, _ in py._fields_:
+            lines.append(f'  printf("{cname} {field} %zu\\n", offsetof({cname}, {field}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    inc = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include")
+    subprocess.run([cc, "-std=c11", "-I", inc, str(src), "-o", str(exe)], check=True)
+    got = {}
+    for line in subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.splitlines():
+        cname, field, value = line.split()
+        got[(cname, field)] = int(value)
+    for cname, py in structs.items():
+        assert got[(cname, "size")] == ctypes.sizeof(py), cname
+        for field, _ in py._fields_:
+            assert got[(cname, field)] == getattr(py, field).offset, (cname, field)
