@@ -121,8 +121,9 @@ void launch_min_edges(EdgeList in, uint64_t m, uint32_t n, int validate, KeyLayo
 void launch_max_weight(const uint32_t *w, uint64_t m, uint32_t *out, int sms, cudaStream_t s);
 void launch_hook(const HookArgs &a, uint64_t max_cand, cudaStream_t s);
 // max_steps: parent steps per thread and launch (0: the default of 64).
-// gbits (jumps over all vertices only, act == count_dev == nullptr): bit v of
-// the bitmap is set iff v's walk reached the root *groot in this launch.
+// With act == count_dev == nullptr the launch covers every vertex
+// 0..count_host-1 and, given gbits, sets bit v of that bitmap iff v's walk
+// reached the root *groot in this launch (gbits is ignored for lists).
 void launch_jump(const uint32_t *act, const u64 *count_dev, uint64_t count_host, uint64_t max_count,
                  uint32_t *parent, u64 *best, int reset_best, uint32_t *flag, int sms, cudaStream_t s,
                  uint32_t max_steps = 0, const uint32_t *groot = nullptr, uint32_t *gbits = nullptr);

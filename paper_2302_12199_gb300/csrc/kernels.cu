@@ -862,7 +862,7 @@ constexpr int JUMP_TILE = BLOCK * JUMP_ITEMS;
 
 __global__ void __launch_bounds__(BLOCK) jump_kernel(const uint32_t *act, const u64 *count_dev, uint64_t count_host,
                                                      uint32_t *parent, u64 *best, int reset_best, uint32_t *flag,
-                                                     uint32_t max_steps, const uint32_t *groot, uint32_t *gbits) {
+                                                     uint32_t max_steps) {
   const uint64_t cnt = count_dev ? *count_dev : count_host;
   // each thread takes JUMP_ITEMS vertices of a block tile (striped, so the list
   // and parent[] reads are coalesced) and advances their walks together: every
@@ -902,16 +902,81 @@ __global__ void __launch_bounds__(BLOCK) jump_kernel(const uint32_t *act, const 
 #pragma unroll
     for (int k = 0; k < JUMP_ITEMS; ++k)
       if (moved >> k & 1) __stcg(parent + c[k], p[k]);
-    if (gbits) {  // all vertices (no list): a warp's item k is 32 consecutive vertices, one bitmap word
-      const uint32_t r = *groot;
-      const uint64_t w0 = tb + (threadIdx.x & ~31u);
+  }
+}
+
+// The same over all n vertices (no list): lane l of a warp takes the four
+// consecutive vertices 4q..4q+3 (one 16-byte load and, if one moved, one
+// 16-byte store of parent), so that the pass is a plain stream plus the walk
+// steps, which mostly hit L1 (most walks end at a few large components'
+// roots).  Warps stride over warp-aligned bases and stay converged; with
+// gbits, eight lanes' four marks form one 32-vertex bitmap word.
+__global__ void __launch_bounds__(BLOCK) jump_all_kernel(uint32_t *parent, u64 *best, int reset_best, uint64_t n,
+                                                         uint32_t *flag, uint32_t max_steps, const uint32_t *groot,
+                                                         uint32_t *gbits) {
+  const uint32_t lane = threadIdx.x & 31u;
+  const uint64_t nq = (n + 3) / 4;
+  const uint64_t stride = (uint64_t)gridDim.x * BLOCK;
+  const bool vec = aligned16_dev(parent);
+  const uint32_t r = gbits ? *groot : 0u;
+  for (uint64_t qb = (uint64_t)blockIdx.x * BLOCK + (threadIdx.x & ~31u); qb < nq; qb += stride) {  // uniform per warp
+    const uint64_t q = qb + lane, c0 = 4 * q;
+    const bool full = vec && c0 + 4 <= n;
+    uint32_t p[4];
+    uint32_t live = 0;
+    if (full) {
+      const uint4 v = __ldcs(reinterpret_cast<const uint4 *>(parent) + q);
+      p[0] = v.x; p[1] = v.y; p[2] = v.z; p[3] = v.w;
+      live = 0xfu;
+    } else {
 #pragma unroll
-      for (int k = 0; k < JUMP_ITEMS; ++k) {
-        const bool in = ((live & ~pending) >> k & 1) && p[k] == r;  // an unfinished walk marks nothing
-        const uint32_t word = __ballot_sync(0xffffffffu, in);
-        const uint64_t v0 = w0 + (uint64_t)k * BLOCK;
-        if ((threadIdx.x & 31) == 0 && v0 < cnt) gbits[v0 >> 5] = word;
+      for (int k = 0; k < 4; ++k) {
+        const bool ok = c0 + k < n;
+        p[k] = ok ? __ldcg(parent + c0 + k) : 0u;
+        live |= (ok ? 1u : 0u) << k;
       }
+    }
+    if (reset_best) {
+#pragma unroll
+      for (int k = 0; k < 4; ++k)
+        if (live >> k & 1) best[c0 + k] = KEY_INF;
+    }
+    uint32_t pending = live, moved = 0;
+    for (uint32_t steps = 0; pending && steps < max_steps; ++steps) {
+      uint32_t pp[4];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) pp[k] = (pending >> k & 1) ? __ldca(parent + p[k]) : 0u;
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        if (!(pending >> k & 1)) continue;
+        if (pp[k] == p[k]) {
+          pending &= ~(1u << k);
+        } else {
+          p[k] = pp[k];
+          moved |= 1u << k;
+        }
+      }
+    }
+    if (pending) atomicOr(flag, 1u);
+    if (moved) {
+      if (full) {
+        __stcg(reinterpret_cast<uint4 *>(parent) + q, make_uint4(p[0], p[1], p[2], p[3]));
+      } else {
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+          if (moved >> k & 1) __stcg(parent + c0 + k, p[k]);
+      }
+    }
+    if (gbits) {
+      uint32_t nib = 0;  // an unfinished walk marks nothing
+#pragma unroll
+      for (int k = 0; k < 4; ++k) nib |= (((live & ~pending) >> k & 1) && p[k] == r ? 1u : 0u) << k;
+      uint32_t word = nib << (4 * (lane & 7u));
+      word |= __shfl_xor_sync(0xffffffffu, word, 1);
+      word |= __shfl_xor_sync(0xffffffffu, word, 2);
+      word |= __shfl_xor_sync(0xffffffffu, word, 4);
+      const uint64_t wi = (qb >> 3) + (lane >> 3);  // vertices 32 wi .. 32 wi + 31
+      if ((lane & 7u) == 0 && 32 * wi < n) gbits[wi] = word;
     }
   }
 }
@@ -2296,10 +2361,15 @@ void launch_jump(const uint32_t *act, const u64 *count_dev, uint64_t count_host,
                  uint32_t *parent, u64 *best, int reset_best, uint32_t *flag, int sms, cudaStream_t s,
                  uint32_t max_steps, const uint32_t *groot, uint32_t *gbits) {
   if (max_count == 0) return;
-  if (act || count_dev) gbits = nullptr;  // the bitmap needs every vertex in order
+  if (!act && !count_dev) {  // every vertex 0..count_host-1
+    const unsigned g = grid_for(((count_host + 3) / 4 + BLOCK - 1) / BLOCK, sms, 8);
+    jump_all_kernel<<<g, BLOCK, 0, s>>>(parent, best, reset_best, count_host, flag, max_steps ? max_steps : JUMP_STEPS,
+                                        groot, gbits);
+    return;
+  }
   const unsigned grid = grid_for((max_count + JUMP_TILE - 1) / JUMP_TILE, sms, 8);
   jump_kernel<<<grid, BLOCK, 0, s>>>(act, count_dev, count_host, parent, best, reset_best, flag,
-                                     max_steps ? max_steps : JUMP_STEPS, groot, gbits);
+                                     max_steps ? max_steps : JUMP_STEPS);
 }
 
 void launch_range_check(const uint32_t *x, uint64_t count, uint32_t bound, uint32_t *err, int sms, cudaStream_t s) {
