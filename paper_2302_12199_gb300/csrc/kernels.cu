@@ -745,8 +745,8 @@ constexpr uint32_t FIND_STEPS = 1u << 12;  // bound on one parent-chain walk
 // of independent loads.  The start vertex of a walk longer than one step is
 // then pointed at its label directly (a concurrent walker sees either pointer,
 // both on the same path).
-template <bool IOTA>
-__global__ void __launch_bounds__(BLOCK) hook_kernel(HookArgs a) {
+template <bool IOTA, bool PACKED>
+__global__ void __launch_bounds__(BLOCK, PACKED ? 6 : 3) hook_kernel(HookArgs a) {
   __shared__ uint32_t s_c[TILE];
   __shared__ uint32_t s_warp[BLOCK / 32 + 1];
   __shared__ uint32_t s_base[1];
@@ -768,7 +768,7 @@ __global__ void __launch_bounds__(BLOCK) hook_kernel(HookArgs a) {
 #pragma unroll
   for (int k = 0; k < ITEMS; ++k) kk[k] = (tb + item_off(k) < nc) ? a.best[c[k]] : KEY_INF;
   uint32_t keep = 0;
-  if (a.kl.packed) {  // the chosen neighbour is in the key
+  if (PACKED) {  // the chosen neighbour is in the key (a.kl.packed)
 #pragma unroll
     for (int k = 0; k < ITEMS; ++k) {
       if (kk[k] == KEY_INF) continue;
@@ -2351,10 +2351,12 @@ void launch_hook(const HookArgs &a, uint64_t max_cand, cudaStream_t s) {
   // memory (up to max_cand) gets a bounded grid that strides over the tiles
   const unsigned tiles = (unsigned)max_scan_tiles(max_cand);
   const unsigned grid = a.ncand_dev ? std::min(tiles, 152u * 8u) : tiles;
+  // the packed layout needs no parent-chain walks: its own instantiation
+  // keeps far fewer registers live (higher occupancy)
   if (a.cand)
-    hook_kernel<false><<<grid, BLOCK, 0, s>>>(a);
+    a.kl.packed ? hook_kernel<false, true><<<grid, BLOCK, 0, s>>>(a) : hook_kernel<false, false><<<grid, BLOCK, 0, s>>>(a);
   else
-    hook_kernel<true><<<grid, BLOCK, 0, s>>>(a);
+    a.kl.packed ? hook_kernel<true, true><<<grid, BLOCK, 0, s>>>(a) : hook_kernel<true, false><<<grid, BLOCK, 0, s>>>(a);
 }
 
 void launch_jump(const uint32_t *act, const u64 *count_dev, uint64_t count_host, uint64_t max_count,
