@@ -65,7 +65,9 @@ typedef struct {
   uint64_t seed;               /* seed of the pivot sampling stream */
   uint64_t filter_min_edges;   /* isSparse: lists shorter than this are not partitioned */
   float filter_max_avg_degree; /* isSparse: stop partitioning at average degree 2m/n <= this (the paper's
-                                  Section 6.3 uses 4; the default 1 is the measured optimum on GB300) */
+                                  Section 6.3 uses 4; the default 1.25 is measured on GB300: the range
+                                  1.0-1.5 is flat, and 1.25 keeps the number of levels stable where
+                                  halving lists reach m = n/2) */
   int base_case;               /* 1 (default): once a Borůvka call's live components (<= 4096) and
                                   edges (<= 6144) fit one block's shared memory, finish its rounds in
                                   one launch (the role of the paper's base case, Section 4.4); 0: run
@@ -92,7 +94,7 @@ typedef struct {
 } mst_config;
 
 /* Fills *cfg with the defaults (Borůvka variant, automatic dedupe, pivot sample
- * 2^16, isSparse average degree 1, lists below 2^20 edges not partitioned). */
+ * 2^16, isSparse average degree 1.25, lists below 2^20 edges not partitioned). */
 void mst_config_default(mst_config *cfg);
 
 /* Creates a handle on cfg->device (cfg == NULL: defaults on device 0). */

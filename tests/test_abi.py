@@ -26,7 +26,7 @@ def test_default_config(lib):
     lib.mst_config_default(ctypes.byref(cfg))
     assert cfg.variant == 0 and cfg.dedupe == 0
     assert cfg.pivot_sample == 1 << 16
-    assert cfg.filter_max_avg_degree == 1.0
+    assert cfg.filter_max_avg_degree == 1.25
     assert cfg.tile_contract == 0 and cfg.tile_vertices == 1024
     assert cfg.base_case == 1 and cfg.graph_rounds == 1 and cfg.graph_jump_launches == 2
     assert cfg.jump_steps == 64
