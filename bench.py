@@ -345,13 +345,26 @@ def gpu_main(args, rank: int, world: int, local_rank: int):
         uuid = "GPU-" + str(torch.cuda.get_device_properties(dev).uuid)
     except Exception:
         pass
+    # a profiled pass outside the timed region: every kernel class timed with
+    # CUDA events (per-class table; picks the dominant class)
+    prof_steps = max(1, min(args.steps, 5))
+    solver.profile(True)
+    for _ in range(prof_steps):
+        solver.solve(n, src, dst, w, out=out)
+    torch.cuda.synchronize(dev)
+    solver.profile(False)
+    stats_all = solver.profile_stats()
+    dom = max(stats_all, key=lambda k: stats_all[k][1])
     sampler = ClockSampler(uuid)
     if dist:
         dist.barrier()
     torch.cuda.synchronize(dev)
     sampler.start()
     time.sleep(0.3)
-    solver.profile(True)
+    # the timed region: events around the dominant class's launches only (the
+    # roofline's measured durations); every class still counts its launches
+    # and algorithmic bytes, which costs the host almost nothing per launch
+    solver.profile(True, classes=[dom])
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     nvtx_mark(torch, "push")  # lets a profiler capture the timed solves only
     e0.record(stream)
@@ -413,14 +426,14 @@ def gpu_main(args, rank: int, world: int, local_rank: int):
     kernels = {}
     all_bytes = 0.0
     launches = 0
-    for name, (nl, kms, kbytes) in stats.items():
+    for name, (nl, kms, kbytes) in stats.items():  # timed region: launches and bytes of every class
         launches += nl
         all_bytes += kbytes
+    for name, (nl, kms, kbytes) in stats_all.items():  # profiled pass: every class timed
         if nl:
-            kernels[name] = {"launches_per_step": nl / args.steps, "ms_per_step": kms / args.steps,
-                             "bytes_per_step": kbytes / args.steps,
+            kernels[name] = {"launches_per_step": nl / prof_steps, "ms_per_step": kms / prof_steps,
+                             "bytes_per_step": kbytes / prof_steps,
                              "GBps": (kbytes / (kms / 1e3) / 1e9) if kms > 0 else None}
-    dom = max(stats, key=lambda k: stats[k][1])
     nl, kms, kbytes = stats[dom]
     achieved = kbytes / (kms / 1e3) / 1e9
     traffic = None
@@ -445,6 +458,8 @@ def gpu_main(args, rank: int, world: int, local_rank: int):
         "effective_bw": {"GBps": effective, "frac": effective / peaks["hbm_gbs"],
                          "note": "sum of algorithmic bytes of all kernels / solve time"},
         "kernels": kernels,
+        "kernels_note": f"per-class CUDA-event times of {prof_steps} profiled solves outside the timed region; "
+                        "inside it only the dominant class is timed",
         "gpu_launches": launches,
         "e2e": e2e,
         "clocks": clocks,

@@ -205,6 +205,11 @@ typedef struct {
 /* enable != 0: start collecting (and clear the totals); 0: stop. */
 mst_status mst_profile_enable(mst_handle h, int enable);
 
+/* Classes (bit MST_K_x) timed with CUDA events while profiling; the others
+ * only count their launches and algorithmic bytes, which costs the host almost
+ * nothing per launch.  Default: all classes. */
+mst_status mst_profile_classes(mst_handle h, uint32_t mask);
+
 /* Totals of class `kind` (MST_K_*) since the last enable. */
 mst_status mst_profile_get(mst_handle h, int kind, mst_kernel_stats *out);
 

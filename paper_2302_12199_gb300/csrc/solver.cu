@@ -45,6 +45,7 @@ struct mst_ctx {
     double per1, per2;
   };
   bool prof_on = false;
+  uint32_t prof_mask = ~0u;  // classes that get event timing (the others: launches and bytes only)
   cudaStream_t cap_stream = nullptr;  // stream the round graphs are captured on
   cudaStream_t copy_stream = nullptr; // input copies of mst_solve_host_many
   cudaEvent_t in_ready[2] = {nullptr, nullptr}, in_free[2] = {nullptr, nullptr};
@@ -207,14 +208,17 @@ cudaEvent_t take_event(mst_ctx *c) {
   return e;
 }
 
-// Opens a timing record around the next launch(es) on `s`; -1 when profiling is off.
-int prof_begin(mst_ctx *c, cudaStream_t s) {
+// Opens a record around the next launch(es) of class `kind` on `s`; -1 when
+// profiling is off.  Only the classes in prof_mask are timed with events.
+int prof_begin(mst_ctx *c, cudaStream_t s, int kind) {
   if (!c->prof_on) return -1;
   mst_ctx::ProfRec r{};
-  r.a = take_event(c);
-  r.b = take_event(c);
-  if (!r.a || !r.b) return -1;
-  cudaEventRecord(r.a, s);
+  if (c->prof_mask >> kind & 1u) {
+    r.a = take_event(c);
+    r.b = take_event(c);
+    if (!r.a || !r.b) return -1;
+    cudaEventRecord(r.a, s);
+  }
   c->prof_pending.push_back(r);
   return (int)c->prof_pending.size() - 1;
 }
@@ -225,7 +229,7 @@ void prof_end(mst_ctx *c, cudaStream_t s, int idx, int kind, double bytes, int s
               int slot2 = -1, double per2 = 0) {
   if (idx < 0) return;
   mst_ctx::ProfRec &r = c->prof_pending[idx];
-  cudaEventRecord(r.b, s);
+  if (r.b) cudaEventRecord(r.b, s);
   r.kind = kind;
   r.bytes = bytes;
   r.slot1 = slot1;
@@ -238,7 +242,7 @@ void prof_end(mst_ctx *c, cudaStream_t s, int idx, int kind, double bytes, int s
 void prof_resolve(mst_ctx *c) {
   for (auto &r : c->prof_pending) {
     float ms = 0.f;
-    if (cudaEventElapsedTime(&ms, r.a, r.b) != cudaSuccess) {
+    if (r.a && cudaEventElapsedTime(&ms, r.a, r.b) != cudaSuccess) {
       cudaGetLastError();
       ms = 0.f;
     }
@@ -249,15 +253,17 @@ void prof_resolve(mst_ctx *c) {
     if (r.slot1 >= 0) b += (double)c->hs->count[r.slot1] * r.per1;
     if (r.slot2 >= 0) b += (double)c->hs->count[r.slot2] * r.per2;
     k.bytes += b;
-    c->ev_pool.push_back(r.a);
-    c->ev_pool.push_back(r.b);
+    if (r.a) {
+      c->ev_pool.push_back(r.a);
+      c->ev_pool.push_back(r.b);
+    }
   }
   c->prof_pending.clear();
 }
 
 #define PROF(kind, bytes, slot1, per1, slot2, per2, launch)       \
   do {                                                           \
-    const int _p = prof_begin(c, s);                             \
+    const int _p = prof_begin(c, s, kind);                       \
     launch;                                                      \
     prof_end(c, s, _p, kind, bytes, slot1, per1, slot2, per2);   \
   } while (0)
@@ -1319,8 +1325,8 @@ void mst_destroy(mst_handle h) {
     if (h->grounds) cudaFree(h->grounds);
     if (h->pool) cudaMemPoolDestroy(h->pool);
     for (auto &r : h->prof_pending) {
-      h->ev_pool.push_back(r.a);
-      h->ev_pool.push_back(r.b);
+      if (r.a) h->ev_pool.push_back(r.a);
+      if (r.b) h->ev_pool.push_back(r.b);
     }
     for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
     cudaGetLastError();
@@ -1347,6 +1353,12 @@ mst_status mst_profile_enable(mst_handle h, int enable) {
   if (!h) return MST_ERR_INVALID_ARG;
   h->prof_on = enable != 0;
   if (h->prof_on) std::memset(h->prof, 0, sizeof(h->prof));
+  return MST_OK;
+}
+
+mst_status mst_profile_classes(mst_handle h, uint32_t mask) {
+  if (!h) return MST_ERR_INVALID_ARG;
+  h->prof_mask = mask;
   return MST_OK;
 }
 

@@ -83,6 +83,7 @@ _SIGNATURES = {
     "mst_step_finalize": (_I, [_P, _U64, _P, _P, _P, _P, _P, _P]),
     "mst_step_tile_contract": (_I, [_P, _U32, _U64, _P, _P, _P, _U32, _P, _P, _P]),
     "mst_profile_enable": (_I, [_P, _I]),
+    "mst_profile_classes": (_I, [_P, _U32]),
     "mst_profile_get": (_I, [_P, _I, ctypes.POINTER(KernelStats)]),
     "mst_pivot_noalloc": (_I, [_U64, _P, _P, _U64, _U32, _P, _P]),
 }
@@ -197,8 +198,12 @@ class Solver:
             setattr(self.cfg, k, v)
         self._check(self.lib.mst_set_config(self.h, ctypes.byref(self.cfg)), "mst_set_config")
 
-    def profile(self, enable: bool = True):
-        """Start (and clear) or stop per-kernel-class event timing."""
+    def profile(self, enable: bool = True, classes=None):
+        """Start (and clear) or stop per-kernel-class statistics.  `classes`
+        (names from KERNEL_CLASSES; None = all) are timed with CUDA events; the
+        others only count launches and algorithmic bytes."""
+        mask = 0xFFFFFFFF if classes is None else sum(1 << KERNEL_CLASSES.index(c) for c in classes)
+        self._check(self.lib.mst_profile_classes(self.h, mask), "mst_profile_classes")
         self._check(self.lib.mst_profile_enable(self.h, 1 if enable else 0), "mst_profile_enable")
 
     def profile_stats(self) -> dict:

@@ -599,3 +599,25 @@ def test_jump_steps_range(dev):
         with pytest.raises(MstError) as e:
             Solver(0, jump_steps=bad)
         assert e.value.status == 1
+
+
+def test_profile_class_mask(dev):
+    """With a class mask only the named classes are timed; every class still
+    counts its launches and algorithmic bytes, and the forest is unchanged."""
+    g = W.rmat(16, (1 << 21) + 7, 111)
+    s = Solver(0, variant="filter", filter_min_edges=1 << 12)
+    try:
+        s.profile(True)
+        assert_same_forest(s, g.n, g.src, g.dst, g.w, dev, "all classes")
+        s.profile(False)
+        full = s.profile_stats()
+        s.profile(True, classes=["filter"])
+        assert_same_forest(s, g.n, g.src, g.dst, g.w, dev, "filter class")
+        s.profile(False)
+        masked = s.profile_stats()
+        assert full["filter"][0] > 0 and masked["filter"][0] > 0 and masked["filter"][1] > 0
+        timed_elsewhere = [k for k, v in masked.items() if k != "filter" and v[1] > 0]
+        assert not timed_elsewhere, timed_elsewhere
+        assert masked["partition"][0] > 0 and masked["partition"][2] > 0
+    finally:
+        s.close()
