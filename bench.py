@@ -326,6 +326,8 @@ def gpu_main(args, rank: int, world: int, local_rank: int):
         cfg["filter_split"] = args.filter_split
     if args.min_edges_sort is not None:
         cfg["min_edges_sort"] = args.min_edges_sort
+    if args.tile_filter is not None:
+        cfg["tile_filter"] = args.tile_filter
     g = gen(W)
     n, m = g.n, g.m
     src = torch.from_numpy(g.src.view(np.int32)).to(dev)
@@ -831,6 +833,7 @@ def main():
     ap.add_argument("--filter-carry", type=int, default=None, choices=[0, 1])
     ap.add_argument("--filter-split", type=int, default=None, choices=[0, 1])
     ap.add_argument("--min-edges-sort", type=int, default=None, choices=[0, 1])
+    ap.add_argument("--tile-filter", type=int, default=None, choices=[0, 1])
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "gpu":
         args.warmup = 3

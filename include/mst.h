@@ -91,6 +91,10 @@ typedef struct {
                                   1..4096 (default 64); a launch that leaves a walk short is repeated
                                   (at most 64 more times, then MST_ERR_INTERNAL).  1 makes every launch
                                   one pointer-doubling step (Section 4.2) */
+  int tile_filter;             /* 1: inside local contraction and the base case, the rounds use the light
+                                  half of a tile's edges first and drop heavy edges that fall inside a
+                                  component (recursive filtering in local preprocessing, Section 6.2);
+                                  0 (default, measured faster on GB300): every edge from the first round */
 } mst_config;
 
 /* Fills *cfg with the defaults (Borůvka variant, automatic dedupe, pivot sample

@@ -157,7 +157,8 @@ void launch_tile_scatter(EdgeList in, uint64_t m, uint32_t n, uint32_t B, const 
                          cudaStream_t s);
 bool launch_tile_contract(uint32_t n, uint32_t B, uint64_t nlocal, const u64 *cutmin, const u64 *offsets,
                           const uint32_t *b_ends, const uint32_t *b_w, const uint32_t *b_id, uint32_t *parent,
-                          uint32_t *bits, EdgeOut rest, u64 *rest_fill, uint32_t *err, cudaStream_t s);
+                          uint32_t *bits, EdgeOut rest, u64 *rest_fill, uint32_t *err, cudaStream_t s,
+                          int filter_heavy);
 void launch_tile_sample(EdgeList in, uint64_t m, uint32_t n, uint32_t B, u64 state, uint32_t samples,
                         uint32_t *local_count, cudaStream_t s);
 // Stable LSD radix sort of (u64 key, u32 value) pairs over the low `bits` bits;
@@ -209,7 +210,7 @@ struct BaseScratch {
 };
 // False (nothing launched) when the call does not fit the base case.
 bool launch_base_case(const uint32_t *act, uint32_t n_act, EdgeList cur, uint64_t m, uint32_t *parent, uint32_t *bits,
-                      const BaseScratch &b, uint32_t *err, cudaStream_t s);
+                      const BaseScratch &b, uint32_t *err, cudaStream_t s, int filter_heavy);
 void launch_iota(uint32_t *p, uint64_t n, int sms, cudaStream_t s);
 void launch_u64_to_u32(const u64 *src, uint32_t *dst, cudaStream_t s);
 

@@ -1494,7 +1494,7 @@ __global__ void __launch_bounds__(TC_THREADS) tile_contract_kernel(uint32_t n, u
                                                                     const uint32_t *b_w, const uint32_t *b_id,
                                                                     uint32_t edge_cap, uint32_t *parent,
                                                                     uint32_t *bits, EdgeOut rest, u64 *rest_fill,
-                                                                    uint32_t *err) {
+                                                                    uint32_t *err, int filter_heavy) {
   extern __shared__ __align__(128) unsigned char smem_dyn[];
   u64 *best = reinterpret_cast<u64 *>(smem_dyn);  // [B]
   u64 *comp = best + B;                           // [B] component cut minimum (valid at roots)
@@ -1503,8 +1503,8 @@ __global__ void __launch_bounds__(TC_THREADS) tile_contract_kernel(uint32_t n, u
   uint32_t *hook = lab + B;                                        // [B]
   uint32_t *other = hook + B;                                      // [B]
   uint32_t *sends = other + B;                                     // [edge_cap]
-  __shared__ uint32_t s_any, s_ne, s_warp[TC_THREADS / 32 + 1];
-  __shared__ u64 s_base;
+  __shared__ uint32_t s_any, s_ne, s_light, s_warp[TC_THREADS / 32 + 1];
+  __shared__ u64 s_base, s_pivot;
 
   const uint32_t t = blockIdx.x;
   const uint64_t vbase = (uint64_t)t * B;
@@ -1527,8 +1527,32 @@ __global__ void __launch_bounds__(TC_THREADS) tile_contract_kernel(uint32_t n, u
   }
   if (threadIdx.x == 0) s_ne = ne0;
   __syncthreads();
-  for (uint32_t round = 0; round <= nv; ++round) {
+  // Recursive filtering inside the tile (the Filter-Borůvka idea applied to
+  // local preprocessing, Section 6.2): the rounds first use only the light
+  // edges (key <= the median of 32 evenly spaced keys); the heavy ones are
+  // relabelled with them and the compaction drops those that fall inside a
+  // component (the filter).  When the light edges no longer hook, every edge
+  // takes part.  A light edge is lighter than every heavy one, so the hooking
+  // rule (lightest incident edge, below the cut minimum) is unchanged.
+  if (threadIdx.x < 32) {
+    const uint32_t lane = threadIdx.x;
+    const bool on = filter_heavy && in_smem && ne0 >= 64;
+    u64 v = on ? skey[(uint32_t)(((uint64_t)lane * ne0) / 32)] : 0ULL;
+    for (uint32_t k = 2; k <= 32; k <<= 1)  // bitonic sort of the warp's 32 keys, ascending
+      for (uint32_t j = k >> 1; j > 0; j >>= 1) {
+        const u64 o = __shfl_xor_sync(0xffffffffu, v, j);
+        v = (((lane & j) == 0) == ((lane & k) == 0)) ? (o < v ? o : v) : (o > v ? o : v);
+      }
+    const u64 med = __shfl_sync(0xffffffffu, v, 15);
+    if (lane == 0) {
+      s_light = on ? 1u : 0u;
+      s_pivot = on ? med : KEY_INF;
+    }
+  }
+  __syncthreads();
+  for (uint32_t round = 0; round <= 2 * nv + 2; ++round) {
     const uint32_t ne = s_ne;
+    const u64 lim = s_light ? s_pivot : KEY_INF;  // edges above it wait for the second phase
     for (uint32_t c = threadIdx.x; c < nv; c += TC_THREADS) best[c] = KEY_INF;
     if (threadIdx.x == 0) s_any = 0;
     __syncthreads();
@@ -1536,7 +1560,7 @@ __global__ void __launch_bounds__(TC_THREADS) tile_contract_kernel(uint32_t n, u
       const uint32_t pe = in_smem ? sends[e] : b_ends[e0 + e];
       const u64 k = in_smem ? skey[e] : edge_key(b_w[e0 + e], b_id[e0 + e]);
       const uint32_t a = in_smem ? (pe & 0xffffu) : lab[pe & 0xffffu], b = in_smem ? (pe >> 16) : lab[pe >> 16];
-      if (a != b) {
+      if (a != b && k <= lim) {
         if (k < best[a]) atomicMin(best + a, k);
         if (k < best[b]) atomicMin(best + b, k);
       }
@@ -1549,7 +1573,7 @@ __global__ void __launch_bounds__(TC_THREADS) tile_contract_kernel(uint32_t n, u
       const uint32_t pe = in_smem ? sends[e] : b_ends[e0 + e];
       const u64 k = in_smem ? skey[e] : edge_key(b_w[e0 + e], b_id[e0 + e]);
       const uint32_t a = in_smem ? (pe & 0xffffu) : lab[pe & 0xffffu], b = in_smem ? (pe >> 16) : lab[pe >> 16];
-      if (a != b) {
+      if (a != b && k <= lim) {
         if (best[a] == k) other[a] = b;
         if (best[b] == k) other[b] = a;
       }
@@ -1569,7 +1593,13 @@ __global__ void __launch_bounds__(TC_THREADS) tile_contract_kernel(uint32_t n, u
       }
     }
     __syncthreads();
-    if (!s_any) break;
+    if (!s_any) {
+      if (!s_light) break;
+      __syncthreads();  // every thread has read s_light
+      if (threadIdx.x == 0) s_light = 0;
+      __syncthreads();
+      continue;  // the heavy edges left join the rounds
+    }
     // every component of the last round follows its hooks to the new root
     // (the hooks form a forest: at most nv steps)
     for (uint32_t c = threadIdx.x; c < nv; c += TC_THREADS) {
@@ -2098,14 +2128,14 @@ __global__ void base_unmap_kernel(const uint32_t *act, uint32_t n_act, const uin
 }
 
 bool launch_base_case(const uint32_t *act, uint32_t n_act, EdgeList cur, uint64_t m, uint32_t *parent, uint32_t *bits,
-                      const BaseScratch &b, uint32_t *err, cudaStream_t s) {
+                      const BaseScratch &b, uint32_t *err, cudaStream_t s, int filter_heavy) {
   if (n_act == 0 || n_act > BASE_MAX_N || m > BASE_MAX_M || !cur.id) return false;
   base_map_kernel<<<(n_act + 255) / 256, 256, 0, s>>>(act, n_act, b.loc, b.offsets, m);
   if (m) base_pack_kernel<<<(unsigned)((m + 255) / 256), 256, 0, s>>>(cur.u, cur.v, m, parent, b.loc, b.ends);
   cudaMemsetAsync(b.cutmin, 0xff, (size_t)n_act * 8, s);
   cudaMemsetAsync(b.rest_fill, 0, sizeof(u64), s);
   if (!launch_tile_contract(n_act, n_act, m, b.cutmin, b.offsets, b.ends, cur.w, cur.id, b.plocal, bits, b.rest,
-                            b.rest_fill, err, s))
+                            b.rest_fill, err, s, filter_heavy))
     return false;
   base_unmap_kernel<<<(n_act + 255) / 256, 256, 0, s>>>(act, n_act, b.plocal, parent);
   return true;
@@ -2445,7 +2475,8 @@ void launch_tile_scatter(EdgeList in, uint64_t m, uint32_t n, uint32_t B, const 
 
 bool launch_tile_contract(uint32_t n, uint32_t B, uint64_t nlocal, const u64 *cutmin, const u64 *offsets,
                           const uint32_t *b_ends, const uint32_t *b_w, const uint32_t *b_id, uint32_t *parent,
-                          uint32_t *bits, EdgeOut rest, u64 *rest_fill, uint32_t *err, cudaStream_t s) {
+                          uint32_t *bits, EdgeOut rest, u64 *rest_fill, uint32_t *err, cudaStream_t s,
+                          int filter_heavy) {
   static int smem_full = 0;
   if (!smem_full) {
     int dev = 0, optin = 0;
@@ -2466,7 +2497,7 @@ bool launch_tile_contract(uint32_t n, uint32_t B, uint64_t nlocal, const u64 *cu
   cap = min(cap, ((size_t)smem_full - vbytes) / 12);
   const size_t bytes = vbytes + (size_t)cap * 12;
   tile_contract_kernel<<<ntiles, TC_THREADS, bytes, s>>>(n, B, cutmin, offsets, b_ends, b_w, b_id, (uint32_t)cap,
-                                                         parent, bits, rest, rest_fill, err);
+                                                         parent, bits, rest, rest_fill, err, filter_heavy);
   return true;
 }
 

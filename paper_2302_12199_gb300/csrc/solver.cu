@@ -765,7 +765,7 @@ struct Solve {
     b.rest_fill = (u64 *)p;
     bool launched = false;
     PROF(MST_K_BASE, 16.0 * (double)cur_m + 28.0 * (double)n_act, -1, 0.0, -1, 0.0,
-         launched = launch_base_case(act_list, n_act, cur, cur_m, parent, bits, b, &c->ds->err, s));
+         launched = launch_base_case(act_list, n_act, cur, cur_m, parent, bits, b, &c->ds->err, s, c->cfg.tile_filter));
     if (!launched) return MST_ERR_INTERNAL;
     return readback(c, s);
   }
@@ -824,7 +824,7 @@ struct Solve {
     PROF(MST_K_TILE, 12.0 * (double)nlocal + 12.0 * (double)n, -1, 0.0, -1, 0.0,
          launched = launch_tile_contract(n, B, nlocal, cut_b.as<u64>(), off_b.as<u64>(), (uint32_t *)bb,
                                          (uint32_t *)(bb + stride), (uint32_t *)(bb + 2 * stride), parent, bits,
-                                         cutl.out, &c->ds->count[CNT_CUT], &c->ds->err, s));
+                                         cutl.out, &c->ds->count[CNT_CUT], &c->ds->err, s, c->cfg.tile_filter));
     if (!launched) return MST_ERR_INVALID_ARG;  // tile too large for shared memory
     // the cut edges, relabelled to the tile roots, are the contracted graph
     TRY(out.alloc(c, mcut, s));
@@ -1086,6 +1086,7 @@ mst_status validate_cfg(const mst_config *cfg) {
   if (cfg->filter_split < 0 || cfg->filter_split > 1) return MST_ERR_INVALID_ARG;
   if (cfg->min_edges_sort < 0 || cfg->min_edges_sort > 1) return MST_ERR_INVALID_ARG;
   if (cfg->jump_steps < 1 || cfg->jump_steps > 4096) return MST_ERR_INVALID_ARG;
+  if (cfg->tile_filter < 0 || cfg->tile_filter > 1) return MST_ERR_INVALID_ARG;
   if (cfg->tile_vertices < 32 || cfg->tile_vertices > 4096) return MST_ERR_INVALID_ARG;
   return MST_OK;
 }
@@ -1244,6 +1245,7 @@ void mst_config_default(mst_config *cfg) {
   cfg->filter_split = 0;
   cfg->min_edges_sort = 0;
   cfg->jump_steps = 64;
+  cfg->tile_filter = 0;  // measured slower on GB300: the light phase adds synchronised rounds in each tile
 }
 
 const char *mst_status_string(mst_status s) {
@@ -1777,6 +1779,7 @@ mst_status mst_step_tile_contract(mst_handle h, uint32_t n, uint64_t m, const ui
   const mst_config saved = h->cfg;
   h->cfg.tile_contract = 1;
   h->cfg.tile_vertices = tile_vertices;
+  h->cfg.tile_filter = 0;  // the step contracts exactly what the rounds without filtering contract
   mst_status st;
   {
     Solve S(h, s, n, m);

@@ -54,7 +54,8 @@ class MstConfig(ctypes.Structure):
                 ("filter_max_avg_degree", ctypes.c_float), ("base_case", ctypes.c_int),
                 ("graph_rounds", ctypes.c_int), ("graph_jump_launches", ctypes.c_int),
                 ("filter_carry", ctypes.c_int), ("filter_split", ctypes.c_int),
-                ("min_edges_sort", ctypes.c_int), ("jump_steps", ctypes.c_uint32)]
+                ("min_edges_sort", ctypes.c_int), ("jump_steps", ctypes.c_uint32),
+                ("tile_filter", ctypes.c_int)]
 
 
 _P = ctypes.c_void_p

@@ -29,7 +29,7 @@ def test_default_config(lib):
     assert cfg.filter_max_avg_degree == 1.25
     assert cfg.tile_contract == 0 and cfg.tile_vertices == 1024
     assert cfg.base_case == 1 and cfg.graph_rounds == 1 and cfg.graph_jump_launches == 2
-    assert cfg.jump_steps == 64
+    assert cfg.jump_steps == 64 and cfg.tile_filter == 0
     assert cfg.filter_carry == 0
 
 

@@ -621,3 +621,27 @@ def test_profile_class_mask(dev):
         assert masked["partition"][0] > 0 and masked["partition"][2] > 0
     finally:
         s.close()
+
+
+@pytest.mark.parametrize("family", ["rgg2", "grid", "gnm", "rmat", "path"])
+def test_tile_filter_on_and_off_agree(dev, family):
+    """Recursive filtering inside local contraction and the base case (light
+    edges first, heavy edges inside a component dropped) gives the oracle's
+    forest, on families with many tile-local edges and on ones with few."""
+    g = {
+        "rgg2": lambda: W.rgg(2, 60000, 8.0, 121),
+        "grid": lambda: W.grid2d(300, 300, 122),
+        "gnm": lambda: W.gnm(40000, 300000, 123),
+        "rmat": lambda: W.rmat(15, 400000, 124),
+        "path": lambda: W.Graph(100000, np.arange(99999, dtype=np.uint32), np.arange(1, 100000, dtype=np.uint32),
+                                (np.arange(99999, dtype=np.uint32) % 7 + 1).astype(np.uint32)),
+    }[family]()
+    kid, ktot = oracle.kruskal(g.n, g.src, g.dst, g.w)
+    for tf in (0, 1):
+        for variant in ("boruvka", "filter"):
+            s = Solver(0, variant=variant, tile_contract=1, tile_vertices=512, tile_filter=tf, filter_min_edges=1 << 10)
+            try:
+                ids, tot = gpu_msf(s, g.n, g.src, g.dst, g.w, dev)
+                assert np.array_equal(ids, kid) and tot == ktot, (tf, variant)
+            finally:
+                s.close()
