@@ -212,6 +212,5 @@ struct BaseScratch {
 bool launch_base_case(const uint32_t *act, uint32_t n_act, EdgeList cur, uint64_t m, uint32_t *parent, uint32_t *bits,
                       const BaseScratch &b, uint32_t *err, cudaStream_t s, int filter_heavy);
 void launch_iota(uint32_t *p, uint64_t n, int sms, cudaStream_t s);
-void launch_u64_to_u32(const u64 *src, uint32_t *dst, cudaStream_t s);
 
 }  // namespace mstgpu

@@ -1027,7 +1027,6 @@ __global__ void iota_kernel(uint32_t *p, uint64_t n) {
     p[i] = (uint32_t)i;
 }
 
-__global__ void u64_to_u32_kernel(const u64 *src, uint32_t *dst) { *dst = (uint32_t)*src; }
 
 // ------------------------------------------------------------------ pivot
 
@@ -2512,6 +2511,5 @@ void launch_iota(uint32_t *p, uint64_t n, int sms, cudaStream_t s) {
   iota_kernel<<<grid_for((n + BLOCK - 1) / BLOCK, sms, 8), BLOCK, 0, s>>>(p, n);
 }
 
-void launch_u64_to_u32(const u64 *src, uint32_t *dst, cudaStream_t s) { u64_to_u32_kernel<<<1, 1, 0, s>>>(src, dst); }
 
 }  // namespace mstgpu
