@@ -297,6 +297,17 @@ mst_status zero_counters(mst_ctx *c, cudaStream_t s) {
   return MST_OK;
 }
 
+// The same plus the jump flag (one memset over jump_flag .. count[2]; the
+// error word stays): a Borůvka round's first operation, so that the round's
+// jump launch needs no memset of its own.
+mst_status zero_round_state(mst_ctx *c, cudaStream_t s) {
+  static_assert(offsetof(DevState, jump_flag) == sizeof(uint32_t) && offsetof(DevState, count) == 4 * sizeof(uint32_t),
+                "DevState layout");
+  CK(cudaMemsetAsync(&c->ds->jump_flag, 0, offsetof(DevState, count) + 3 * sizeof(u64) - offsetof(DevState, jump_flag),
+                     s));
+  return MST_OK;
+}
+
 // Per-solve state: vertex arrays and the chosen-edge bitmap.
 struct Solve {
   mst_ctx *c;
@@ -385,8 +396,9 @@ struct Solve {
   // One pointer-jumping launch over the list (or all n), with the flag cleared
   // first; the flag is read back by the caller's next readback.
   mst_status jump_launch(const uint32_t *act_list, const u64 *count_dev, uint64_t count_host, uint64_t max_count,
-                         int reset_best, const uint32_t *groot = nullptr, uint32_t *gbits = nullptr) {
-    CK(cudaMemsetAsync(&c->ds->jump_flag, 0, sizeof(uint32_t), s));
+                         int reset_best, const uint32_t *groot = nullptr, uint32_t *gbits = nullptr,
+                         bool flag_clear = false) {
+    if (!flag_clear) CK(cudaMemsetAsync(&c->ds->jump_flag, 0, sizeof(uint32_t), s));
     const int slot = count_dev ? CNT_ACTIVE : -1;
     const double fixed = count_dev ? 0.0 : (8.0 + (gbits ? 0.125 : 0.0)) * (double)count_host;
     PROF(MST_K_JUMP, fixed, slot, reset_best ? 20.0 : 12.0, -1, 0.0,
@@ -406,9 +418,12 @@ struct Solve {
     return MST_OK;
   }
 
+  // flag_clear: the jump flag is known to be zero (zero_round_state began the
+  // round and nothing since touched it)
   mst_status jump_until_stars(const uint32_t *act_list, const u64 *count_dev, uint64_t count_host, uint64_t max_count,
-                              int reset_best, const uint32_t *groot = nullptr, uint32_t *gbits = nullptr) {
-    TRY(jump_launch(act_list, count_dev, count_host, max_count, reset_best, groot, gbits));
+                              int reset_best, const uint32_t *groot = nullptr, uint32_t *gbits = nullptr,
+                              bool flag_clear = false) {
+    TRY(jump_launch(act_list, count_dev, count_host, max_count, reset_best, groot, gbits, flag_clear));
     TRY(readback(c, s));
     return jump_finish(act_list, count_dev, count_host, max_count, groot, gbits);
   }
@@ -446,7 +461,7 @@ struct Solve {
         PROF(MST_K_MIN_EDGES, 12.0 * (double)mE, -1, 0.0, -1, 0.0,
              launch_min_edges(E, mE, n, validate ? 1 : 0, kl, best, &c->ds->err, c->sms, s));
     }
-    TRY(zero_counters(c, s));
+    TRY(zero_round_state(c, s));
     HookArgs ha{};
     ha.cand = nullptr;
     ha.ncand = n;
@@ -461,7 +476,7 @@ struct Solve {
     ha.counter = &c->ds->count[CNT_ACTIVE];
     ha.err = &c->ds->err;
     PROF(MST_K_HOOK, 8.0 * (double)n, CNT_ACTIVE, 8.0, -1, 0.0, launch_hook(ha, n, s));
-    TRY(jump_until_stars(act[0], &c->ds->count[CNT_ACTIVE], 0, n, 1));
+    TRY(jump_until_stars(act[0], &c->ds->count[CNT_ACTIVE], 0, n, 1, nullptr, nullptr, true));
     uint64_t n_act = c->hs->count[CNT_ACTIVE];
     ++rounds;
 
@@ -488,7 +503,7 @@ struct Solve {
       }
       ListBuf &out = (cur.u == X.out.u) ? Y : X;
       if (out.cap < cur_m) TRY(out.alloc(c, cur_m, s));
-      TRY(zero_counters(c, s));
+      TRY(zero_round_state(c, s));
       CompactArgs ca{};
       ca.in = cur;
       ca.m = cur_m;
@@ -565,7 +580,7 @@ struct Solve {
       hb.counter = &c->ds->count[CNT_ACTIVE];
       hb.err = &c->ds->err;
       PROF(MST_K_HOOK, 12.0 * (double)n_act, CNT_ACTIVE, 8.0, -1, 0.0, launch_hook(hb, n_act, s));
-      TRY(jump_until_stars(act[1 - a], &c->ds->count[CNT_ACTIVE], 0, n_act, 1));
+      TRY(jump_until_stars(act[1 - a], &c->ds->count[CNT_ACTIVE], 0, n_act, 1, nullptr, nullptr, true));
       table_b.release();
       a = 1 - a;
       n_act = c->hs->count[CNT_ACTIVE];
