@@ -735,9 +735,14 @@ constexpr uint32_t FIND_STEPS = 1u << 12;  // bound on one parent-chain walk
 // edge's id is set once in the bitmap (by the vertex that is not the root).
 // The active vertices (best != INF) are compacted into active_out.
 //
-// The ends of e are found through the input arrays: src[e] and dst[e] are
-// input vertices, and their current labels are reached by following parent
-// pointers until the first vertex that is active this round (best != INF).
+// IOTA: the candidates are 0..ncand-1 (a call's first round), else the list
+// cand.  PACKED: the key holds the other end (see KeyLayout), so no walk is
+// needed and this instantiation keeps few registers (6 blocks per SM).
+//
+// Otherwise the ends of e are found through the ends recorded by id (or the
+// input arrays): src[e] and dst[e] are vertices whose current labels are
+// reached by following parent pointers until the first vertex that is active
+// this round (best != INF).
 // Every vertex passed on the way was merged in an earlier round and has no edge
 // now, and best[] is not written during the hook, so the hooks of other threads
 // (which only change parent[] of active vertices) cannot redirect a walk.  All
