@@ -111,7 +111,13 @@ struct HookArgs {
   uint32_t *active_out;    // active vertices (best != INF), unspecified order
   u64 *counter;            // number written to active_out; zero before the launch
   uint32_t *err;
+  u64 *wsum;               // if set: the weights of the chosen edges are added into these
+                           //   WSUM_SLOTS counters (one add per warp, spread over the slots)
 };
+
+// Counters the kernels that choose MSF edges add the chosen weights into, so
+// that the forest's total needs no gather of w at the end.
+constexpr int WSUM_SLOTS = 256;
 
 // ---- launchers (kernels.cu); all asynchronous on `s` ----
 int max_scan_tiles(uint64_t count);
@@ -139,8 +145,11 @@ void launch_pivot(EdgeList in, uint64_t m, const u64 *m_dev, u64 state, uint32_t
 size_t pivot_scratch_bytes();
 bool launch_pivot_coop(EdgeList in, uint64_t m, u64 state, uint32_t sample, u64 *keys, void *scratch,
                        u64 *pivot_out, cudaStream_t s);
+// w == nullptr: ids and count only (total_weight untouched).
 void launch_finalize(const uint32_t *bits, uint64_t m, const uint32_t *w, uint32_t *out_ids, uint32_t *out_count,
                      u64 *total_weight, ScanState st, cudaStream_t s);
+// *total = the sum of the WSUM_SLOTS counters.
+void launch_wsum_total(const u64 *wsum, u64 *total, cudaStream_t s);
 // The giant component's root: the most frequent root among the labels of
 // sampled edge ends (P is walked to the roots); launch_giant_bits also marks
 // its vertices (bit v set iff P[v] is that root; P fully contracted).
@@ -158,7 +167,7 @@ void launch_tile_scatter(EdgeList in, uint64_t m, uint32_t n, uint32_t B, const 
 bool launch_tile_contract(uint32_t n, uint32_t B, uint64_t nlocal, const u64 *cutmin, const u64 *offsets,
                           const uint32_t *b_ends, const uint32_t *b_w, const uint32_t *b_id, uint32_t *parent,
                           uint32_t *bits, EdgeOut rest, u64 *rest_fill, uint32_t *err, cudaStream_t s,
-                          int filter_heavy);
+                          int filter_heavy, u64 *wsum);
 void launch_tile_sample(EdgeList in, uint64_t m, uint32_t n, uint32_t B, u64 state, uint32_t samples,
                         uint32_t *local_count, cudaStream_t s);
 // Stable LSD radix sort of (u64 key, u32 value) pairs over the low `bits` bits;
@@ -210,7 +219,7 @@ struct BaseScratch {
 };
 // False (nothing launched) when the call does not fit the base case.
 bool launch_base_case(const uint32_t *act, uint32_t n_act, EdgeList cur, uint64_t m, uint32_t *parent, uint32_t *bits,
-                      const BaseScratch &b, uint32_t *err, cudaStream_t s, int filter_heavy);
+                      const BaseScratch &b, uint32_t *err, cudaStream_t s, int filter_heavy, u64 *wsum);
 void launch_iota(uint32_t *p, uint64_t n, int sms, cudaStream_t s);
 
 }  // namespace mstgpu

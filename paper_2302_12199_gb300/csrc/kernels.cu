@@ -725,6 +725,17 @@ __global__ void __launch_bounds__(BLOCK) min_edges_kernel(EdgeList in, uint64_t 
   }
 }
 
+// Adds this thread's sum of chosen weights into a spread counter: one atomic
+// per warp (all 32 lanes call together).
+__device__ __forceinline__ void wsum_add(u64 *wsum, u64 v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if (wsum && (threadIdx.x & 31) == 0 && v)
+    atomicAdd(reinterpret_cast<unsigned long long *>(wsum) +
+                  ((blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) & (WSUM_SLOTS - 1)),
+              (unsigned long long)v);
+}
+
 // -------------------------------------------------------------------- hook
 
 constexpr uint32_t FIND_STEPS = 1u << 12;  // bound on one parent-chain walk
@@ -757,6 +768,8 @@ __global__ void __launch_bounds__(BLOCK, PACKED ? 6 : 3) hook_kernel(HookArgs a)
   __shared__ uint32_t s_base[1];
 
   const uint64_t nc = a.ncand_dev ? *a.ncand_dev : a.ncand;
+  const int wshift = PACKED ? a.kl.idbits + a.kl.vbits : 32;  // the weight's place in a key
+  u64 wacc = 0;  // weights of the edges this thread chose
   for (uint64_t tile = blockIdx.x; tile * TILE < nc; tile += gridDim.x) {  // uniform per block
   const uint64_t tb = tile * TILE;
   uint32_t c[ITEMS];
@@ -782,7 +795,10 @@ __global__ void __launch_bounds__(BLOCK, PACKED ? 6 : 3) hook_kernel(HookArgs a)
       const uint32_t other = (uint32_t)(kk[k] & ((1ULL << a.kl.vbits) - 1));
       const bool root = same_edge(a.kl, a.best[other], kk[k]) && c[k] < other;
       a.parent[c[k]] = root ? c[k] : other;
-      if (!root) atomicOr(a.chosen_bits + (e >> 5), 1u << (e & 31));
+      if (!root) {
+        atomicOr(a.chosen_bits + (e >> 5), 1u << (e & 31));
+        wacc += kk[k] >> wshift;
+      }
     }
   } else {
   uint32_t start[2 * ITEMS], cur[2 * ITEMS];
@@ -829,7 +845,10 @@ __global__ void __launch_bounds__(BLOCK, PACKED ? 6 : 3) hook_kernel(HookArgs a)
     const uint32_t other = cur[2 * k] ^ cur[2 * k + 1] ^ c[k];
     const bool root = a.best[other] == kk[k] && c[k] < other;
     a.parent[c[k]] = root ? c[k] : other;
-    if (!root) atomicOr(a.chosen_bits + (e >> 5), 1u << (e & 31));
+    if (!root) {
+      atomicOr(a.chosen_bits + (e >> 5), 1u << (e & 31));
+      wacc += kk[k] >> wshift;
+    }
   }
   // shortcut the walked start vertices to their labels
 #pragma unroll
@@ -849,6 +868,7 @@ __global__ void __launch_bounds__(BLOCK, PACKED ? 6 : 3) hook_kernel(HookArgs a)
   for (uint32_t i = threadIdx.x; i < total; i += BLOCK) a.active_out[obase + i] = s_c[i];
   __syncthreads();  // s_c, s_warp and s_base are reused by the block's next tile
   }
+  wsum_add(a.wsum, wacc);
 }
 
 // --------------------------------------------------------- pointer jumping
@@ -1493,12 +1513,12 @@ __device__ __forceinline__ uint32_t tc_exclusive_scan(uint32_t x, uint32_t &tota
   return s_warp[wid] + incl - x;
 }
 
-__global__ void __launch_bounds__(TC_THREADS) tile_contract_kernel(uint32_t n, uint32_t B, const u64 *cutmin,
+__global__ void __launch_bounds__(TC_THREADS, 2) tile_contract_kernel(uint32_t n, uint32_t B, const u64 *cutmin,
                                                                     const u64 *offsets, const uint32_t *b_ends,
                                                                     const uint32_t *b_w, const uint32_t *b_id,
                                                                     uint32_t edge_cap, uint32_t *parent,
                                                                     uint32_t *bits, EdgeOut rest, u64 *rest_fill,
-                                                                    uint32_t *err, int filter_heavy) {
+                                                                    uint32_t *err, int filter_heavy, u64 *wsum) {
   extern __shared__ __align__(128) unsigned char smem_dyn[];
   u64 *best = reinterpret_cast<u64 *>(smem_dyn);  // [B]
   u64 *comp = best + B;                           // [B] component cut minimum (valid at roots)
@@ -1515,6 +1535,8 @@ __global__ void __launch_bounds__(TC_THREADS) tile_contract_kernel(uint32_t n, u
   const uint32_t nv = (uint32_t)min((uint64_t)B, (uint64_t)n - vbase);
   const u64 e0 = offsets[t];
   const uint32_t ne0 = (uint32_t)(offsets[t + 1] - e0);
+  __shared__ unsigned long long s_wsum;  // weights of the edges this block's components chose
+  if (threadIdx.x == 0) s_wsum = 0;
   // In shared memory the edges hold the labels of their ends' components and
   // are compacted after every round (edges inside a component are dropped);
   // from global memory they are read as input ends and mapped through lab[].
@@ -1592,6 +1614,7 @@ __global__ void __launch_bounds__(TC_THREADS) tile_contract_kernel(uint32_t n, u
           hook[c] = o;
           const uint32_t id = (uint32_t)best[c];
           atomicOr(bits + (id >> 5), 1u << (id & 31));
+          atomicAdd(&s_wsum, (unsigned long long)(best[c] >> 32));
           s_any = 1;
         }
       }
@@ -1659,6 +1682,9 @@ __global__ void __launch_bounds__(TC_THREADS) tile_contract_kernel(uint32_t n, u
     }
     __syncthreads();
   }
+  // every hook step ends in a barrier, so the block's sum of chosen weights is complete
+  if (threadIdx.x == 0 && wsum && s_wsum)
+    atomicAdd(reinterpret_cast<unsigned long long *>(wsum) + (t & (WSUM_SLOTS - 1)), s_wsum);
   for (uint32_t x = threadIdx.x; x < nv; x += TC_THREADS) parent[vbase + x] = (uint32_t)(vbase + lab[x]);
   // The local edges left between different components of the tile join the
   // cut edges in the contracted graph, with their ends at the tile roots.
@@ -2132,14 +2158,14 @@ __global__ void base_unmap_kernel(const uint32_t *act, uint32_t n_act, const uin
 }
 
 bool launch_base_case(const uint32_t *act, uint32_t n_act, EdgeList cur, uint64_t m, uint32_t *parent, uint32_t *bits,
-                      const BaseScratch &b, uint32_t *err, cudaStream_t s, int filter_heavy) {
+                      const BaseScratch &b, uint32_t *err, cudaStream_t s, int filter_heavy, u64 *wsum) {
   if (n_act == 0 || n_act > BASE_MAX_N || m > BASE_MAX_M || !cur.id) return false;
   base_map_kernel<<<(n_act + 255) / 256, 256, 0, s>>>(act, n_act, b.loc, b.offsets, m);
   if (m) base_pack_kernel<<<(unsigned)((m + 255) / 256), 256, 0, s>>>(cur.u, cur.v, m, parent, b.loc, b.ends);
   cudaMemsetAsync(b.cutmin, 0xff, (size_t)n_act * 8, s);
   cudaMemsetAsync(b.rest_fill, 0, sizeof(u64), s);
   if (!launch_tile_contract(n_act, n_act, m, b.cutmin, b.offsets, b.ends, cur.w, cur.id, b.plocal, bits, b.rest,
-                            b.rest_fill, err, s, filter_heavy))
+                            b.rest_fill, err, s, filter_heavy, wsum))
     return false;
   base_unmap_kernel<<<(n_act + 255) / 256, 256, 0, s>>>(act, n_act, b.plocal, parent);
   return true;
@@ -2293,7 +2319,7 @@ __global__ void __launch_bounds__(BLOCK) finalize_kernel(const uint32_t *bits, u
         word &= word - 1;
         const uint32_t id = (uint32_t)((tb + item_off(k)) * 32 + b);
         out_ids[pos++] = id;
-        wsum += __ldg(w + id);
+        if (w) wsum += __ldg(w + id);
       }
     }
   }
@@ -2304,8 +2330,23 @@ __global__ void __launch_bounds__(BLOCK) finalize_kernel(const uint32_t *bits, u
   if (threadIdx.x == 0) {
     u64 s = 0;
     for (int i = 0; i < BLOCK / 32; ++i) s += s_sum[i];
-    if (s) atomicAdd(total_weight, s);
+    if (s && w) atomicAdd(total_weight, s);
     if (t.tile == t.ntiles - 1) *out_count = (uint32_t)(obase + total);
+  }
+}
+
+// *total = the sum of the WSUM_SLOTS counters (one block of WSUM_SLOTS threads).
+__global__ void wsum_total_kernel(const u64 *wsum, u64 *total) {
+  __shared__ u64 s_part[WSUM_SLOTS / 32];
+  u64 v = wsum[threadIdx.x];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if ((threadIdx.x & 31) == 0) s_part[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    u64 t = 0;
+    for (int i = 0; i < WSUM_SLOTS / 32; ++i) t += s_part[i];
+    *total = t;
   }
 }
 
@@ -2439,6 +2480,10 @@ bool launch_pivot_coop(EdgeList in, uint64_t m, u64 state, uint32_t sample, u64 
   return false;
 }
 
+void launch_wsum_total(const u64 *wsum, u64 *total, cudaStream_t s) {
+  wsum_total_kernel<<<1, WSUM_SLOTS, 0, s>>>(wsum, total);
+}
+
 void launch_finalize(const uint32_t *bits, uint64_t m, const uint32_t *w, uint32_t *out_ids, uint32_t *out_count,
                      u64 *total_weight, ScanState st, cudaStream_t s) {
   const uint64_t nwords = (m + 31) / 32;
@@ -2480,7 +2525,7 @@ void launch_tile_scatter(EdgeList in, uint64_t m, uint32_t n, uint32_t B, const 
 bool launch_tile_contract(uint32_t n, uint32_t B, uint64_t nlocal, const u64 *cutmin, const u64 *offsets,
                           const uint32_t *b_ends, const uint32_t *b_w, const uint32_t *b_id, uint32_t *parent,
                           uint32_t *bits, EdgeOut rest, u64 *rest_fill, uint32_t *err, cudaStream_t s,
-                          int filter_heavy) {
+                          int filter_heavy, u64 *wsum) {
   static int smem_full = 0;
   if (!smem_full) {
     int dev = 0, optin = 0;
@@ -2501,7 +2546,7 @@ bool launch_tile_contract(uint32_t n, uint32_t B, uint64_t nlocal, const u64 *cu
   cap = min(cap, ((size_t)smem_full - vbytes) / 12);
   const size_t bytes = vbytes + (size_t)cap * 12;
   tile_contract_kernel<<<ntiles, TC_THREADS, bytes, s>>>(n, B, cutmin, offsets, b_ends, b_w, b_id, (uint32_t)cap,
-                                                         parent, bits, rest, rest_fill, err, filter_heavy);
+                                                         parent, bits, rest, rest_fill, err, filter_heavy, wsum);
   return true;
 }
 

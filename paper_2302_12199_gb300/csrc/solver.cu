@@ -35,6 +35,7 @@ struct mst_ctx {
   u64 *sample_buf = nullptr;
   uint32_t sample_cap = 0;
   void *pivot_scratch = nullptr;  // histograms of the multi-block pivot selection
+  u64 *wsum = nullptr;            // WSUM_SLOTS counters of the chosen weights (zeroed per solve)
   uint64_t pivot_counter = 0;
   // per-kernel-class event timing (mst_profile_enable)
   struct ProfRec {
@@ -367,6 +368,7 @@ struct Solve {
     }
     TRY(ensure_status(c, (uint64_t)n > m ? (uint64_t)n : m, s));
     TRY(clear_device_flags(c, s));
+    CK(cudaMemsetAsync(c->wsum, 0, WSUM_SLOTS * sizeof(u64), s));
     return MST_OK;
   }
 
@@ -475,6 +477,7 @@ struct Solve {
     ha.active_out = act[0];
     ha.counter = &c->ds->count[CNT_ACTIVE];
     ha.err = &c->ds->err;
+    ha.wsum = c->wsum;
     PROF(MST_K_HOOK, 8.0 * (double)n, CNT_ACTIVE, 8.0, -1, 0.0, launch_hook(ha, n, s));
     TRY(jump_until_stars(act[0], &c->ds->count[CNT_ACTIVE], 0, n, 1, nullptr, nullptr, true));
     uint64_t n_act = c->hs->count[CNT_ACTIVE];
@@ -579,6 +582,7 @@ struct Solve {
       hb.active_out = act[1 - a];
       hb.counter = &c->ds->count[CNT_ACTIVE];
       hb.err = &c->ds->err;
+      hb.wsum = c->wsum;
       PROF(MST_K_HOOK, 12.0 * (double)n_act, CNT_ACTIVE, 8.0, -1, 0.0, launch_hook(hb, n_act, s));
       TRY(jump_until_stars(act[1 - a], &c->ds->count[CNT_ACTIVE], 0, n_act, 1, nullptr, nullptr, true));
       table_b.release();
@@ -728,6 +732,7 @@ struct Solve {
       hb.active_out = A[out];
       hb.counter = &g->ca[out];
       hb.err = &c->ds->err;
+      hb.wsum = c->wsum;
       launch_hook(hb, nmax, cs);
       // pointer jumping: jl launches of up to 256 steps each; only the last
       // launch reports a vertex short of its root
@@ -780,7 +785,8 @@ struct Solve {
     b.rest_fill = (u64 *)p;
     bool launched = false;
     PROF(MST_K_BASE, 16.0 * (double)cur_m + 28.0 * (double)n_act, -1, 0.0, -1, 0.0,
-         launched = launch_base_case(act_list, n_act, cur, cur_m, parent, bits, b, &c->ds->err, s, c->cfg.tile_filter));
+         launched = launch_base_case(act_list, n_act, cur, cur_m, parent, bits, b, &c->ds->err, s, c->cfg.tile_filter,
+                                     c->wsum));
     if (!launched) return MST_ERR_INTERNAL;
     return readback(c, s);
   }
@@ -839,7 +845,8 @@ struct Solve {
     PROF(MST_K_TILE, 12.0 * (double)nlocal + 12.0 * (double)n, -1, 0.0, -1, 0.0,
          launched = launch_tile_contract(n, B, nlocal, cut_b.as<u64>(), off_b.as<u64>(), (uint32_t *)bb,
                                          (uint32_t *)(bb + stride), (uint32_t *)(bb + 2 * stride), parent, bits,
-                                         cutl.out, &c->ds->count[CNT_CUT], &c->ds->err, s, c->cfg.tile_filter));
+                                         cutl.out, &c->ds->count[CNT_CUT], &c->ds->err, s, c->cfg.tile_filter,
+                                         c->wsum));
     if (!launched) return MST_ERR_INVALID_ARG;  // tile too large for shared memory
     // the cut edges, relabelled to the tile roots, are the contracted graph
     TRY(out.alloc(c, mcut, s));
@@ -1034,10 +1041,12 @@ struct Solve {
     return filter(H.list(), mH, false, depth + 1, relaxed, cf.cur_u != nullptr);
   }
 
-  mst_status finalize(const uint32_t *w, uint32_t *out_ids, uint32_t *out_count, u64 *total_weight) {
-    CK(cudaMemsetAsync(total_weight, 0, sizeof(u64), s));
+  // The ids come from the chosen-edge bitmap; the total from the counters the
+  // hooking kernels added each chosen edge's weight into (no gather of w).
+  mst_status finalize(uint32_t *out_ids, uint32_t *out_count, u64 *total_weight) {
     PROF(MST_K_FINALIZE, (double)((m + 31) / 32 * 4), CNT_AUX, 4.0, -1, 0.0,
-         launch_finalize(bits, m, w, out_ids, out_count, total_weight, next_scan(c, CNT_AUX), s));
+         launch_finalize(bits, m, nullptr, out_ids, out_count, total_weight, next_scan(c, CNT_AUX), s);
+         launch_wsum_total(c->wsum, total_weight, s));
     return readback(c, s);
   }
 };
@@ -1083,7 +1092,7 @@ mst_status solve_device(mst_ctx *c, uint32_t n, uint64_t m, const uint32_t *src,
   } else {
     TRY(S.boruvka(in, m, true));
   }
-  return S.finalize(w, out_ids, out_count, total_weight);
+  return S.finalize(out_ids, out_count, total_weight);
 }
 
 mst_status validate_cfg(const mst_config *cfg) {
@@ -1309,6 +1318,7 @@ mst_status mst_create(mst_handle *out, const mst_config *cfg) {
   ok = ok && cudaMallocHost(&c->hs, sizeof(DevState)) == cudaSuccess;
   ok = ok && ensure_sample(c) == MST_OK;
   ok = ok && cudaMalloc(&c->pivot_scratch, pivot_scratch_bytes()) == cudaSuccess;
+  ok = ok && cudaMalloc(&c->wsum, WSUM_SLOTS * sizeof(u64)) == cudaSuccess;
   ok = ok && cudaDeviceSynchronize() == cudaSuccess;
   if (!ok) {
     cudaGetLastError();
@@ -1329,6 +1339,7 @@ void mst_destroy(mst_handle h) {
     if (h->status) cudaFree(h->status);
     if (h->sample_buf) cudaFree(h->sample_buf);
     if (h->pivot_scratch) cudaFree(h->pivot_scratch);
+    if (h->wsum) cudaFree(h->wsum);
     if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
     if (h->copy_stream) cudaStreamDestroy(h->copy_stream);
     for (int k = 0; k < 2; ++k) {
@@ -1647,6 +1658,7 @@ mst_status mst_step_contract(mst_handle h, uint32_t n, uint64_t m, const uint32_
   ha.active_out = S.act[0];
   ha.counter = &h->ds->count[CNT_ACTIVE];
   ha.err = &h->ds->err;
+  ha.wsum = h->wsum;
   launch_hook(ha, n, s);
   return record(h, S.jump_until_stars(S.act[0], &h->ds->count[CNT_ACTIVE], 0, n, 1));
 }
