@@ -256,6 +256,9 @@ def reference_batched(args):
     return 0
 
 
+REF_BUDGET_S = 100.0  # wall time of a --impl reference run (steps + warm-up)
+
+
 def reference_main(args, rank: int):
     if rank != 0:
         return 0
@@ -265,7 +268,14 @@ def reference_main(args, rank: int):
     desc, gen, cfg = WORKLOADS[args.workload]
     g = gen(W)
     sample = min(g.m, args.cpu_sample_edges)
-    for _ in range(args.warmup):
+    # the first warm-up step sizes the sample so that the whole run (steps and
+    # warm-up) takes about REF_BUDGET_S; the rate is per edge, so a smaller
+    # sample of the same list only shortens the run
+    _, dt0 = cpu_oracle_rate(g, sample)
+    per_step = REF_BUDGET_S / max(1, args.steps + args.warmup - 1)
+    if dt0 > per_step:
+        sample = max(min(sample, 1 << 20), int(sample * per_step / dt0))
+    for _ in range(max(0, args.warmup - 1)):
         cpu_oracle_rate(g, sample)
     times = []
     for _ in range(args.steps):
