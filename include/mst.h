@@ -46,7 +46,7 @@ typedef enum {
   MST_ERR_OOM = 4,          /* scratch allocation failed */
   MST_ERR_CUDA = 5,         /* a CUDA runtime call failed */
   MST_ERR_INTERNAL = 6,     /* a bounded device loop ran out of iterations */
-  MST_ERR_NOT_SUPPORTED = 7 /* option not available in this build */
+  MST_ERR_NOT_SUPPORTED = 7 /* option not available in this library */
 } mst_status;
 
 enum { MST_VARIANT_BORUVKA = 0, MST_VARIANT_FILTER = 1, MST_VARIANT_AUTO = 2 };
