@@ -348,6 +348,53 @@ def test_partition_and_filter_cover_the_list():
     assert np.intersect1d(lid, hid).size == 0
 
 
+@pytest.mark.parametrize("seed", [11, 12, 13, 14])
+def test_filter_keeps_exactly_the_heavy_edges_between_light_components(seed):
+    """Filter (Alg. 2): with P holding the components of the light part, the
+    survivors are exactly the heavy edges whose ends lie in different
+    components.  The components come from Kruskal's forest of the light edges
+    and a plain union-find here, not from the step oracles; the Borůvka
+    rounds' P must give the same partition."""
+    rng = np.random.default_rng(seed)
+    n = 800  # sparse enough that the light part falls into ~150 components
+    u, v, w = rand_multigraph(rng, n, 1500, wmax=20)  # many equal weights
+    ids = np.arange(u.size, dtype=np.uint32)
+    pv = S.pivot(w, ids, seed, 1024)
+    light = S.keys(w, ids) <= np.uint64(pv)
+    lid = ids[light]
+    forest = oracle.kruskal(n, u[light], v[light], w[light])[0]  # positions in the light sublist
+    comp = list(range(n))
+
+    def find(x):
+        while comp[x] != x:
+            comp[x] = comp[comp[x]]
+            x = comp[x]
+        return x
+
+    for j in forest:
+        e = int(lid[j])
+        a, b = find(int(u[e])), find(int(v[e]))
+        if a != b:
+            comp[a] = b
+    rep_of = np.array([find(x) for x in range(n)], dtype=np.uint32)
+    expect = sorted(int(e) for e in ids[~light] if rep_of[u[e]] != rep_of[v[e]])
+    assert 0 < len(expect) < int(np.sum(~light))  # some heavy edges survive, some are filtered
+    hu, hv, hw, hid = S.filter_heavy(u, v, w, ids, pv, rep_of)
+    assert sorted(hid.tolist()) == expect
+    assert np.all(hu == rep_of[u[hid]]) and np.all(hv == rep_of[v[hid]])
+    # the representative array that the Borůvka rounds build gives the same components
+    P = np.arange(n, dtype=np.uint32)
+    uu, vv, ww_, ii = S.partition_light(u, v, w, ids, pv)
+    while uu.size:
+        r, _, (uu, vv, ww_, ii) = S.boruvka_round(n, uu, vv, ww_, ii)
+        moved = r != np.arange(n, dtype=np.uint32)
+        P[moved] = r[moved]
+    roots = S.roots(P)
+    for x in range(n):
+        for y in (0, 1, 2, x // 2, (x * 7) % n):
+            assert (roots[x] == roots[y]) == (rep_of[x] == rep_of[y])
+
+
 def test_filter_survivors_are_linear_in_n():
     # Theorem 1 / KKT sampling: heavy edges surviving the filter by the light
     # MSF number about n/p - n for a split fraction p = 1/2, i.e. O(n).
