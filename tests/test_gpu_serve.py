@@ -51,6 +51,30 @@ def test_batched_mix_matches_oracle(dev, cfg):
         s.close()
 
 
+def test_full_size_batch_matches_oracle(dev):
+    """The batched benchmark's batch at its full size (4096 graphs, n
+    log-uniform in [2^8, 2^16], about 335 M edges), under the configurations
+    its autotuner chooses between for the solve: every graph's forest and
+    total equal its own Kruskal forest."""
+    b = W.mix(4096, W.DEFAULT_SEED, log_hi=16)
+    exp = oracle_answers(b)
+    src, dst, w = to_dev(b.src, dev), to_dev(b.dst, dev), to_dev(b.w, dev)
+    for cfg in (dict(variant="filter"), dict(variant="boruvka")):
+        s = Solver(0, **cfg)
+        try:
+            ids, moff, tot = s.solve_batched(b.n, b.edge_off, src, dst, w)
+            ids = ids.cpu().numpy().view(np.uint32)
+            moff = moff.cpu().numpy().astype(np.int64)
+            tot = tot.cpu().numpy().view(np.uint64)
+            bad = [g for g, (kid, ktot) in enumerate(exp)
+                   if not (np.array_equal(ids[moff[g]:moff[g + 1]], kid) and int(tot[g]) == ktot)]
+            assert not bad, (cfg, bad[:5])
+        finally:
+            s.close()
+    del src, dst, w
+    torch.cuda.empty_cache()
+
+
 def test_batched_with_empty_and_tiny_graphs(dev):
     n = np.array([1, 5, 3, 1, 4], dtype=np.uint32)
     src = np.array([0, 1, 2, 3, 0, 1, 2, 0, 0, 1], dtype=np.uint32)
