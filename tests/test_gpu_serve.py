@@ -75,6 +75,34 @@ def test_full_size_batch_matches_oracle(dev):
     torch.cuda.empty_cache()
 
 
+def test_full_size_served_pool_matches_oracle(dev):
+    """The served benchmark's request pool at its full size (256 graphs, n
+    log-uniform in [2^8, 2^20]): each graph solved alone through the server
+    equals its Kruskal forest, and a stream of requests drawn from the pool
+    (several batches in flight on three slots) returns exactly those answers."""
+    from paper_2302_12199_gb300.serve import PoolGraph, Response, Server, poisson_arrivals
+    b = W.mix(256, W.DEFAULT_SEED + 5, log_lo=8, log_hi=20)
+    exp = oracle_answers(b)
+    pool = []
+    for g in range(b.num_graphs):
+        gr = b.graph(g)
+        pool.append(PoolGraph(gr.n, to_dev(gr.src, dev), to_dev(gr.dst, dev), to_dev(gr.w, dev)))
+    expected = {g: Response(kid, ktot) for g, (kid, ktot) in enumerate(exp)}
+    server = Server(0, slots=3, budget_bytes=6 << 30, stall_seconds=60.0)
+    try:
+        for g in range(len(pool)):
+            r = server.solve_alone(pool[g])
+            assert np.array_equal(r.ids, expected[g].ids) and r.total == expected[g].total, g
+        arr = poisson_arrivals(4096.0, 0.25, seed=11)
+        picks = np.random.default_rng(12).integers(0, len(pool), arr.size)
+        st = server.run(pool, picks, arr, expected=expected, rate=4096.0, seconds=0.25)
+        assert st.requests == arr.size and st.mismatches == 0 and st.batches >= 2
+    finally:
+        server.close()
+        del pool
+        torch.cuda.empty_cache()
+
+
 def test_batched_with_empty_and_tiny_graphs(dev):
     n = np.array([1, 5, 3, 1, 4], dtype=np.uint32)
     src = np.array([0, 1, 2, 3, 0, 1, 2, 0, 0, 1], dtype=np.uint32)
