@@ -282,6 +282,42 @@ def test_min_edges_pick_forest_edges_and_rounds_halve():
     assert np.all(parent[r] == r)
 
 
+def test_hook_two_cycles_and_chains():
+    """Hooking (Section 2.3): both ends of a mutually chosen edge form a 2-cycle
+    whose smaller vertex stays root; every other active vertex points to the
+    far end of its own choice, and each chosen edge is reported once."""
+    def run(n, edges):
+        u = np.array([e[0] for e in edges], np.uint32)
+        v = np.array([e[1] for e in edges], np.uint32)
+        w = np.array([e[2] for e in edges], np.uint32)
+        ids = np.arange(len(edges), dtype=np.uint32)
+        best = S.min_edges(n, u, v, w, ids)
+        return S.hook(n, u, v, w, ids, best)
+
+    parent, chosen = run(2, [(1, 0, 7)])  # one edge: a 2-cycle, vertex 0 is the root
+    assert parent.tolist() == [0, 0] and chosen.tolist() == [0]
+    # path 0-1 (w 1), 1-2 (w 2): 0 and 1 both choose edge 0 (2-cycle, root 0); 2 chooses edge 1
+    parent, chosen = run(3, [(0, 1, 1), (1, 2, 2)])
+    assert parent.tolist() == [0, 0, 1] and chosen.tolist() == [0, 1]
+    # 2-cycle between 1 and 2 (edge 1, the lightest); 0 hangs off 1; 3 isolated
+    parent, chosen = run(4, [(0, 1, 5), (2, 1, 3), (0, 2, 9)])
+    assert parent.tolist() == [1, 1, 1, 3] and chosen.tolist() == [0, 1]
+    # random multigraphs: one chosen edge per non-root active vertex, roots only in 2-cycles
+    rng = np.random.default_rng(5)
+    for _ in range(20):
+        n = int(rng.integers(2, 60))
+        src, dst, w = rand_multigraph(rng, n, int(rng.integers(1, 200)), wmax=4)
+        ids = np.arange(src.size, dtype=np.uint32)
+        best = S.min_edges(n, src, dst, w, ids)
+        parent, chosen = S.hook(n, src, dst, w, ids, best)
+        active = np.nonzero(best != S.INF)[0]
+        nonroot = active[parent[active] != active]
+        assert chosen.size == nonroot.size
+        for c in active[parent[active] == active]:  # an active root has a partner choosing the same edge
+            partners = np.nonzero((best == best[c]) & (np.arange(n) != c))[0]
+            assert partners.size == 1 and parent[partners[0]] == c and c < partners[0]
+
+
 @pytest.mark.parametrize("dd", [True, False])
 def test_boruvka_composition_equals_kruskal(dd):
     for g in (W.gnm(2000, 16000, 21), W.rmat(11, 20000, 22), W.rgg(2, 3000, 8.0, 23), W.gnm(4000, 1000, 24)):
