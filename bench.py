@@ -70,7 +70,6 @@ TRAFFIC = {
     "kernel": "compact_tma_kernel<CM_FILTER>",
     "dram_per_algorithmic_byte": 1.354,
     "source_sha256": "6f730b384a84122742ec9b298f1ff24e57921fcab8966ae0c4d2b6414b44972b",
-    "summary": "profiles/filter_compaction_rmat.md",
 }
 TRAFFIC_SOURCE = ("paper_2302_12199_gb300/csrc/kernels.cu",
                   "__device__ __forceinline__ uint32_t keep_flags",
@@ -298,6 +297,56 @@ def reference_main(args, rank: int):
 
 # --------------------------------------------------------------------- gpu
 
+def e2e_breakdown(torch, solver, dev, stream, n, m, pin, d_in, out, ids_h, cnt, reps=3):
+    """Parts of one end-to-end step, each timed with CUDA events (medians of
+    `reps`): the input copy from pinned host memory alone, the solve alone,
+    the solve while the next step's input copy runs on another stream (what
+    the overlapped entry point does), and the read-back of the forest."""
+    side = torch.cuda.Stream(dev)
+    bufs = [torch.empty(m, dtype=torch.int32, device=dev) for _ in range(3)]
+
+    def copy_in():
+        with torch.cuda.stream(side):
+            for d, h in zip(bufs, pin):
+                d.copy_(h, non_blocking=True)
+
+    def ev_pair():
+        return torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    h2d, solo, during, d2h = [], [], [], []
+    for _ in range(reps):
+        torch.cuda.synchronize(dev)
+        a, b = ev_pair()
+        a.record(side)
+        copy_in()
+        b.record(side)
+        torch.cuda.synchronize(dev)
+        h2d.append(a.elapsed_time(b))
+        a, b = ev_pair()
+        a.record(stream)
+        solver.solve(n, *d_in, out=out)
+        b.record(stream)
+        torch.cuda.synchronize(dev)
+        solo.append(a.elapsed_time(b))
+        copy_in()
+        a, b = ev_pair()
+        a.record(stream)
+        solver.solve(n, *d_in, out=out)
+        b.record(stream)
+        torch.cuda.synchronize(dev)
+        during.append(a.elapsed_time(b))
+        a, b = ev_pair()
+        a.record(stream)
+        ids_h[:cnt].copy_(out.ids[:cnt], non_blocking=True)
+        b.record(stream)
+        torch.cuda.synchronize(dev)
+        d2h.append(a.elapsed_time(b))
+    del bufs
+    med = statistics.median
+    return {"h2d": med(h2d), "solve": med(solo), "solve_during_h2d": med(during), "d2h": med(d2h),
+            "h2d_GBps": 12 * m / med(h2d) / 1e6}
+
+
 def gpu_main(args, rank: int, world: int, local_rank: int):
     import numpy as np
     import torch
@@ -390,7 +439,7 @@ def gpu_main(args, rank: int, world: int, local_rank: int):
         dist.barrier()
     clocks = sampler.stop()
     ms = e0.elapsed_time(e1)
-    stats = solver.profile_stats()
+    stats = solver.profile_stats(with_min=True)
     ids, total = out.to_host()
     if not (np.array_equal(ids, ref_ids) and total == ref_total):
         raise RuntimeError("timed solves returned a different forest than the warm-up solve")
@@ -432,13 +481,14 @@ def gpu_main(args, rank: int, world: int, local_rank: int):
     e2e = {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 12 * m,
            "d2h_bytes_per_step": 4 * cnt + 12, "steps": e2e_steps,
            "api": "mst_solve_host_many: step k+1's input copy overlaps step k's solve",
-           "one_call_per_step": {"value": seq_value, "api": "mst_solve_host"}}
+           "one_call_per_step": {"value": seq_value, "api": "mst_solve_host"},
+           "breakdown_ms": e2e_breakdown(torch, solver, dev, stream, n, m, pin, (src, dst, w), out, ids_h, cnt)}
 
     peaks = measured_peaks()
     kernels = {}
     all_bytes = 0.0
     launches = 0
-    for name, (nl, kms, kbytes) in stats.items():  # timed region: launches and bytes of every class
+    for name, (nl, kms, kbytes, _) in stats.items():  # timed region: launches and bytes of every class
         launches += nl
         all_bytes += kbytes
     for name, (nl, kms, kbytes) in stats_all.items():  # profiled pass: every class timed
@@ -446,8 +496,9 @@ def gpu_main(args, rank: int, world: int, local_rank: int):
             kernels[name] = {"launches_per_step": nl / prof_steps, "ms_per_step": kms / prof_steps,
                              "bytes_per_step": kbytes / prof_steps,
                              "GBps": (kbytes / (kms / 1e3) / 1e9) if kms > 0 else None}
-    nl, kms, kbytes = stats[dom]
+    nl, kms, kbytes, kmin = stats[dom]
     achieved = kbytes / (kms / 1e3) / 1e9
+    achieved_min = kmin / (kms / 1e3) / 1e9
     traffic = None
     if (dom == TRAFFIC["class"] and TRAFFIC["dram_per_algorithmic_byte"] and nl
             and traffic_source_digest() == TRAFFIC["source_sha256"]):
@@ -455,7 +506,13 @@ def gpu_main(args, rank: int, world: int, local_rank: int):
     roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                 "frac": achieved / peaks["hbm_gbs"], "peak_source": peaks["source"],
                 "bytes_per_launch": kbytes / nl if nl else None,
-                "traffic": traffic, "traffic_source": TRAFFIC["summary"] if traffic is not None else None,
+                # the method's own bytes: for the filter only the heavy edges
+                # read (the pass re-reads the light ones too) and the survivors
+                "min_bytes_per_launch": kmin / nl if nl else None,
+                "achieved_min": achieved_min, "frac_min": achieved_min / peaks["hbm_gbs"],
+                "traffic": traffic,
+                "traffic_source": (f"ncu DRAM bytes of {TRAFFIC['kernel']} (kernel source sha256 "
+                                   f"{TRAFFIC['source_sha256'][:12]})") if traffic is not None else None,
                 "time_share": kms / ms if ms > 0 else None}
     effective = all_bytes / args.steps / (ms / args.steps / 1e3) / 1e9
 

@@ -202,8 +202,12 @@ enum {
 };
 typedef struct {
   uint64_t launches;
-  double ms;    /* summed event time of the class's launches */
-  double bytes; /* summed algorithmic bytes */
+  double ms;        /* summed event time of the class's launches */
+  double bytes;     /* summed algorithmic bytes of the passes as built */
+  double min_bytes; /* summed bytes the method itself must move: equal to `bytes` except for the
+                       filter, whose pass also re-reads the light edges of its list (the paper's
+                       filter reads only the heavy edges, Alg. 2): there the heavy edges read
+                       plus the survivors written */
 } mst_kernel_stats;
 
 /* enable != 0: start collecting (and clear the totals); 0: stop. */
@@ -258,7 +262,8 @@ mst_status mst_step_dedupe(mst_handle h, uint64_t m, const uint32_t *d_u, const 
 /* PivotSelection (Alg. 2; Section 5): sample k = 0..sample-1 is the edge at
  * position floor(splitmix64(state, k) * m / 2^64), where splitmix64(s, k) is
  * output k of the splitmix64 sequence started at state s; the pivot is the
- * sample key of rank sample/2 (0-based, ascending).  d_pivot: one uint64. */
+ * sample key of rank sample/2 (0-based, ascending).  d_pivot: one uint64.
+ * MST_ERR_TOO_LARGE if m >= 2^32 (edge ids are uint32). */
 mst_status mst_step_pivot(mst_handle h, uint64_t m, const uint32_t *d_w, const uint32_t *d_id, uint64_t state,
                           uint32_t sample, uint64_t *d_pivot, void *stream);
 
@@ -315,7 +320,12 @@ mst_status mst_step_finalize(mst_handle h, uint64_t m, const uint32_t *d_chosen,
  *   d_pivot  [out] one uint64, device memory, written in stream order
  * Runs on the current CUDA device and returns without waiting for the GPU.
  * The first call on a device looks the array's device address up once (with
- * that device current); make that first call before any stream capture.
+ * that device current) and keeps it for the life of the process; make that
+ * first call before any stream capture.  cudaDeviceReset on that device after
+ * the first call is not supported (the array may move and the kept address
+ * would be stale).  An error that earlier work on the calling thread left
+ * pending (cudaPeekAtLastError) makes the call return MST_ERR_CUDA without
+ * launching; the pending error is left in place for its owner.
  * All calls share the one array and it keeps the last call's samples: calls
  * whose work overlaps on the GPU (different streams, or different host threads
  * without ordering) race on it and may return wrong pivots.

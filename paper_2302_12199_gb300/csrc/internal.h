@@ -15,6 +15,7 @@ enum : uint32_t {
   ERR_LOOKBACK = 2u,  // a scan predecessor never published (bounded wait ran out)
   ERR_HASH = 4u,      // hash table probe sequence exhausted
   ERR_JUMP = 8u,      // pointer doubling did not reach a root within its bound
+  ERR_TMA = 16u,      // a bulk copy never completed (bounded mbarrier wait ran out); tiles were skipped
 };
 
 // Small per-handle device state.

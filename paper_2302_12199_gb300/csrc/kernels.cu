@@ -318,17 +318,24 @@ __device__ __forceinline__ u64 hash_lookup(const HashSlot *t, uint64_t mask, u64
 
 // ---------------------------------------------------------------- compaction
 
-// Keep flags of one tile for a compaction mode (see CompactMode); relabels
-// eu/ev in place where the mode relabels.  Bit k = item k.
-template <int MODE>
-__device__ __forceinline__ uint32_t keep_flags(const CompactArgs &a, uint64_t tb, uint64_t m, u64 pivot,
-                                               uint32_t (&eu)[ITEMS], uint32_t (&ev)[ITEMS],
-                                               const uint32_t (&ew)[ITEMS], const uint32_t (&ei)[ITEMS]) {
+// Bit k set iff item k of this thread's striped tile (base tb) is below m.
+__device__ __forceinline__ uint32_t valid_items(uint64_t tb, uint64_t m) {
+  uint32_t valid = 0;
+#pragma unroll
+  for (int k = 0; k < ITEMS; ++k) valid |= (tb + item_off(k) < m ? 1u : 0u) << k;
+  return valid;
+}
+
+// Keep flags of a thread's ITEMS items for a compaction mode (see
+// CompactMode); relabels eu/ev in place where the mode relabels.  Bit k =
+// item k; only items whose bit is set in `valid` can be kept.
+template <int MODE, int N>
+__device__ __forceinline__ uint32_t keep_flags(const CompactArgs &a, uint32_t valid, u64 pivot, uint32_t (&eu)[N],
+                                               uint32_t (&ev)[N], const uint32_t (&ew)[N], const uint32_t (&ei)[N]) {
   uint32_t keep = 0;
 #pragma unroll
-  for (int k = 0; k < ITEMS; ++k) {
-    const uint64_t j = tb + item_off(k);
-    bool ok = j < m;
+  for (int k = 0; k < N; ++k) {
+    bool ok = (valid >> k) & 1u;
     if (ok && a.validate && (eu[k] >= a.n || ev[k] >= a.n)) {
       atomicOr(a.st.err, ERR_VERTEX);
       ok = false;
@@ -349,15 +356,15 @@ __device__ __forceinline__ uint32_t keep_flags(const CompactArgs &a, uint64_t tb
     keep |= (ok ? 1u : 0u) << k;
   }
   if (MODE == CM_HEAVY && a.giant_bits) {  // drop heavy edges inside the giant component; keep the ends
-    uint32_t bu[ITEMS], bv[ITEMS];
+    uint32_t bu[N], bv[N];
 #pragma unroll
-    for (int k = 0; k < ITEMS; ++k) {
+    for (int k = 0; k < N; ++k) {
       const bool h = keep >> k & 1;
       bu[k] = h ? __ldg(a.giant_bits + (eu[k] >> 5)) : 0u;
       bv[k] = h ? __ldg(a.giant_bits + (ev[k] >> 5)) : 0u;
     }
 #pragma unroll
-    for (int k = 0; k < ITEMS; ++k)
+    for (int k = 0; k < N; ++k)
       if ((bu[k] >> (eu[k] & 31)) & (bv[k] >> (ev[k] & 31)) & 1u) keep &= ~(1u << k);
   }
   if (MODE == CM_FILTER) {
@@ -366,26 +373,26 @@ __device__ __forceinline__ uint32_t keep_flags(const CompactArgs &a, uint64_t tb
     // the labels of the remaining items, so that each thread has one round of
     // independent loads in flight per step.
     if (a.giant_bits) {
-      uint32_t bu[ITEMS], bv[ITEMS];
+      uint32_t bu[N], bv[N];
 #pragma unroll
-      for (int k = 0; k < ITEMS; ++k) {
+      for (int k = 0; k < N; ++k) {
         const bool h = keep >> k & 1;
         bu[k] = h ? __ldg(a.giant_bits + (eu[k] >> 5)) : 0u;
         bv[k] = h ? __ldg(a.giant_bits + (ev[k] >> 5)) : 0u;
       }
 #pragma unroll
-      for (int k = 0; k < ITEMS; ++k)
+      for (int k = 0; k < N; ++k)
         if ((bu[k] >> (eu[k] & 31)) & (bv[k] >> (ev[k] & 31)) & 1u) keep &= ~(1u << k);
     }
-    uint32_t lu[ITEMS], lv[ITEMS];
+    uint32_t lu[N], lv[N];
 #pragma unroll
-    for (int k = 0; k < ITEMS; ++k) {
+    for (int k = 0; k < N; ++k) {
       const bool h = keep >> k & 1;
       lu[k] = h ? __ldg(a.label + eu[k]) : 0u;
       lv[k] = h ? __ldg(a.label + ev[k]) : 0u;
     }
 #pragma unroll
-    for (int k = 0; k < ITEMS; ++k) {
+    for (int k = 0; k < N; ++k) {
       eu[k] = lu[k];
       ev[k] = lv[k];
       if (lu[k] == lv[k]) keep &= ~(1u << k);
@@ -499,7 +506,7 @@ __global__ void __launch_bounds__(BLOCK, 4) compact_kernel(CompactArgs a) {
       }
     }
   }
-  const uint32_t keep = keep_flags<MODE>(a, tb, m, compact_pivot(a, MODE), eu, ev, ew, ei);
+  const uint32_t keep = keep_flags<MODE>(a, valid_items(tb, m), compact_pivot(a, MODE), eu, ev, ew, ei);
   if (a.max_w) {  // largest weight of the input, folded into this pass
     uint32_t mx = 0;
 #pragma unroll
@@ -650,7 +657,7 @@ __global__ void __launch_bounds__(BLOCK, 3 * 256 / BLOCK) compact_tma_kernel(Com
         }
       }
     }
-    const uint32_t keep = keep_flags<MODE>(a, tb, m, pivot, eu, ev, ew, ei);
+    const uint32_t keep = keep_flags<MODE>(a, valid_items(tb, m), pivot, eu, ev, ew, ei);
     if (a.max_w) {
       uint32_t mx = 0;
 #pragma unroll
@@ -665,15 +672,237 @@ __global__ void __launch_bounds__(BLOCK, 3 * 256 / BLOCK) compact_tma_kernel(Com
     emit_survivors(a, keep, excl, totp, obase, eu, ev, ew, ei, out->u, out->v, out->w, out->id);
     __syncthreads();  // the output stage is reused by the next tile
   }
-  // On an abort, wait (bounded) for the copies this block still has in flight
-  // before its shared memory goes away.
+  // On an abort the block's remaining tiles were not compacted: latch the
+  // error (the solve then fails instead of returning a short list), and wait
+  // (bounded) for the copies this block still has in flight before its shared
+  // memory goes away.
   __syncthreads();
   if (s_abort && threadIdx.x == 0) {
+    atomicOr(a.st.err, ERR_TMA);
     for (uint64_t k = it; k < it + TMA_STAGES; ++k) {
       const uint64_t tile = blockIdx.x + k * G;
       if (tile < nfull) mbar_wait_bounded(&mbar[k % TMA_STAGES], (uint32_t)((k / TMA_STAGES) & 1));
     }
   }
+}
+
+// ------------------------------------------------- warp-streamed filter pass
+
+// The filter keeps few of the edges it reads (on RMAT about 2% of a level's
+// list: the heavy edges between different components of the light forest,
+// Thm. 1), so its pass is a stream with gathers more than a compaction, and
+// the gathers (giant-component bitmap words, then labels) set its speed.  Here
+// every warp streams its own tiles of FW_TILE edges: warp gw of the G warps in
+// the grid takes tiles gw, gw + G, gw + 2G, ...; a full tile arrives in one of
+// the warp's FW_STAGES shared-memory stages by bulk copies (one per array,
+// completion counted on the stage's mbarrier) issued FW_STAGES tiles ahead, and
+// the stage is refilled as soon as the tile is in registers, so the next
+// tile's copy overlaps this tile's gathers.  The warp's survivors go to its
+// own FW_OUT-entry staging buffer, which is written out (one atomic claim of
+// output slots, coalesced stores, then the best[] relaxation and recorded
+// ends) when it fills and when the warp finishes.  No block-wide barrier is on
+// the path: a warp waiting on its gathers never holds up another.
+//
+// The shapes are measured on GB300 (RMAT n=2^24, m=2^28, filter class per
+// solve): 32 warps x 4 edges per lane, one stage: 2.49 ms; 16 warps x 8, two
+// blocks per SM: 2.49; 24 x 8, one stage: 2.58; 24 x 8, two stages: 4.39; the
+// block-synchronous compaction kernel: 4.02.  Shared memory is the lever: the
+// rest of the SM's 256 KB is L1, which serves the hub vertices' bitmap words
+// and labels, so a deep ring (216 KB) lost to a single stage (80 KB).
+constexpr int FW_WARPS = 32;              // warps per block; one block per SM
+constexpr int FW_ITEMS = 4;               // edges per lane and tile (a multiple of 4)
+constexpr int FW_STAGES = 1;              // input stages per warp
+constexpr int FW_OUT = 32;                // survivor staging entries per warp
+constexpr int FW_MINB = 1;                // resident blocks per SM the registers are sized for
+constexpr int FW_THREADS = FW_WARPS * 32;
+constexpr int FW_TILE = 32 * FW_ITEMS;    // edges per warp tile
+
+struct __align__(16) WarpStage {
+  uint32_t u[FW_TILE], v[FW_TILE], w[FW_TILE], id[FW_TILE];
+};
+struct __align__(16) WarpOut {
+  uint32_t u[FW_OUT], v[FW_OUT], w[FW_OUT], id[FW_OUT];
+};
+constexpr size_t FW_SMEM = sizeof(WarpStage) * FW_STAGES * FW_WARPS + sizeof(WarpOut) * FW_WARPS;
+
+// Item k of lane l in a warp tile sits at (k / 4) * 128 + 4 l + k % 4, so each
+// 16-byte shared-memory read of the warp covers 512 contiguous bytes.
+__device__ __forceinline__ uint32_t witem_off(int k) {
+  return (uint32_t)((k >> 2) * 128 + 4 * (threadIdx.x & 31) + (k & 3));
+}
+
+__device__ __forceinline__ void read_wstage(const uint32_t *p, uint32_t (&x)[FW_ITEMS]) {
+  const uint4 *q = reinterpret_cast<const uint4 *>(p);
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int c = 0; c < FW_ITEMS / 4; ++c) {
+    const uint4 t = q[32 * c + lane];
+    x[4 * c] = t.x;
+    x[4 * c + 1] = t.y;
+    x[4 * c + 2] = t.z;
+    x[4 * c + 3] = t.w;
+  }
+}
+
+// Issues the bulk copies of full warp tile `tile` into stage `st` (one lane).
+__device__ __forceinline__ void issue_wtile(const CompactArgs &a, uint64_t tile, WarpStage *st, u64 *bar) {
+  const uint32_t bytes = FW_TILE * 4;
+  const uint64_t off = tile * FW_TILE;
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // order the stage's earlier generic reads
+  mbar_arrive_expect_tx(bar, (a.in.id ? 4u : 3u) * bytes);
+  bulk_load(st->u, a.in.u + off, bytes, bar);
+  bulk_load(st->v, a.in.v + off, bytes, bar);
+  bulk_load(st->w, a.in.w + off, bytes, bar);
+  if (a.in.id) bulk_load(st->id, a.in.id + off, bytes, bar);
+}
+
+// Writes the warp's `count` staged survivors to the output list (all lanes).
+__device__ __forceinline__ void warp_flush(const CompactArgs &a, const WarpOut *o, uint32_t count) {
+  const int lane = threadIdx.x & 31;
+  unsigned long long base = 0;
+  if (lane == 0) base = atomicAdd(a.st.total, (unsigned long long)count);
+  base = __shfl_sync(0xffffffffu, base, 0);
+  for (uint32_t i = lane; i < count; i += 32) {
+    const uint32_t x = o->u[i], y = o->v[i], w = o->w[i], id = o->id[i];
+    a.out.u[base + i] = x;
+    a.out.v[base + i] = y;
+    a.out.w[base + i] = w;
+    a.out.id[base + i] = id;
+    if (a.cur_u) {  // ends by id, for the hook of the round that relaxes this list
+      a.cur_u[id] = x;
+      a.cur_v[id] = y;
+    }
+    if (a.best) {  // the next round's minEdges, fused
+      const u64 kx = relax_key(a.kl, w, id, y), ky = relax_key(a.kl, w, id, x);
+      const u64 cx = __ldca(a.best + x), cy = __ldca(a.best + y);
+      if (kx < cx) atomicMin(a.best + x, kx);
+      if (ky < cy) atomicMin(a.best + y, ky);
+    }
+  }
+  __syncwarp();  // the staging buffer is refilled next
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(FW_THREADS, FW_MINB) filter_warp_kernel(CompactArgs a) {
+  static_assert(MODE == CM_FILTER || MODE == CM_HEAVY, "the warp-streamed pass serves the filter modes");
+  extern __shared__ __align__(128) unsigned char smem_dyn[];
+  __shared__ __align__(8) u64 mbar[FW_WARPS][FW_STAGES];
+  const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  WarpStage *stage = reinterpret_cast<WarpStage *>(smem_dyn) + wid * FW_STAGES;
+  WarpOut *o = reinterpret_cast<WarpOut *>(smem_dyn + sizeof(WarpStage) * FW_STAGES * FW_WARPS) + wid;
+  u64 *bar = mbar[wid];
+
+  const uint64_t m = a.m_dev ? *a.m_dev : a.m;
+  const uint64_t ntiles = (m + FW_TILE - 1) / FW_TILE, nfull = m / FW_TILE;
+  const uint64_t G = (uint64_t)gridDim.x * FW_WARPS;
+  const uint64_t gw = (uint64_t)blockIdx.x * FW_WARPS + wid;
+  if (lane == 0) {
+    for (int s = 0; s < FW_STAGES; ++s) mbar_init(&bar[s], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    for (int s = 0; s < FW_STAGES; ++s) {
+      const uint64_t tile = gw + (uint64_t)s * G;
+      if (tile < nfull) issue_wtile(a, tile, &stage[s], &bar[s]);
+    }
+  }
+  __syncwarp();
+  const u64 pivot = compact_pivot(a, MODE);
+  uint32_t fill = 0;  // staged survivors (the same in every lane)
+  bool abort = false;
+  uint64_t it = 0;
+  for (;; ++it) {
+    const uint64_t tile = gw + it * G;
+    if (tile >= ntiles) break;
+    const uint64_t tb = tile * FW_TILE;
+    uint32_t eu[FW_ITEMS], ev[FW_ITEMS], ew[FW_ITEMS], ei[FW_ITEMS];
+    uint32_t valid = (FW_ITEMS >= 32 ? 0xffffffffu : (1u << FW_ITEMS) - 1u);
+    if (tile < nfull) {
+      const int si = (int)(it % FW_STAGES);
+      WarpStage *st = &stage[si];
+      const bool ok = mbar_wait_bounded(&bar[si], (uint32_t)((it / FW_STAGES) & 1));
+      if (!__all_sync(0xffffffffu, ok)) {
+        abort = true;
+        break;
+      }
+      read_wstage(st->u, eu);
+      read_wstage(st->v, ev);
+      read_wstage(st->w, ew);
+      if (a.in.id) {
+        read_wstage(st->id, ei);
+      } else {
+#pragma unroll
+        for (int k = 0; k < FW_ITEMS; ++k) ei[k] = (uint32_t)(tb + witem_off(k));
+      }
+      __syncwarp();  // every lane has the tile: refill the stage with the tile FW_STAGES ahead
+      if (lane == 0) {
+        const uint64_t next = tile + (uint64_t)FW_STAGES * G;
+        if (next < nfull) issue_wtile(a, next, st, &bar[si]);
+      }
+    } else {  // the partial last tile: plain loads
+      valid = 0;
+#pragma unroll
+      for (int k = 0; k < FW_ITEMS; ++k) {
+        const uint64_t j = tb + witem_off(k);
+        if (j < m) {
+          eu[k] = __ldg(a.in.u + j);
+          ev[k] = __ldg(a.in.v + j);
+          ew[k] = __ldg(a.in.w + j);
+          ei[k] = a.in.id ? __ldg(a.in.id + j) : (uint32_t)j;
+          valid |= 1u << k;
+        } else {
+          eu[k] = ev[k] = ew[k] = ei[k] = 0;
+        }
+      }
+    }
+    const uint32_t keep = keep_flags<MODE>(a, valid, pivot, eu, ev, ew, ei);
+    // warp-wide exclusive prefix of the kept counts: survivor ranks 0..total-1
+    const uint32_t c = (uint32_t)__popc(keep);
+    uint32_t incl = c;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, incl, d);
+      if (lane >= d) incl += y;
+    }
+    const uint32_t total = __shfl_sync(0xffffffffu, incl, 31), excl = incl - c;
+    // append the ranks [lo, lo + take) to the free part of the staging buffer
+    for (uint32_t lo = 0; lo < total;) {
+      const uint32_t take = min((uint32_t)FW_OUT - fill, total - lo);
+#pragma unroll
+      for (int k = 0; k < FW_ITEMS; ++k) {
+        if (!(keep >> k & 1)) continue;
+        const uint32_t r = excl + (uint32_t)__popc(keep & ((1u << k) - 1u));
+        if (r >= lo && r < lo + take) {
+          const uint32_t p = fill + r - lo;
+          o->u[p] = eu[k];
+          o->v[p] = ev[k];
+          o->w[p] = ew[k];
+          o->id[p] = ei[k];
+        }
+      }
+      __syncwarp();
+      fill += take;
+      lo += take;
+      if (fill == FW_OUT) {
+        warp_flush(a, o, fill);
+        fill = 0;
+      }
+    }
+  }
+  if (!abort) {
+    if (fill) warp_flush(a, o, fill);
+    return;
+  }
+  // A bulk copy never completed: this warp's remaining tiles were not read.
+  // Latch the error (the solve fails instead of returning a short list) and
+  // wait (bounded) for the copies still in flight into this warp's stages
+  // before the block's shared memory goes away.
+  if (lane == 0) {
+    atomicOr(a.st.err, ERR_TMA);
+    for (uint64_t k = it; k < it + FW_STAGES; ++k) {
+      const uint64_t tile = gw + k * G;
+      if (tile < nfull) mbar_wait_bounded(&bar[k % FW_STAGES], (uint32_t)((k / FW_STAGES) & 1));
+    }
+  }
+  __syncwarp();
 }
 
 // --------------------------------------------------------------- min edges
@@ -2385,6 +2614,29 @@ static void launch_compact_mode(const CompactArgs &a, uint64_t max_count, cudaSt
   const uint64_t tiles = (max_count + TILE - 1) / TILE;
   if (tiles == 0) return;
   const bool aligned = aligned16(a.in.u) && aligned16(a.in.v) && aligned16(a.in.w) && (!a.in.id || aligned16(a.in.id));
+  if constexpr (MODE == CM_FILTER || MODE == CM_HEAVY) {
+    static int fw_blocks = -1;  // resident blocks of the warp-streamed pass (0: not available)
+    if (fw_blocks < 0) {
+      int dev = 0, sms = 0, per_sm = 0;
+      cudaGetDevice(&dev);
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+      if (cudaFuncSetAttribute(filter_warp_kernel<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)FW_SMEM) ==
+              cudaSuccess &&
+          cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, filter_warp_kernel<MODE>, FW_THREADS, FW_SMEM) ==
+              cudaSuccess)
+        fw_blocks = sms * per_sm;
+      else
+        fw_blocks = 0;
+      cudaGetLastError();
+    }
+    if (aligned && fw_blocks > 0) {
+      const uint64_t wtiles = (max_count + FW_TILE - 1) / FW_TILE;
+      const uint64_t want = (wtiles + FW_WARPS - 1) / FW_WARPS;
+      const unsigned grid = (unsigned)std::min<uint64_t>(want, (uint64_t)fw_blocks);
+      filter_warp_kernel<MODE><<<grid, FW_THREADS, FW_SMEM, s>>>(a);
+      return;
+    }
+  }
   if (aligned && tma_blocks > 0 && tiles >= (uint64_t)tma_blocks * TMA_STAGES) {
     compact_tma_kernel<MODE><<<(unsigned)tma_blocks, BLOCK, tma_smem, s>>>(a);
     return;

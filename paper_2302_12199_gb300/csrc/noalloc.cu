@@ -61,6 +61,10 @@ extern "C" mst_status mst_pivot_noalloc(uint64_t m, const uint32_t *d_w, const u
                                         uint32_t sample, uint64_t *d_pivot, void *stream) {
   if (!d_pivot || sample == 0 || (m > 0 && !d_w)) return MST_ERR_INVALID_ARG;
   if (sample > kMaxSample || m >= (1ULL << 32)) return MST_ERR_TOO_LARGE;
+  // An error that earlier work on this host thread left pending is the
+  // caller's: report it without launching and without clearing it, so that
+  // the launch check below only ever sees this call's own launch.
+  if (cudaPeekAtLastError() != cudaSuccess) return MST_ERR_CUDA;
   u64 *scratch = nullptr;
   const mst_status st = scratch_for_current_device(&scratch);
   if (st != MST_OK) return st;

@@ -41,7 +41,7 @@ struct mst_ctx {
   struct ProfRec {
     int kind;
     cudaEvent_t a, b;
-    double bytes;
+    double bytes, min_bytes;  // fixed parts known at launch (see prof_end)
     int slot1, slot2;
     double per1, per2;
   };
@@ -225,14 +225,18 @@ int prof_begin(mst_ctx *c, cudaStream_t s, int kind) {
 }
 
 // Closes a record: `bytes` known at launch, plus count[slot] * per for counts the
-// kernel itself produces (read at the next readback).
+// kernel itself produces (read at the next readback).  `min_bytes` (< 0: the
+// same as `bytes`) replaces the fixed part in the method's own count, for a
+// pass that reads more than the method needs (the filter re-reads the light
+// edges of its list along with the heavy ones).
 void prof_end(mst_ctx *c, cudaStream_t s, int idx, int kind, double bytes, int slot1 = -1, double per1 = 0,
-              int slot2 = -1, double per2 = 0) {
+              int slot2 = -1, double per2 = 0, double min_bytes = -1.0) {
   if (idx < 0) return;
   mst_ctx::ProfRec &r = c->prof_pending[idx];
   if (r.b) cudaEventRecord(r.b, s);
   r.kind = kind;
   r.bytes = bytes;
+  r.min_bytes = min_bytes < 0.0 ? bytes : min_bytes;
   r.slot1 = slot1;
   r.per1 = per1;
   r.slot2 = slot2;
@@ -250,10 +254,11 @@ void prof_resolve(mst_ctx *c) {
     mst_kernel_stats &k = c->prof[r.kind];
     k.launches += 1;
     k.ms += ms;
-    double b = r.bytes;
+    double b = 0.0;
     if (r.slot1 >= 0) b += (double)c->hs->count[r.slot1] * r.per1;
     if (r.slot2 >= 0) b += (double)c->hs->count[r.slot2] * r.per2;
-    k.bytes += b;
+    k.bytes += r.bytes + b;
+    k.min_bytes += r.min_bytes + b;
     if (r.a) {
       c->ev_pool.push_back(r.a);
       c->ev_pool.push_back(r.b);
@@ -267,6 +272,14 @@ void prof_resolve(mst_ctx *c) {
     const int _p = prof_begin(c, s, kind);                       \
     launch;                                                      \
     prof_end(c, s, _p, kind, bytes, slot1, per1, slot2, per2);   \
+  } while (0)
+
+// The same with the method's own fixed byte count `min_bytes` (see prof_end).
+#define PROF_MIN(kind, bytes, min_bytes, slot1, per1, slot2, per2, launch)     \
+  do {                                                                         \
+    const int _p = prof_begin(c, s, kind);                                     \
+    launch;                                                                    \
+    prof_end(c, s, _p, kind, bytes, slot1, per1, slot2, per2, min_bytes);      \
   } while (0)
 
 mst_status readback(mst_ctx *c, cudaStream_t s) {
@@ -974,6 +987,8 @@ struct Solve {
     cf.kl = kl;
     record_ends(cf);
     TRY(zero_counters(c, s));
+    // the method reads only the heavy edges of E (the light ones went into L)
+    const double heavy_bytes = (E.id ? 16.0 : 12.0) * (double)(mE - mL);
     ListBuf C;
     // The filter runs against P before the contraction's flag is known: a P
     // that is not fully contracted (labels that are ancestors, not roots) only
@@ -995,14 +1010,15 @@ struct Solve {
         ch.n = n;
         ch.kl = kl;
         ch.st = next_scan(c, CNT_TMP);
-        PROF(MST_K_FILTER, in_bytes, CNT_TMP, 16.0, -1, 0.0, launch_compact(CM_HEAVY, ch, mE, s));
+        PROF_MIN(MST_K_FILTER, in_bytes, heavy_bytes, CNT_TMP, 16.0, -1, 0.0, launch_compact(CM_HEAVY, ch, mE, s));
         cf.in = C.list();
         cf.m = mE - mL;
         cf.m_dev = &c->ds->count[CNT_TMP];
         cf.giant_bits = nullptr;
         PROF(MST_K_FILTER, 0.0, CNT_TMP, 16.0, CNT_EDGES, 16.0, launch_compact(CM_FILTER, cf, mE - mL, s));
       } else {
-        PROF(MST_K_FILTER, in_bytes, CNT_EDGES, 16.0, -1, 0.0, launch_compact(CM_FILTER, cf, mE, s));
+        PROF_MIN(MST_K_FILTER, in_bytes, heavy_bytes, CNT_EDGES, 16.0, -1, 0.0,
+                 launch_compact(CM_FILTER, cf, mE, s));
       }
       TRY(readback(c, s));
       if (!c->hs->jump_flag) break;
@@ -1783,6 +1799,7 @@ mst_status mst_step_filter(mst_handle h, uint32_t n, uint64_t m, const uint32_t 
 mst_status mst_step_pivot(mst_handle h, uint64_t m, const uint32_t *d_w, const uint32_t *d_id, uint64_t state,
                           uint32_t sample, uint64_t *d_pivot, void *stream) {
   if (!h || !d_pivot || sample == 0 || (m > 0 && !d_w)) return MST_ERR_INVALID_ARG;
+  if (m >= (1ULL << 32)) return record(h, MST_ERR_TOO_LARGE);
   DeviceGuard g(h->device);
   cudaStream_t s = (cudaStream_t)stream;
   Buf sb;

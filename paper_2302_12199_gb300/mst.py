@@ -44,7 +44,8 @@ class HostGraph(ctypes.Structure):
 
 
 class KernelStats(ctypes.Structure):
-    _fields_ = [("launches", ctypes.c_uint64), ("ms", ctypes.c_double), ("bytes", ctypes.c_double)]
+    _fields_ = [("launches", ctypes.c_uint64), ("ms", ctypes.c_double), ("bytes", ctypes.c_double),
+                ("min_bytes", ctypes.c_double)]
 
 
 class MstConfig(ctypes.Structure):
@@ -207,13 +208,14 @@ class Solver:
         self._check(self.lib.mst_profile_classes(self.h, mask), "mst_profile_classes")
         self._check(self.lib.mst_profile_enable(self.h, 1 if enable else 0), "mst_profile_enable")
 
-    def profile_stats(self) -> dict:
-        """{class: (launches, ms, algorithmic bytes)} since profiling was enabled."""
+    def profile_stats(self, with_min: bool = False) -> dict:
+        """{class: (launches, ms, algorithmic bytes)} since profiling was enabled;
+        with_min adds the method's own byte count as a fourth entry."""
         out = {}
         for k, name in enumerate(KERNEL_CLASSES):
             st = KernelStats()
             self._check(self.lib.mst_profile_get(self.h, k, ctypes.byref(st)), "mst_profile_get")
-            out[name] = (int(st.launches), float(st.ms), float(st.bytes))
+            out[name] = (int(st.launches), float(st.ms), float(st.bytes)) + ((float(st.min_bytes),) if with_min else ())
         return out
 
     def workspace_bytes(self, n: int, m: int) -> int:
