@@ -194,16 +194,20 @@ class ClockSampler:
 
 # --------------------------------------------------------------- reference
 
-def cpu_oracle_rate(g, sample_edges: int, repeats: int = 1) -> tuple[float, float]:
-    """Kruskal (the CPU oracle, single-threaded) on the first `sample_edges`
-    edges of the graph; returns (edges/s, seconds per run)."""
+def cpu_oracle_rate(g, sample_edges: int, repeats: int = 1, threads: int = 1) -> tuple[float, float]:
+    """Kruskal (the CPU oracle; single-threaded, or with its sort on `threads`
+    host threads) on the first `sample_edges` edges of the graph; returns
+    (edges/s, seconds per run)."""
     import oracle
     k = min(sample_edges, g.m)
     src, dst, w = g.src[:k], g.dst[:k], g.w[:k]
     best = None
     for _ in range(repeats):
         t0 = time.perf_counter()
-        oracle.kruskal(g.n, src, dst, w)
+        if threads > 1:
+            oracle.kruskal_par(g.n, src, dst, w, threads)
+        else:
+            oracle.kruskal(g.n, src, dst, w)
         dt = time.perf_counter() - t0
         best = dt if best is None else min(best, dt)
     return k / best, best
@@ -536,12 +540,27 @@ def gpu_main(args, rank: int, world: int, local_rank: int):
     }
     if rank == 0 and not args.no_cpu_baseline:
         rate, dt = cpu_oracle_rate(g, args.cpu_sample_edges)
+        sample = f"first {min(g.m, args.cpu_sample_edges)} of the {g.m} edges (n={n})"
         line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
-                                "sample": f"first {min(g.m, args.cpu_sample_edges)} of the {g.m} edges (n={n}), "
-                                          f"Kruskal, single thread, {dt:.1f} s"}
+                                "sample": f"{sample}, Kruskal, single thread, {dt:.1f} s"}
+        cores = host_cores()
+        prate, pdt = cpu_oracle_rate(g, args.cpu_sample_edges, threads=cores)
+        line["cpu_baseline_parallel_sort"] = {
+            "value": prate, "unit": UNIT, "cores": cores, "kind": "oracle, sort on all host cores",
+            "sample": f"{sample}, Kruskal with its radix sort on {cores} threads (union-find sequential), {pdt:.1f} s"}
+    solver.close()
+    del src, dst, w, pin
+    torch.cuda.empty_cache()
+    if not args.no_batched and args.workload == "rmat_filter":
+        # the batched workload (4096 mixed graphs), compact: graphs/s, batch
+        # latency and the one-solve-per-graph baseline on the same GPU
+        import types
+        bargs = types.SimpleNamespace(graphs=args.graphs, log_hi=args.log_hi, no_autotune=args.no_autotune,
+                                      base_case=args.base_case, graph_rounds=args.graph_rounds,
+                                      steps=args.batched_steps, warmup=3, e2e_steps=1)
+        line["batched"] = measure_batched(bargs, rank, world, local_rank, dev, dist, compact=True)
     if rank == 0:
         print(json.dumps(line), flush=True)
-    solver.close()
     if dist:
         dist.destroy_process_group()
     return 0
@@ -554,10 +573,31 @@ def percentiles(xs, qs=(50, 99, 99.9)):
 
 
 def batched_main(args, rank: int, world: int, local_rank: int):
+    """The batched configuration as its own bench line (see measure_batched)."""
+    import torch
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    line = measure_batched(args, rank, world, local_rank, dev, dist)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+def measure_batched(args, rank: int, world: int, local_rank: int, dev, dist, compact: bool = False) -> dict:
     """The batched configuration: G mixed graphs (n log-uniform in [2^8, 2^16];
     1/3 GNM with average degree in [4,32], 1/3 RGG2D degree 8, 1/3 RMAT degree
-    16; w in [1,255]) solved by one mst_solve_batched call per step, against
-    one mst_solve call per graph (plain Borůvka) on the same GPU."""
+    16; w in [1,255]) solved by one mst_solve_batched call per step (the
+    configuration chosen by the autotuner), against one mst_solve call per
+    graph (plain Borůvka) on the same GPU; every batched forest is compared
+    with the graph's own solve.  compact: only the throughput, the batch
+    latencies and the per-graph baseline (no per-class profile, no clocks, no
+    end-to-end leg)."""
     import numpy as np
     import torch
 
@@ -565,12 +605,6 @@ def batched_main(args, rank: int, world: int, local_rank: int):
     from paper_2302_12199_gb300.autotune import autotune, label
     from paper_2302_12199_gb300.mst import Solver
 
-    torch.cuda.set_device(local_rank)
-    dev = torch.device("cuda", local_rank)
-    dist = None
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl", device_id=dev)
     G = args.graphs
     b = W.mix(G, W.DEFAULT_SEED + rank, log_hi=args.log_hi)
     n_per = np.asarray(b.n, dtype=np.uint32)
@@ -579,12 +613,14 @@ def batched_main(args, rank: int, world: int, local_rank: int):
     n_tot = int(n_per.astype(np.int64).sum())
     to_dev = lambda a: torch.from_numpy(a.view(np.int32)).to(dev)
     src, dst, w = to_dev(b.src), to_dev(b.dst), to_dev(b.w)
+    d_n = to_dev(n_per)  # the size tables stay on the device, like the edges
+    d_off = torch.from_numpy(off.view(np.int64)).to(dev)
     stream = torch.cuda.current_stream(dev)
 
     def timed_batch(solver):
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        res = solver.solve_batched(n_per, off, src, dst, w)
+        res = solver.solve_batched(d_n, d_off, src, dst, w, capacity=n_tot)
         e1.record(stream)
         torch.cuda.synchronize(dev)
         return e0.elapsed_time(e1) / 1e3, res
@@ -612,12 +648,14 @@ def batched_main(args, rank: int, world: int, local_rank: int):
     # profiled batches outside the timed region (every class timed), as for
     # the single-graph workloads; inside it only the dominant class is timed
     prof_steps = max(1, min(args.steps, 3))
-    solver.profile(True)
-    for _ in range(prof_steps):
-        timed_batch(solver)
-    solver.profile(False)
-    stats_all = solver.profile_stats()
-    dom = max(stats_all, key=lambda k: stats_all[k][1])
+    dom = None
+    if not compact:
+        solver.profile(True)
+        for _ in range(prof_steps):
+            timed_batch(solver)
+        solver.profile(False)
+        stats_all = solver.profile_stats()
+        dom = max(stats_all, key=lambda k: stats_all[k][1])
 
     uuid = None
     try:
@@ -627,9 +665,10 @@ def batched_main(args, rank: int, world: int, local_rank: int):
     sampler = ClockSampler(uuid)
     if dist:
         dist.barrier()
-    sampler.start()
-    time.sleep(0.3)
-    solver.profile(True, classes=[dom])
+    if not compact:
+        sampler.start()
+        time.sleep(0.3)
+    solver.profile(True, classes=[dom] if dom else [])
     lat = []
     nvtx_mark(torch, "push")
     for _ in range(args.steps):
@@ -673,6 +712,21 @@ def batched_main(args, rank: int, world: int, local_rank: int):
     if mismatch:
         raise RuntimeError(f"{mismatch} graphs differ between the batched and the per-graph solves")
     base.close()
+    launches = sum(v[0] for v in stats.values())
+    if compact:
+        solver.close()
+        return {"metric": "batched graphs/s (one mst_solve_batched call per step)", "value": value,
+                "unit": "graphs/s", "steps": args.steps, "ms_per_step": total_s * 1e3 / args.steps,
+                "config": {"workload": "batched", "graphs": G, "n_total": n_tot, "m_total": m_tot,
+                           "mix": f"n log-uniform [2^8,2^{args.log_hi}]; 1/3 GNM deg 4-32, 1/3 RGG2D deg 8, "
+                                  "1/3 RMAT deg 16; w in [1,255]", "autotuned": best,
+                           "autotune_trials_s": {k: v for k, v in tuning}},
+                "latency_ms": {k: v * 1e3 for k, v in percentiles(lat).items()},
+                "edges_per_s": m_tot * args.steps * world / total_s,
+                "one_launch_per_graph": {"value": base_value, "unit": "graphs/s", "variant": "boruvka",
+                                         "latency_ms": {k: v * 1e3 for k, v in percentiles(per).items()},
+                                         "batched_over_per_graph": value / world / base_value},
+                "gpu_launches": launches, "forests": "every batched forest equals the graph solved alone"}
 
     # end to end: pinned host batch -> device, solve, forests back to pinned
     # host memory.  Two device input sets: batch k+1 is copied on its own
@@ -706,7 +760,7 @@ def batched_main(args, rank: int, world: int, local_rank: int):
                 copy_in(k + 1)
             solve_s.wait_event(ev_in[k % 2])
             with torch.cuda.stream(solve_s):
-                r_ids, r_off, r_tot = solver.solve_batched(n_per, off, *sets[k % 2], stream=solve_s)
+                r_ids, r_off, r_tot = solver.solve_batched(d_n, d_off, *sets[k % 2], stream=solve_s, capacity=n_tot)
                 ev_free[k % 2].record(solve_s)
                 off_pin.copy_(r_off, non_blocking=True)
                 tot_pin.copy_(r_tot[:G], non_blocking=True)
@@ -732,9 +786,8 @@ def batched_main(args, rank: int, world: int, local_rank: int):
            "api": "mst_solve_batched on device buffers; batch k+1's input copy overlaps batch k's solve"}
 
     peaks = measured_peaks()
-    kernels, all_bytes, launches = {}, 0.0, 0
+    kernels, all_bytes = {}, 0.0
     for name, (nl, kms, kbytes) in stats.items():
-        launches += nl
         all_bytes += kbytes
     for name, (nl, kms, kbytes) in stats_all.items():
         if nl:
@@ -770,12 +823,8 @@ def batched_main(args, rank: int, world: int, local_rank: int):
         "e2e": e2e,
         "clocks": clocks,
     }
-    if rank == 0:
-        print(json.dumps(line), flush=True)
     solver.close()
-    if dist:
-        dist.destroy_process_group()
-    return 0
+    return line
 
 
 def served_main(args, rank: int, world: int, local_rank: int):
@@ -888,6 +937,9 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--cpu-sample-edges", type=int, default=1 << 25)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batched", action="store_true",
+                    help="default workload: skip the batched sub-record (4096 mixed graphs)")
+    ap.add_argument("--batched-steps", type=int, default=20, help="timed batches of the batched sub-record")
     ap.add_argument("--variant", default=None, choices=["boruvka", "filter", "auto"],
                     help="override the workload's solver variant")
     ap.add_argument("--dedupe", default=None, choices=["auto", "sort", "hash", "none"])

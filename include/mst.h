@@ -18,10 +18,13 @@
  * aligned; 16-byte alignment enables vector loads.  The library allocates its
  * own scratch memory (stream-ordered) and frees it when the handle is destroyed.
  *
- * Streams: `stream` is a cudaStream_t (NULL = the legacy default stream).  Work
- * is issued on that stream.  A call returns once its results are written: the
- * round loop reads counters back from the device on that stream between
- * rounds.  A handle must not be used by two host threads at once.
+ * Streams: `stream` is a cudaStream_t (NULL = the legacy default stream).  All
+ * of a call's device work is issued on that stream, after the work the caller
+ * queued on it before the call.  A call returns once its results are written:
+ * the Borůvka round loop and the Filter-Borůvka recursion are steered by
+ * counts (list lengths, active components) that the host reads back on that
+ * stream, so a solve is stream-ordered but not asynchronous to the host.  A
+ * handle must not be used by two host threads at once.
  *
  * Errors: every call returns an mst_status.  Errors detected on the device
  * (vertex ids out of range, a bounded loop that ran out of iterations) are
@@ -95,6 +98,10 @@ typedef struct {
                                   half of a tile's edges first and drop heavy edges that fall inside a
                                   component (recursive filtering in local preprocessing, Section 6.2);
                                   0 (default, measured faster on GB300): every edge from the first round */
+  uint32_t spin_limit;         /* polls of a predecessor's status word in the ordered output scan before the
+                                  wait gives up (>= 1; default 2^21, about a second); a wait that runs out
+                                  makes the call return MST_ERR_INTERNAL.  Small values exist to exercise
+                                  that error path */
 } mst_config;
 
 /* Fills *cfg with the defaults (Borůvka variant, automatic dedupe, pivot sample
@@ -113,8 +120,11 @@ mst_status mst_set_config(mst_handle h, const mst_config *cfg);
 /* Human-readable name of a status code (static storage). */
 const char *mst_status_string(mst_status s);
 
-/* Status of the last call made with this handle. */
-mst_status mst_get_error(mst_handle h);
+/* Waits for `stream`, then returns the status of the last call made with
+ * this handle, or, if that call succeeded, the error flags the device has
+ * latched since it began (vertex range, an exhausted bounded loop), as a
+ * status.  MST_ERR_CUDA if the stream reports a CUDA error. */
+mst_status mst_get_error(mst_handle h, void *stream);
 
 /* The CUDA runtime error code (cudaError_t) behind the last MST_ERR_CUDA
  * returned for this handle, 0 if none; *line (if line != NULL) receives the
@@ -166,17 +176,23 @@ typedef struct {
  * MST_OK if every graph was solved, else the first failing graph's status. */
 mst_status mst_solve_host_many(mst_handle h, uint32_t count, mst_host_graph *graphs, void *stream);
 
-/* Minimum spanning forests of G independent graphs in one solve.  Graph g has
- * d_n[g] vertices (graph-local ids 0..d_n[g]-1) and the edges
- * d_edge_off[g] .. d_edge_off[g+1]-1 of d_src/d_dst/d_w.  The graphs are solved
- * together as one disjoint union, so their rounds share launches.
- *   h_n, h_edge_off  HOST copies of the size tables ([G] and [G+1] entries)
- *   d_msf_ids   [out] capacity >= sum_g min(m_g, n_g - 1); segment g starts at
- *               d_msf_off[g] and holds graph-local edge ids (index - d_edge_off[g])
+/* Minimum spanning forests of G independent graphs in one solve (each graph
+ * the Section 2.2 problem).  Graph g has d_n[g] vertices (graph-local ids
+ * 0..d_n[g]-1) and the edges d_edge_off[g] .. d_edge_off[g+1]-1 of
+ * d_src/d_dst/d_w.  The graphs are solved together as one disjoint union, so
+ * their rounds share launches.
+ *   d_n         [G] uint32 vertex counts, device memory
+ *   d_edge_off  [G+1] uint64 edge offsets, device memory; d_edge_off[0] == 0,
+ *               non-decreasing (else MST_ERR_INVALID_ARG); d_edge_off[G] = m
+ *   d_msf_ids   [out] capacity >= sum_g min(m_g, n_g - 1) (min(m, sum_g n_g)
+ *               always suffices); segment g starts at d_msf_off[g] and holds
+ *               graph-local edge ids (index - d_edge_off[g]), ascending
  *   d_msf_off   [out] [G+1] uint64 segment offsets
  *   d_total_weight [out] [G] uint64 MSF weight of each graph
+ * The totals (all vertices, all edges) are read back from the device tables
+ * before the solve is sized.  MST_ERR_TOO_LARGE if either reaches 2^32.
  * Errors as mst_solve; a vertex id out of range in any graph fails the call. */
-mst_status mst_solve_batched(mst_handle h, uint32_t num_graphs, const uint32_t *h_n, const uint64_t *h_edge_off,
+mst_status mst_solve_batched(mst_handle h, uint32_t num_graphs, const uint32_t *d_n, const uint64_t *d_edge_off,
                              const uint32_t *d_src, const uint32_t *d_dst, const uint32_t *d_w, uint32_t *d_msf_ids,
                              uint64_t *d_msf_off, uint64_t *d_total_weight, void *stream);
 

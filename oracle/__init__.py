@@ -42,7 +42,7 @@ def build(force: bool = False) -> str:
     if force or not os.path.exists(_OUT) or os.path.getmtime(_OUT) < os.path.getmtime(_SRC):
         os.makedirs(os.path.dirname(_OUT), exist_ok=True)
         tmp = _OUT + f".tmp{os.getpid()}"
-        subprocess.run(["gcc", "-O2", "-fPIC", "-shared", _SRC, "-o", tmp], check=True)
+        subprocess.run(["gcc", "-O2", "-fPIC", "-shared", "-pthread", _SRC, "-o", tmp], check=True)
         os.replace(tmp, _OUT)
     return _OUT
 
@@ -55,6 +55,9 @@ def _load():
             f = getattr(lib, name)
             f.restype = ctypes.c_int
             f.argtypes = [ctypes.c_uint64, ctypes.c_uint64, _u32p, _u32p, _u32p, _u32p, _u64p, _u64p]
+        lib.oracle_kruskal_par.restype = ctypes.c_int
+        lib.oracle_kruskal_par.argtypes = [ctypes.c_uint64, ctypes.c_uint64, _u32p, _u32p, _u32p, ctypes.c_int,
+                                           _u32p, _u64p, _u64p]
         lib.oracle_brute.restype = ctypes.c_int
         lib.oracle_brute.argtypes = [ctypes.c_uint64, ctypes.c_uint64, _u32p, _u32p, _u32p, _u32p, _u64p, _u64p,
                                      _u64p]
@@ -95,6 +98,22 @@ def kruskal(n: int, src, dst, w):
     Pinned by: brute force on tiny graphs, Prim, cut/cycle checks, closed forms."""
     m = len(src)
     return _run("oracle_kruskal", n, src, dst, w, min(m, max(n - 1, 0)) if n > 0 else 0)
+
+
+def kruskal_par(n: int, src, dst, w, threads: int):
+    """Kruskal with its radix sort spread over `threads` host threads (the
+    union-find pass stays sequential).  Same output as kruskal(); for timing
+    the CPU baseline on many cores.  Pinned by equality with kruskal()."""
+    src, dst, w = _arr(src), _arr(dst), _arr(w)
+    m = int(src.shape[0])
+    out = np.empty(max(min(m, max(n - 1, 0)) if n > 0 else 0, 1), dtype=np.uint32)
+    cnt = ctypes.c_uint64(0)
+    tot = ctypes.c_uint64(0)
+    rc = _load().oracle_kruskal_par(n, m, _p32(src), _p32(dst), _p32(w), int(threads), _p32(out),
+                                    ctypes.byref(cnt), ctypes.byref(tot))
+    if rc != 0:
+        raise OracleError(f"oracle_kruskal_par: {_STATUS.get(rc, rc)}")
+    return out[: cnt.value].copy(), int(tot.value)
 
 
 def prim(n: int, src, dst, w):

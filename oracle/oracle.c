@@ -18,6 +18,11 @@
  * Functions:
  *   oracle_kruskal   Kruskal: edges in (w,id) order, union-find, keep an edge
  *                    iff it joins two different trees.
+ *   oracle_kruskal_par  The same Kruskal with its sort spread over host
+ *                    threads (each radix pass: per-thread digit counts over
+ *                    contiguous chunks, then a stable scatter); the
+ *                    union-find pass stays sequential.  For timing on many
+ *                    cores; its output equals oracle_kruskal's.
  *   oracle_prim      Jarnik-Prim with a binary heap keyed by (w,id), restarted
  *                    from every unvisited vertex (an independent cross-check).
  *   oracle_brute     Exhaustive search over edge subsets for tiny graphs.
@@ -25,6 +30,7 @@
  * Status codes: 0 ok, 1 vertex id out of range, 2 graph too large for the
  * routine, 3 out of memory.
  */
+#include <pthread.h>
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
@@ -451,4 +457,133 @@ done:
   free(par_edge);
   free(depth);
   return bad;
+}
+
+/* --------------------------------------------------- Kruskal, parallel sort */
+
+#define PAR_MAX_THREADS 256
+
+/* One pass of the parallel stable radix sort: thread t owns the contiguous
+ * chunk [lo, hi) of the current order and first counts its digits; after all
+ * counts are known, every (digit, thread) pair gets its output start (digits
+ * ascending, threads ascending within a digit: the order a sequential stable
+ * pass would give), and each thread scatters its chunk in order. */
+typedef struct {
+  const uint32_t *w;
+  const uint32_t *in;
+  uint32_t *out;
+  uint64_t lo, hi;
+  int shift;
+  uint64_t cnt[256];  /* digit counts of the chunk, then output starts */
+} par_pass;
+
+static void *par_count(void *arg) {
+  par_pass *a = (par_pass *)arg;
+  memset(a->cnt, 0, sizeof(a->cnt));
+  for (uint64_t i = a->lo; i < a->hi; ++i) a->cnt[(a->w[a->in[i]] >> a->shift) & 0xff]++;
+  return NULL;
+}
+
+static void *par_scatter(void *arg) {
+  par_pass *a = (par_pass *)arg;
+  for (uint64_t i = a->lo; i < a->hi; ++i) {
+    const uint32_t id = a->in[i];
+    a->out[a->cnt[(a->w[id] >> a->shift) & 0xff]++] = id;
+  }
+  return NULL;
+}
+
+/* Runs fn over the T pass records: records 1..T-1 on new threads, record 0
+ * on the calling thread.  Returns 0, or 3 if a thread could not be started
+ * (the records it would have run are then run here). */
+static int par_run(void *(*fn)(void *), par_pass *rec, int T) {
+  pthread_t th[PAR_MAX_THREADS];
+  int started[PAR_MAX_THREADS];
+  for (int t = 1; t < T; ++t) started[t] = pthread_create(&th[t], NULL, fn, &rec[t]) == 0;
+  fn(&rec[0]);
+  for (int t = 1; t < T; ++t) {
+    if (started[t])
+      pthread_join(th[t], NULL);
+    else
+      fn(&rec[t]);
+  }
+  return 0;
+}
+
+int oracle_kruskal_par(uint64_t n, uint64_t m, const uint32_t *src, const uint32_t *dst, const uint32_t *w,
+                       int nthreads, uint32_t *out_ids, uint64_t *out_count, uint64_t *out_weight) {
+  *out_count = 0;
+  *out_weight = 0;
+  if (n > 0xFFFFFFFFULL || m > 0xFFFFFFFFULL) return 2;
+  if (check_range(n, m, src, dst)) return 1;
+  int T = nthreads < 1 ? 1 : (nthreads > PAR_MAX_THREADS ? PAR_MAX_THREADS : nthreads);
+  uint32_t *order = (uint32_t *)malloc((m ? m : 1) * sizeof(uint32_t));
+  uint32_t *tmp = (uint32_t *)malloc((m ? m : 1) * sizeof(uint32_t));
+  uint32_t *p = (uint32_t *)malloc((n ? n : 1) * sizeof(uint32_t));
+  uint32_t *sz = (uint32_t *)malloc((n ? n : 1) * sizeof(uint32_t));
+  uint8_t *in_f = (uint8_t *)calloc(m ? m : 1, 1);
+  par_pass *rec = (par_pass *)malloc((size_t)T * sizeof(par_pass));
+  if (!order || !tmp || !p || !sz || !in_f || !rec) {
+    free(order);
+    free(tmp);
+    free(p);
+    free(sz);
+    free(in_f);
+    free(rec);
+    return 3;
+  }
+  uint64_t k = 0;
+  for (uint64_t e = 0; e < m; ++e)
+    if (src[e] != dst[e]) order[k++] = (uint32_t)e; /* self-loops never join two trees */
+  if ((uint64_t)T > k) T = k > 0 ? (int)k : 1;
+  for (int shift = 0; shift < 32; shift += 8) {
+    for (int t = 0; t < T; ++t) {
+      rec[t].w = w;
+      rec[t].in = order;
+      rec[t].out = tmp;
+      rec[t].lo = k * (uint64_t)t / (uint64_t)T;
+      rec[t].hi = k * (uint64_t)(t + 1) / (uint64_t)T;
+      rec[t].shift = shift;
+    }
+    par_run(par_count, rec, T);
+    uint64_t start = 0;
+    int trivial = 0;
+    for (int d = 0; d < 256; ++d) {
+      uint64_t digit_total = 0;
+      for (int t = 0; t < T; ++t) digit_total += rec[t].cnt[d];
+      if (digit_total == k) trivial = 1;
+    }
+    if (trivial) continue; /* every element has the same digit: the pass keeps the order */
+    for (int d = 0; d < 256; ++d)
+      for (int t = 0; t < T; ++t) {
+        const uint64_t c = rec[t].cnt[d];
+        rec[t].cnt[d] = start;
+        start += c;
+      }
+    par_run(par_scatter, rec, T);
+    uint32_t *sw = order;
+    order = tmp;
+    tmp = sw;
+  }
+  for (uint64_t v = 0; v < n; ++v) {
+    p[v] = (uint32_t)v;
+    sz[v] = 1;
+  }
+  uint64_t total = 0;
+  for (uint64_t i = 0; i < k; ++i) {
+    const uint32_t e = order[i];
+    if (uf_union(p, sz, src[e], dst[e])) {
+      in_f[e] = 1;
+      total += w[e];
+    }
+  }
+  *out_count = bits_to_ids(in_f, m, out_ids);
+  *out_weight = total;
+  free(order);
+  free(tmp);
+  free(p);
+  free(sz);
+  free(in_f);
+  free(rec);
+  return 0;
 }

@@ -16,6 +16,7 @@ enum : uint32_t {
   ERR_HASH = 4u,      // hash table probe sequence exhausted
   ERR_JUMP = 8u,      // pointer doubling did not reach a root within its bound
   ERR_TMA = 16u,      // a bulk copy never completed (bounded mbarrier wait ran out); tiles were skipped
+  ERR_TABLE = 32u,    // a batched size table is inconsistent (offsets not starting at 0 or decreasing)
 };
 
 // Small per-handle device state.
@@ -42,6 +43,7 @@ struct ScanState {
   uint32_t epoch;    // 1 .. 2^30-1, different for every ordered launch
   u64 *total;
   uint32_t *err;
+  uint32_t spin_limit;  // polls of a predecessor's status word before the wait gives up (ERR_LOOKBACK)
 };
 
 struct HashSlot {

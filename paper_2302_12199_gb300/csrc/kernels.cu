@@ -25,7 +25,6 @@ namespace mstgpu {
 constexpr int BLOCK = 256;
 constexpr int ITEMS = 8;
 constexpr int TILE = BLOCK * ITEMS;
-constexpr uint32_t SPIN_LIMIT = 1u << 21;  // look-back polls before giving up (about a second)
 constexpr uint32_t JUMP_STEPS = 64;        // pointer steps per jump launch
 constexpr u64 PAIR_EMPTY = ~0ULL;
 
@@ -175,7 +174,7 @@ __device__ uint32_t decoupled_lookback(const ScanState &st, uint32_t tile, uint3
           flag[k] = ((uint32_t)(s >> 34) == st.epoch) ? (uint32_t)((s >> 32) & 3u) : 0u;
           val[k] = (uint32_t)s;
           if (flag[k] != 0) break;
-          if (++spins > SPIN_LIMIT) {
+          if (++spins >= st.spin_limit) {  // bounded: the predecessor never published
             flag[k] = 3;
             break;
           }

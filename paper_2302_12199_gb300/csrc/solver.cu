@@ -29,6 +29,7 @@ struct mst_ctx {
   cudaMemPool_t pool = nullptr;
   DevState *ds = nullptr;    // device
   DevState *hs = nullptr;    // pinned host mirror
+  u64 *hres = nullptr;       // pinned host words for the forest size and weight of the host entry points
   u64 *status = nullptr;     // scan status words
   uint64_t status_cap = 0;   // in tiles
   uint32_t epoch = 0;
@@ -50,6 +51,13 @@ struct mst_ctx {
   cudaStream_t cap_stream = nullptr;  // stream the round graphs are captured on
   cudaStream_t copy_stream = nullptr; // input copies of mst_solve_host_many
   cudaEvent_t in_ready[2] = {nullptr, nullptr}, in_free[2] = {nullptr, nullptr};
+  // device buffers of the host entry points (inputs, two sets; the forest),
+  // grown on demand and kept: outside the pool, so that the solves' scratch
+  // never splits them and the pool never has to grow while a copy runs
+  void *hin[2] = {nullptr, nullptr};
+  size_t hin_cap[2] = {0, 0};
+  void *hout = nullptr;
+  size_t hout_cap = 0;
   GraphRounds *grounds = nullptr;     // device state of the graph round loop
   struct RoundGraph {
     u64 sig;  // every pointer and size the graph was built with
@@ -192,7 +200,7 @@ ScanState next_scan(mst_ctx *c, int total_slot) {
     cudaMemset(c->ds->tile_ctr, 0, sizeof(c->ds->tile_ctr));
     c->epoch = 1;
   }
-  return ScanState{c->status, c->ds->tile_ctr, c->epoch, &c->ds->count[total_slot], &c->ds->err};
+  return ScanState{c->status, c->ds->tile_ctr, c->epoch, &c->ds->count[total_slot], &c->ds->err, c->cfg.spin_limit};
 }
 
 cudaEvent_t take_event(mst_ctx *c) {
@@ -287,6 +295,7 @@ mst_status readback(mst_ctx *c, cudaStream_t s) {
   CK(cudaStreamSynchronize(s));
   prof_resolve(c);
   if (c->hs->err & ERR_VERTEX) return MST_ERR_VERTEX_RANGE;
+  if (c->hs->err & ERR_TABLE) return MST_ERR_INVALID_ARG;
   if (c->hs->err) return MST_ERR_INTERNAL;
   return MST_OK;
 }
@@ -731,7 +740,7 @@ struct Solve {
       ca.kl = kl;
       ca.best = best;
       record_ends(ca);
-      ca.st = ScanState{c->status, c->ds->tile_ctr, 0, &g->ce[out], &c->ds->err};
+      ca.st = ScanState{c->status, c->ds->tile_ctr, 0, &g->ce[out], &c->ds->err, c->cfg.spin_limit};
       launch_compact(CM_RELABEL, ca, cap, cs);
       HookArgs hb{};
       hb.cand = A[in];
@@ -1128,6 +1137,7 @@ mst_status validate_cfg(const mst_config *cfg) {
   if (cfg->jump_steps < 1 || cfg->jump_steps > 4096) return MST_ERR_INVALID_ARG;
   if (cfg->tile_filter < 0 || cfg->tile_filter > 1) return MST_ERR_INVALID_ARG;
   if (cfg->tile_vertices < 32 || cfg->tile_vertices > 4096) return MST_ERR_INVALID_ARG;
+  if (cfg->spin_limit < 1) return MST_ERR_INVALID_ARG;
   return MST_OK;
 }
 
@@ -1178,6 +1188,60 @@ __device__ __forceinline__ uint32_t batch_graph_of(const uint64_t *off, uint32_t
       hi = mid;
   }
   return lo;
+}
+
+// The batched size tables, read on the device: vert_off[g] = n[0] + ... +
+// n[g-1] (g = 0..G, an exclusive scan in one block), totals[0] = all vertices,
+// totals[1] = edge_off[G] (all edges); ERR_TABLE if edge_off[0] != 0 or the
+// offsets decrease somewhere.
+constexpr int TAB_THREADS = 1024;
+__global__ void __launch_bounds__(TAB_THREADS) batch_tables_kernel(const uint32_t *gn, const uint64_t *edge_off,
+                                                                  uint32_t G, uint64_t *vert_off, u64 *totals,
+                                                                  uint32_t *err) {
+  __shared__ u64 s_warp[TAB_THREADS / 32];
+  __shared__ u64 s_carry;
+  __shared__ uint32_t s_bad;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (threadIdx.x == 0) {
+    s_carry = 0;
+    s_bad = edge_off[0] != 0 ? 1u : 0u;
+  }
+  __syncthreads();
+  for (uint64_t base = 0; base < G; base += TAB_THREADS) {
+    const uint64_t g = base + threadIdx.x;
+    const u64 x = g < G ? (u64)gn[g] : 0ULL;
+    if (g < G && edge_off[g + 1] < edge_off[g]) atomicOr(&s_bad, 1u);
+    u64 incl = x;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const u64 y = __shfl_up_sync(0xffffffffu, incl, d);
+      if (lane >= d) incl += y;
+    }
+    if (lane == 31) s_warp[wid] = incl;
+    __syncthreads();
+    if (wid == 0) {
+      const u64 v = s_warp[lane];
+      u64 wi = v;
+#pragma unroll
+      for (int d = 1; d < 32; d <<= 1) {
+        const u64 y = __shfl_up_sync(0xffffffffu, wi, d);
+        if (lane >= d) wi += y;
+      }
+      s_warp[lane] = wi - v;  // exclusive prefix of the warps' sums
+    }
+    __syncthreads();
+    const u64 excl = s_carry + s_warp[wid] + incl - x;
+    if (g < G) vert_off[g] = excl;
+    __syncthreads();  // every thread has read s_carry and s_warp
+    if (threadIdx.x == TAB_THREADS - 1) s_carry = excl + x;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    vert_off[G] = s_carry;
+    totals[0] = s_carry;
+    totals[1] = edge_off[G];
+    if (s_bad) atomicOr(err, ERR_TABLE);
+  }
 }
 
 // Union vertex ids: edge e of graph g gets its ends offset by vert_off[g].
@@ -1259,6 +1323,38 @@ __global__ void batch_split_kernel(const uint32_t *ids, const uint32_t *count, c
 
 }  // namespace
 
+// A device buffer of the host entry points of at least `bytes`, grown (after
+// the device is idle, since the old one may still be read) when too small.
+static mst_status host_side_buffer(void *&buf, size_t &cap, size_t bytes) {
+  if (cap >= bytes && buf) return MST_OK;
+  CK(cudaDeviceSynchronize());
+  if (buf) cudaFree(buf);
+  buf = nullptr;
+  cap = 0;
+  const size_t want = bytes < 256 ? 256 : bytes;
+  if (cudaMalloc(&buf, want) != cudaSuccess) {
+    cudaGetLastError();
+    return MST_ERR_OOM;
+  }
+  cap = want;
+  return MST_OK;
+}
+
+// The forest size and weight of a solve, read back through the handle's
+// page-locked words.  A copy into pageable host memory is synchronous and
+// staged by the driver, and it can queue behind a large host-to-device copy
+// in flight on another stream (the next graph's input in
+// mst_solve_host_many), which would serialise copy and solve.
+static mst_status read_size_and_weight(mst_ctx *c, const uint32_t *d_count, const u64 *d_total, cudaStream_t s,
+                                uint32_t &cnt, uint64_t &total) {
+  CK(cudaMemcpyAsync(&c->hres[0], d_count, 4, cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(&c->hres[1], d_total, 8, cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  cnt = (uint32_t)(c->hres[0] & 0xffffffffu);
+  total = c->hres[1];
+  return MST_OK;
+}
+
 // ===================================================================== ABI
 
 extern "C" {
@@ -1286,6 +1382,7 @@ void mst_config_default(mst_config *cfg) {
   cfg->min_edges_sort = 0;
   cfg->jump_steps = 64;
   cfg->tile_filter = 0;  // measured slower on GB300: the light phase adds synchronised rounds in each tile
+  cfg->spin_limit = 1u << 21;  // about a second of polling at the measured poll rate
 }
 
 const char *mst_status_string(mst_status s) {
@@ -1332,6 +1429,7 @@ mst_status mst_create(mst_handle *out, const mst_config *cfg) {
   ok = ok && cudaMalloc(&c->ds, sizeof(DevState)) == cudaSuccess;
   ok = ok && cudaMemset(c->ds, 0, sizeof(DevState)) == cudaSuccess;
   ok = ok && cudaMallocHost(&c->hs, sizeof(DevState)) == cudaSuccess;
+  ok = ok && cudaMallocHost(&c->hres, 2 * sizeof(u64)) == cudaSuccess;
   ok = ok && ensure_sample(c) == MST_OK;
   ok = ok && cudaMalloc(&c->pivot_scratch, pivot_scratch_bytes()) == cudaSuccess;
   ok = ok && cudaMalloc(&c->wsum, WSUM_SLOTS * sizeof(u64)) == cudaSuccess;
@@ -1352,6 +1450,10 @@ void mst_destroy(mst_handle h) {
     cudaDeviceSynchronize();
     if (h->ds) cudaFree(h->ds);
     if (h->hs) cudaFreeHost(h->hs);
+    if (h->hres) cudaFreeHost(h->hres);
+    for (int k = 0; k < 2; ++k)
+      if (h->hin[k]) cudaFree(h->hin[k]);
+    if (h->hout) cudaFree(h->hout);
     if (h->status) cudaFree(h->status);
     if (h->sample_buf) cudaFree(h->sample_buf);
     if (h->pivot_scratch) cudaFree(h->pivot_scratch);
@@ -1386,7 +1488,13 @@ mst_status mst_set_config(mst_handle h, const mst_config *cfg) {
   return record(h, ensure_sample(h));
 }
 
-mst_status mst_get_error(mst_handle h) { return h ? h->last : MST_ERR_INVALID_ARG; }
+mst_status mst_get_error(mst_handle h, void *stream) {
+  if (!h) return MST_ERR_INVALID_ARG;
+  DeviceGuard g(h->device);
+  if (cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess) return record_cuda(h, __LINE__);
+  const mst_status dev = readback(h, (cudaStream_t)stream);  // flags the device latched since the last call began
+  return h->last != MST_OK ? h->last : dev;
+}
 
 int mst_last_cuda_error(mst_handle h, int *line) {
   if (line) *line = h ? h->last_cuda_line : 0;
@@ -1444,14 +1552,13 @@ mst_status mst_solve_host(mst_handle h, uint32_t n, uint64_t m, const uint32_t *
   DeviceGuard g(h->device);
   cudaStream_t s = (cudaStream_t)stream;
   const uint64_t cap = m < (uint64_t)(n > 0 ? n - 1 : 0) ? m : (uint64_t)(n > 0 ? n - 1 : 0);
-  Buf in_b, out_b;
   const uint64_t stride = round_up(m * 4 + 16, 256);
-  mst_status st = in_b.alloc(h, stride * 3, s);
-  if (st == MST_OK) st = out_b.alloc(h, cap * 4 + 256, s);
+  mst_status st = host_side_buffer(h->hin[0], h->hin_cap[0], stride * 3);
+  if (st == MST_OK) st = host_side_buffer(h->hout, h->hout_cap, cap * 4 + 256);
   if (st != MST_OK) return record(h, st);
-  char *b = in_b.as<char>();
+  char *b = static_cast<char *>(h->hin[0]);
   uint32_t *d_src = (uint32_t *)b, *d_dst = (uint32_t *)(b + stride), *d_w = (uint32_t *)(b + 2 * stride);
-  uint32_t *d_out = out_b.as<uint32_t>();
+  uint32_t *d_out = static_cast<uint32_t *>(h->hout);
   uint32_t *d_count = (uint32_t *)((char *)d_out + cap * 4);
   u64 *d_total = (u64 *)((char *)d_out + round_up(cap * 4 + 4, 8));
   if (m > 0) {
@@ -1463,10 +1570,7 @@ mst_status mst_solve_host(mst_handle h, uint32_t n, uint64_t m, const uint32_t *
   st = solve_device(h, n, m, d_src, d_dst, d_w, d_out, d_count, d_total, s);
   if (st != MST_OK) return record(h, st);
   uint32_t cnt = 0;
-  if (cudaMemcpyAsync(&cnt, d_count, 4, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
-      cudaMemcpyAsync(h_total_weight, d_total, 8, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
-      cudaStreamSynchronize(s) != cudaSuccess)
-    return record_cuda(h, __LINE__);
+  if (read_size_and_weight(h, d_count, d_total, s, cnt, *h_total_weight) != MST_OK) return record_cuda(h, __LINE__);
   *h_msf_count = cnt;
   if (cnt > 0 && (cudaMemcpyAsync(h_msf_ids, d_out, (size_t)cnt * 4, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
                   cudaStreamSynchronize(s) != cudaSuccess))
@@ -1503,19 +1607,18 @@ mst_status mst_solve_host_many(mst_handle h, uint32_t count, mst_host_graph *gs,
       return record_cuda(h, __LINE__);
   }
   const uint64_t stride = round_up(max_m * 4 + 16, 256);
-  Buf in_b[2], out_b;
   mst_status st = MST_OK;
-  for (int k = 0; k < 2 && st == MST_OK; ++k) st = in_b[k].alloc(h, stride * 3, s);
-  if (st == MST_OK) st = out_b.alloc(h, max_cap * 4 + 256, s);
+  for (int k = 0; k < 2 && st == MST_OK; ++k) st = host_side_buffer(h->hin[k], h->hin_cap[k], stride * 3);
+  if (st == MST_OK) st = host_side_buffer(h->hout, h->hout_cap, max_cap * 4 + 256);
   if (st != MST_OK) return record(h, gs[0].status = st);
-  // the buffers come from the stream-ordered pool on s: both count as free
-  // (for the copy stream) once s reaches this point
+  // both input sets count as free (for the copy stream) once s reaches this
+  // point: earlier work of this handle on s may still read them
   for (int k = 0; k < 2; ++k)
     if (cudaEventRecord(h->in_free[k], s) != cudaSuccess) return record_cuda(h, __LINE__);
-  uint32_t *d_out = out_b.as<uint32_t>();
+  uint32_t *d_out = static_cast<uint32_t *>(h->hout);
   uint32_t *d_count = (uint32_t *)((char *)d_out + max_cap * 4);
   u64 *d_total = (u64 *)((char *)d_out + round_up(max_cap * 4 + 4, 8));
-  auto set_of = [&](uint32_t i, int a) { return (uint32_t *)(in_b[i % 2].as<char>() + (size_t)a * stride); };
+  auto set_of = [&](uint32_t i, int a) { return (uint32_t *)(static_cast<char *>(h->hin[i % 2]) + (size_t)a * stride); };
   auto issue_copy = [&](uint32_t i) -> bool {
     const int k = (int)(i % 2);
     if (cudaStreamWaitEvent(h->copy_stream, h->in_free[k], 0) != cudaSuccess) return false;
@@ -1549,9 +1652,8 @@ mst_status mst_solve_host_many(mst_handle h, uint32_t count, mst_host_graph *gs,
     }
     if (st == MST_OK) {
       uint32_t cnt = 0;
-      if (cudaMemcpyAsync(&cnt, d_count, 4, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
-          cudaMemcpyAsync(&g.total_weight, d_total, 8, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
-          cudaStreamSynchronize(s) != cudaSuccess ||
+      uint64_t tot = 0;
+      if (read_size_and_weight(h, d_count, d_total, s, cnt, tot) != MST_OK ||
           (cnt > 0 && (cudaMemcpyAsync(g.msf_ids, d_out, (size_t)cnt * 4, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
                        cudaStreamSynchronize(s) != cudaSuccess))) {
         st = record_cuda(h, __LINE__);
@@ -1561,6 +1663,7 @@ mst_status mst_solve_host_many(mst_handle h, uint32_t count, mst_host_graph *gs,
         break;
       }
       g.msf_count = cnt;
+      g.total_weight = tot;
     }
     g.status = st;
     if (st != MST_OK && first == MST_OK) first = st;
@@ -1570,65 +1673,58 @@ mst_status mst_solve_host_many(mst_handle h, uint32_t count, mst_host_graph *gs,
     }
   }
   // a copy issued for a graph that was not solved must finish before the
-  // buffers return to the pool (each event marks the last copy into its buffer)
+  // buffers are used again (each event marks the last copy into its buffer)
   for (int k = 0; k < 2; ++k) cudaStreamWaitEvent(s, h->in_ready[k], 0);
   if (st == MST_ERR_CUDA && first == MST_OK) first = st;
   return record(h, first);
 }
 
-mst_status mst_solve_batched(mst_handle h, uint32_t num_graphs, const uint32_t *h_n, const uint64_t *h_edge_off,
+mst_status mst_solve_batched(mst_handle h, uint32_t num_graphs, const uint32_t *d_n, const uint64_t *d_edge_off,
                              const uint32_t *d_src, const uint32_t *d_dst, const uint32_t *d_w, uint32_t *d_msf_ids,
                              uint64_t *d_msf_off, uint64_t *d_total_weight, void *stream) {
   if (!h) return MST_ERR_INVALID_ARG;
   if (num_graphs == 0) return record(h, MST_OK);
-  if (!h_n || !h_edge_off || !d_msf_off || !d_total_weight) return record(h, MST_ERR_INVALID_ARG);
+  if (!d_n || !d_edge_off || !d_msf_off || !d_total_weight) return record(h, MST_ERR_INVALID_ARG);
   DeviceGuard g(h->device);
   cudaStream_t s = (cudaStream_t)stream;
-  const uint64_t m = h_edge_off[num_graphs];
-  if (h_edge_off[0] != 0) return record(h, MST_ERR_INVALID_ARG);
-  std::vector<uint64_t> voff(num_graphs + 1, 0);
-  for (uint32_t gi = 0; gi < num_graphs; ++gi) {
-    if (h_edge_off[gi + 1] < h_edge_off[gi]) return record(h, MST_ERR_INVALID_ARG);
-    voff[gi + 1] = voff[gi] + h_n[gi];
-  }
-  if (voff[num_graphs] >= (1ULL << 32)) return record(h, MST_ERR_TOO_LARGE);
-  if (m >= (1ULL << 32)) return record(h, MST_ERR_TOO_LARGE);
+  // vertex offsets of the disjoint union and the totals, from the device tables
+  Buf voff_b;
+  mst_status st = voff_b.alloc(h, ((size_t)num_graphs + 1) * 8, s);
+  if (st != MST_OK) return record(h, st);
+  uint64_t *d_voff = voff_b.as<uint64_t>();
+  if (clear_device_flags(h, s) != MST_OK) return record_cuda(h, __LINE__);
+  batch_tables_kernel<<<1, TAB_THREADS, 0, s>>>(d_n, d_edge_off, num_graphs, d_voff, &h->ds->count[CNT_AUX],
+                                                &h->ds->err);
+  st = readback(h, s);
+  if (st != MST_OK) return record(h, st);
+  const uint64_t n_total = h->hs->count[CNT_AUX], m = h->hs->count[CNT_AUX + 1];
+  if (n_total >= (1ULL << 32) || m >= (1ULL << 32)) return record(h, MST_ERR_TOO_LARGE);
   if (m > 0 && (!d_src || !d_dst || !d_w || !d_msf_ids)) return record(h, MST_ERR_INVALID_ARG);
-  const uint32_t n = (uint32_t)voff[num_graphs];
-  // tables + union endpoints
-  Buf tab_b, uni_b, ids_b;
-  const size_t tab_bytes = round_up((num_graphs + 1) * 8, 256) * 2 + round_up(num_graphs * 4, 256);
-  mst_status st = tab_b.alloc(h, tab_bytes, s);
+  const uint32_t n = (uint32_t)n_total;
+  // union endpoints, union ids
+  Buf uni_b, ids_b;
   const uint64_t stride = round_up(m * 4 + 16, 256);
-  if (st == MST_OK) st = uni_b.alloc(h, stride * 2, s);
+  st = uni_b.alloc(h, stride * 2, s);
   const uint64_t cap = m < (uint64_t)n ? m : (uint64_t)n;
   // ids, then (256-byte aligned) the forest size, then 256 bytes on, its weight
   if (st == MST_OK) st = ids_b.alloc(h, round_up(cap * 4, 256) + 512, s);
   if (st != MST_OK) return record(h, st);
-  uint64_t *d_eoff = tab_b.as<uint64_t>();
-  uint64_t *d_voff = (uint64_t *)((char *)tab_b.p + round_up((num_graphs + 1) * 8, 256));
-  uint32_t *d_gn = (uint32_t *)((char *)tab_b.p + 2 * round_up((num_graphs + 1) * 8, 256));
   uint32_t *usrc = uni_b.as<uint32_t>(), *udst = (uint32_t *)((char *)uni_b.p + stride);
   uint32_t *ids = ids_b.as<uint32_t>();
   uint32_t *d_count = (uint32_t *)((char *)ids + round_up(cap * 4, 256));
   u64 *d_sum = (u64 *)((char *)d_count + 256);
-  if (cudaMemcpyAsync(d_eoff, h_edge_off, (num_graphs + 1) * 8, cudaMemcpyHostToDevice, s) != cudaSuccess ||
-      cudaMemcpyAsync(d_voff, voff.data(), (num_graphs + 1) * 8, cudaMemcpyHostToDevice, s) != cudaSuccess ||
-      cudaMemcpyAsync(d_gn, h_n, num_graphs * 4, cudaMemcpyHostToDevice, s) != cudaSuccess ||
-      cudaMemsetAsync(&h->ds->err, 0, 4, s) != cudaSuccess)
-    return record_cuda(h, __LINE__);
   const unsigned grid = (unsigned)std::max<uint64_t>(1, std::min<uint64_t>((m + 2047) / 2048, (uint64_t)h->sms * 8));
   if (m > 0)
-    batch_offset_kernel<<<grid, 256, 0, s>>>(d_src, d_dst, d_eoff, d_voff, usrc, udst, d_gn, num_graphs, m,
+    batch_offset_kernel<<<grid, 256, 0, s>>>(d_src, d_dst, d_edge_off, d_voff, usrc, udst, d_n, num_graphs, m,
                                              &h->ds->err);
   st = readback(h, s);
   if (st != MST_OK) return record(h, st);
   st = solve_device(h, n, m, usrc, udst, d_w, ids, d_count, d_sum, s);
   if (st != MST_OK) return record(h, st);
   if (cudaMemsetAsync(d_total_weight, 0, (size_t)num_graphs * 8, s) != cudaSuccess) return record_cuda(h, __LINE__);
-  batch_seg_kernel<<<(num_graphs + 1 + 255) / 256, 256, 0, s>>>(ids, d_count, d_eoff, num_graphs, d_msf_off);
+  batch_seg_kernel<<<(num_graphs + 1 + 255) / 256, 256, 0, s>>>(ids, d_count, d_edge_off, num_graphs, d_msf_off);
   const unsigned sgrid = (unsigned)std::max<uint64_t>(1, std::min<uint64_t>((cap + 2047) / 2048, (uint64_t)h->sms * 8));
-  batch_split_kernel<<<sgrid, 256, 0, s>>>(ids, d_count, d_eoff, num_graphs, d_w, d_msf_ids, (u64 *)d_total_weight);
+  batch_split_kernel<<<sgrid, 256, 0, s>>>(ids, d_count, d_edge_off, num_graphs, d_w, d_msf_ids, (u64 *)d_total_weight);
   if (cudaStreamSynchronize(s) != cudaSuccess) return record_cuda(h, __LINE__);
   return record(h, MST_OK);
 }

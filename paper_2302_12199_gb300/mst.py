@@ -56,7 +56,7 @@ class MstConfig(ctypes.Structure):
                 ("graph_rounds", ctypes.c_int), ("graph_jump_launches", ctypes.c_int),
                 ("filter_carry", ctypes.c_int), ("filter_split", ctypes.c_int),
                 ("min_edges_sort", ctypes.c_int), ("jump_steps", ctypes.c_uint32),
-                ("tile_filter", ctypes.c_int)]
+                ("tile_filter", ctypes.c_int), ("spin_limit", ctypes.c_uint32)]
 
 
 _P = ctypes.c_void_p
@@ -68,7 +68,7 @@ _SIGNATURES = {
     "mst_destroy": (None, [_P]),
     "mst_set_config": (_I, [_P, ctypes.POINTER(MstConfig)]),
     "mst_status_string": (ctypes.c_char_p, [_I]),
-    "mst_get_error": (_I, [_P]),
+    "mst_get_error": (_I, [_P, _P]),
     "mst_last_cuda_error": (_I, [_P, _P]),
     "mst_workspace_bytes": (_U64, [_U32, _U64, ctypes.POINTER(MstConfig)]),
     "mst_solve": (_I, [_P, _U32, _U64, _P, _P, _P, _P, _P, _P, _P]),
@@ -295,25 +295,46 @@ class Solver:
         return [(outs[i][:cnt].copy(), tot) for i, (cnt, tot) in enumerate(res)]
 
     def solve_batched(self, n_per_graph, edge_off, src: torch.Tensor, dst: torch.Tensor, w: torch.Tensor,
-                      stream=None):
+                      stream=None, capacity: int | None = None):
         """mst_solve_batched: returns (ids, msf_off, totals) device tensors; segment g of ids holds
-        graph-local edge ids."""
+        graph-local edge ids.  The size tables may be host arrays (copied to the device here) or
+        device tensors (uint32/int32 vertex counts, uint64/int64 edge offsets).  `capacity`: the
+        total vertex count when the caller knows it (otherwise it is summed from the table)."""
         import numpy as np
-        n_h = np.ascontiguousarray(n_per_graph, dtype=np.uint32)
-        off_h = np.ascontiguousarray(edge_off, dtype=np.uint64)
-        G = n_h.size
         m = src.numel()
         for t, name in ((src, "src"), (dst, "dst"), (w, "w")):
             _u32(t, name, self.device)
-        cap = max(1, int(np.minimum(np.diff(off_h), np.maximum(n_h.astype(np.int64) - 1, 0)).sum()))
+        if isinstance(n_per_graph, torch.Tensor) and n_per_graph.is_cuda:
+            d_n = n_per_graph.contiguous()
+            G = d_n.numel()
+            n_total = int(capacity) if capacity is not None else int(d_n.to(torch.int64).sum().item())
+        else:
+            n_h = np.ascontiguousarray(n_per_graph, dtype=np.uint32)
+            G = n_h.size
+            n_total = int(capacity) if capacity is not None else int(n_h.astype(np.int64).sum())
+            d_n = torch.from_numpy(n_h.view(np.int32)).to(self.device)
+        if isinstance(edge_off, torch.Tensor) and edge_off.is_cuda:
+            d_off = edge_off.contiguous()
+        else:
+            d_off = torch.from_numpy(np.ascontiguousarray(edge_off, dtype=np.uint64).view(np.int64)).to(self.device)
+        if d_n.dtype not in (torch.int32, torch.uint32) or d_off.dtype not in (torch.int64, torch.uint64):
+            raise TypeError("vertex counts must be 32-bit and edge offsets 64-bit integers")
+        if d_off.numel() != G + 1:
+            raise ValueError("edge_off needs num_graphs + 1 entries")
+        cap = max(1, min(m, n_total))
         ids = torch.empty(cap, dtype=torch.int32, device=self.device)
         msf_off = torch.zeros(G + 1, dtype=torch.int64, device=self.device)
         totals = torch.zeros(max(G, 1), dtype=torch.int64, device=self.device)
-        del m
-        self._check(self.lib.mst_solve_batched(self.h, G, n_h.ctypes.data_as(_P), off_h.ctypes.data_as(_P), _ptr(src),
-                                          _ptr(dst), _ptr(w), _ptr(ids), _ptr(msf_off), _ptr(totals),
-                                          _stream(stream)), "mst_solve_batched")
+        if stream is not None:  # the tables were copied on the current stream
+            stream.wait_stream(torch.cuda.current_stream(self.device))
+        self._check(self.lib.mst_solve_batched(self.h, G, _ptr(d_n), _ptr(d_off), _ptr(src), _ptr(dst), _ptr(w),
+                                               _ptr(ids), _ptr(msf_off), _ptr(totals), _stream(stream)),
+                    "mst_solve_batched")
         return ids, msf_off, totals
+
+    def get_error(self, stream=None) -> int:
+        """mst_get_error: waits for the stream and returns the handle's status code."""
+        return int(self.lib.mst_get_error(self.h, _stream(stream)))
 
     # ----------------------------------------------------------- steps
     def _list(self, u, v, w, ids):

@@ -43,7 +43,7 @@ def test_invalid_arguments_without_device(lib):
     h = ctypes.c_void_p()
     assert lib.mst_create(None, None) == 1
     assert lib.mst_solve(None, 1, 1, None, None, None, None, None, None, None) == 1
-    assert lib.mst_get_error(None) == 1
+    assert lib.mst_get_error(None, None) == 1
     assert lib.mst_solve_host_many(None, 0, None, None) == 1
     assert lib.mst_profile_classes(None, 0) == 1
     assert lib.mst_profile_enable(None, 1) == 1

@@ -431,6 +431,39 @@ def test_step_finalize(step_solver, dev):
     assert tot == int(w[chosen_ids].astype(np.uint64).sum())
 
 
+def test_ordered_scan_wait_that_runs_out_is_an_error(dev):
+    """The ordered output scan is the one place where blocks wait on each
+    other (a tile polls the prefixes its predecessors publish), and that wait
+    is bounded.  With a bound of one poll (config spin_limit = 1) a tile that
+    finds a predecessor not yet published gives up: the call returns
+    MST_ERR_INTERNAL, never a wrong list, and the same handle with the default
+    bound then gives the exact ids."""
+    rng = np.random.default_rng(40)
+    m = 1 << 27  # 2^22 bitmap words: 2048 scan tiles
+    chosen_ids = np.unique(rng.integers(0, m, 300_000)).astype(np.uint32)
+    bits = np.zeros(m // 32, np.uint32)
+    np.bitwise_or.at(bits, chosen_ids >> 5, (np.uint32(1) << (chosen_ids & 31)).astype(np.uint32))
+    d_bits = to_dev(bits, dev)
+    d_w = torch.ones(m, dtype=torch.int32, device=dev)
+    s = Solver(0, spin_limit=1)
+    statuses = []
+    try:
+        for _ in range(12):
+            try:
+                ids, tot = s.finalize(m, d_bits, d_w).to_host()
+                assert np.array_equal(ids, chosen_ids) and tot == chosen_ids.size  # OK means exact
+                statuses.append(0)
+            except MstError as e:
+                assert e.status == 6  # MST_ERR_INTERNAL
+                statuses.append(e.status)
+        assert 6 in statuses, statuses
+        s.configure(spin_limit=1 << 21)
+        ids, tot = s.finalize(m, d_bits, d_w).to_host()
+        assert np.array_equal(ids, chosen_ids) and tot == chosen_ids.size
+    finally:
+        s.close()
+
+
 @pytest.mark.parametrize("case", ["rgg2", "rgg3", "gnm", "dense_tile"])
 def test_step_tile_contract(step_solver, dev, case):
     g, tile = {
@@ -647,17 +680,22 @@ def test_tile_filter_on_and_off_agree(dev, family):
                 s.close()
 
 
-@pytest.mark.parametrize("workload", ["rmat_filter", "rgg2d", "rgg3d", "gnm"])
+@pytest.mark.parametrize("workload", ["rmat_filter", "rmat_boruvka", "rgg2d", "rgg3d", "rgg2d_tile", "rgg3d_tile",
+                                      "gnm"])
 def test_full_size_workloads_equal_kruskal(dev, workload):
     """The benchmark's workloads at their full sizes (RMAT n=2^24, m=2^28 under
-    Filter-Borůvka; RGG2D n=2^22; RGG3D n=2^21; GNM n=2^16, m=2^20), solved in
-    the configuration the benchmark times: the whole forest and its uint64
-    total equal Kruskal's (the oracle finishes the 2^28 edges in tens of
-    seconds, so every output is compared, not a sample)."""
+    Filter-Borůvka and under plain Borůvka; RGG2D n=2^22 and RGG3D n=2^21,
+    with the rounds alone and with tile-local contraction (Section 4.1) on;
+    GNM n=2^16, m=2^20): the whole forest and its uint64 total equal
+    Kruskal's (the oracle finishes the 2^28 edges in tens of seconds, so every
+    output is compared, not a sample)."""
     g, cfg = {
         "rmat_filter": (W.rmat_large, dict(variant="filter")),
+        "rmat_boruvka": (W.rmat_large, dict(variant="boruvka")),
         "rgg2d": (W.rgg2d_large, dict(variant="boruvka")),
         "rgg3d": (W.rgg3d_large, dict(variant="boruvka")),
+        "rgg2d_tile": (W.rgg2d_large, dict(variant="boruvka", tile_contract=1)),
+        "rgg3d_tile": (W.rgg3d_large, dict(variant="boruvka", tile_contract=1)),
         "gnm": (W.gnm_small, dict(variant="boruvka")),
     }[workload]
     g = g()

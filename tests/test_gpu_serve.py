@@ -51,6 +51,46 @@ def test_batched_mix_matches_oracle(dev, cfg):
         s.close()
 
 
+def test_batched_device_tables_and_errors(dev):
+    """The size tables of mst_solve_batched live in device memory: given as
+    device tensors they give each graph its Kruskal forest; an offset table that
+    does not start at 0, or that decreases, is MST_ERR_INVALID_ARG, reported by
+    the call and by mst_get_error on the stream; the handle then solves again."""
+    from paper_2302_12199_gb300.mst import MstError
+    b = W.mix(30, 94, log_lo=5, log_hi=11)
+    exp = oracle_answers(b)
+    src, dst, w = to_dev(b.src, dev), to_dev(b.dst, dev), to_dev(b.w, dev)
+    d_n = to_dev(b.n, dev)
+    d_off = torch.from_numpy(np.asarray(b.edge_off, dtype=np.uint64).view(np.int64)).to(dev)
+    s = Solver(0)
+    try:
+        stream = torch.cuda.Stream(dev)
+        ids, moff, tot = s.solve_batched(d_n, d_off, src, dst, w, stream=stream)
+        assert s.get_error(stream) == 0
+        ids = ids.cpu().numpy().view(np.uint32)
+        moff = moff.cpu().numpy().astype(np.int64)
+        tot = tot.cpu().numpy().view(np.uint64)
+        for g, (kid, ktot) in enumerate(exp):
+            assert np.array_equal(ids[moff[g]:moff[g + 1]], kid) and int(tot[g]) == ktot, g
+        for bad in ("first", "decreasing"):
+            off_bad = np.asarray(b.edge_off, dtype=np.uint64).copy()
+            if bad == "first":
+                off_bad[0] = 1
+            else:  # graph k's end lies before its start
+                k = len(off_bad) // 2
+                off_bad[k] = off_bad[k + 1] + 1
+            with pytest.raises(MstError) as e:
+                s.solve_batched(b.n, off_bad, src, dst, w)
+            assert e.value.status == 1, bad
+            assert s.get_error() == 1
+        ids2, moff2, tot2 = s.solve_batched(b.n, b.edge_off, src, dst, w)
+        assert s.get_error() == 0
+        assert torch.equal(moff2.cpu(), torch.from_numpy(moff)) and np.array_equal(
+            tot2.cpu().numpy().view(np.uint64), tot)
+    finally:
+        s.close()
+
+
 def test_full_size_batch_matches_oracle(dev):
     """The batched benchmark's batch at its full size (4096 graphs, n
     log-uniform in [2^8, 2^16], about 335 M edges), under the configurations
@@ -145,6 +185,14 @@ def test_served_responses_alone_and_in_the_mix(dev):
         assert st.batches >= 2 and sum(st.batch_sizes) == arr.size
         assert max(st.batch_sizes) <= 16
         assert np.all(st.latency > 0)
+        # a burst of requests all waiting at once: both slots take a batch, so
+        # two batches are on the device together, and every response is still
+        # the graph's own forest
+        burst = np.zeros(64)
+        picks_b = np.random.default_rng(11).integers(0, len(pool), burst.size)
+        stb = server.run(pool, picks_b, burst, expected=expected)
+        assert stb.requests == burst.size and stb.mismatches == 0
+        assert stb.max_in_flight >= 2 and stb.batches >= 2
         # the same server serves a second stream
         arr2 = poisson_arrivals(5000.0, 0.02, seed=7)
         picks2 = np.random.default_rng(8).integers(0, len(pool), arr2.size)

@@ -90,6 +90,23 @@ def test_kruskal_equals_prim(family):
     assert np.array_equal(kid, pid) and ktot == ptot
 
 
+@pytest.mark.parametrize("threads", [1, 3, 8, 64])
+def test_parallel_sort_kruskal_equals_kruskal(threads):
+    """The CPU-baseline Kruskal whose sort runs on several threads returns the
+    same forest as the plain one: heavy weight ties (w in [1, 255], where the
+    id order inside a weight must survive the threaded scatter), 32-bit weights
+    (all four radix passes), self-loops, parallel edges, more threads than
+    edges, and the empty graph."""
+    cases = [W.rmat(14, 200000, 31), W.gnm(20000, 100000, 32, wmin=1, wmax=0xFFFFFFFF), W.rgg(2, 5000, 8.0, 33),
+             W.Graph(5, np.array([0, 1, 1, 2, 4], np.uint32), np.array([1, 1, 0, 2, 3], np.uint32),
+                     np.array([7, 1, 7, 3, 2], np.uint32)),
+             W.Graph(3, np.empty(0, np.uint32), np.empty(0, np.uint32), np.empty(0, np.uint32))]
+    for g in cases:
+        kid, ktot = oracle.kruskal(g.n, g.src, g.dst, g.w)
+        pid, ptot = oracle.kruskal_par(g.n, g.src, g.dst, g.w, threads)
+        assert np.array_equal(kid, pid) and ktot == ptot
+
+
 @pytest.mark.parametrize("seed", [1, 2, 3])
 def test_kruskal_satisfies_cut_and_cycle_properties(seed):
     rng = np.random.default_rng(seed)
