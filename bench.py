@@ -58,18 +58,22 @@ WORKLOADS = {
 }
 
 
-# DRAM traffic of the dominant kernel, from one single-pass ncu capture of the
-# default workload (dram__bytes_read.sum + dram__bytes_write.sum over the
-# filter launches of one timed solve, divided by the algorithmic bytes the
-# library's profiler counted for them).  A launch's traffic is taken as that
-# ratio times its algorithmic bytes.  The ratio holds only for the kernel source it was measured
-# on: when the source region below hashes differently, traffic is reported as
-# null until it is captured again.
+# DRAM traffic of the dominant kernel, from one ncu capture of the
+# filter launches of a timed solve at RMAT scale 22 (n=2^22, m=2^26; the
+# full-size workload holds tens of GB on the device, too much for a capture
+# of many passes): dram__bytes_read.sum + dram__bytes_write.sum over those
+# launches divided by the algorithmic bytes the library's profiler counted for
+# them.  A full-size launch's traffic is taken as that ratio times its
+# algorithmic bytes (at scale 24 the 64 MB label array shares the L2 with a
+# longer stream, so the true ratio there is somewhat higher).  The ratio holds
+# only for the kernel source it was measured on: when the source region below
+# hashes differently, traffic is reported as null until it is captured again.
 TRAFFIC = {
     "class": "filter",
-    "kernel": "compact_tma_kernel<CM_FILTER>",
-    "dram_per_algorithmic_byte": 1.354,
-    "source_sha256": "6f730b384a84122742ec9b298f1ff24e57921fcab8966ae0c4d2b6414b44972b",
+    "kernel": "filter_warp_kernel<CM_FILTER>",
+    "dram_per_algorithmic_byte": 1.209,
+    "measured_on": "RMAT n=2^22 m=2^26, all 5 filter launches of one timed solve",
+    "source_sha256": "dc6afd65e3c4f333ed37cdb3095f13cb51bff708c5e396fb095dca3f9539a475",
 }
 TRAFFIC_SOURCE = ("paper_2302_12199_gb300/csrc/kernels.cu",
                   "__device__ __forceinline__ uint32_t keep_flags",
@@ -515,7 +519,9 @@ def gpu_main(args, rank: int, world: int, local_rank: int):
                 "min_bytes_per_launch": kmin / nl if nl else None,
                 "achieved_min": achieved_min, "frac_min": achieved_min / peaks["hbm_gbs"],
                 "traffic": traffic,
-                "traffic_source": (f"ncu DRAM bytes of {TRAFFIC['kernel']} (kernel source sha256 "
+                "traffic_source": (f"ncu DRAM bytes / algorithmic bytes of {TRAFFIC['kernel']} on "
+                                   f"{TRAFFIC['measured_on']} ({TRAFFIC['dram_per_algorithmic_byte']}), times this "
+                                   f"launch's algorithmic bytes (kernel source sha256 "
                                    f"{TRAFFIC['source_sha256'][:12]})") if traffic is not None else None,
                 "time_share": kms / ms if ms > 0 else None}
     effective = all_bytes / args.steps / (ms / args.steps / 1e3) / 1e9

@@ -92,3 +92,53 @@ def test_struct_layouts_match_the_header(tmp_path):
         assert got[(cname, "size")] == ctypes.sizeof(py), cname
         for field, _ in py._fields_:
             assert got[(cname, field)] == getattr(py, field).offset, (cname, field)
+
+
+def _header_prototypes():
+    """{name: (return class, [parameter classes])} from include/mst.h, where a
+    class is 'ptr' (any pointer or handle), 'u32', 'u64', 'int' (int and enums)
+    or 'f32'."""
+    import os
+    import re
+    path = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "mst.h")
+    text = re.sub(r"/\*.*?\*/", " ", open(path).read(), flags=re.S)
+    text = re.sub(r"#[^\n]*", " ", text)
+    out = {}
+    for m in re.finditer(r"([A-Za-z_][\w\s\*]*?)\b(mst_[a-z_]+)\s*\(([^;{]*?)\)\s*;", text):
+        ret, name, params = m.group(1), m.group(2), m.group(3)
+
+        def cls(decl):
+            decl = decl.strip()
+            if "*" in decl or decl.startswith("mst_handle"):
+                return "ptr"
+            if decl.startswith("uint32_t"):
+                return "u32"
+            if decl.startswith("uint64_t"):
+                return "u64"
+            if decl.startswith("float"):
+                return "f32"
+            if decl.startswith("void"):
+                return "void"
+            return "int"  # int, mst_status
+        plist = [] if params.strip() in ("", "void") else [cls(p) for p in params.split(",")]
+        out[name] = (cls(ret.split()[-1] if "*" not in ret else "*"), plist)
+    return out
+
+
+def test_binding_signatures_match_the_header():
+    """Every declared function's ctypes signature in the binding has the
+    header's parameter count and the same class (pointer, 32-bit, 64-bit, int)
+    for every parameter and for the result."""
+    def cls(t):
+        if t is None:
+            return "void"
+        if t in (ctypes.c_void_p, ctypes.c_char_p) or getattr(t, "_type_", None) is not None and \
+                isinstance(t, type) and issubclass(t, ctypes._Pointer):
+            return "ptr"
+        return {ctypes.c_uint32: "u32", ctypes.c_uint64: "u64", ctypes.c_int: "int", ctypes.c_float: "f32"}[t]
+    protos = _header_prototypes()
+    assert set(protos) == set(mst.declared_symbols())
+    for name, (ret, params) in protos.items():
+        res, args = mst._SIGNATURES[name]
+        assert [cls(a) for a in args] == params, name
+        assert cls(res) == ret, name
