@@ -102,6 +102,11 @@ typedef struct {
                                   wait gives up (>= 1; default 2^21, about a second); a wait that runs out
                                   makes the call return MST_ERR_INTERNAL.  Small values exist to exercise
                                   that error path */
+  uint32_t block_threads;      /* threads per block of the relabel / partition compactions and the hooking
+                                  kernel: 128, 256 or 512 (0 = 256) */
+  uint32_t items_per_thread;   /* edges (or vertices) per thread of those kernels: 4, 8 or 16 (0 = 8); a
+                                  block handles block_threads x items_per_thread per tile.  Both are
+                                  autotuner choices; every shape computes the same forest */
 } mst_config;
 
 /* Fills *cfg with the defaults (Borůvka variant, automatic dedupe, pivot sample
@@ -242,8 +247,8 @@ mst_status mst_profile_get(mst_handle h, int kind, mst_kernel_stats *out);
  * every step can be checked on its own.  Edge lists are SoA (u, v, w, id) of
  * length m; d_id may be NULL, meaning id = index.  "key" means the uint64
  * (w << 32) | id.  The list-producing steps write their survivors in an
- * unspecified order (each block of 2048 input edges keeps its order, blocks
- * land in the order they finish); the set of survivors is exact.
+ * unspecified order (tiles land in the order they finish); the set of
+ * survivors is exact.
  * -------------------------------------------------------------------- */
 
 /* minEdges (Alg. 1; Section 2.3): d_best[c] = minimum key over the

@@ -25,6 +25,12 @@ DEFAULT_CANDIDATES: Tuple[dict, ...] = (
     dict(variant="boruvka", dedupe="none", tile_contract=0, min_edges_sort=1),
 )
 
+# Tile shapes of the compaction and hook kernels: threads per block x items
+# per thread.  Tuned on top of the best configuration above (every shape
+# computes the same forest).
+SHAPE_CANDIDATES: Tuple[dict, ...] = tuple(dict(block_threads=b, items_per_thread=i)
+                                           for b in (128, 256, 512) for i in (4, 8, 16))
+
 _cache: Dict[str, dict] = {}
 
 
@@ -33,26 +39,40 @@ def label(cfg: dict) -> str:
 
 
 def autotune(trial: Callable[[dict], float], candidates: Iterable[dict] = DEFAULT_CANDIDATES, reps: int = 2,
-             key: str | None = None) -> Tuple[dict, List[Tuple[str, float]]]:
-    """Returns (best configuration, [(label, best seconds)] for every candidate).
+             key: str | None = None,
+             shapes: Iterable[dict] | None = SHAPE_CANDIDATES) -> Tuple[dict, List[Tuple[str, float]]]:
+    """Returns (best configuration, [(label, best seconds)] for every trial).
 
     trial(cfg) runs one solve of the workload with configuration cfg and
     returns its duration in seconds (the caller times it on the device).  Each
     candidate gets one untimed run and `reps` timed runs; its score is the
-    fastest timed run.  With `key`, the choice is remembered for the process
-    and later calls with the same key return it without trials."""
+    fastest timed run.  The candidates are tried first; then each of `shapes`
+    (kernel tile shapes; None or empty: none) is tried on top of the best of
+    them.  With `key`, the choice is remembered for the process and later
+    calls with the same key return it without trials."""
     if key is not None and key in _cache:
         return dict(_cache[key]), []
     results: List[Tuple[str, float]] = []
     best, best_t = None, float("inf")
-    for cfg in candidates:
+
+    def run(cfg):
+        nonlocal best, best_t
         trial(cfg)
         t = min(trial(cfg) for _ in range(max(1, reps)))
         results.append((label(cfg), t))
         if t < best_t:
             best, best_t = dict(cfg), t
+
+    for cfg in candidates:
+        run(cfg)
     if best is None:
         raise ValueError("autotune needs at least one candidate")
+    base = dict(best)
+    defaults = dict(block_threads=256, items_per_thread=8)  # the shape a configuration without one gets
+    for shape in shapes or ():
+        if all(base.get(k, defaults.get(k)) == v for k, v in shape.items()):
+            continue  # already timed
+        run({**base, **shape})
     if key is not None:
         _cache[key] = dict(best)
     return best, results

@@ -99,6 +99,7 @@ struct CompactArgs {
   uint32_t *max_w;         // if set: atomicMax of every input weight (key layout)
   uint32_t *cur_u, *cur_v; // if set: cur_u[id], cur_v[id] = the survivor's written ends
   ScanState st;
+  int shape;               // tile shape of the relabel / partition compaction (see shape_index)
 };
 
 struct HookArgs {
@@ -116,7 +117,25 @@ struct HookArgs {
   uint32_t *err;
   u64 *wsum;               // if set: the weights of the chosen edges are added into these
                            //   WSUM_SLOTS counters (one add per warp, spread over the slots)
+  int shape;               // tile shape (see shape_index)
 };
+
+// Tile shapes of the compaction and hook kernels, as the `shape` field of
+// their argument structs: 0 is the default, 256 threads per block x 8 items
+// per thread (so a zero-initialised struct gets it); 1 + 3 * b + i is the b-th
+// of {128, 256, 512} threads with the i-th of {4, 8, 16} items per thread.
+constexpr int SHAPE_COUNT = 10;
+inline int shape_index(uint32_t block_threads, uint32_t items_per_thread) {
+  if (block_threads == 0 && items_per_thread == 0) return 0;
+  const uint32_t bt = block_threads ? block_threads : 256, it = items_per_thread ? items_per_thread : 8;
+  const int b = bt == 128 ? 0 : bt == 256 ? 1 : bt == 512 ? 2 : -1;
+  const int i = it == 4 ? 0 : it == 8 ? 1 : it == 16 ? 2 : -1;
+  return (b < 0 || i < 0) ? -1 : 1 + 3 * b + i;
+}
+inline uint32_t shape_tile(int shape) {
+  static const uint32_t b[3] = {128, 256, 512}, i[3] = {4, 8, 16};
+  return shape <= 0 ? 2048u : b[(shape - 1) / 3] * i[(shape - 1) % 3];
+}
 
 // Counters the kernels that choose MSF edges add the chosen weights into, so
 // that the forest's total needs no gather of w at the end.

@@ -5,12 +5,13 @@
 // total order (paper Section 2.3: ties broken consistently so that the MST is
 // unique); id is the edge's index in the caller's input.
 //
-// Stream compaction (relabel, partition, filter, dedupe, active vertices) is
-// one pass per list: each 256-thread block takes a tile of 2048 items, keeps
-// the tile's survivors in order, and claims its output range with one atomic
-// add.  Tiles therefore land in an unspecified order; nothing downstream
-// depends on list order, because edges are keyed by id and a vertex finds its
-// chosen edge through the input arrays.  The output ids (finalize) are the one
+// Stream compaction (relabel, partition, dedupe, active vertices) is one pass
+// per list: each block takes a tile of B x I items (256 x 8 by default; the
+// shape is a run-time choice), stages the tile's survivors in shared memory,
+// and claims its output range with one atomic add.  The filter pass streams
+// per warp instead (filter_warp_kernel).  Lists therefore come out in an
+// unspecified order; nothing downstream depends on list order, because edges
+// are keyed by id and a vertex finds its chosen edge through the input arrays.  The output ids (finalize) are the one
 // ordered compaction: a decoupled look-back scan (Merrill & Garland, 2016).
 // Every wait is bounded.
 #include <algorithm>
@@ -40,19 +41,27 @@ __device__ __forceinline__ void st_relaxed(u64 *p, u64 v) {
   asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
 
-// Striped item layout inside a tile of TILE items: item k (0..7) of thread t
-// sits at tile offset (k / 4) * (BLOCK * 4) + 4 * t + k % 4.  Each warp-wide
-// 16-byte load then covers 512 contiguous bytes (whole sectors, used once).
-// Output order is tile order: chunk 0 (k < 4) of every thread, then chunk 1.
+// Striped item layout inside a tile of B * I items (B threads, I items each, I
+// a multiple of 4): item k of thread t sits at tile offset
+// (k / 4) * (B * 4) + 4 * t + k % 4.  Each warp-wide 16-byte load then covers
+// 512 contiguous bytes (whole sectors, used once).  The defaults are the
+// shape of the kernels that do not take one (BLOCK x ITEMS).
+template <int B = BLOCK>
 __device__ __forceinline__ uint32_t item_off(int k) {
-  return (uint32_t)((k >> 2) * (BLOCK * 4) + 4 * threadIdx.x + (k & 3));
+  return (uint32_t)((k >> 2) * (B * 4) + 4 * threadIdx.x + (k & 3));
 }
 
-__device__ __forceinline__ void load_striped(const uint32_t *p, uint64_t tile_base, uint32_t (&x)[ITEMS]) {
+template <int B = BLOCK, int I = ITEMS>
+__device__ __forceinline__ void load_striped(const uint32_t *p, uint64_t tile_base, uint32_t (&x)[I]) {
   const uint4 *q = reinterpret_cast<const uint4 *>(p + tile_base);
-  const uint4 a = __ldg(q + threadIdx.x), b = __ldg(q + BLOCK + threadIdx.x);
-  x[0] = a.x; x[1] = a.y; x[2] = a.z; x[3] = a.w;
-  x[4] = b.x; x[5] = b.y; x[6] = b.z; x[7] = b.w;
+#pragma unroll
+  for (int c = 0; c < I / 4; ++c) {
+    const uint4 t = __ldg(q + c * B + threadIdx.x);
+    x[4 * c] = t.x;
+    x[4 * c + 1] = t.y;
+    x[4 * c + 2] = t.z;
+    x[4 * c + 3] = t.w;
+  }
 }
 
 // Per-thread counts of kept items in the two chunks, packed for one scan.
@@ -99,7 +108,9 @@ __device__ __forceinline__ u64 splitmix64_at(u64 state, u64 i) {
   return mix64(state + (i + 1ULL) * 0x9e3779b97f4a7c15ULL);
 }
 
-// Exclusive block-wide scan of one uint32 per thread (BLOCK threads).
+// Exclusive block-wide scan of one uint32 per thread (B threads; s_warp holds
+// B / 32 + 1 words).
+template <int B = BLOCK>
 __device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t x, uint32_t &total, uint32_t *s_warp) {
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   uint32_t incl = x;
@@ -111,18 +122,18 @@ __device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t x, uint32_t &t
   if (lane == 31) s_warp[wid] = incl;
   __syncthreads();
   if (wid == 0) {
-    const uint32_t wv = lane < BLOCK / 32 ? s_warp[lane] : 0u;
+    const uint32_t wv = lane < B / 32 ? s_warp[lane] : 0u;
     uint32_t wi = wv;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
       const uint32_t y = __shfl_up_sync(0xffffffffu, wi, o);
       if (lane >= o) wi += y;
     }
-    if (lane < BLOCK / 32) s_warp[lane] = wi - wv;
-    if (lane == BLOCK / 32 - 1) s_warp[BLOCK / 32] = wi;
+    if (lane < B / 32) s_warp[lane] = wi - wv;
+    if (lane == B / 32 - 1) s_warp[B / 32] = wi;
   }
   __syncthreads();
-  total = s_warp[BLOCK / 32];
+  total = s_warp[B / 32];
   return s_warp[wid] + incl - x;
 }
 
@@ -317,14 +328,6 @@ __device__ __forceinline__ u64 hash_lookup(const HashSlot *t, uint64_t mask, u64
 
 // ---------------------------------------------------------------- compaction
 
-// Bit k set iff item k of this thread's striped tile (base tb) is below m.
-__device__ __forceinline__ uint32_t valid_items(uint64_t tb, uint64_t m) {
-  uint32_t valid = 0;
-#pragma unroll
-  for (int k = 0; k < ITEMS; ++k) valid |= (tb + item_off(k) < m ? 1u : 0u) << k;
-  return valid;
-}
-
 // Keep flags of a thread's ITEMS items for a compaction mode (see
 // CompactMode); relabels eu/ev in place where the mode relabels.  Bit k =
 // item k; only items whose bit is set in `valid` can be kept.
@@ -400,20 +403,21 @@ __device__ __forceinline__ uint32_t keep_flags(const CompactArgs &a, uint32_t va
   return keep;
 }
 
-// Writes the kept items of a tile to shared memory at their tile-local output
-// positions, stores them coalesced at obase, then runs the post actions on the
-// survivors: relax best[] (the next round's minEdges, fused) and/or insert the
-// pair into the dedupe hash table.
-__device__ __forceinline__ void emit_survivors(const CompactArgs &a, uint32_t keep, uint32_t excl, uint32_t totp,
-                                               uint64_t obase, const uint32_t (&eu)[ITEMS],
-                                               const uint32_t (&ev)[ITEMS], const uint32_t (&ew)[ITEMS],
-                                               const uint32_t (&ei)[ITEMS], uint32_t *s_u, uint32_t *s_v,
-                                               uint32_t *s_w, uint32_t *s_id) {
-  const uint32_t total = (totp & 0xffffu) + (totp >> 16);
+// Writes the kept items of a tile (B threads, I items each) to shared memory
+// at their tile-local output positions (thread-major: thread t's kept items,
+// in item order, follow those of threads 0..t-1; `excl` is the exclusive scan
+// of the per-thread kept counts), stores them coalesced at obase, then runs
+// the post actions on the survivors: relax best[] (the next round's minEdges,
+// fused) and/or insert the pair into the dedupe hash table.
+template <int B, int I>
+__device__ __forceinline__ void emit_survivors(const CompactArgs &a, uint32_t keep, uint32_t excl, uint32_t total,
+                                               uint64_t obase, const uint32_t (&eu)[I], const uint32_t (&ev)[I],
+                                               const uint32_t (&ew)[I], const uint32_t (&ei)[I], uint32_t *s_u,
+                                               uint32_t *s_v, uint32_t *s_w, uint32_t *s_id) {
 #pragma unroll
-  for (int k = 0; k < ITEMS; ++k) {
+  for (int k = 0; k < I; ++k) {
     if (keep >> k & 1) {
-      const uint32_t lp = local_pos(keep, k, excl, totp);
+      const uint32_t lp = excl + (uint32_t)__popc(keep & ((1u << k) - 1u));
       s_u[lp] = eu[k];
       s_v[lp] = ev[k];
       s_w[lp] = ew[k];
@@ -421,14 +425,14 @@ __device__ __forceinline__ void emit_survivors(const CompactArgs &a, uint32_t ke
     }
   }
   __syncthreads();
-  for (uint32_t i = threadIdx.x; i < total; i += BLOCK) {
+  for (uint32_t i = threadIdx.x; i < total; i += B) {
     a.out.u[obase + i] = s_u[i];
     a.out.v[obase + i] = s_v[i];
     a.out.w[obase + i] = s_w[i];
     a.out.id[obase + i] = s_id[i];
   }
   if (a.cur_u) {  // ends by id, for the hook of the round that relaxes this list
-    for (uint32_t i = threadIdx.x; i < total; i += BLOCK) {
+    for (uint32_t i = threadIdx.x; i < total; i += B) {
       a.cur_u[s_id[i]] = s_u[i];
       a.cur_v[s_id[i]] = s_v[i];
     }
@@ -436,12 +440,12 @@ __device__ __forceinline__ void emit_survivors(const CompactArgs &a, uint32_t ke
   // post actions read the survivors back from shared memory (coalesced; the
   // loaded edges' registers are dead by now)
   if (a.best) {
-    for (uint32_t i0 = 0; i0 < total; i0 += 4 * BLOCK) {
+    for (uint32_t i0 = 0; i0 < total; i0 += 4 * B) {
       uint32_t x[4], y[4];
       u64 kx[4], ky[4], cx[4], cy[4];
 #pragma unroll
       for (int k = 0; k < 4; ++k) {
-        const uint32_t i = i0 + k * BLOCK + threadIdx.x;
+        const uint32_t i = i0 + k * B + threadIdx.x;
         const bool ok = i < total;
         x[k] = ok ? s_u[i] : 0u;
         y[k] = ok ? s_v[i] : 0u;
@@ -458,7 +462,7 @@ __device__ __forceinline__ void emit_survivors(const CompactArgs &a, uint32_t ke
     }
   }
   if (a.hash_insert) {
-    for (uint32_t i = threadIdx.x; i < total; i += BLOCK)
+    for (uint32_t i = threadIdx.x; i < total; i += B)
       if (!hash_insert(a.table, a.tmask, pair_of(s_u[i], s_v[i]), edge_key(s_w[i], s_id[i])))
         atomicOr(a.st.err, ERR_HASH);
   }
@@ -469,32 +473,65 @@ __device__ __forceinline__ u64 compact_pivot(const CompactArgs &a, int mode) {
                                                                          : 0ULL;
 }
 
-// One stream-compaction pass over an edge list, one tile per block.
-template <int MODE, bool VEC>
-__global__ void __launch_bounds__(BLOCK, 4) compact_kernel(CompactArgs a) {
-  __shared__ uint32_t s_u[TILE], s_v[TILE], s_w[TILE], s_id[TILE];
-  __shared__ uint32_t s_warp[BLOCK / 32 + 1];
+// Bit k set iff item k of this thread's striped tile (base tb) is below m.
+template <int B, int I>
+__device__ __forceinline__ uint32_t valid_items_s(uint64_t tb, uint64_t m) {
+  uint32_t valid = 0;
+#pragma unroll
+  for (int k = 0; k < I; ++k) valid |= (tb + item_off<B>(k) < m ? 1u : 0u) << k;
+  return valid;
+}
+
+// Tile shapes the compaction and hook kernels are built for (threads per
+// block B, items per thread I), chosen at run time (mst_config block_threads /
+// items_per_thread).  Launch bounds come from a register budget per thread
+// that each kernel needs at I items (measured with -Xptxas -v: the budgets
+// below build without spills): resident blocks = 64K registers / (B x budget),
+// at least 1 and at most 2048 threads.
+template <int B, int I>
+struct Shape {
+  static constexpr int T = B * I;  // items per tile
+  static constexpr int minb(int regs) {
+    const int b = 65536 / (B * regs), cap = 2048 / B;
+    return b < 1 ? 1 : (b > cap ? cap : b);
+  }
+  // budgets: the compaction, the persistent TMA compaction, the hook with and
+  // without the far end packed in the key
+  static constexpr int compact_regs = I <= 8 ? 64 : 128;
+  static constexpr int tma_regs = I <= 4 ? 64 : (I <= 8 ? 80 : 128);
+  static constexpr int hook_packed_regs = I <= 4 ? 32 : (I <= 8 ? 40 : 72);
+  static constexpr int hook_regs = I <= 4 ? 64 : (I <= 8 ? 80 : 168);
+};
+
+// One stream-compaction pass over an edge list, one tile of B * I items per
+// block; the staging buffer (16 bytes per item) is dynamic shared memory.
+template <int MODE, bool VEC, int B, int I>
+__global__ void __launch_bounds__(B, Shape<B, I>::minb(Shape<B, I>::compact_regs)) compact_kernel(CompactArgs a) {
+  constexpr int T = Shape<B, I>::T;
+  extern __shared__ __align__(16) uint32_t s_stage[];  // u, v, w, id: T each
+  __shared__ uint32_t s_warp[B / 32 + 1];
   __shared__ uint32_t s_base[1];
+  uint32_t *s_u = s_stage, *s_v = s_stage + T, *s_w = s_stage + 2 * T, *s_id = s_stage + 3 * T;
 
   const uint64_t m = a.m_dev ? *a.m_dev : a.m;
-  const uint64_t tb = (uint64_t)blockIdx.x * TILE;
+  const uint64_t tb = (uint64_t)blockIdx.x * T;
   if (tb >= m) return;
 
-  uint32_t eu[ITEMS], ev[ITEMS], ew[ITEMS], ei[ITEMS];
-  if (VEC && tb + TILE <= m) {
-    load_striped(a.in.u, tb, eu);
-    load_striped(a.in.v, tb, ev);
-    load_striped(a.in.w, tb, ew);
+  uint32_t eu[I], ev[I], ew[I], ei[I];
+  if (VEC && tb + T <= m) {
+    load_striped<B, I>(a.in.u, tb, eu);
+    load_striped<B, I>(a.in.v, tb, ev);
+    load_striped<B, I>(a.in.w, tb, ew);
     if (a.in.id) {
-      load_striped(a.in.id, tb, ei);
+      load_striped<B, I>(a.in.id, tb, ei);
     } else {
 #pragma unroll
-      for (int k = 0; k < ITEMS; ++k) ei[k] = (uint32_t)(tb + item_off(k));
+      for (int k = 0; k < I; ++k) ei[k] = (uint32_t)(tb + item_off<B>(k));
     }
   } else {
 #pragma unroll
-    for (int k = 0; k < ITEMS; ++k) {
-      const uint64_t j = tb + item_off(k);
+    for (int k = 0; k < I; ++k) {
+      const uint64_t j = tb + item_off<B>(k);
       if (j < m) {
         eu[k] = __ldg(a.in.u + j);
         ev[k] = __ldg(a.in.v + j);
@@ -505,19 +542,20 @@ __global__ void __launch_bounds__(BLOCK, 4) compact_kernel(CompactArgs a) {
       }
     }
   }
-  const uint32_t keep = keep_flags<MODE>(a, valid_items(tb, m), compact_pivot(a, MODE), eu, ev, ew, ei);
+  const uint32_t valid = valid_items_s<B, I>(tb, m);
+  const uint32_t keep = keep_flags<MODE>(a, valid, compact_pivot(a, MODE), eu, ev, ew, ei);
   if (a.max_w) {  // largest weight of the input, folded into this pass
     uint32_t mx = 0;
 #pragma unroll
-    for (int k = 0; k < ITEMS; ++k) mx = max(mx, tb + item_off(k) < m ? ew[k] : 0u);
+    for (int k = 0; k < I; ++k) mx = max(mx, (valid >> k & 1) ? ew[k] : 0u);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
     if ((threadIdx.x & 31) == 0 && mx > __ldca(a.max_w)) atomicMax(a.max_w, mx);  // rarely true after a few tiles
   }
-  uint32_t totp;
-  const uint32_t excl = block_exclusive_scan(packed_counts(keep), totp, s_warp);
-  const uint64_t obase = tile_claim(a.st.total, (totp & 0xffffu) + (totp >> 16), s_base);
-  emit_survivors(a, keep, excl, totp, obase, eu, ev, ew, ei, s_u, s_v, s_w, s_id);
+  uint32_t total;
+  const uint32_t excl = block_exclusive_scan<B>((uint32_t)__popc(keep), total, s_warp);
+  const uint64_t obase = tile_claim(a.st.total, total, s_base);
+  emit_survivors<B, I>(a, keep, excl, total, obase, eu, ev, ew, ei, s_u, s_v, s_w, s_id);
 }
 
 // ------------------------------------------------ TMA-pipelined compaction
@@ -532,8 +570,9 @@ __global__ void __launch_bounds__(BLOCK, 4) compact_kernel(CompactArgs a) {
 constexpr int TMA_STAGES = 1;
 constexpr uint32_t MBAR_SPIN_LIMIT = 1u << 24;
 
+template <int T>
 struct __align__(16) EdgeStage {
-  uint32_t u[TILE], v[TILE], w[TILE], id[TILE];
+  uint32_t u[T], v[T], w[T], id[T];
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -574,9 +613,10 @@ __device__ __forceinline__ void bulk_load(void *dst, const void *src, uint32_t b
 }
 
 // Issues the bulk copies of full tile `tile` into stage `st` (one thread).
-__device__ __forceinline__ void issue_tile(const CompactArgs &a, uint64_t tile, EdgeStage *st, u64 *bar) {
-  const uint32_t bytes = TILE * 4;
-  const uint64_t off = tile * TILE;
+template <int T>
+__device__ __forceinline__ void issue_tile(const CompactArgs &a, uint64_t tile, EdgeStage<T> *st, u64 *bar) {
+  const uint32_t bytes = T * 4;
+  const uint64_t off = tile * T;
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // order the stage's earlier generic reads
   mbar_arrive_expect_tx(bar, (a.in.id ? 4u : 3u) * bytes);
   bulk_load(st->u, a.in.u + off, bytes, bar);
@@ -585,25 +625,36 @@ __device__ __forceinline__ void issue_tile(const CompactArgs &a, uint64_t tile, 
   if (a.in.id) bulk_load(st->id, a.in.id + off, bytes, bar);
 }
 
-__device__ __forceinline__ void read_striped_smem(const uint32_t *p, uint32_t (&x)[ITEMS]) {
+template <int B, int I>
+__device__ __forceinline__ void read_striped_smem(const uint32_t *p, uint32_t (&x)[I]) {
   const uint4 *q = reinterpret_cast<const uint4 *>(p);
-  const uint4 lo = q[threadIdx.x], hi = q[BLOCK + threadIdx.x];
-  x[0] = lo.x; x[1] = lo.y; x[2] = lo.z; x[3] = lo.w;
-  x[4] = hi.x; x[5] = hi.y; x[6] = hi.z; x[7] = hi.w;
+#pragma unroll
+  for (int c = 0; c < I / 4; ++c) {
+    const uint4 t = q[c * B + threadIdx.x];
+    x[4 * c] = t.x;
+    x[4 * c + 1] = t.y;
+    x[4 * c + 2] = t.z;
+    x[4 * c + 3] = t.w;
+  }
 }
 
-template <int MODE>
-__global__ void __launch_bounds__(BLOCK, 3 * 256 / BLOCK) compact_tma_kernel(CompactArgs a) {
+// Input stages plus one output stage of T items.
+template <int B, int I>
+constexpr size_t tma_smem_bytes() { return sizeof(EdgeStage<B * I>) * (TMA_STAGES + 1); }
+
+template <int MODE, int B, int I>
+__global__ void __launch_bounds__(B, Shape<B, I>::minb(Shape<B, I>::tma_regs)) compact_tma_kernel(CompactArgs a) {
+  constexpr int T = Shape<B, I>::T;
   extern __shared__ __align__(128) unsigned char smem_dyn[];
-  EdgeStage *stage = reinterpret_cast<EdgeStage *>(smem_dyn);  // TMA_STAGES input stages + 1 output stage
-  EdgeStage *out = stage + TMA_STAGES;
+  EdgeStage<T> *stage = reinterpret_cast<EdgeStage<T> *>(smem_dyn);  // TMA_STAGES input stages + 1 output stage
+  EdgeStage<T> *out = stage + TMA_STAGES;
   __shared__ __align__(8) u64 mbar[TMA_STAGES];
-  __shared__ uint32_t s_warp[BLOCK / 32 + 1];
+  __shared__ uint32_t s_warp[B / 32 + 1];
   __shared__ uint32_t s_base[1];
   __shared__ uint32_t s_abort;
 
   const uint64_t m = a.m_dev ? *a.m_dev : a.m;
-  const uint64_t ntiles = (m + TILE - 1) / TILE, nfull = m / TILE;
+  const uint64_t ntiles = (m + T - 1) / T, nfull = m / T;
   const uint64_t G = gridDim.x;
   if (threadIdx.x == 0) {
     for (int s = 0; s < TMA_STAGES; ++s) mbar_init(&mbar[s], 1);
@@ -611,7 +662,7 @@ __global__ void __launch_bounds__(BLOCK, 3 * 256 / BLOCK) compact_tma_kernel(Com
     s_abort = 0;
     for (int s = 0; s < TMA_STAGES; ++s) {
       const uint64_t tile = blockIdx.x + (uint64_t)s * G;
-      if (tile < nfull) issue_tile(a, tile, &stage[s], &mbar[s]);
+      if (tile < nfull) issue_tile<T>(a, tile, &stage[s], &mbar[s]);
     }
   }
   __syncthreads();
@@ -621,31 +672,31 @@ __global__ void __launch_bounds__(BLOCK, 3 * 256 / BLOCK) compact_tma_kernel(Com
     const uint64_t tile = blockIdx.x + it * G;
     if (tile >= ntiles) break;
     const int si = (int)(it % TMA_STAGES);
-    EdgeStage *st = &stage[si];
-    const uint64_t tb = tile * TILE;
-    uint32_t eu[ITEMS], ev[ITEMS], ew[ITEMS], ei[ITEMS];
+    EdgeStage<T> *st = &stage[si];
+    const uint64_t tb = tile * T;
+    uint32_t eu[I], ev[I], ew[I], ei[I];
     if (tile < nfull) {
       if (!mbar_wait_bounded(&mbar[si], (uint32_t)((it / TMA_STAGES) & 1))) atomicOr(&s_abort, 1u);
       __syncthreads();
       if (s_abort) break;
-      read_striped_smem(st->u, eu);
-      read_striped_smem(st->v, ev);
-      read_striped_smem(st->w, ew);
+      read_striped_smem<B, I>(st->u, eu);
+      read_striped_smem<B, I>(st->v, ev);
+      read_striped_smem<B, I>(st->w, ew);
       if (a.in.id) {
-        read_striped_smem(st->id, ei);
+        read_striped_smem<B, I>(st->id, ei);
       } else {
 #pragma unroll
-        for (int k = 0; k < ITEMS; ++k) ei[k] = (uint32_t)(tb + item_off(k));
+        for (int k = 0; k < I; ++k) ei[k] = (uint32_t)(tb + item_off<B>(k));
       }
       __syncthreads();  // the stage is consumed: refill it with the tile TMA_STAGES ahead
       if (threadIdx.x == 0) {
         const uint64_t next = tile + (uint64_t)TMA_STAGES * G;
-        if (next < nfull) issue_tile(a, next, st, &mbar[si]);
+        if (next < nfull) issue_tile<T>(a, next, st, &mbar[si]);
       }
     } else {  // the partial last tile: plain loads
 #pragma unroll
-      for (int k = 0; k < ITEMS; ++k) {
-        const uint64_t j = tb + item_off(k);
+      for (int k = 0; k < I; ++k) {
+        const uint64_t j = tb + item_off<B>(k);
         if (j < m) {
           eu[k] = __ldg(a.in.u + j);
           ev[k] = __ldg(a.in.v + j);
@@ -656,19 +707,20 @@ __global__ void __launch_bounds__(BLOCK, 3 * 256 / BLOCK) compact_tma_kernel(Com
         }
       }
     }
-    const uint32_t keep = keep_flags<MODE>(a, valid_items(tb, m), pivot, eu, ev, ew, ei);
+    const uint32_t valid = valid_items_s<B, I>(tb, m);
+    const uint32_t keep = keep_flags<MODE>(a, valid, pivot, eu, ev, ew, ei);
     if (a.max_w) {
       uint32_t mx = 0;
 #pragma unroll
-      for (int k = 0; k < ITEMS; ++k) mx = max(mx, tb + item_off(k) < m ? ew[k] : 0u);
+      for (int k = 0; k < I; ++k) mx = max(mx, (valid >> k & 1) ? ew[k] : 0u);
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
       if ((threadIdx.x & 31) == 0 && mx > __ldca(a.max_w)) atomicMax(a.max_w, mx);
     }
-    uint32_t totp;
-    const uint32_t excl = block_exclusive_scan(packed_counts(keep), totp, s_warp);
-    const uint64_t obase = tile_claim(a.st.total, (totp & 0xffffu) + (totp >> 16), s_base);
-    emit_survivors(a, keep, excl, totp, obase, eu, ev, ew, ei, out->u, out->v, out->w, out->id);
+    uint32_t total;
+    const uint32_t excl = block_exclusive_scan<B>((uint32_t)__popc(keep), total, s_warp);
+    const uint64_t obase = tile_claim(a.st.total, total, s_base);
+    emit_survivors<B, I>(a, keep, excl, total, obase, eu, ev, ew, ei, out->u, out->v, out->w, out->id);
     __syncthreads();  // the output stage is reused by the next tile
   }
   // On an abort the block's remaining tiles were not compacted: latch the
@@ -989,34 +1041,36 @@ constexpr uint32_t FIND_STEPS = 1u << 12;  // bound on one parent-chain walk
 // of independent loads.  The start vertex of a walk longer than one step is
 // then pointed at its label directly (a concurrent walker sees either pointer,
 // both on the same path).
-template <bool IOTA, bool PACKED>
-__global__ void __launch_bounds__(BLOCK, PACKED ? 6 : 3) hook_kernel(HookArgs a) {
-  __shared__ uint32_t s_c[TILE];
-  __shared__ uint32_t s_warp[BLOCK / 32 + 1];
+template <bool IOTA, bool PACKED, int B, int I>
+__global__ void __launch_bounds__(B, Shape<B, I>::minb(PACKED ? Shape<B, I>::hook_packed_regs
+                                                                  : Shape<B, I>::hook_regs)) hook_kernel(HookArgs a) {
+  constexpr int T = Shape<B, I>::T;
+  __shared__ uint32_t s_c[T];
+  __shared__ uint32_t s_warp[B / 32 + 1];
   __shared__ uint32_t s_base[1];
 
   const uint64_t nc = a.ncand_dev ? *a.ncand_dev : a.ncand;
   const int wshift = PACKED ? a.kl.idbits + a.kl.vbits : 32;  // the weight's place in a key
   u64 wacc = 0;  // weights of the edges this thread chose
-  for (uint64_t tile = blockIdx.x; tile * TILE < nc; tile += gridDim.x) {  // uniform per block
-  const uint64_t tb = tile * TILE;
-  uint32_t c[ITEMS];
-  u64 kk[ITEMS];
-  if (!IOTA && tb + TILE <= nc && (((uintptr_t)a.cand) & 15u) == 0) {
-    load_striped(a.cand, tb, c);
+  for (uint64_t tile = blockIdx.x; tile * T < nc; tile += gridDim.x) {  // uniform per block
+  const uint64_t tb = tile * T;
+  uint32_t c[I];
+  u64 kk[I];
+  if (!IOTA && tb + T <= nc && (((uintptr_t)a.cand) & 15u) == 0) {
+    load_striped<B, I>(a.cand, tb, c);
   } else {
 #pragma unroll
-    for (int k = 0; k < ITEMS; ++k) {
-      const uint64_t j = tb + item_off(k);
+    for (int k = 0; k < I; ++k) {
+      const uint64_t j = tb + item_off<B>(k);
       c[k] = IOTA ? (uint32_t)j : (j < nc ? __ldg(a.cand + j) : 0u);
     }
   }
 #pragma unroll
-  for (int k = 0; k < ITEMS; ++k) kk[k] = (tb + item_off(k) < nc) ? a.best[c[k]] : KEY_INF;
+  for (int k = 0; k < I; ++k) kk[k] = (tb + item_off<B>(k) < nc) ? a.best[c[k]] : KEY_INF;
   uint32_t keep = 0;
   if (PACKED) {  // the chosen neighbour is in the key (a.kl.packed)
 #pragma unroll
-    for (int k = 0; k < ITEMS; ++k) {
+    for (int k = 0; k < I; ++k) {
       if (kk[k] == KEY_INF) continue;
       keep |= 1u << k;
       const uint32_t e = key_edge_id(a.kl, kk[k]);
@@ -1029,9 +1083,9 @@ __global__ void __launch_bounds__(BLOCK, PACKED ? 6 : 3) hook_kernel(HookArgs a)
       }
     }
   } else {
-  uint32_t start[2 * ITEMS], cur[2 * ITEMS];
+  uint32_t start[2 * I], cur[2 * I];
 #pragma unroll
-  for (int k = 0; k < ITEMS; ++k) {
+  for (int k = 0; k < I; ++k) {
     keep |= (kk[k] != KEY_INF ? 1u : 0u) << k;
     const uint32_t e = (uint32_t)kk[k];
     start[2 * k] = kk[k] != KEY_INF ? __ldg(a.src + e) : c[k];
@@ -1040,7 +1094,7 @@ __global__ void __launch_bounds__(BLOCK, PACKED ? 6 : 3) hook_kernel(HookArgs a)
   // lockstep walks to the current labels
   uint32_t pending = 0;
 #pragma unroll
-  for (int i = 0; i < 2 * ITEMS; ++i) {
+  for (int i = 0; i < 2 * I; ++i) {
     cur[i] = start[i];
     pending |= ((keep >> (i >> 1)) & 1u) << i;
   }
@@ -1050,15 +1104,15 @@ __global__ void __launch_bounds__(BLOCK, PACKED ? 6 : 3) hook_kernel(HookArgs a)
       atomicOr(a.err, ERR_JUMP);
       break;
     }
-    u64 bv[2 * ITEMS];
-    uint32_t pv[2 * ITEMS];
+    u64 bv[2 * I];
+    uint32_t pv[2 * I];
 #pragma unroll
-    for (int i = 0; i < 2 * ITEMS; ++i) {
+    for (int i = 0; i < 2 * I; ++i) {
       bv[i] = (pending >> i & 1) ? a.best[cur[i]] : 0ULL;
       pv[i] = (pending >> i & 1) ? __ldcg(a.parent + cur[i]) : 0u;
     }
 #pragma unroll
-    for (int i = 0; i < 2 * ITEMS; ++i) {
+    for (int i = 0; i < 2 * I; ++i) {
       if (!(pending >> i & 1)) continue;
       if (bv[i] != KEY_INF || pv[i] == cur[i])
         pending &= ~(1u << i);
@@ -1067,7 +1121,7 @@ __global__ void __launch_bounds__(BLOCK, PACKED ? 6 : 3) hook_kernel(HookArgs a)
     }
   }
 #pragma unroll
-  for (int k = 0; k < ITEMS; ++k) {
+  for (int k = 0; k < I; ++k) {
     if (!(keep >> k & 1)) continue;
     const uint32_t e = (uint32_t)kk[k];
     const uint32_t other = cur[2 * k] ^ cur[2 * k + 1] ^ c[k];
@@ -1080,20 +1134,19 @@ __global__ void __launch_bounds__(BLOCK, PACKED ? 6 : 3) hook_kernel(HookArgs a)
   }
   // shortcut the walked start vertices to their labels
 #pragma unroll
-  for (int i = 0; i < 2 * ITEMS; ++i)
+  for (int i = 0; i < 2 * I; ++i)
     if ((keep >> (i >> 1) & 1) && cur[i] != start[i] && __ldcg(a.parent + start[i]) != cur[i])
       __stcg(a.parent + start[i], cur[i]);
   }
 
-  uint32_t totp;
-  const uint32_t excl = block_exclusive_scan(packed_counts(keep), totp, s_warp);
-  const uint32_t total = (totp & 0xffffu) + (totp >> 16);
+  uint32_t total;
+  const uint32_t excl = block_exclusive_scan<B>((uint32_t)__popc(keep), total, s_warp);
   const uint64_t obase = tile_claim(a.counter, total, s_base);
 #pragma unroll
-  for (int k = 0; k < ITEMS; ++k)
-    if (keep >> k & 1) s_c[local_pos(keep, k, excl, totp)] = c[k];
+  for (int k = 0; k < I; ++k)
+    if (keep >> k & 1) s_c[excl + (uint32_t)__popc(keep & ((1u << k) - 1u))] = c[k];
   __syncthreads();
-  for (uint32_t i = threadIdx.x; i < total; i += BLOCK) a.active_out[obase + i] = s_c[i];
+  for (uint32_t i = threadIdx.x; i < total; i += B) a.active_out[obase + i] = s_c[i];
   __syncthreads();  // s_c, s_warp and s_base are reused by the block's next tile
   }
   wsum_add(a.wsum, wacc);
@@ -2177,10 +2230,10 @@ __global__ void __launch_bounds__(BLOCK) sd_emit_kernel(const u64 *pk, const uin
       if (eu[k] != ev[k]) keep |= 1u << k;  // self-loops are never kept
     }
   }
-  uint32_t totp;
-  const uint32_t excl = block_exclusive_scan(packed_counts(keep), totp, s_warp);
-  const uint64_t obase = tile_claim(a.st.total, (totp & 0xffffu) + (totp >> 16), s_base);
-  emit_survivors(a, keep, excl, totp, obase, eu, ev, ew, ei, s_u, s_v, s_w, s_id);
+  uint32_t total;
+  const uint32_t excl = block_exclusive_scan((uint32_t)__popc(keep), total, s_warp);
+  const uint64_t obase = tile_claim(a.st.total, total, s_base);
+  emit_survivors<BLOCK, ITEMS>(a, keep, excl, total, obase, eu, ev, ew, ei, s_u, s_v, s_w, s_id);
 }
 
 size_t sort_dedupe_scratch_bytes(uint64_t m, int sms) {
@@ -2592,26 +2645,57 @@ static inline unsigned grid_for(uint64_t items_per_block_units, int sms, int per
 
 int max_scan_tiles(uint64_t count) { return (int)((count + TILE - 1) / TILE); }
 
-template <int MODE>
-static void launch_compact_mode(const CompactArgs &a, uint64_t max_count, cudaStream_t s) {
+// One compaction launch in tile shape (B, I): the persistent TMA kernel for
+// long lists whose tiles fit two shared-memory stages, else one block per tile.
+template <int MODE, int B, int I>
+static void launch_compact_shaped(const CompactArgs &a, uint64_t max_count, bool aligned, cudaStream_t s) {
+  constexpr int T = B * I;
+  constexpr size_t stage_bytes = 16 * (size_t)T;  // compact_kernel's staging buffer
+  constexpr bool tma_fits = tma_smem_bytes<B, I>() <= 200 * 1024;
   static int attrs = 0, tma_blocks = 0;
-  const size_t tma_smem = sizeof(EdgeStage) * (TMA_STAGES + 1);
-  if (!attrs) {  // prefer shared memory over L1; size the persistent grid
-    cudaFuncSetAttribute(compact_kernel<MODE, true>, cudaFuncAttributePreferredSharedMemoryCarveout,
+  if (!attrs) {  // prefer shared memory over L1; allow the staging buffer; size the persistent grid
+    cudaFuncSetAttribute(compact_kernel<MODE, true, B, I>, cudaFuncAttributePreferredSharedMemoryCarveout,
                          cudaSharedmemCarveoutMaxShared);
-    cudaFuncSetAttribute(compact_kernel<MODE, false>, cudaFuncAttributePreferredSharedMemoryCarveout,
-                         cudaSharedmemCarveoutMaxShared);
-    cudaFuncSetAttribute(compact_tma_kernel<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tma_smem);
-    int dev = 0, sms = 0, per_sm = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, compact_tma_kernel<MODE>, BLOCK, tma_smem);
+    cudaFuncSetAttribute(compact_kernel<MODE, true, B, I>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)stage_bytes);
+    if constexpr (tma_fits) {
+      cudaFuncSetAttribute(compact_tma_kernel<MODE, B, I>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)tma_smem_bytes<B, I>());
+      int dev = 0, sms = 0, per_sm = 0;
+      cudaGetDevice(&dev);
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, compact_tma_kernel<MODE, B, I>, B,
+                                                    tma_smem_bytes<B, I>());
+      tma_blocks = sms * per_sm;
+    }
     cudaGetLastError();
-    tma_blocks = sms * per_sm;
     attrs = 1;
   }
-  const uint64_t tiles = (max_count + TILE - 1) / TILE;
+  const uint64_t tiles = (max_count + T - 1) / T;
   if (tiles == 0) return;
+  if constexpr (tma_fits) {
+    if (aligned && tma_blocks > 0 && tiles >= (uint64_t)tma_blocks * TMA_STAGES) {
+      compact_tma_kernel<MODE, B, I><<<(unsigned)tma_blocks, B, tma_smem_bytes<B, I>(), s>>>(a);
+      return;
+    }
+  }
+  if (aligned) {
+    compact_kernel<MODE, true, B, I><<<(unsigned)tiles, B, stage_bytes, s>>>(a);
+  } else {  // unaligned lists: scalar loads in the default shape
+    static int attrs_u = 0;
+    if (!attrs_u) {
+      cudaFuncSetAttribute(compact_kernel<MODE, false, BLOCK, ITEMS>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                           cudaSharedmemCarveoutMaxShared);
+      cudaGetLastError();
+      attrs_u = 1;
+    }
+    compact_kernel<MODE, false, BLOCK, ITEMS><<<(unsigned)((max_count + TILE - 1) / TILE), BLOCK, 16 * TILE, s>>>(a);
+  }
+}
+
+template <int MODE>
+static void launch_compact_mode(const CompactArgs &a, uint64_t max_count, cudaStream_t s) {
+  if (max_count == 0) return;
   const bool aligned = aligned16(a.in.u) && aligned16(a.in.v) && aligned16(a.in.w) && (!a.in.id || aligned16(a.in.id));
   if constexpr (MODE == CM_FILTER || MODE == CM_HEAVY) {
     static int fw_blocks = -1;  // resident blocks of the warp-streamed pass (0: not available)
@@ -2636,14 +2720,20 @@ static void launch_compact_mode(const CompactArgs &a, uint64_t max_count, cudaSt
       return;
     }
   }
-  if (aligned && tma_blocks > 0 && tiles >= (uint64_t)tma_blocks * TMA_STAGES) {
-    compact_tma_kernel<MODE><<<(unsigned)tma_blocks, BLOCK, tma_smem, s>>>(a);
-    return;
+  if constexpr (MODE == CM_RELABEL || MODE == CM_PARTITION) {
+    switch (a.shape) {  // the shapes of shape_index
+      case 1: launch_compact_shaped<MODE, 128, 4>(a, max_count, aligned, s); return;
+      case 2: launch_compact_shaped<MODE, 128, 8>(a, max_count, aligned, s); return;
+      case 3: launch_compact_shaped<MODE, 128, 16>(a, max_count, aligned, s); return;
+      case 4: launch_compact_shaped<MODE, 256, 4>(a, max_count, aligned, s); return;
+      case 6: launch_compact_shaped<MODE, 256, 16>(a, max_count, aligned, s); return;
+      case 7: launch_compact_shaped<MODE, 512, 4>(a, max_count, aligned, s); return;
+      case 8: launch_compact_shaped<MODE, 512, 8>(a, max_count, aligned, s); return;
+      case 9: launch_compact_shaped<MODE, 512, 16>(a, max_count, aligned, s); return;
+      default: break;  // 0 and 5: 256 x 8
+    }
   }
-  if (aligned)
-    compact_kernel<MODE, true><<<(unsigned)tiles, BLOCK, 0, s>>>(a);
-  else
-    compact_kernel<MODE, false><<<(unsigned)tiles, BLOCK, 0, s>>>(a);
+  launch_compact_shaped<MODE, BLOCK, ITEMS>(a, max_count, aligned, s);
 }
 
 void launch_compact(CompactMode mode, const CompactArgs &a, uint64_t max_count, cudaStream_t s) {
@@ -2671,18 +2761,36 @@ void launch_max_weight(const uint32_t *w, uint64_t m, uint32_t *out, int sms, cu
   max_weight_kernel<<<grid_for((m / 4 + BLOCK - 1) / BLOCK, sms, 8), BLOCK, 0, s>>>(w, m, out);
 }
 
-void launch_hook(const HookArgs &a, uint64_t max_cand, cudaStream_t s) {
-  if (max_cand == 0) return;
+template <int B, int I>
+static void launch_hook_shaped(const HookArgs &a, uint64_t max_cand, cudaStream_t s) {
+  constexpr int T = B * I;
   // a count known on the host gets one block per tile; a count in device
   // memory (up to max_cand) gets a bounded grid that strides over the tiles
-  const unsigned tiles = (unsigned)max_scan_tiles(max_cand);
-  const unsigned grid = a.ncand_dev ? std::min(tiles, 152u * 8u) : tiles;
+  const uint64_t tiles = (max_cand + T - 1) / T;
+  const unsigned grid = (unsigned)(a.ncand_dev ? std::min<uint64_t>(tiles, 152u * 8u * 256u / B) : tiles);
   // the packed layout needs no parent-chain walks: its own instantiation
   // keeps far fewer registers live (higher occupancy)
   if (a.cand)
-    a.kl.packed ? hook_kernel<false, true><<<grid, BLOCK, 0, s>>>(a) : hook_kernel<false, false><<<grid, BLOCK, 0, s>>>(a);
+    a.kl.packed ? hook_kernel<false, true, B, I><<<grid, B, 0, s>>>(a)
+                : hook_kernel<false, false, B, I><<<grid, B, 0, s>>>(a);
   else
-    a.kl.packed ? hook_kernel<true, true><<<grid, BLOCK, 0, s>>>(a) : hook_kernel<true, false><<<grid, BLOCK, 0, s>>>(a);
+    a.kl.packed ? hook_kernel<true, true, B, I><<<grid, B, 0, s>>>(a)
+                : hook_kernel<true, false, B, I><<<grid, B, 0, s>>>(a);
+}
+
+void launch_hook(const HookArgs &a, uint64_t max_cand, cudaStream_t s) {
+  if (max_cand == 0) return;
+  switch (a.shape) {  // the shapes of shape_index
+    case 1: launch_hook_shaped<128, 4>(a, max_cand, s); return;
+    case 2: launch_hook_shaped<128, 8>(a, max_cand, s); return;
+    case 3: launch_hook_shaped<128, 16>(a, max_cand, s); return;
+    case 4: launch_hook_shaped<256, 4>(a, max_cand, s); return;
+    case 6: launch_hook_shaped<256, 16>(a, max_cand, s); return;
+    case 7: launch_hook_shaped<512, 4>(a, max_cand, s); return;
+    case 8: launch_hook_shaped<512, 8>(a, max_cand, s); return;
+    case 9: launch_hook_shaped<512, 16>(a, max_cand, s); return;
+    default: launch_hook_shaped<BLOCK, ITEMS>(a, max_cand, s); return;  // 0 and 5: 256 x 8
+  }
 }
 
 void launch_jump(const uint32_t *act, const u64 *count_dev, uint64_t count_host, uint64_t max_count,

@@ -362,8 +362,10 @@ struct Solve {
   uint32_t *parent = nullptr, *act[2] = {nullptr, nullptr}, *bits = nullptr;
   int wbits = 32;  // bits of the largest weight (set with the key layout)
   int rounds = 0;
+  int shape = 0;   // tile shape of the compaction and hook kernels (shape_index of the configuration)
 
-  Solve(mst_ctx *c_, cudaStream_t s_, uint32_t n_, uint64_t m_) : c(c_), s(s_), n(n_), m(m_) {}
+  Solve(mst_ctx *c_, cudaStream_t s_, uint32_t n_, uint64_t m_)
+      : c(c_), s(s_), n(n_), m(m_), shape(shape_index(c_->cfg.block_threads, c_->cfg.items_per_thread)) {}
 
   mst_status init(uint32_t *parent_external = nullptr, uint32_t *bits_external = nullptr) {
     TRY(best_b.alloc(c, (size_t)n * 8, s));
@@ -487,6 +489,7 @@ struct Solve {
     }
     TRY(zero_round_state(c, s));
     HookArgs ha{};
+    ha.shape = shape;
     ha.cand = nullptr;
     ha.ncand = n;
     ha.best = best;
@@ -530,6 +533,7 @@ struct Solve {
       if (out.cap < cur_m) TRY(out.alloc(c, cur_m, s));
       TRY(zero_round_state(c, s));
       CompactArgs ca{};
+      ca.shape = shape;
       ca.in = cur;
       ca.m = cur_m;
       ca.out = out.out;
@@ -554,6 +558,7 @@ struct Solve {
         Buf sd_b;
         TRY(sd_b.alloc(c, sort_dedupe_scratch_bytes(mT, c->sms), s));
         CompactArgs cd{};
+        cd.shape = shape;
         cd.in = T.list();
         cd.m = mT;
         cd.out = out.out;
@@ -580,6 +585,7 @@ struct Solve {
         ca.st = next_scan(c, CNT_TMP);
         PROF(MST_K_DEDUPE, in_bytes, CNT_TMP, 16.0, -1, 0.0, launch_compact(CM_RELABEL, ca, cur_m, s));
         CompactArgs cd{};
+        cd.shape = shape;
         cd.in = T.list();
         cd.m_dev = &c->ds->count[CNT_TMP];
         cd.out = out.out;
@@ -593,6 +599,7 @@ struct Solve {
         PROF(MST_K_DEDUPE, 0.0, CNT_TMP, 16.0, CNT_EDGES, 16.0, launch_compact(CM_DEDUPE, cd, cur_m, s));
       }
       HookArgs hb{};
+      hb.shape = shape;
       hb.cand = act[a];
       hb.ncand = n_act;
       hb.best = best;
@@ -650,7 +657,8 @@ struct Solve {
     const u64 vals[] = {(u64)parent,  (u64)best,    (u64)bits,     (u64)cur_u,  (u64)cur_v,
                         (u64)src,     (u64)dst,     (u64)c->status, (u64)c->ds,  (u64)g,
                         (u64)kl.packed, (u64)kl.vbits, (u64)kl.idbits, (u64)n,     (u64)cap,
-                        (u64)nmax,    (u64)jl,      (u64)base_ok,  (u64)max_iter, (u64)c->sms};
+                        (u64)nmax,    (u64)jl,      (u64)base_ok,  (u64)max_iter, (u64)c->sms,
+                        (u64)shape};
     for (u64 v : vals) fold(v);
     cudaGraphExec_t exec = nullptr;
     for (size_t i = 0; i < c->round_graphs.size(); ++i)
@@ -731,6 +739,7 @@ struct Solve {
     for (int half = 0; half < 2; ++half) {
       const int in = half, out = 1 - half;
       CompactArgs ca{};
+      ca.shape = shape;
       ca.in = L[in]->list();
       ca.m = cap;
       ca.m_dev = &g->ce[in];
@@ -743,6 +752,7 @@ struct Solve {
       ca.st = ScanState{c->status, c->ds->tile_ctr, 0, &g->ce[out], &c->ds->err, c->cfg.spin_limit};
       launch_compact(CM_RELABEL, ca, cap, cs);
       HookArgs hb{};
+      hb.shape = shape;
       hb.cand = A[in];
       hb.ncand_dev = &g->ca[in];
       hb.best = best;
@@ -874,6 +884,7 @@ struct Solve {
     TRY(out.alloc(c, mcut, s));
     TRY(zero_counters(c, s));
     CompactArgs ca{};
+    ca.shape = shape;
     ca.in = cutl.list();
     ca.m = mcut;
     ca.m_dev = &c->ds->count[CNT_CUT];
@@ -943,6 +954,7 @@ struct Solve {
     ListBuf L;
     TRY(L.alloc(c, mE, s));
     CompactArgs cp{};
+    cp.shape = shape;
     cp.in = E;
     cp.m = mE;
     cp.out = L.out;
@@ -985,6 +997,7 @@ struct Solve {
     ListBuf H;
     TRY(H.alloc(c, mE - mL + lcarry_m, s));
     CompactArgs cf{};
+    cf.shape = shape;
     cf.in = E;
     cf.m = mE;
     cf.out = H.out;
@@ -1011,6 +1024,7 @@ struct Solve {
         // labels for that short list
         TRY(C.alloc(c, mE - mL, s));
         CompactArgs ch{};
+        ch.shape = shape;
         ch.in = E;
         ch.m = mE;
         ch.out = C.out;
@@ -1138,6 +1152,7 @@ mst_status validate_cfg(const mst_config *cfg) {
   if (cfg->tile_filter < 0 || cfg->tile_filter > 1) return MST_ERR_INVALID_ARG;
   if (cfg->tile_vertices < 32 || cfg->tile_vertices > 4096) return MST_ERR_INVALID_ARG;
   if (cfg->spin_limit < 1) return MST_ERR_INVALID_ARG;
+  if (shape_index(cfg->block_threads, cfg->items_per_thread) < 0) return MST_ERR_INVALID_ARG;
   return MST_OK;
 }
 
@@ -1383,6 +1398,8 @@ void mst_config_default(mst_config *cfg) {
   cfg->jump_steps = 64;
   cfg->tile_filter = 0;  // measured slower on GB300: the light phase adds synchronised rounds in each tile
   cfg->spin_limit = 1u << 21;  // about a second of polling at the measured poll rate
+  cfg->block_threads = 0;      // 0: 256 threads per block
+  cfg->items_per_thread = 0;   // 0: 8 edges per thread
 }
 
 const char *mst_status_string(mst_status s) {
@@ -1760,6 +1777,7 @@ mst_status mst_step_contract(mst_handle h, uint32_t n, uint64_t m, const uint32_
   launch_min_edges(E, m, n, 1, S.kl, S.best, &h->ds->err, h->sms, s);
   if (zero_counters(h, s) != MST_OK) return record_cuda(h, __LINE__);
   HookArgs ha{};
+  ha.shape = shape_index(h->cfg.block_threads, h->cfg.items_per_thread);
   ha.ncand = n;
   ha.best = S.best;
   ha.kl = S.kl;
@@ -1789,6 +1807,7 @@ static mst_status step_compact(mst_handle h, CompactMode mode, uint32_t n, uint6
   if (clear_device_flags(h, s) != MST_OK) return record_cuda(h, __LINE__);
   const EdgeList E{d_u, d_v, d_w, d_id};
   CompactArgs a{};
+  a.shape = shape_index(h->cfg.block_threads, h->cfg.items_per_thread);
   a.in = E;
   a.m = m;
   a.out = EdgeOut{d_ou, d_ov, d_ow, d_oid};
@@ -1855,6 +1874,7 @@ mst_status mst_step_dedupe(mst_handle h, uint64_t m, const uint32_t *d_u, const 
   st = sd_b.alloc(h, sort_dedupe_scratch_bytes(m, h->sms), s);
   if (st != MST_OK) return record(h, st);
   CompactArgs cd{};
+  cd.shape = shape_index(h->cfg.block_threads, h->cfg.items_per_thread);
   cd.in = EdgeList{d_u, d_v, d_w, ids};
   cd.m = m;
   cd.out = EdgeOut{d_ou, d_ov, d_ow, d_oid};

@@ -56,7 +56,8 @@ class MstConfig(ctypes.Structure):
                 ("graph_rounds", ctypes.c_int), ("graph_jump_launches", ctypes.c_int),
                 ("filter_carry", ctypes.c_int), ("filter_split", ctypes.c_int),
                 ("min_edges_sort", ctypes.c_int), ("jump_steps", ctypes.c_uint32),
-                ("tile_filter", ctypes.c_int), ("spin_limit", ctypes.c_uint32)]
+                ("tile_filter", ctypes.c_int), ("spin_limit", ctypes.c_uint32),
+                ("block_threads", ctypes.c_uint32), ("items_per_thread", ctypes.c_uint32)]
 
 
 _P = ctypes.c_void_p

@@ -31,6 +31,18 @@ def test_default_config(lib):
     assert cfg.base_case == 1 and cfg.graph_rounds == 1 and cfg.graph_jump_launches == 2
     assert cfg.jump_steps == 64 and cfg.tile_filter == 0
     assert cfg.filter_carry == 0
+    assert cfg.spin_limit == 1 << 21 and cfg.block_threads == 0 and cfg.items_per_thread == 0
+
+
+def test_bad_kernel_shapes_are_refused_without_device(lib):
+    """Tile shapes outside 128/256/512 threads x 4/8/16 items are an invalid
+    configuration (checked before any device is touched)."""
+    for bt, it in ((384, 8), (256, 12), (1024, 8), (256, 2)):
+        cfg = mst.MstConfig()
+        lib.mst_config_default(ctypes.byref(cfg))
+        cfg.block_threads, cfg.items_per_thread = bt, it
+        h = ctypes.c_void_p()
+        assert lib.mst_create(ctypes.byref(h), ctypes.byref(cfg)) == 1, (bt, it)
 
 
 def test_status_strings(lib):

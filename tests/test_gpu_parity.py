@@ -431,6 +431,49 @@ def test_step_finalize(step_solver, dev):
     assert tot == int(w[chosen_ids].astype(np.uint64).sum())
 
 
+_SHAPE_CASES = {}
+
+
+def _shape_case(name):
+    """Graphs for the shape test, each with its Kruskal forest (built once)."""
+    if name not in _SHAPE_CASES:
+        g, cfg = {
+            # a top-level list long enough for the persistent TMA compaction in
+            # every shape that has one; packed keys
+            "rmat_filter": (lambda: W.rmat(18, 3_000_000, 51), dict(variant="filter", filter_min_edges=1 << 18)),
+            # 32-bit weights: unpacked keys, ends recorded by id, walking hook
+            "rgg2d": (lambda: W.rgg(2, 1 << 17, 8.0, 52), dict(variant="boruvka")),
+            # pair insertion into the hash table from the shaped compaction
+            "gnm_hash": (lambda: W.gnm(1 << 14, 1 << 18, 53), dict(variant="boruvka", dedupe="hash")),
+            # deepest pointer jumping, ragged tiles
+            "path": (lambda: W.Graph(200_001, np.arange(200_000, dtype=np.uint32),
+                                     np.arange(1, 200_001, dtype=np.uint32),
+                                     (np.arange(200_000, dtype=np.uint32) % 13 + 1).astype(np.uint32)),
+                     dict(variant="boruvka")),
+        }[name]
+        g = g()
+        _SHAPE_CASES[name] = (g, cfg, oracle.kruskal(g.n, g.src, g.dst, g.w))
+    return _SHAPE_CASES[name]
+
+
+@pytest.mark.parametrize("items", [4, 8, 16])
+@pytest.mark.parametrize("threads", [128, 256, 512])
+def test_every_kernel_shape_equals_kruskal(dev, threads, items):
+    """Every tile shape the relabel / partition compactions and the hooking
+    kernel are built for (threads per block x items per thread, chosen at run
+    time) gives exactly Kruskal's forest, on the first solve of a handle (host
+    round loop) and on the second (rounds as a CUDA graph)."""
+    for name in ("rmat_filter", "rgg2d", "gnm_hash", "path"):
+        g, cfg, (kid, ktot) = _shape_case(name)
+        s = Solver(0, block_threads=threads, items_per_thread=items, **cfg)
+        try:
+            for rep in range(2):
+                ids, tot = gpu_msf(s, g.n, g.src, g.dst, g.w, dev)
+                assert np.array_equal(ids, kid) and tot == ktot, (name, rep)
+        finally:
+            s.close()
+
+
 def test_ordered_scan_wait_that_runs_out_is_an_error(dev):
     """The ordered output scan is the one place where blocks wait on each
     other (a tile polls the prefixes its predecessors publish), and that wait

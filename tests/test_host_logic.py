@@ -28,7 +28,7 @@ def test_autotune_picks_the_fastest_and_caches():
         calls.append(cfg["k"])
         return cost[cfg["k"]]
     cands = [dict(k="a"), dict(k="b"), dict(k="c")]
-    best, res = autotune(trial, cands, reps=2, key="t1")
+    best, res = autotune(trial, cands, reps=2, key="t1", shapes=None)
     assert best == dict(k="b")
     assert [r[0] for r in res] == [label(c) for c in cands] and [r[1] for r in res] == [3.0, 1.0, 2.0]
     assert len(calls) == 9  # one untimed + two timed runs each
@@ -36,6 +36,26 @@ def test_autotune_picks_the_fastest_and_caches():
     assert best2 == best and res2 == [] and len(calls) == 9
     with pytest.raises(ValueError):
         autotune(trial, [], key=None)
+
+
+def test_autotune_tunes_the_kernel_shape_on_the_best_configuration():
+    """The shape stage runs every tile shape except the default one on top of
+    the best configuration of the first stage, and keeps a faster shape."""
+    from paper_2302_12199_gb300.autotune import SHAPE_CANDIDATES
+    seen = []
+
+    def trial(cfg):
+        seen.append(dict(cfg))
+        t = {"a": 3.0, "b": 2.0}[cfg["k"]]
+        if cfg.get("block_threads") == 512 and cfg.get("items_per_thread") == 4:
+            t -= 0.5
+        return t
+    best, res = autotune(trial, [dict(k="a"), dict(k="b")], reps=1, shapes=SHAPE_CANDIDATES)
+    assert best == dict(k="b", block_threads=512, items_per_thread=4)
+    shaped = [c for c in seen if "block_threads" in c]
+    assert all(c["k"] == "b" for c in shaped)  # shapes only on the first stage's winner
+    assert len({(c["block_threads"], c["items_per_thread"]) for c in shaped}) == 8  # 256 x 8 is the default
+    assert len(res) == 2 + 8
 
 
 class _FakeSlot:
