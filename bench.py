@@ -858,7 +858,18 @@ def served_main(args, rank: int, world: int, local_rank: int):
     if args.graph_rounds is not None:
         scfg["graph_rounds"] = args.graph_rounds
     server = Server(local_rank, slots=args.slots, budget_bytes=int(args.slot_budget_gb * (1 << 30)), config=scfg)
+    t_pre = time.perf_counter()
     expected = {g: server.solve_alone(pool[g]) for g in range(args.pool)}  # each graph solved alone
+    t_pre = time.perf_counter() - t_pre
+    verified = 0
+    if args.verify_oracle:  # tie the pre-computed answers to the CPU oracle on a sample of the pool
+        import oracle
+        for g in range(min(args.verify_oracle, args.pool)):
+            lo, hi = off[g], off[g + 1]
+            kid, ktot = oracle.kruskal(int(b.n[g]), b.src[lo:hi], b.dst[lo:hi], b.w[lo:hi])
+            if not (np.array_equal(kid, expected[g].ids) and ktot == expected[g].total):
+                raise RuntimeError(f"pool graph {g}: the GPU's answer differs from Kruskal")
+            verified += 1
     for s in server.slots:  # warm every slot
         s.solve(pool[:8])
     uuid = None
@@ -885,12 +896,13 @@ def served_main(args, rank: int, world: int, local_rank: int):
     # response compared with the graph solved alone
     best = max(per_rate, key=lambda r: r["graphs_per_s"])
     to_pin = lambda a: torch.from_numpy(np.ascontiguousarray(a).view(np.int32)).pin_memory()
+    e2e_pool = min(args.pool, args.e2e_pool) if args.e2e_pool else args.pool
     host_pool = [PoolGraph(int(b.n[g]), to_pin(b.src[off[g]:off[g + 1]]), to_pin(b.dst[off[g]:off[g + 1]]),
-                           to_pin(b.w[off[g]:off[g + 1]])) for g in range(args.pool)]
+                           to_pin(b.w[off[g]:off[g + 1]])) for g in range(e2e_pool)]
     rate = best["rate"]
-    seconds = min(args.serve_seconds, args.max_requests / rate)
+    seconds = min(args.serve_seconds, (args.e2e_max_requests or args.max_requests) / rate)
     arr = poisson_arrivals(rate, seconds, seed=2000)
-    picks = rng.integers(0, args.pool, arr.size)
+    picks = rng.integers(0, e2e_pool, arr.size)
     st = server.run(host_pool, picks, arr, expected=expected, rate=rate, seconds=seconds)
     if st.mismatches:
         raise RuntimeError(f"{st.mismatches} end-to-end responses differ from the graphs solved alone")
@@ -900,7 +912,7 @@ def served_main(args, rank: int, world: int, local_rank: int):
            "h2d_bytes_per_step": float(12 * np.mean(sizes[picks])),
            "d2h_bytes_per_step": float(np.mean([4 * expected[int(p)].ids.size + 8 for p in picks])),
            "step": "one request", "rate": rate, "latency_ms": e2e_sum["latency_ms"],
-           "payloads": "page-locked host memory, copied in per batch"}
+           "payloads": f"page-locked host memory, copied in per batch (the first {e2e_pool} pool graphs)"}
     clocks = sampler.stop()
     server.close()
     line = {
@@ -912,7 +924,9 @@ def served_main(args, rank: int, world: int, local_rank: int):
                    "pool_mean_m": float(np.mean(sizes)),
                    "mix": "n log-uniform [2^8,2^20]; 1/3 GNM deg 4-32, 1/3 RGG2D deg 8, 1/3 RMAT deg 16; w in [1,255]",
                    "slots": args.slots, "slot_budget_gb": args.slot_budget_gb,
-                   "payloads": "device-resident request pool, gathered per batch"},
+                   "payloads": "device-resident request pool, gathered per batch",
+                   "pool_answers": f"every pool graph solved alone first ({t_pre:.1f} s); "
+                                   f"{verified} of them checked against the CPU oracle (Kruskal)"},
         "rates": per_rate,
         "latency_ms_at_best": best["latency_ms"],
         "clocks": clocks,
@@ -940,6 +954,12 @@ def main():
                     help="served: log2 of the offered arrival rates (requests/s)")
     ap.add_argument("--serve-seconds", type=float, default=60.0, help="served: arrival window per rate")
     ap.add_argument("--max-requests", type=int, default=20000, help="served: cap on requests per rate")
+    ap.add_argument("--e2e-pool", type=int, default=0,
+                    help="served: graphs of the pool copied to page-locked host memory for the e2e leg (0: all)")
+    ap.add_argument("--e2e-max-requests", type=int, default=0,
+                    help="served: cap on requests of the e2e leg (0: --max-requests)")
+    ap.add_argument("--verify-oracle", type=int, default=0,
+                    help="served: pool graphs whose pre-computed answer is checked against Kruskal")
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--cpu-sample-edges", type=int, default=1 << 25)
     ap.add_argument("--no-cpu-baseline", action="store_true")

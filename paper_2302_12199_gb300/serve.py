@@ -64,6 +64,7 @@ class ServeStats:
     max_in_flight: int = 0      # most batches on the device at once
     mismatches: int = 0         # responses that differ from the expected ones
     phases_ms: dict = field(default_factory=dict)  # mean host time per batch by phase
+    done_in_window: int = 0     # requests answered before the arrival window (seconds) ended
 
     def summary(self) -> dict:
         lat = self.latency * 1e3
@@ -73,7 +74,10 @@ class ServeStats:
                 "latency_ms": pct, "batches": self.batches,
                 "mean_batch": float(np.mean(self.batch_sizes)) if self.batch_sizes else 0.0,
                 "max_batches_in_flight": self.max_in_flight, "mismatches": self.mismatches,
-                "batch_phases_ms": self.phases_ms}
+                "batch_phases_ms": self.phases_ms,
+                # past saturation the queue grows through the window and drains after it
+                "answered_in_window": self.done_in_window,
+                "drain_s": max(0.0, self.wall - self.seconds) if self.seconds > 0 else 0.0}
 
 
 def poisson_arrivals(rate: float, seconds: float, seed: int) -> np.ndarray:
@@ -302,7 +306,8 @@ class Server:
         return ServeStats(rate=rate, seconds=seconds, requests=nreq, wall=wall, latency=latency,
                           batches=state["batches"], batch_sizes=state["sizes"],
                           max_in_flight=state["max_in_flight"], mismatches=state["mismatches"],
-                          phases_ms=phases_ms)
+                          phases_ms=phases_ms,
+                          done_in_window=int((done_at <= seconds).sum()) if seconds > 0 else nreq)
 
     def close(self):
         for s in self.slots:
