@@ -631,17 +631,25 @@ def measure_batched(args, rank: int, world: int, local_rank: int, dev, dist, com
         torch.cuda.synchronize(dev)
         return e0.elapsed_time(e1) / 1e3, res
 
-    # autotuned configuration (tile contraction and dedupe strategy, variant)
+    # autotuned configuration (variant, dedupe strategy, tile contraction,
+    # then the kernels' tile shape); each candidate keeps one handle across its
+    # runs, so the timed runs see the steady state (pool grown, round graphs
+    # built), not a handle's first solves
+    trial_solver = {}
+
     def trial(cfg):
-        s = Solver(local_rank, **cfg)
-        try:
-            return timed_batch(s)[0]
-        finally:
-            s.close()
+        key = label(cfg)
+        if key not in trial_solver:
+            for k in list(trial_solver):
+                trial_solver.pop(k).close()
+            trial_solver[key] = Solver(local_rank, **cfg)
+        return timed_batch(trial_solver[key])[0]
     if args.no_autotune:
         best, tuning = dict(variant="boruvka", dedupe="none", tile_contract=0), []
     else:
-        best, tuning = autotune(trial, reps=1)
+        best, tuning = autotune(trial, reps=3)
+    for k in list(trial_solver):
+        trial_solver.pop(k).close()
     if args.base_case is not None:
         best["base_case"] = args.base_case
     if args.graph_rounds is not None:

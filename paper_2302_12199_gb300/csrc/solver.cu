@@ -28,7 +28,11 @@ struct mst_ctx {
   int sms = 152;
   cudaMemPool_t pool = nullptr;
   DevState *ds = nullptr;    // device
-  DevState *hs = nullptr;    // pinned host mirror
+  DevState *hs = nullptr;    // page-locked, mapped host mirror of ds, written by readback_kernel
+  DevState *hs_dev = nullptr;   // its device-side address
+  uint32_t *hflag = nullptr;    // mapped host word: sequence number of the last completed readback
+  uint32_t *hflag_dev = nullptr;
+  uint32_t rb_seq = 0;
   u64 *hres = nullptr;       // pinned host words for the forest size and weight of the host entry points
   u64 *status = nullptr;     // scan status words
   uint64_t status_cap = 0;   // in tiles
@@ -58,6 +62,12 @@ struct mst_ctx {
   size_t hin_cap[2] = {0, 0};
   void *hout = nullptr;
   size_t hout_cap = 0;
+  // the two ping-pong edge lists of the Borůvka rounds (u, v, w, id each),
+  // kept by the handle and grown on demand: with stable addresses and a stable
+  // capacity bound, one captured round graph serves every Borůvka call (and
+  // every later solve) of the handle
+  void *rl_mem = nullptr;
+  uint64_t rl_cap = 0;  // edges per list
   GraphRounds *grounds = nullptr;     // device state of the graph round loop
   struct RoundGraph {
     u64 sig;  // every pointer and size the graph was built with
@@ -174,6 +184,40 @@ struct ListBuf {
   EdgeList list() const { return EdgeList{out.u, out.v, out.w, out.id}; }
 };
 
+// A view of one of the handle's round lists.
+struct RoundList {
+  EdgeOut out{};
+  uint64_t cap = 0;
+  EdgeList list() const { return EdgeList{out.u, out.v, out.w, out.id}; }
+};
+
+// Points X and Y at the handle's round lists, first growing them (a quarter
+// above `need`, in steps of 2^16 edges, after the device is idle: earlier
+// work may still read the old ones) when they hold fewer than `need` edges.
+mst_status round_lists(mst_ctx *c, uint64_t need, RoundList &X, RoundList &Y) {
+  if (!c->rl_mem || c->rl_cap < need) {
+    const uint64_t want = round_up(std::max<uint64_t>(need + need / 4, 1ULL << 16), 1ULL << 16);
+    CK(cudaDeviceSynchronize());
+    if (c->rl_mem) cudaFree(c->rl_mem);
+    c->rl_mem = nullptr;
+    c->rl_cap = 0;
+    if (cudaMalloc(&c->rl_mem, 8 * round_up(want * 4 + 16, 256)) != cudaSuccess) {
+      cudaGetLastError();
+      return MST_ERR_OOM;
+    }
+    c->rl_cap = want;
+  }
+  const uint64_t stride = round_up(c->rl_cap * 4 + 16, 256);
+  char *b = static_cast<char *>(c->rl_mem);
+  RoundList *L[2] = {&X, &Y};
+  for (int k = 0; k < 2; ++k) {
+    char *q = b + (size_t)4 * k * stride;
+    L[k]->out = EdgeOut{(uint32_t *)q, (uint32_t *)(q + stride), (uint32_t *)(q + 2 * stride), (uint32_t *)(q + 3 * stride)};
+    L[k]->cap = c->rl_cap;
+  }
+  return MST_OK;
+}
+
 mst_status ensure_status(mst_ctx *c, uint64_t max_items, cudaStream_t s) {
   const uint64_t tiles = (max_items + TILE_ITEMS - 1) / TILE_ITEMS + 1;
   if (tiles <= c->status_cap) return MST_OK;
@@ -255,6 +299,7 @@ void prof_end(mst_ctx *c, cudaStream_t s, int idx, int kind, double bytes, int s
 void prof_resolve(mst_ctx *c) {
   for (auto &r : c->prof_pending) {
     float ms = 0.f;
+    if (r.b) cudaEventSynchronize(r.b);  // done on the device; let the runtime see it
     if (r.a && cudaEventElapsedTime(&ms, r.a, r.b) != cudaSuccess) {
       cudaGetLastError();
       ms = 0.f;
@@ -290,9 +335,42 @@ void prof_resolve(mst_ctx *c) {
     prof_end(c, s, _p, kind, bytes, slot1, per1, slot2, per2, min_bytes);      \
   } while (0)
 
+// Copies the device state into the mapped host mirror, then publishes `seq`
+// in the mapped flag word (one warp, after everything before it on the
+// stream).  The system-scope fence orders the mirror's words before the flag.
+__global__ void readback_kernel(const DevState *ds, DevState *hs, uint32_t *flag, uint32_t seq) {
+  constexpr int words = (int)(sizeof(DevState) / 4);
+  const uint32_t *src = reinterpret_cast<const uint32_t *>(ds);
+  volatile uint32_t *dst = reinterpret_cast<volatile uint32_t *>(hs);
+  for (int i = threadIdx.x; i < words; i += 32) dst[i] = src[i];
+  __threadfence_system();
+  __syncwarp();
+  if (threadIdx.x == 0) *reinterpret_cast<volatile uint32_t *>(flag) = seq;
+}
+
+// The host side of a readback: the state of the device counters and flags
+// after all work queued on s so far.  The host spins on the mapped flag
+// (a few microseconds after the GPU gets there, where a copy plus a stream
+// synchronisation costs about ten); after about a second without the flag it
+// falls back to synchronising the stream, which also reports a CUDA error.
 mst_status readback(mst_ctx *c, cudaStream_t s) {
-  CK(cudaMemcpyAsync(c->hs, c->ds, sizeof(DevState), cudaMemcpyDeviceToHost, s));
-  CK(cudaStreamSynchronize(s));
+  static_assert(sizeof(DevState) % 4 == 0, "DevState is copied in words");
+  const uint32_t seq = ++c->rb_seq;
+  readback_kernel<<<1, 32, 0, s>>>(c->ds, c->hs_dev, c->hflag_dev, seq);
+  CK(cudaGetLastError());
+  bool seen = false;
+  for (uint64_t spin = 0; spin < (1ULL << 26); ++spin) {
+    if (__atomic_load_n(c->hflag, __ATOMIC_ACQUIRE) == seq) {
+      seen = true;
+      break;
+    }
+    if ((spin & 0x3ffff) == 0x3ffff && cudaStreamQuery(s) != cudaErrorNotReady) {  // a fault: stop waiting
+      seen = __atomic_load_n(c->hflag, __ATOMIC_ACQUIRE) == seq;
+      break;
+    }
+  }
+  if (!seen) CK(cudaStreamSynchronize(s));
+  if (__atomic_load_n(c->hflag, __ATOMIC_ACQUIRE) != seq) return MST_ERR_CUDA;
   prof_resolve(c);
   if (c->hs->err & ERR_VERTEX) return MST_ERR_VERTEX_RANGE;
   if (c->hs->err & ERR_TABLE) return MST_ERR_INVALID_ARG;
@@ -508,7 +586,9 @@ struct Solve {
     uint64_t n_act = c->hs->count[CNT_ACTIVE];
     ++rounds;
 
-    ListBuf X, Y, T;
+    RoundList X, Y;  // the handle's round lists (lists only shrink within a call: mE edges suffice)
+    TRY(round_lists(c, mE, X, Y));
+    ListBuf T;
     Buf table_b;
     EdgeList cur = E;
     uint64_t cur_m = mE;
@@ -529,8 +609,7 @@ struct Solve {
           continue;
         }
       }
-      ListBuf &out = (cur.u == X.out.u) ? Y : X;
-      if (out.cap < cur_m) TRY(out.alloc(c, cur_m, s));
+      RoundList &out = (cur.u == X.out.u) ? Y : X;
       TRY(zero_round_state(c, s));
       CompactArgs ca{};
       ca.shape = shape;
@@ -632,20 +711,22 @@ struct Solve {
   // host when the base case fits, when a round's pointer jumping needs more
   // than the four launches a round holds, or at the round bound.  Counts live
   // in device memory; nothing in the body waits for the host.
-  mst_status graph_rounds(ListBuf &X, ListBuf &Y, EdgeList &cur, uint64_t &cur_m, uint64_t &n_act, int &a,
+  mst_status graph_rounds(RoundList &X, RoundList &Y, EdgeList &cur, uint64_t &cur_m, uint64_t &n_act, int &a,
                           int rounds_left, bool &used, bool &done, int &ran) {
     used = false;
     done = false;
     ran = 0;
-    const uint64_t cap = cur_m, nmax = n_act;
-    if (Y.cap < cap) TRY(Y.alloc(c, cap, s));
+    // launch bounds baked into the graph: the lists' capacity and n (the
+    // kernels read the actual counts from device memory), so the graph does
+    // not depend on this call's sizes
+    const uint64_t cap = std::min(X.cap, Y.cap), nmax = n;
     if (!c->grounds) CK(cudaMalloc(&c->grounds, sizeof(GraphRounds)));
     if (!c->cap_stream) CK(cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
     GraphRounds *g = c->grounds;
     const int base_ok = c->cfg.base_case ? 1 : 0;
     const int jl = c->cfg.graph_jump_launches;
     const uint32_t max_iter = (uint32_t)(rounds_left > 2 ? rounds_left / 2 : 1);
-    const ListBuf *L[2] = {&X, &Y};
+    const RoundList *L[2] = {&X, &Y};
     uint32_t *A[2] = {act[a], act[1 - a]};
     // A built graph is reused when every value baked into it is unchanged.
     u64 sig = 0x2302121990ULL;
@@ -705,7 +786,7 @@ struct Solve {
   // body is two rounds (slot 0 -> 1, slot 1 -> 0), each compaction (relabel +
   // minEdges relaxation), hooking, `jl` pointer-jumping launches and a check;
   // the body ends with the kernel that sets the loop condition.
-  mst_status build_round_graph(u64 sig, const ListBuf *const L[2], uint32_t *const A[2], uint64_t cap, uint64_t nmax,
+  mst_status build_round_graph(u64 sig, const RoundList *const L[2], uint32_t *const A[2], uint64_t cap, uint64_t nmax,
                                int base_ok, int jl, uint32_t max_iter, cudaGraphExec_t &exec_out) {
     GraphRounds *g = c->grounds;
     cudaStream_t cs = c->cap_stream;
@@ -1445,7 +1526,11 @@ mst_status mst_create(mst_handle *out, const mst_config *cfg) {
   }
   ok = ok && cudaMalloc(&c->ds, sizeof(DevState)) == cudaSuccess;
   ok = ok && cudaMemset(c->ds, 0, sizeof(DevState)) == cudaSuccess;
-  ok = ok && cudaMallocHost(&c->hs, sizeof(DevState)) == cudaSuccess;
+  ok = ok && cudaHostAlloc(&c->hs, sizeof(DevState), cudaHostAllocMapped) == cudaSuccess;
+  ok = ok && cudaHostGetDevicePointer((void **)&c->hs_dev, c->hs, 0) == cudaSuccess;
+  ok = ok && cudaHostAlloc(&c->hflag, 64, cudaHostAllocMapped) == cudaSuccess;
+  ok = ok && cudaHostGetDevicePointer((void **)&c->hflag_dev, c->hflag, 0) == cudaSuccess;
+  if (ok) *c->hflag = 0;
   ok = ok && cudaMallocHost(&c->hres, 2 * sizeof(u64)) == cudaSuccess;
   ok = ok && ensure_sample(c) == MST_OK;
   ok = ok && cudaMalloc(&c->pivot_scratch, pivot_scratch_bytes()) == cudaSuccess;
@@ -1467,10 +1552,12 @@ void mst_destroy(mst_handle h) {
     cudaDeviceSynchronize();
     if (h->ds) cudaFree(h->ds);
     if (h->hs) cudaFreeHost(h->hs);
+    if (h->hflag) cudaFreeHost(h->hflag);
     if (h->hres) cudaFreeHost(h->hres);
     for (int k = 0; k < 2; ++k)
       if (h->hin[k]) cudaFree(h->hin[k]);
     if (h->hout) cudaFree(h->hout);
+    if (h->rl_mem) cudaFree(h->rl_mem);
     if (h->status) cudaFree(h->status);
     if (h->sample_buf) cudaFree(h->sample_buf);
     if (h->pivot_scratch) cudaFree(h->pivot_scratch);
@@ -1544,7 +1631,8 @@ uint64_t mst_workspace_bytes(uint32_t n, uint64_t m, const mst_config *cfg) {
   const uint64_t vert = (uint64_t)n * (8 + 4 + 4 + 4);  // best, parent, two active lists
   const uint64_t bits = (m + 31) / 32 * 4;
   const uint64_t list = 16 * m + 1024;
-  uint64_t edges = 2 * list;                                    // ping-pong lists
+  uint64_t edges = 2 * (list + list / 4 + (16ULL << 16));       // the handle's ping-pong round lists (grown with
+                                                                 // a quarter of headroom, in steps of 2^16 edges)
   if (cfg->dedupe != MST_DEDUPE_NONE) edges += list + 32 * m + 16384;  // dedupe list + hash table
   if (cfg->variant != MST_VARIANT_BORUVKA) edges += 2 * list;   // partition levels and filtered lists
   return vert + bits + edges;
