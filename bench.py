@@ -70,10 +70,10 @@ WORKLOADS = {
 # hashes differently, traffic is reported as null until it is captured again.
 TRAFFIC = {
     "class": "filter",
-    "kernel": "filter_warp_kernel<CM_FILTER>",
-    "dram_per_algorithmic_byte": 1.209,
+    "kernel": "stream_warp_kernel<CM_FILTER>",
+    "dram_per_algorithmic_byte": 1.212,
     "measured_on": "RMAT n=2^22 m=2^26, all 5 filter launches of one timed solve",
-    "source_sha256": "dc6afd65e3c4f333ed37cdb3095f13cb51bff708c5e396fb095dca3f9539a475",
+    "source_sha256": "1403187f59ad670281435b533e34535ff9e1a068df6ab05bad431532ee5e596a",
 }
 TRAFFIC_SOURCE = ("paper_2302_12199_gb300/csrc/kernels.cu",
                   "__device__ __forceinline__ uint32_t keep_flags",

@@ -9,7 +9,7 @@
 // per list: each block takes a tile of B x I items (256 x 8 by default; the
 // shape is a run-time choice), stages the tile's survivors in shared memory,
 // and claims its output range with one atomic add.  The filter pass streams
-// per warp instead (filter_warp_kernel).  Lists therefore come out in an
+// per warp instead (stream_warp_kernel).  Lists therefore come out in an
 // unspecified order; nothing downstream depends on list order, because edges
 // are keyed by id and a vertex finds its chosen edge through the input arrays.  The output ids (finalize) are the one
 // ordered compaction: a decoupled look-back scan (Merrill & Garland, 2016).
@@ -737,44 +737,43 @@ __global__ void __launch_bounds__(B, Shape<B, I>::minb(Shape<B, I>::tma_regs)) c
   }
 }
 
-// ------------------------------------------------- warp-streamed filter pass
+// ------------------------------------------------- warp-streamed passes
 
 // The filter keeps few of the edges it reads (on RMAT about 2% of a level's
 // list: the heavy edges between different components of the light forest,
 // Thm. 1), so its pass is a stream with gathers more than a compaction, and
 // the gathers (giant-component bitmap words, then labels) set its speed.  Here
-// every warp streams its own tiles of FW_TILE edges: warp gw of the G warps in
+// every warp streams its own tiles of 32 x I edges: warp gw of the G warps in
 // the grid takes tiles gw, gw + G, gw + 2G, ...; a full tile arrives in one of
-// the warp's FW_STAGES shared-memory stages by bulk copies (one per array,
-// completion counted on the stage's mbarrier) issued FW_STAGES tiles ahead, and
-// the stage is refilled as soon as the tile is in registers, so the next
-// tile's copy overlaps this tile's gathers.  The warp's survivors go to its
-// own FW_OUT-entry staging buffer, which is written out (one atomic claim of
-// output slots, coalesced stores, then the best[] relaxation and recorded
-// ends) when it fills and when the warp finishes.  No block-wide barrier is on
-// the path: a warp waiting on its gathers never holds up another.
+// the warp's S shared-memory stages by bulk copies (one per array, completion
+// counted on the stage's mbarrier) issued S tiles ahead, and the stage is
+// refilled as soon as the tile is in registers, so the next tile's copy
+// overlaps this tile's gathers.  The warp's survivors go to its own O-entry
+// staging buffer, which is written out (one atomic claim of output slots,
+// coalesced stores, then the best[] relaxation and recorded ends) when it
+// fills and when the warp finishes.  No block-wide barrier is on the path: a
+// warp waiting on its gathers never holds up another.
 //
-// The shapes are measured on GB300 (RMAT n=2^24, m=2^28, filter class per
-// solve): 32 warps x 4 edges per lane, one stage: 2.49 ms; 16 warps x 8, two
-// blocks per SM: 2.49; 24 x 8, one stage: 2.58; 24 x 8, two stages: 4.39; the
-// block-synchronous compaction kernel: 4.02.  Shared memory is the lever: the
-// rest of the SM's 256 KB is L1, which serves the hub vertices' bitmap words
-// and labels, so a deep ring (216 KB) lost to a single stage (80 KB).
-constexpr int FW_WARPS = 32;              // warps per block; one block per SM
-constexpr int FW_ITEMS = 4;               // edges per lane and tile (a multiple of 4)
-constexpr int FW_STAGES = 1;              // input stages per warp
-constexpr int FW_OUT = 32;                // survivor staging entries per warp
-constexpr int FW_MINB = 1;                // resident blocks per SM the registers are sized for
-constexpr int FW_THREADS = FW_WARPS * 32;
-constexpr int FW_TILE = 32 * FW_ITEMS;    // edges per warp tile
-
-struct __align__(16) WarpStage {
-  uint32_t u[FW_TILE], v[FW_TILE], w[FW_TILE], id[FW_TILE];
+// The filter's shape is measured on GB300 (RMAT n=2^24, m=2^28, filter class
+// per solve): 32 warps x 4 edges per lane, one stage: 2.49 ms; 16 warps x 8,
+// two blocks per SM: 2.49; 24 x 8, one stage: 2.58; 24 x 8, two stages: 4.39;
+// the block-synchronous compaction kernel: 4.02.  Shared memory is the lever:
+// the rest of the SM's 256 KB is L1, which serves the hub vertices' bitmap
+// words and labels, so a deep ring (216 KB) lost to a single stage (80 KB).
+template <int W, int I, int S, int O, int MINB>
+struct WarpShape {
+  static constexpr int warps = W, items = I, stages = S, out = O, minb = MINB;
+  static constexpr int threads = W * 32;
+  static constexpr int tile = 32 * I;  // edges per warp tile
+  struct __align__(16) Stage {
+    uint32_t u[tile], v[tile], w[tile], id[tile];
+  };
+  struct __align__(16) Out {
+    uint32_t u[O], v[O], w[O], id[O];
+  };
+  static constexpr size_t smem = sizeof(Stage) * S * W + sizeof(Out) * W;
 };
-struct __align__(16) WarpOut {
-  uint32_t u[FW_OUT], v[FW_OUT], w[FW_OUT], id[FW_OUT];
-};
-constexpr size_t FW_SMEM = sizeof(WarpStage) * FW_STAGES * FW_WARPS + sizeof(WarpOut) * FW_WARPS;
+using FilterWarp = WarpShape<32, 4, 1, 32, 1>;
 
 // Item k of lane l in a warp tile sits at (k / 4) * 128 + 4 l + k % 4, so each
 // 16-byte shared-memory read of the warp covers 512 contiguous bytes.
@@ -782,11 +781,12 @@ __device__ __forceinline__ uint32_t witem_off(int k) {
   return (uint32_t)((k >> 2) * 128 + 4 * (threadIdx.x & 31) + (k & 3));
 }
 
-__device__ __forceinline__ void read_wstage(const uint32_t *p, uint32_t (&x)[FW_ITEMS]) {
+template <int I>
+__device__ __forceinline__ void read_wstage(const uint32_t *p, uint32_t (&x)[I]) {
   const uint4 *q = reinterpret_cast<const uint4 *>(p);
   const int lane = threadIdx.x & 31;
 #pragma unroll
-  for (int c = 0; c < FW_ITEMS / 4; ++c) {
+  for (int c = 0; c < I / 4; ++c) {
     const uint4 t = q[32 * c + lane];
     x[4 * c] = t.x;
     x[4 * c + 1] = t.y;
@@ -796,9 +796,10 @@ __device__ __forceinline__ void read_wstage(const uint32_t *p, uint32_t (&x)[FW_
 }
 
 // Issues the bulk copies of full warp tile `tile` into stage `st` (one lane).
-__device__ __forceinline__ void issue_wtile(const CompactArgs &a, uint64_t tile, WarpStage *st, u64 *bar) {
-  const uint32_t bytes = FW_TILE * 4;
-  const uint64_t off = tile * FW_TILE;
+template <class WS>
+__device__ __forceinline__ void issue_wtile(const CompactArgs &a, uint64_t tile, typename WS::Stage *st, u64 *bar) {
+  const uint32_t bytes = WS::tile * 4;
+  const uint64_t off = tile * WS::tile;
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // order the stage's earlier generic reads
   mbar_arrive_expect_tx(bar, (a.in.id ? 4u : 3u) * bytes);
   bulk_load(st->u, a.in.u + off, bytes, bar);
@@ -808,7 +809,8 @@ __device__ __forceinline__ void issue_wtile(const CompactArgs &a, uint64_t tile,
 }
 
 // Writes the warp's `count` staged survivors to the output list (all lanes).
-__device__ __forceinline__ void warp_flush(const CompactArgs &a, const WarpOut *o, uint32_t count) {
+template <class WS>
+__device__ __forceinline__ void warp_flush(const CompactArgs &a, const typename WS::Out *o, uint32_t count) {
   const int lane = threadIdx.x & 31;
   unsigned long long base = 0;
   if (lane == 0) base = atomicAdd(a.st.total, (unsigned long long)count);
@@ -833,26 +835,29 @@ __device__ __forceinline__ void warp_flush(const CompactArgs &a, const WarpOut *
   __syncwarp();  // the staging buffer is refilled next
 }
 
-template <int MODE>
-__global__ void __launch_bounds__(FW_THREADS, FW_MINB) filter_warp_kernel(CompactArgs a) {
+template <int MODE, class WS>
+__global__ void __launch_bounds__(WS::threads, WS::minb) stream_warp_kernel(CompactArgs a) {
   static_assert(MODE == CM_FILTER || MODE == CM_HEAVY, "the warp-streamed pass serves the filter modes");
+  constexpr int I = WS::items, S = WS::stages, O = WS::out, T = WS::tile;
+  using Stage = typename WS::Stage;
+  using Out = typename WS::Out;
   extern __shared__ __align__(128) unsigned char smem_dyn[];
-  __shared__ __align__(8) u64 mbar[FW_WARPS][FW_STAGES];
+  __shared__ __align__(8) u64 mbar[WS::warps][S];
   const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  WarpStage *stage = reinterpret_cast<WarpStage *>(smem_dyn) + wid * FW_STAGES;
-  WarpOut *o = reinterpret_cast<WarpOut *>(smem_dyn + sizeof(WarpStage) * FW_STAGES * FW_WARPS) + wid;
+  Stage *stage = reinterpret_cast<Stage *>(smem_dyn) + wid * S;
+  Out *o = reinterpret_cast<Out *>(smem_dyn + sizeof(Stage) * S * WS::warps) + wid;
   u64 *bar = mbar[wid];
 
   const uint64_t m = a.m_dev ? *a.m_dev : a.m;
-  const uint64_t ntiles = (m + FW_TILE - 1) / FW_TILE, nfull = m / FW_TILE;
-  const uint64_t G = (uint64_t)gridDim.x * FW_WARPS;
-  const uint64_t gw = (uint64_t)blockIdx.x * FW_WARPS + wid;
+  const uint64_t ntiles = (m + T - 1) / T, nfull = m / T;
+  const uint64_t G = (uint64_t)gridDim.x * WS::warps;
+  const uint64_t gw = (uint64_t)blockIdx.x * WS::warps + wid;
   if (lane == 0) {
-    for (int s = 0; s < FW_STAGES; ++s) mbar_init(&bar[s], 1);
+    for (int s = 0; s < S; ++s) mbar_init(&bar[s], 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    for (int s = 0; s < FW_STAGES; ++s) {
+    for (int s = 0; s < S; ++s) {
       const uint64_t tile = gw + (uint64_t)s * G;
-      if (tile < nfull) issue_wtile(a, tile, &stage[s], &bar[s]);
+      if (tile < nfull) issue_wtile<WS>(a, tile, &stage[s], &bar[s]);
     }
   }
   __syncwarp();
@@ -863,35 +868,35 @@ __global__ void __launch_bounds__(FW_THREADS, FW_MINB) filter_warp_kernel(Compac
   for (;; ++it) {
     const uint64_t tile = gw + it * G;
     if (tile >= ntiles) break;
-    const uint64_t tb = tile * FW_TILE;
-    uint32_t eu[FW_ITEMS], ev[FW_ITEMS], ew[FW_ITEMS], ei[FW_ITEMS];
-    uint32_t valid = (FW_ITEMS >= 32 ? 0xffffffffu : (1u << FW_ITEMS) - 1u);
+    const uint64_t tb = tile * T;
+    uint32_t eu[I], ev[I], ew[I], ei[I];
+    uint32_t valid = (I >= 32 ? 0xffffffffu : (1u << I) - 1u);
     if (tile < nfull) {
-      const int si = (int)(it % FW_STAGES);
-      WarpStage *st = &stage[si];
-      const bool ok = mbar_wait_bounded(&bar[si], (uint32_t)((it / FW_STAGES) & 1));
+      const int si = (int)(it % S);
+      Stage *st = &stage[si];
+      const bool ok = mbar_wait_bounded(&bar[si], (uint32_t)((it / S) & 1));
       if (!__all_sync(0xffffffffu, ok)) {
         abort = true;
         break;
       }
-      read_wstage(st->u, eu);
-      read_wstage(st->v, ev);
-      read_wstage(st->w, ew);
+      read_wstage<I>(st->u, eu);
+      read_wstage<I>(st->v, ev);
+      read_wstage<I>(st->w, ew);
       if (a.in.id) {
-        read_wstage(st->id, ei);
+        read_wstage<I>(st->id, ei);
       } else {
 #pragma unroll
-        for (int k = 0; k < FW_ITEMS; ++k) ei[k] = (uint32_t)(tb + witem_off(k));
+        for (int k = 0; k < I; ++k) ei[k] = (uint32_t)(tb + witem_off(k));
       }
-      __syncwarp();  // every lane has the tile: refill the stage with the tile FW_STAGES ahead
+      __syncwarp();  // every lane has the tile: refill the stage with the tile S ahead
       if (lane == 0) {
-        const uint64_t next = tile + (uint64_t)FW_STAGES * G;
-        if (next < nfull) issue_wtile(a, next, st, &bar[si]);
+        const uint64_t next = tile + (uint64_t)S * G;
+        if (next < nfull) issue_wtile<WS>(a, next, st, &bar[si]);
       }
     } else {  // the partial last tile: plain loads
       valid = 0;
 #pragma unroll
-      for (int k = 0; k < FW_ITEMS; ++k) {
+      for (int k = 0; k < I; ++k) {
         const uint64_t j = tb + witem_off(k);
         if (j < m) {
           eu[k] = __ldg(a.in.u + j);
@@ -916,9 +921,9 @@ __global__ void __launch_bounds__(FW_THREADS, FW_MINB) filter_warp_kernel(Compac
     const uint32_t total = __shfl_sync(0xffffffffu, incl, 31), excl = incl - c;
     // append the ranks [lo, lo + take) to the free part of the staging buffer
     for (uint32_t lo = 0; lo < total;) {
-      const uint32_t take = min((uint32_t)FW_OUT - fill, total - lo);
+      const uint32_t take = min((uint32_t)O - fill, total - lo);
 #pragma unroll
-      for (int k = 0; k < FW_ITEMS; ++k) {
+      for (int k = 0; k < I; ++k) {
         if (!(keep >> k & 1)) continue;
         const uint32_t r = excl + (uint32_t)__popc(keep & ((1u << k) - 1u));
         if (r >= lo && r < lo + take) {
@@ -932,14 +937,14 @@ __global__ void __launch_bounds__(FW_THREADS, FW_MINB) filter_warp_kernel(Compac
       __syncwarp();
       fill += take;
       lo += take;
-      if (fill == FW_OUT) {
-        warp_flush(a, o, fill);
+      if (fill == (uint32_t)O) {
+        warp_flush<WS>(a, o, fill);
         fill = 0;
       }
     }
   }
   if (!abort) {
-    if (fill) warp_flush(a, o, fill);
+    if (fill) warp_flush<WS>(a, o, fill);
     return;
   }
   // A bulk copy never completed: this warp's remaining tiles were not read.
@@ -948,9 +953,9 @@ __global__ void __launch_bounds__(FW_THREADS, FW_MINB) filter_warp_kernel(Compac
   // before the block's shared memory goes away.
   if (lane == 0) {
     atomicOr(a.st.err, ERR_TMA);
-    for (uint64_t k = it; k < it + FW_STAGES; ++k) {
+    for (uint64_t k = it; k < it + S; ++k) {
       const uint64_t tile = gw + k * G;
-      if (tile < nfull) mbar_wait_bounded(&bar[k % FW_STAGES], (uint32_t)((k / FW_STAGES) & 1));
+      if (tile < nfull) mbar_wait_bounded(&bar[k % S], (uint32_t)((k / S) & 1));
     }
   }
   __syncwarp();
@@ -2693,32 +2698,38 @@ static void launch_compact_shaped(const CompactArgs &a, uint64_t max_count, bool
   }
 }
 
+// The warp-streamed pass over a list, if the device runs it (false: not
+// launched, the caller uses the block kernels).
+template <int MODE, class WS>
+static bool launch_warp_stream(const CompactArgs &a, uint64_t max_count, cudaStream_t s) {
+  static int blocks = -1;  // resident blocks of the pass (0: not available)
+  if (blocks < 0) {
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (cudaFuncSetAttribute(stream_warp_kernel<MODE, WS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)WS::smem) == cudaSuccess &&
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, stream_warp_kernel<MODE, WS>, WS::threads, WS::smem) ==
+            cudaSuccess)
+      blocks = sms * per_sm;
+    else
+      blocks = 0;
+    cudaGetLastError();
+  }
+  if (blocks <= 0) return false;
+  const uint64_t wtiles = (max_count + WS::tile - 1) / WS::tile;
+  const uint64_t want = (wtiles + WS::warps - 1) / WS::warps;
+  const unsigned grid = (unsigned)std::min<uint64_t>(want, (uint64_t)blocks);
+  stream_warp_kernel<MODE, WS><<<grid, WS::threads, WS::smem, s>>>(a);
+  return true;
+}
+
 template <int MODE>
 static void launch_compact_mode(const CompactArgs &a, uint64_t max_count, cudaStream_t s) {
   if (max_count == 0) return;
   const bool aligned = aligned16(a.in.u) && aligned16(a.in.v) && aligned16(a.in.w) && (!a.in.id || aligned16(a.in.id));
   if constexpr (MODE == CM_FILTER || MODE == CM_HEAVY) {
-    static int fw_blocks = -1;  // resident blocks of the warp-streamed pass (0: not available)
-    if (fw_blocks < 0) {
-      int dev = 0, sms = 0, per_sm = 0;
-      cudaGetDevice(&dev);
-      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-      if (cudaFuncSetAttribute(filter_warp_kernel<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)FW_SMEM) ==
-              cudaSuccess &&
-          cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, filter_warp_kernel<MODE>, FW_THREADS, FW_SMEM) ==
-              cudaSuccess)
-        fw_blocks = sms * per_sm;
-      else
-        fw_blocks = 0;
-      cudaGetLastError();
-    }
-    if (aligned && fw_blocks > 0) {
-      const uint64_t wtiles = (max_count + FW_TILE - 1) / FW_TILE;
-      const uint64_t want = (wtiles + FW_WARPS - 1) / FW_WARPS;
-      const unsigned grid = (unsigned)std::min<uint64_t>(want, (uint64_t)fw_blocks);
-      filter_warp_kernel<MODE><<<grid, FW_THREADS, FW_SMEM, s>>>(a);
-      return;
-    }
+    if (aligned && launch_warp_stream<MODE, FilterWarp>(a, max_count, s)) return;
   }
   if constexpr (MODE == CM_RELABEL || MODE == CM_PARTITION) {
     switch (a.shape) {  // the shapes of shape_index
