@@ -901,7 +901,9 @@ struct Solve {
          launched = launch_base_case(act_list, n_act, cur, cur_m, parent, bits, b, &c->ds->err, s, c->cfg.tile_filter,
                                      c->wsum));
     if (!launched) return MST_ERR_INTERNAL;
-    return readback(c, s);
+    // no readback: the base case produces no count the host needs, and an
+    // error bit it sets stays latched until the next readback reports it
+    return MST_OK;
   }
 
   // Local preprocessing (Section 4.1) on vertex-range tiles.  When applied,
