@@ -395,6 +395,8 @@ def gpu_main(args, rank: int, world: int, local_rank: int):
         cfg["min_edges_sort"] = args.min_edges_sort
     if args.tile_filter is not None:
         cfg["tile_filter"] = args.tile_filter
+    if args.filter_plan is not None:
+        cfg["filter_plan"] = args.filter_plan
     g = gen(W)
     n, m = g.n, g.m
     src = torch.from_numpy(g.src.view(np.int32)).to(dev)
@@ -434,6 +436,7 @@ def gpu_main(args, rank: int, world: int, local_rank: int):
     # roofline's measured durations); every class still counts its launches
     # and algorithmic bytes, which costs the host almost nothing per launch
     solver.profile(True, classes=[dom])
+    hc0 = solver.host_counters()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     nvtx_mark(torch, "push")  # lets a profiler capture the timed solves only
     e0.record(stream)
@@ -441,6 +444,12 @@ def gpu_main(args, rank: int, world: int, local_rank: int):
         solver.solve(n, src, dst, w, out=out)
     e1.record(stream)
     nvtx_mark(torch, "pop")
+    hc1 = solver.host_counters()
+    host = {"readbacks_per_step": (hc1["readbacks"] - hc0["readbacks"]) / args.steps,
+            "planned_steps": hc1["planned"] - hc0["planned"],
+            "plan_fallbacks": hc1["plan_fallbacks"] - hc0["plan_fallbacks"],
+            "note": "host waits for device counts per solve; planned: Filter-Borůvka recursion laid out "
+                    "from the top-level light count, lengths kept on the device"}
     torch.cuda.synchronize(dev)
     solver.profile(False)
     if dist:
@@ -540,6 +549,7 @@ def gpu_main(args, rank: int, world: int, local_rank: int):
         "kernels_note": f"per-class CUDA-event times of {prof_steps} profiled solves outside the timed region; "
                         "inside it only the dominant class is timed",
         "gpu_launches": launches,
+        "host": host,
         "e2e": e2e,
         "clocks": clocks,
         "msf": {"edges": int(ids.size), "weight": int(total)},
@@ -834,6 +844,7 @@ def measure_batched(args, rank: int, world: int, local_rank: int, dev, dist, com
         "kernels_note": f"per-class CUDA-event times of {prof_steps} profiled batches outside the timed region; "
                         "inside it only the dominant class is timed",
         "gpu_launches": launches,
+        "host": host,
         "e2e": e2e,
         "clocks": clocks,
     }
@@ -987,6 +998,7 @@ def main():
     ap.add_argument("--filter-split", type=int, default=None, choices=[0, 1])
     ap.add_argument("--min-edges-sort", type=int, default=None, choices=[0, 1])
     ap.add_argument("--tile-filter", type=int, default=None, choices=[0, 1])
+    ap.add_argument("--filter-plan", type=int, default=None, choices=[0, 1])
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "gpu":
         args.warmup = 3

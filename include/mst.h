@@ -107,6 +107,15 @@ typedef struct {
   uint32_t items_per_thread;   /* edges (or vertices) per thread of those kernels: 4, 8 or 16 (0 = 8); a
                                   block handles block_threads x items_per_thread per tile.  Both are
                                   autotuner choices; every shape computes the same forest */
+  int filter_plan;             /* Filter-Borůvka (Alg. 2) with the default filter options (no carry, one
+                                  filter pass, CUDA-graph rounds, no dedupe, no local contraction):
+                                  1 (default): after the top-level partition, the host plans the
+                                  remaining recursion levels and list capacities from its light count
+                                  and queues every level without reading counts back (lengths stay in
+                                  device memory; Borůvka rounds run as device-ended graph loops); the
+                                  call reads back twice.  If a list outgrows its planned capacity or a
+                                  round needs the host, the call starts over on the host-driven path
+                                  (same result).  0: the host reads every level's counts */
 } mst_config;
 
 /* Fills *cfg with the defaults (Borůvka variant, automatic dedupe, pivot sample
@@ -241,6 +250,17 @@ mst_status mst_profile_classes(mst_handle h, uint32_t mask);
 
 /* Totals of class `kind` (MST_K_*) since the last enable. */
 mst_status mst_profile_get(mst_handle h, int kind, mst_kernel_stats *out);
+
+/* Host-side counters of a handle since its creation (always on). */
+typedef struct {
+  uint64_t solves;         /* solves that reached the device (a batched solve counts once) */
+  uint64_t readbacks;      /* times the host waited for device counts (each ends the GPU's queue for a
+                              few microseconds; the planned Filter-Borůvka needs two per solve) */
+  uint64_t planned;        /* solves that took the planned Filter-Borůvka path (mst_config.filter_plan) */
+  uint64_t plan_fallbacks; /* of those, solves whose plan did not hold and that started over on the
+                              host-driven path */
+} mst_host_counters;
+mst_status mst_host_counters_get(mst_handle h, mst_host_counters *out);
 
 /* ----------------------------------------------------------------------
  * Step entry points: one step of the method each, on caller buffers, so that

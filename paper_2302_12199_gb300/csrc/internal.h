@@ -17,21 +17,27 @@ enum : uint32_t {
   ERR_JUMP = 8u,      // pointer doubling did not reach a root within its bound
   ERR_TMA = 16u,      // a bulk copy never completed (bounded mbarrier wait ran out); tiles were skipped
   ERR_TABLE = 32u,    // a batched size table is inconsistent (offsets not starting at 0 or decreasing)
+  ERR_OVERFLOW = 64u, // a compaction's survivors exceeded its output capacity (nothing past it was written)
+  ERR_HANDBACK = 128u,  // device-driven rounds met a case that needs the host (long jump chain, round bound)
 };
 
 // Small per-handle device state.
+constexpr int LVL_MAX = 32;  // recursion levels of a planned Filter-Borůvka
 struct DevState {
   uint32_t err;
   uint32_t jump_flag;   // set when a pointer-jump launch left a vertex short of its root
   uint32_t tile_ctr[2]; // reserved
-  u64 count[6];         // counts written by the last tile of a scan kernel
+  u64 count[6 + 2 * LVL_MAX];  // counts written by the last tile of a scan kernel; from CNT_LVL on,
+                               //   the list lengths of a planned Filter-Borůvka (see CNT_LVL)
   u64 pivot;            // result of the pivot selection
   uint32_t giant_root;  // root of the largest sampled component (filter fast path)
   uint32_t max_w;       // largest input weight (key layout)
   uint32_t local_samples;  // sampled local edges (automatic tile contraction)
   uint32_t pad;
 };
-enum { CNT_EDGES = 0, CNT_ACTIVE = 1, CNT_TMP = 2, CNT_AUX = 3, CNT_USER = 4, CNT_CUT = 5 };
+// CNT_LVL + k: length of the light list of recursion level k (level 0: the
+// input); CNT_LVL + LVL_MAX + k: the filtered heavy edges of level k.
+enum { CNT_EDGES = 0, CNT_ACTIVE = 1, CNT_TMP = 2, CNT_AUX = 3, CNT_USER = 4, CNT_CUT = 5, CNT_LVL = 6 };
 
 // Output bookkeeping of a compaction launch.  Unordered compactions claim
 // their output ranges by atomic adds on *total (zero before the launch); the
@@ -82,8 +88,8 @@ enum CompactMode : int {
 
 struct CompactArgs {
   EdgeList in;
-  uint64_t m;              // input length (used when m_dev == nullptr)
-  const u64 *m_dev;        // input length in device memory, or nullptr
+  uint64_t m;              // input length, or with m_dev the input list's capacity
+  const u64 *m_dev;        // input length in device memory (read as min(*m_dev, m)), or nullptr
   EdgeOut out;
   const uint32_t *label;   // relabel / filter
   const uint32_t *giant_bits;  // filter: bitmap of the vertices in the largest component, or nullptr
@@ -100,6 +106,8 @@ struct CompactArgs {
   uint32_t *cur_u, *cur_v; // if set: cur_u[id], cur_v[id] = the survivor's written ends
   ScanState st;
   int shape;               // tile shape of the relabel / partition compaction (see shape_index)
+  uint64_t out_cap;        // if nonzero: output capacity; a tile that would write past it writes
+                           //   nothing and sets ERR_OVERFLOW (with m_dev, m bounds the input count)
 };
 
 struct HookArgs {
@@ -166,7 +174,7 @@ void launch_pivot(EdgeList in, uint64_t m, const u64 *m_dev, u64 state, uint32_t
 // cooperative launch was refused.
 size_t pivot_scratch_bytes();
 bool launch_pivot_coop(EdgeList in, uint64_t m, u64 state, uint32_t sample, u64 *keys, void *scratch,
-                       u64 *pivot_out, cudaStream_t s);
+                       u64 *pivot_out, cudaStream_t s, const u64 *m_dev = nullptr);
 // w == nullptr: ids and count only (total_weight untouched).
 void launch_finalize(const uint32_t *bits, uint64_t m, const uint32_t *w, uint32_t *out_ids, uint32_t *out_count,
                      u64 *total_weight, ScanState st, cudaStream_t s);
@@ -176,7 +184,7 @@ void launch_wsum_total(const u64 *wsum, u64 *total, cudaStream_t s);
 // sampled edge ends (P is walked to the roots); launch_giant_bits also marks
 // its vertices (bit v set iff P[v] is that root; P fully contracted).
 void launch_giant_root(EdgeList in, uint64_t m, u64 state, const uint32_t *P, uint32_t n, uint32_t *root_tmp,
-                       cudaStream_t s);
+                       cudaStream_t s, const u64 *m_dev = nullptr);
 void launch_giant_bits(EdgeList in, uint64_t m, u64 state, const uint32_t *P, uint32_t n, uint32_t *root_tmp,
                        uint32_t *bits, int sms, cudaStream_t s);
 // tile-local contraction (Section 4.1)
@@ -223,9 +231,17 @@ struct GraphRounds {
   uint32_t reason, slot;
 };
 void launch_round_init(GraphRounds *g, uint64_t m, uint64_t n_act, cudaStream_t s);
-void launch_round_check(GraphRounds *g, int base_ok, cudaStream_t s);
+// The same from a device count of edges (at most cap); the active count is
+// zeroed for the hooking launch of the call's first round to fill.
+void launch_round_init_dev(GraphRounds *g, const u64 *m_dev, uint64_t cap, cudaStream_t s);
+// The graph's first node: enter the loop only with active vertices and edges
+// and a finished jump (else end it; a jump left short is ERR_HANDBACK in
+// *err_handback when that is given, the device-driven mode).
+void launch_round_pre(GraphRounds *g, cudaGraphConditionalHandle h, u64 *out_counts, uint32_t *err_handback,
+                      cudaStream_t s);
+void launch_round_check(GraphRounds *g, int base_ok, uint32_t *err_handback, cudaStream_t s);
 void launch_round_cond(GraphRounds *g, cudaGraphConditionalHandle h, int base_ok, uint32_t max_iter, u64 *out_counts,
-                       cudaStream_t s);
+                       uint32_t *err_handback, cudaStream_t s);
 
 // single-block base case: the last rounds of a Borůvka call in one launch
 constexpr uint32_t BASE_MAX_N = 4096;  // live components (16-bit local ends; shared-memory vertex arrays)

@@ -468,6 +468,17 @@ __device__ __forceinline__ void emit_survivors(const CompactArgs &a, uint32_t ke
   }
 }
 
+// The number of a tile's `total` survivors to write at obase: all of them, or
+// those that fit below the output capacity (and ERR_OVERFLOW, once per tile).
+// Writing the part that fits keeps every slot below the capacity written, so
+// a reader that takes min(count, capacity) entries never sees an unwritten
+// one.  The same in every thread of the block.
+__device__ __forceinline__ uint32_t within_capacity(const CompactArgs &a, uint64_t obase, uint32_t total) {
+  if (!a.out_cap || obase + total <= a.out_cap) return total;
+  if (threadIdx.x == 0) atomicOr(a.st.err, ERR_OVERFLOW);
+  return obase < a.out_cap ? (uint32_t)(a.out_cap - obase) : 0u;
+}
+
 __device__ __forceinline__ u64 compact_pivot(const CompactArgs &a, int mode) {
   return (mode == CM_PARTITION || mode == CM_FILTER || mode == CM_HEAVY) ? (a.pivot_dev ? *a.pivot_dev : a.pivot)
                                                                          : 0ULL;
@@ -513,7 +524,7 @@ __global__ void __launch_bounds__(B, Shape<B, I>::minb(Shape<B, I>::compact_regs
   __shared__ uint32_t s_base[1];
   uint32_t *s_u = s_stage, *s_v = s_stage + T, *s_w = s_stage + 2 * T, *s_id = s_stage + 3 * T;
 
-  const uint64_t m = a.m_dev ? *a.m_dev : a.m;
+  const uint64_t m = a.m_dev ? min((uint64_t)*a.m_dev, a.m) : a.m;
   const uint64_t tb = (uint64_t)blockIdx.x * T;
   if (tb >= m) return;
 
@@ -555,7 +566,7 @@ __global__ void __launch_bounds__(B, Shape<B, I>::minb(Shape<B, I>::compact_regs
   uint32_t total;
   const uint32_t excl = block_exclusive_scan<B>((uint32_t)__popc(keep), total, s_warp);
   const uint64_t obase = tile_claim(a.st.total, total, s_base);
-  emit_survivors<B, I>(a, keep, excl, total, obase, eu, ev, ew, ei, s_u, s_v, s_w, s_id);
+  emit_survivors<B, I>(a, keep, excl, within_capacity(a, obase, total), obase, eu, ev, ew, ei, s_u, s_v, s_w, s_id);
 }
 
 // ------------------------------------------------ TMA-pipelined compaction
@@ -653,7 +664,7 @@ __global__ void __launch_bounds__(B, Shape<B, I>::minb(Shape<B, I>::tma_regs)) c
   __shared__ uint32_t s_base[1];
   __shared__ uint32_t s_abort;
 
-  const uint64_t m = a.m_dev ? *a.m_dev : a.m;
+  const uint64_t m = a.m_dev ? min((uint64_t)*a.m_dev, a.m) : a.m;
   const uint64_t ntiles = (m + T - 1) / T, nfull = m / T;
   const uint64_t G = gridDim.x;
   if (threadIdx.x == 0) {
@@ -720,7 +731,8 @@ __global__ void __launch_bounds__(B, Shape<B, I>::minb(Shape<B, I>::tma_regs)) c
     uint32_t total;
     const uint32_t excl = block_exclusive_scan<B>((uint32_t)__popc(keep), total, s_warp);
     const uint64_t obase = tile_claim(a.st.total, total, s_base);
-    emit_survivors<B, I>(a, keep, excl, total, obase, eu, ev, ew, ei, out->u, out->v, out->w, out->id);
+    emit_survivors<B, I>(a, keep, excl, within_capacity(a, obase, total), obase, eu, ev, ew, ei, out->u, out->v,
+                         out->w, out->id);
     __syncthreads();  // the output stage is reused by the next tile
   }
   // On an abort the block's remaining tiles were not compacted: latch the
@@ -815,6 +827,10 @@ __device__ __forceinline__ void warp_flush(const CompactArgs &a, const typename 
   unsigned long long base = 0;
   if (lane == 0) base = atomicAdd(a.st.total, (unsigned long long)count);
   base = __shfl_sync(0xffffffffu, base, 0);
+  if (a.out_cap && base + count > a.out_cap) {  // past the output capacity: write the part that fits
+    if (lane == 0) atomicOr(a.st.err, ERR_OVERFLOW);
+    count = base < a.out_cap ? (uint32_t)(a.out_cap - base) : 0u;
+  }
   for (uint32_t i = lane; i < count; i += 32) {
     const uint32_t x = o->u[i], y = o->v[i], w = o->w[i], id = o->id[i];
     a.out.u[base + i] = x;
@@ -848,7 +864,7 @@ __global__ void __launch_bounds__(WS::threads, WS::minb) stream_warp_kernel(Comp
   Out *o = reinterpret_cast<Out *>(smem_dyn + sizeof(Stage) * S * WS::warps) + wid;
   u64 *bar = mbar[wid];
 
-  const uint64_t m = a.m_dev ? *a.m_dev : a.m;
+  const uint64_t m = a.m_dev ? min((uint64_t)*a.m_dev, a.m) : a.m;
   const uint64_t ntiles = (m + T - 1) / T, nfull = m / T;
   const uint64_t G = (uint64_t)gridDim.x * WS::warps;
   const uint64_t gw = (uint64_t)blockIdx.x * WS::warps + wid;
@@ -1461,9 +1477,10 @@ struct PivotScratch {
   uint32_t hist[2][PSEL_BINS];
 };
 
-__global__ void __launch_bounds__(PSEL_THREADS) pivot_coop_kernel(EdgeList in, uint64_t m, u64 state,
-                                                                 uint32_t sample, u64 *keys, PivotScratch *ps,
-                                                                 u64 *out) {
+__global__ void __launch_bounds__(PSEL_THREADS) pivot_coop_kernel(EdgeList in, uint64_t m_bound, const u64 *m_dev,
+                                                                 u64 state, uint32_t sample, u64 *keys,
+                                                                 PivotScratch *ps, u64 *out) {
+  const uint64_t m = m_dev ? min((uint64_t)*m_dev, m_bound) : m_bound;
   namespace cg = cooperative_groups;
   cg::grid_group grid = cg::this_grid();
   __shared__ uint32_t s_hist[PSEL_BINS];
@@ -2354,11 +2371,50 @@ __global__ void round_init_kernel(GraphRounds *g, uint64_t m, uint64_t n_act) {
   g->saved_ce = g->saved_ca = 0;
 }
 
+// The same from a device count of edges; the active count is filled by the
+// hooking launch of the call's first round, which runs before the graph.
+__global__ void round_init_dev_kernel(GraphRounds *g, const u64 *m_dev, uint64_t cap) {
+  g->ce[0] = min((uint64_t)*m_dev, cap);
+  g->ca[0] = 0;
+  g->ce[1] = g->ca[1] = 0;
+  g->jflag = 0;
+  g->iter = 0;
+  g->reason = ROUNDS_RUNNING;
+  g->slot = 0;
+  g->saved_ce = g->saved_ca = 0;
+}
+
+// The graph's first node: run the loop only if there are active vertices and
+// edges and the jump before the graph reached the roots.  Otherwise end here
+// and publish the outcome as round_cond_kernel does.
+__global__ void round_pre_kernel(GraphRounds *g, cudaGraphConditionalHandle h, u64 *out_counts, uint32_t *err_handback) {
+  unsigned int go = 0;
+  if (g->jflag) {
+    g->reason = ROUNDS_JUMP;
+    if (err_handback) atomicOr(err_handback, ERR_HANDBACK);
+  } else if (g->ca[0] == 0 || g->ce[0] == 0) {
+    g->reason = ROUNDS_DONE;
+  } else {
+    go = 1;
+  }
+  if (!go) {
+    g->slot = 0;
+    g->saved_ce = g->ce[0];
+    g->saved_ca = g->ca[0];
+    out_counts[0] = g->saved_ce;
+    out_counts[1] = g->saved_ca;
+    out_counts[2] = (u64)g->reason;
+  }
+  g->jflag = 0;
+  cudaGraphSetConditional(h, go);
+}
+
 // After the first round of the body (slot 0 -> 1): stop early (the second
 // round then sees zero counts and does nothing) when the jump did not reach
 // the roots or the base case fits.
-__global__ void round_check_kernel(GraphRounds *g, int base_ok) {
+__global__ void round_check_kernel(GraphRounds *g, int base_ok, uint32_t *err_handback) {
   if (g->jflag || (base_ok && g->ca[1] > 0 && g->ca[1] <= BASE_MAX_N && g->ce[1] > 0 && g->ce[1] <= BASE_MAX_M)) {
+    if (g->jflag && err_handback) atomicOr(err_handback, ERR_HANDBACK);
     g->reason = g->jflag ? ROUNDS_JUMP : ROUNDS_BASE;
     g->slot = 1;
     g->saved_ce = g->ce[1];
@@ -2372,7 +2428,7 @@ __global__ void round_check_kernel(GraphRounds *g, int base_ok) {
 // After the second round (slot 1 -> 0): decide whether the body runs again,
 // and publish the outcome in the solver's counters (edges, active, info).
 __global__ void round_cond_kernel(GraphRounds *g, cudaGraphConditionalHandle h, int base_ok, uint32_t max_iter,
-                                  u64 *out_counts) {
+                                  u64 *out_counts, uint32_t *err_handback) {
   const uint32_t it = ++g->iter;
   unsigned int go = 0;
   if (g->reason == ROUNDS_RUNNING) {
@@ -2391,6 +2447,7 @@ __global__ void round_cond_kernel(GraphRounds *g, cudaGraphConditionalHandle h, 
       g->slot = 0;
       g->saved_ce = g->ce[0];
       g->saved_ca = g->ca[0];
+      if (err_handback && (g->reason == ROUNDS_JUMP || g->reason == ROUNDS_BOUND)) atomicOr(err_handback, ERR_HANDBACK);
     }
   }
   out_counts[0] = g->saved_ce;
@@ -2404,10 +2461,19 @@ __global__ void round_cond_kernel(GraphRounds *g, cudaGraphConditionalHandle h, 
 void launch_round_init(GraphRounds *g, uint64_t m, uint64_t n_act, cudaStream_t s) {
   round_init_kernel<<<1, 1, 0, s>>>(g, m, n_act);
 }
-void launch_round_check(GraphRounds *g, int base_ok, cudaStream_t s) { round_check_kernel<<<1, 1, 0, s>>>(g, base_ok); }
+void launch_round_init_dev(GraphRounds *g, const u64 *m_dev, uint64_t cap, cudaStream_t s) {
+  round_init_dev_kernel<<<1, 1, 0, s>>>(g, m_dev, cap);
+}
+void launch_round_pre(GraphRounds *g, cudaGraphConditionalHandle h, u64 *out_counts, uint32_t *err_handback,
+                      cudaStream_t s) {
+  round_pre_kernel<<<1, 1, 0, s>>>(g, h, out_counts, err_handback);
+}
+void launch_round_check(GraphRounds *g, int base_ok, uint32_t *err_handback, cudaStream_t s) {
+  round_check_kernel<<<1, 1, 0, s>>>(g, base_ok, err_handback);
+}
 void launch_round_cond(GraphRounds *g, cudaGraphConditionalHandle h, int base_ok, uint32_t max_iter, u64 *out_counts,
-                       cudaStream_t s) {
-  round_cond_kernel<<<1, 1, 0, s>>>(g, h, base_ok, max_iter, out_counts);
+                       uint32_t *err_handback, cudaStream_t s) {
+  round_cond_kernel<<<1, 1, 0, s>>>(g, h, base_ok, max_iter, out_counts, err_handback);
 }
 
 // ---------------------------------------------------- single-block base case
@@ -2479,8 +2545,10 @@ __global__ void tile_sample_kernel(EdgeList in, uint64_t m, uint32_t n, uint32_t
 // sample's first endpoint is taken (P fully contracted), and the most frequent
 // root is written to *out (a sort in shared memory, then the longest run).
 constexpr int MODE_SAMPLES = 1024;
-__global__ void __launch_bounds__(MODE_SAMPLES) giant_root_kernel(EdgeList in, uint64_t m, u64 state,
-                                                                  const uint32_t *P, uint32_t n, uint32_t *out) {
+__global__ void __launch_bounds__(MODE_SAMPLES) giant_root_kernel(EdgeList in, uint64_t m_bound, const u64 *m_dev,
+                                                                  u64 state, const uint32_t *P, uint32_t n,
+                                                                  uint32_t *out) {
+  const uint64_t m = m_dev ? min((uint64_t)*m_dev, m_bound) : m_bound;
   __shared__ uint32_t s_r[MODE_SAMPLES];
   __shared__ uint32_t s_best[MODE_SAMPLES / 32], s_bestv[MODE_SAMPLES / 32];
   const uint32_t t = threadIdx.x;
@@ -2840,9 +2908,9 @@ void launch_pivot(EdgeList in, uint64_t m, const u64 *m_dev, u64 state, uint32_t
 size_t pivot_scratch_bytes() { return sizeof(PivotScratch); }
 
 bool launch_pivot_coop(EdgeList in, uint64_t m, u64 state, uint32_t sample, u64 *keys, void *scratch,
-                       u64 *pivot_out, cudaStream_t s) {
+                       u64 *pivot_out, cudaStream_t s, const u64 *m_dev) {
   PivotScratch *ps = static_cast<PivotScratch *>(scratch);
-  void *args[] = {&in, &m, &state, &sample, &keys, &ps, &pivot_out};
+  void *args[] = {&in, &m, &m_dev, &state, &sample, &keys, &ps, &pivot_out};
   if (cudaLaunchCooperativeKernel((const void *)pivot_coop_kernel, dim3(PSEL_BLOCKS), dim3(PSEL_THREADS), args, 0, s) ==
       cudaSuccess)
     return true;
@@ -2862,13 +2930,13 @@ void launch_finalize(const uint32_t *bits, uint64_t m, const uint32_t *w, uint32
 }
 
 void launch_giant_root(EdgeList in, uint64_t m, u64 state, const uint32_t *P, uint32_t n, uint32_t *root_tmp,
-                       cudaStream_t s) {
-  giant_root_kernel<<<1, MODE_SAMPLES, 0, s>>>(in, m, state, P, n, root_tmp);
+                       cudaStream_t s, const u64 *m_dev) {
+  giant_root_kernel<<<1, MODE_SAMPLES, 0, s>>>(in, m, m_dev, state, P, n, root_tmp);
 }
 
 void launch_giant_bits(EdgeList in, uint64_t m, u64 state, const uint32_t *P, uint32_t n, uint32_t *root_tmp,
                        uint32_t *bits, int sms, cudaStream_t s) {
-  giant_root_kernel<<<1, MODE_SAMPLES, 0, s>>>(in, m, state, P, n, root_tmp);
+  giant_root_kernel<<<1, MODE_SAMPLES, 0, s>>>(in, m, nullptr, state, P, n, root_tmp);
   const uint64_t threads = ((uint64_t)n + 31) / 32 * 32;
   giant_bits_kernel<<<grid_for((threads + BLOCK - 1) / BLOCK, sms, 8), BLOCK, 0, s>>>(P, n, root_tmp, bits);
 }

@@ -10,6 +10,7 @@
 #include <cstdint>
 #include <cstring>
 #include <new>
+#include <memory>
 #include <vector>
 
 #include <cuda_runtime.h>
@@ -33,6 +34,7 @@ struct mst_ctx {
   uint32_t *hflag = nullptr;    // mapped host word: sequence number of the last completed readback
   uint32_t *hflag_dev = nullptr;
   uint32_t rb_seq = 0;
+  uint64_t readbacks = 0;
   u64 *hres = nullptr;       // pinned host words for the forest size and weight of the host entry points
   u64 *status = nullptr;     // scan status words
   uint64_t status_cap = 0;   // in tiles
@@ -42,13 +44,15 @@ struct mst_ctx {
   void *pivot_scratch = nullptr;  // histograms of the multi-block pivot selection
   u64 *wsum = nullptr;            // WSUM_SLOTS counters of the chosen weights (zeroed per solve)
   uint64_t pivot_counter = 0;
+  uint64_t solves = 0, planned = 0;
+  uint64_t plan_fallbacks = 0;  // planned Filter-Borůvka solves that started over on the host-driven path
   // per-kernel-class event timing (mst_profile_enable)
   struct ProfRec {
     int kind;
     cudaEvent_t a, b;
     double bytes, min_bytes;  // fixed parts known at launch (see prof_end)
-    int slot1, slot2;
-    double per1, per2;
+    int slot[3];              // counts the launch's bytes scale with (-1: none)
+    double per[3], per_min[3];
   };
   bool prof_on = false;
   uint32_t prof_mask = ~0u;  // classes that get event timing (the others: launches and bytes only)
@@ -289,10 +293,35 @@ void prof_end(mst_ctx *c, cudaStream_t s, int idx, int kind, double bytes, int s
   r.kind = kind;
   r.bytes = bytes;
   r.min_bytes = min_bytes < 0.0 ? bytes : min_bytes;
-  r.slot1 = slot1;
-  r.per1 = per1;
-  r.slot2 = slot2;
-  r.per2 = per2;
+  r.slot[0] = slot1;
+  r.per[0] = r.per_min[0] = per1;
+  r.slot[1] = slot2;
+  r.per[1] = r.per_min[1] = per2;
+  r.slot[2] = -1;
+  r.per[2] = r.per_min[2] = 0.0;
+}
+
+// Byte terms of a launch whose list lengths are device counts: besides the
+// fixed parts, term i adds count[slot] * per to the bytes moved and
+// count[slot] * per_min to the method's own count.
+struct ProfTerm {
+  int slot;
+  double per, per_min;
+};
+void prof_end_terms(mst_ctx *c, cudaStream_t s, int idx, int kind, double bytes, double min_bytes, ProfTerm t0,
+                    ProfTerm t1 = {-1, 0, 0}, ProfTerm t2 = {-1, 0, 0}) {
+  if (idx < 0) return;
+  mst_ctx::ProfRec &r = c->prof_pending[idx];
+  if (r.b) cudaEventRecord(r.b, s);
+  r.kind = kind;
+  r.bytes = bytes;
+  r.min_bytes = min_bytes;
+  const ProfTerm t[3] = {t0, t1, t2};
+  for (int i = 0; i < 3; ++i) {
+    r.slot[i] = t[i].slot;
+    r.per[i] = t[i].per;
+    r.per_min[i] = t[i].per_min;
+  }
 }
 
 // After a stream synchronisation: folds the finished records into the totals.
@@ -307,11 +336,14 @@ void prof_resolve(mst_ctx *c) {
     mst_kernel_stats &k = c->prof[r.kind];
     k.launches += 1;
     k.ms += ms;
-    double b = 0.0;
-    if (r.slot1 >= 0) b += (double)c->hs->count[r.slot1] * r.per1;
-    if (r.slot2 >= 0) b += (double)c->hs->count[r.slot2] * r.per2;
+    double b = 0.0, bm = 0.0;
+    for (int i = 0; i < 3; ++i)
+      if (r.slot[i] >= 0) {
+        b += (double)c->hs->count[r.slot[i]] * r.per[i];
+        bm += (double)c->hs->count[r.slot[i]] * r.per_min[i];
+      }
     k.bytes += r.bytes + b;
-    k.min_bytes += r.min_bytes + b;
+    k.min_bytes += r.min_bytes + bm;
     if (r.a) {
       c->ev_pool.push_back(r.a);
       c->ev_pool.push_back(r.b);
@@ -325,6 +357,15 @@ void prof_resolve(mst_ctx *c) {
     const int _p = prof_begin(c, s, kind);                       \
     launch;                                                      \
     prof_end(c, s, _p, kind, bytes, slot1, per1, slot2, per2);   \
+  } while (0)
+
+// A launch whose bytes follow device counts (see prof_end_terms; the
+// trailing arguments are its ProfTerms).
+#define PROF_TERMS(kind, bytes, min_bytes, launch, ...)                  \
+  do {                                                                   \
+    const int _p = prof_begin(c, s, kind);                               \
+    launch;                                                              \
+    prof_end_terms(c, s, _p, kind, bytes, min_bytes, __VA_ARGS__);       \
   } while (0)
 
 // The same with the method's own fixed byte count `min_bytes` (see prof_end).
@@ -353,9 +394,11 @@ __global__ void readback_kernel(const DevState *ds, DevState *hs, uint32_t *flag
 // (a few microseconds after the GPU gets there, where a copy plus a stream
 // synchronisation costs about ten); after about a second without the flag it
 // falls back to synchronising the stream, which also reports a CUDA error.
-mst_status readback(mst_ctx *c, cudaStream_t s) {
+// Error bits in `tolerated` are left for the caller to act on.
+mst_status readback(mst_ctx *c, cudaStream_t s, uint32_t tolerated = 0) {
   static_assert(sizeof(DevState) % 4 == 0, "DevState is copied in words");
   const uint32_t seq = ++c->rb_seq;
+  ++c->readbacks;
   readback_kernel<<<1, 32, 0, s>>>(c->ds, c->hs_dev, c->hflag_dev, seq);
   CK(cudaGetLastError());
   bool seen = false;
@@ -372,9 +415,10 @@ mst_status readback(mst_ctx *c, cudaStream_t s) {
   if (!seen) CK(cudaStreamSynchronize(s));
   if (__atomic_load_n(c->hflag, __ATOMIC_ACQUIRE) != seq) return MST_ERR_CUDA;
   prof_resolve(c);
-  if (c->hs->err & ERR_VERTEX) return MST_ERR_VERTEX_RANGE;
-  if (c->hs->err & ERR_TABLE) return MST_ERR_INVALID_ARG;
-  if (c->hs->err) return MST_ERR_INTERNAL;
+  const uint32_t err = c->hs->err & ~tolerated;
+  if (err & ERR_VERTEX) return MST_ERR_VERTEX_RANGE;
+  if (err & ERR_TABLE) return MST_ERR_INVALID_ARG;
+  if (err) return MST_ERR_INTERNAL;
   return MST_OK;
 }
 
@@ -666,6 +710,7 @@ struct Solve {
         CompactArgs cd{};
         cd.shape = shape;
         cd.in = T.list();
+        cd.m = cur_m;
         cd.m_dev = &c->ds->count[CNT_TMP];
         cd.out = out.out;
         cd.table = ca.table;
@@ -704,6 +749,57 @@ struct Solve {
     return MST_OK;
   }
 
+  // The round graph over lists X, Y and active lists A (see build_round_graph),
+  // from the handle's cache.  Not cached yet: built at once when `always`,
+  // else only when the same shape is asked for again (a graph pays for its
+  // capture and instantiation only when its shape comes back); exec stays
+  // null when it is not built.  err_handback: the device-driven mode's error
+  // word (see launch_round_pre), or null.
+  mst_status round_graph(RoundList &X, RoundList &Y, uint32_t *const A[2], uint32_t max_iter, uint32_t *err_handback,
+                         bool always, cudaGraphExec_t &exec) {
+    exec = nullptr;
+    // launch bounds baked into the graph: the lists' capacity and n (the
+    // kernels read the actual counts from device memory), so the graph does
+    // not depend on this call's sizes
+    const uint64_t cap = std::min(X.cap, Y.cap), nmax = n;
+    if (!c->grounds) CK(cudaMalloc(&c->grounds, sizeof(GraphRounds)));
+    if (!c->cap_stream) CK(cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
+    const int base_ok = (c->cfg.base_case && !err_handback) ? 1 : 0;
+    const int jl = c->cfg.graph_jump_launches;
+    const RoundList *L[2] = {&X, &Y};
+    // A built graph is reused when every value baked into it is unchanged.
+    u64 sig = 0x2302121990ULL;
+    auto fold = [&](u64 v) { sig = host_mix64(sig ^ (v + 0x9e3779b97f4a7c15ULL)); };
+    for (int i = 0; i < 2; ++i) {
+      fold((u64)L[i]->out.u), fold((u64)L[i]->out.v), fold((u64)L[i]->out.w), fold((u64)L[i]->out.id);
+      fold((u64)A[i]);
+    }
+    const u64 vals[] = {(u64)parent,  (u64)best,    (u64)bits,     (u64)cur_u,  (u64)cur_v,
+                        (u64)src,     (u64)dst,     (u64)c->status, (u64)c->ds,  (u64)c->grounds,
+                        (u64)kl.packed, (u64)kl.vbits, (u64)kl.idbits, (u64)n,     (u64)cap,
+                        (u64)nmax,    (u64)jl,      (u64)base_ok,  (u64)max_iter, (u64)c->sms,
+                        (u64)shape,   (u64)err_handback};
+    for (u64 v : vals) fold(v);
+    for (size_t i = 0; i < c->round_graphs.size(); ++i)
+      if (c->round_graphs[i].sig == sig) {
+        const mst_ctx::RoundGraph hit = c->round_graphs[i];
+        c->round_graphs.erase(c->round_graphs.begin() + i);
+        c->round_graphs.insert(c->round_graphs.begin(), hit);
+        exec = hit.exec;
+        return MST_OK;
+      }
+    if (!always) {
+      auto &seen = c->round_sigs_seen;
+      const bool again = std::find(seen.begin(), seen.end(), sig) != seen.end();
+      if (!again) {
+        seen.insert(seen.begin(), sig);
+        if (seen.size() > 64) seen.pop_back();
+        return MST_OK;
+      }
+    }
+    return build_round_graph(sig, L, A, cap, nmax, base_ok, jl, max_iter, err_handback, exec);
+  }
+
   // Rounds of a Borůvka call as one CUDA graph launch (the round loop without
   // host round trips): a conditional WHILE node repeats a body of two rounds
   // (list X -> Y, then Y -> X; the active lists alternate the same way) while
@@ -716,52 +812,12 @@ struct Solve {
     used = false;
     done = false;
     ran = 0;
-    // launch bounds baked into the graph: the lists' capacity and n (the
-    // kernels read the actual counts from device memory), so the graph does
-    // not depend on this call's sizes
-    const uint64_t cap = std::min(X.cap, Y.cap), nmax = n;
-    if (!c->grounds) CK(cudaMalloc(&c->grounds, sizeof(GraphRounds)));
-    if (!c->cap_stream) CK(cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
-    GraphRounds *g = c->grounds;
-    const int base_ok = c->cfg.base_case ? 1 : 0;
-    const int jl = c->cfg.graph_jump_launches;
     const uint32_t max_iter = (uint32_t)(rounds_left > 2 ? rounds_left / 2 : 1);
-    const RoundList *L[2] = {&X, &Y};
     uint32_t *A[2] = {act[a], act[1 - a]};
-    // A built graph is reused when every value baked into it is unchanged.
-    u64 sig = 0x2302121990ULL;
-    auto fold = [&](u64 v) { sig = host_mix64(sig ^ (v + 0x9e3779b97f4a7c15ULL)); };
-    for (int i = 0; i < 2; ++i) {
-      fold((u64)L[i]->out.u), fold((u64)L[i]->out.v), fold((u64)L[i]->out.w), fold((u64)L[i]->out.id);
-      fold((u64)A[i]);
-    }
-    const u64 vals[] = {(u64)parent,  (u64)best,    (u64)bits,     (u64)cur_u,  (u64)cur_v,
-                        (u64)src,     (u64)dst,     (u64)c->status, (u64)c->ds,  (u64)g,
-                        (u64)kl.packed, (u64)kl.vbits, (u64)kl.idbits, (u64)n,     (u64)cap,
-                        (u64)nmax,    (u64)jl,      (u64)base_ok,  (u64)max_iter, (u64)c->sms,
-                        (u64)shape};
-    for (u64 v : vals) fold(v);
     cudaGraphExec_t exec = nullptr;
-    for (size_t i = 0; i < c->round_graphs.size(); ++i)
-      if (c->round_graphs[i].sig == sig) {
-        const mst_ctx::RoundGraph hit = c->round_graphs[i];
-        c->round_graphs.erase(c->round_graphs.begin() + i);
-        c->round_graphs.insert(c->round_graphs.begin(), hit);
-        exec = hit.exec;
-        break;
-      }
-    if (!exec) {
-      // a graph pays for its capture and instantiation only when its shape
-      // comes back: the first time, the host runs the rounds
-      auto &seen = c->round_sigs_seen;
-      const bool again = std::find(seen.begin(), seen.end(), sig) != seen.end();
-      if (!again) {
-        seen.insert(seen.begin(), sig);
-        if (seen.size() > 64) seen.pop_back();
-        return MST_OK;
-      }
-      TRY(build_round_graph(sig, L, A, cap, nmax, base_ok, jl, max_iter, exec));
-    }
+    TRY(round_graph(X, Y, A, max_iter, nullptr, false, exec));
+    if (!exec) return MST_OK;  // the first time, the host runs the rounds
+    GraphRounds *g = c->grounds;
     used = true;
     launch_round_init(g, cur_m, n_act, s);
     PROF(MST_K_GRAPH, 0.0, -1, 0.0, -1, 0.0, CK(cudaGraphLaunch(exec, s)));
@@ -772,7 +828,7 @@ struct Solve {
     if (reason == ROUNDS_BOUND || reason == ROUNDS_RUNNING || slot > 1) return MST_ERR_INTERNAL;
     cur_m = c->hs->count[CNT_EDGES];
     n_act = c->hs->count[CNT_ACTIVE];
-    cur = L[slot]->list();
+    cur = (slot == 0 ? X : Y).list();
     if (slot == 1) a = 1 - a;
     if (reason == ROUNDS_DONE) {
       done = true;
@@ -782,12 +838,14 @@ struct Solve {
     return MST_OK;
   }
 
-  // Captures and instantiates the round graph: a conditional WHILE node whose
-  // body is two rounds (slot 0 -> 1, slot 1 -> 0), each compaction (relabel +
-  // minEdges relaxation), hooking, `jl` pointer-jumping launches and a check;
-  // the body ends with the kernel that sets the loop condition.
+  // Captures and instantiates the round graph: an entry kernel that decides
+  // whether the loop runs at all, then a conditional WHILE node whose body is
+  // two rounds (slot 0 -> 1, slot 1 -> 0), each compaction (relabel + minEdges
+  // relaxation), hooking, `jl` pointer-jumping launches and a check; the body
+  // ends with the kernel that sets the loop condition.
   mst_status build_round_graph(u64 sig, const RoundList *const L[2], uint32_t *const A[2], uint64_t cap, uint64_t nmax,
-                               int base_ok, int jl, uint32_t max_iter, cudaGraphExec_t &exec_out) {
+                               int base_ok, int jl, uint32_t max_iter, uint32_t *err_handback,
+                               cudaGraphExec_t &exec_out) {
     GraphRounds *g = c->grounds;
     cudaStream_t cs = c->cap_stream;
     struct Owned {
@@ -806,14 +864,27 @@ struct Solve {
     } o;
     CK(cudaGraphCreate(&o.graph, 0));
     cudaGraphConditionalHandle h;
-    CK(cudaGraphConditionalHandleCreate(&h, o.graph, 1, cudaGraphCondAssignDefault));
+    CK(cudaGraphConditionalHandleCreate(&h, o.graph, 0, cudaGraphCondAssignDefault));
+    // entry: the kernel that decides whether the loop runs at all
+    CK(cudaStreamBeginCaptureToGraph(cs, o.graph, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+    o.capturing = cs;
+    launch_round_pre(g, h, &c->ds->count[CNT_EDGES], err_handback, cs);
+    {
+      cudaGraph_t captured = nullptr;
+      o.capturing = nullptr;
+      CK(cudaStreamEndCapture(cs, &captured));
+    }
+    cudaGraphNode_t pre = nullptr;
+    size_t nodes = 1;
+    CK(cudaGraphGetNodes(o.graph, &pre, &nodes));
+    if (nodes != 1 || !pre) return MST_ERR_INTERNAL;
     cudaGraphNodeParams cp{};
     cp.type = cudaGraphNodeTypeConditional;
     cp.conditional.handle = h;
     cp.conditional.type = cudaGraphCondTypeWhile;
     cp.conditional.size = 1;
     cudaGraphNode_t node;
-    CK(cudaGraphAddNode(&node, o.graph, nullptr, nullptr, 0, &cp));
+    CK(cudaGraphAddNode(&node, o.graph, &pre, nullptr, 1, &cp));
     cudaGraph_t body = cp.conditional.phGraph_out[0];
     CK(cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
     o.capturing = cs;
@@ -852,9 +923,9 @@ struct Solve {
       for (int k = 0; k < jl; ++k)
         launch_jump(A[out], &g->ca[out], 0, nmax, parent, best, k == 0 ? 1 : 0, k == jl - 1 ? &g->jflag : &g->jdummy,
                     c->sms, cs, 256);
-      if (half == 0) launch_round_check(g, base_ok, cs);
+      if (half == 0) launch_round_check(g, base_ok, err_handback, cs);
     }
-    launch_round_cond(g, h, base_ok, max_iter, &c->ds->count[CNT_EDGES], cs);
+    launch_round_cond(g, h, base_ok, max_iter, &c->ds->count[CNT_EDGES], err_handback, cs);
     cudaGraph_t captured = nullptr;
     o.capturing = nullptr;
     CK(cudaStreamEndCapture(cs, &captured));
@@ -1163,13 +1234,234 @@ struct Solve {
     return filter(H.list(), mH, false, depth + 1, relaxed, cf.cur_u != nullptr);
   }
 
+  // ---------------------------------------------------------------- planned
+  // Filter-Borůvka (Alg. 2) with the recursion laid out by the host ahead of
+  // time and every list length kept in device memory.  The top-level
+  // partition's light count (one readback, which also brings the largest
+  // weight for the key layout) fixes the plan: light lists halve from level to
+  // level (the pivot is the median of the sample), so the host knows how many
+  // levels reach isSparse and gives each list a capacity a little above half
+  // of its parent's.  The levels then run without the host reading anything:
+  // pivot and partition from device counts, and the deepest light list and
+  // each level's filtered heavy edges solved by Borůvka rounds whose first
+  // hooking runs before the round graph and whose loop the device ends.  A
+  // list that outgrows its capacity (ERR_OVERFLOW), a round that would need
+  // the host (ERR_HANDBACK) or a contraction left short (the jump flag) makes
+  // the result unusable, and the caller starts over on the host-driven path.
+  // Where the estimate stops the recursion a level early or late the forest
+  // is the same: isSparse only steers the work.
+  bool plan_eligible() const {
+    const mst_config &f = c->cfg;
+    return f.filter_plan && f.graph_rounds && !f.filter_carry && !f.filter_split && !f.min_edges_sort &&
+           f.dedupe != MST_DEDUPE_HASH && f.dedupe != MST_DEDUPE_SORT && !is_sparse(m);
+  }
+  // Capacity planned for the light list of a list of at most `cap` edges:
+  // half of it plus 1/32 of it and 2^16 (the light share of a list split at
+  // a sample median of 2^16 keys strays from 1/2 by about 2^-9 of the list).
+  static uint64_t light_cap(uint64_t cap) { return std::min<uint64_t>(cap, cap / 2 + cap / 32 + (1ULL << 16)); }
+  // The round lists of a plan: the deepest light list, and each level's
+  // filtered heavy edges in turn (room for n of them, or for every heavy edge
+  // of the input if that is fewer; the filter is expected to keep far fewer,
+  // Theorem 1).
+  uint64_t plan_round_edges(uint64_t deepest_cap) const {
+    const uint64_t heavy = std::min<uint64_t>(n, light_cap(m));
+    return std::max<uint64_t>(std::max<uint64_t>(deepest_cap, heavy), 1ULL << 16);
+  }
+
+  // Borůvka rounds on the list in round list X whose length is count[slot]
+  // (best[] holds its minEdges; ends_rec: its ends were recorded by id as it
+  // was written): the first hooking over all n vertices and its pointer
+  // jumping, then the round graph.
+  mst_status boruvka_planned(RoundList &X, RoundList &Y, int slot, bool ends_rec, cudaGraphExec_t exec) {
+    GraphRounds *g = c->grounds;
+    launch_round_init_dev(g, &c->ds->count[slot], std::min(X.cap, Y.cap), s);
+    HookArgs ha{};
+    ha.shape = shape;
+    ha.cand = nullptr;
+    ha.ncand = n;
+    ha.best = best;
+    ha.kl = kl;
+    const bool rec = ends_rec && cur_u;
+    ha.src = rec ? cur_u : src;
+    ha.dst = rec ? cur_v : dst;
+    ha.parent = parent;
+    ha.chosen_bits = bits;
+    ha.active_out = act[0];
+    ha.counter = &g->ca[0];
+    ha.err = &c->ds->err;
+    ha.wsum = c->wsum;
+    PROF(MST_K_HOOK, 8.0 * (double)n, -1, 0.0, -1, 0.0, launch_hook(ha, n, s));
+    const int jl = c->cfg.graph_jump_launches;
+    PROF(MST_K_JUMP, 0.0, -1, 0.0, -1, 0.0,
+         for (int k = 0; k < jl; ++k) launch_jump(act[0], &g->ca[0], 0, n, parent, best, k == 0 ? 1 : 0,
+                                                  k == jl - 1 ? &g->jflag : &g->jdummy, c->sms, s, 256));
+    PROF(MST_K_GRAPH, 0.0, -1, 0.0, -1, 0.0, CK(cudaGraphLaunch(exec, s)));
+    ++rounds;
+    return MST_OK;
+  }
+
+  // planned: set once the call is committed to the plan (its outcome is then
+  // known after the final readback).  Unset on return: the caller runs the
+  // host-driven recursion instead, after restart().
+  mst_status filter_planned(bool &planned) {
+    planned = false;
+    const uint64_t m0 = m;
+    const bool leaf_top = is_sparse(m0 / 2);  // the top level's light list is expected to be the deepest
+    if (leaf_top && !layout_set) TRY(choose_layout(w_in));
+    Buf piv_b, gbits_b;
+    TRY(piv_b.alloc(c, LVL_MAX * sizeof(u64), s));
+    TRY(gbits_b.alloc(c, ((size_t)n + 31) / 32 * 4, s));
+    u64 *piv = piv_b.as<u64>();
+    uint32_t *gbits = gbits_b.as<uint32_t>();
+    CK(cudaMemsetAsync(&c->ds->count[CNT_LVL], 0, 2 * LVL_MAX * sizeof(u64), s));
+    const uint64_t cap1 = light_cap(m0);
+    RoundList X, Y;
+    TRY(round_lists(c, plan_round_edges(leaf_top ? cap1 : 0), X, Y));
+    ListBuf L1;
+    if (!leaf_top) TRY(L1.alloc(c, cap1, s));
+
+    // level 0: pivot and partition of the input (vertex ids checked here)
+    const EdgeList in{src, dst, w_in, nullptr};
+    u64 state[LVL_MAX];
+    state[0] = host_splitmix64_at(c->cfg.seed, c->pivot_counter++);
+    PROF(MST_K_PIVOT, 16.0 * (double)c->cfg.pivot_sample, -1, 0.0, -1, 0.0,
+         if (!launch_pivot_coop(in, m0, state[0], c->cfg.pivot_sample, c->sample_buf, c->pivot_scratch, &piv[0], s))
+             launch_pivot(in, m0, nullptr, state[0], c->cfg.pivot_sample, c->sample_buf, &piv[0], s));
+    CompactArgs cp{};
+    cp.shape = shape;
+    cp.in = in;
+    cp.m = m0;
+    cp.out = leaf_top ? X.out : L1.out;
+    cp.out_cap = leaf_top ? X.cap : L1.cap;
+    cp.pivot_dev = &piv[0];
+    cp.n = n;
+    cp.validate = 1;
+    if (!layout_set) {
+      CK(cudaMemsetAsync(&c->ds->max_w, 0, sizeof(uint32_t), s));
+      cp.max_w = &c->ds->max_w;
+    }
+    cp.best = leaf_top ? best : nullptr;
+    cp.kl = kl;
+    record_ends(cp);
+    cp.st = next_scan(c, CNT_LVL + 1);
+    PROF(MST_K_PARTITION, 12.0 * (double)m0, CNT_LVL + 1, 16.0, -1, 0.0, launch_compact(CM_PARTITION, cp, m0, s));
+    TRY(readback(c, s, ERR_OVERFLOW));
+    if (c->hs->err & ERR_OVERFLOW) return MST_OK;  // outgrew the plan
+    const uint64_t m1 = c->hs->count[CNT_LVL + 1];
+    if (m1 == 0 || m1 == m0) return MST_OK;  // no progress from this pivot
+    if (cp.max_w) {
+      set_layout();
+      TRY(cur_alloc());
+    }
+    // the plan: lists 1 .. K-1 are partitioned, list K is the deepest
+    int K = 1;
+    uint64_t caps[LVL_MAX + 1];
+    caps[0] = m0;
+    caps[1] = leaf_top ? X.cap : m1;
+    for (uint64_t est = m1; !is_sparse(est); est /= 2) {
+      if (K + 1 >= LVL_MAX) return MST_OK;  // deeper than a plan holds
+      caps[K + 1] = light_cap(caps[K]);
+      ++K;
+    }
+    if (leaf_top != (K == 1)) return MST_OK;  // the light count moved the deepest level: host-driven
+    const uint64_t need = plan_round_edges(caps[K]);
+    if (need > X.cap) TRY(round_lists(c, need, X, Y));  // (not when leaf_top: X already holds list 1)
+    planned = true;
+    CK(cudaMemsetAsync(&c->ds->jump_flag, 0, sizeof(uint32_t), s));
+    uint32_t *A[2] = {act[0], act[1]};
+    cudaGraphExec_t exec = nullptr;
+    TRY(round_graph(X, Y, A, (uint32_t)(ceil_log2(n) + 2), &c->ds->err, true, exec));
+    if (!exec) return MST_ERR_INTERNAL;
+
+    // light lists 2 .. K (list K into X, relaxing best[] for its first round)
+    std::unique_ptr<ListBuf[]> Lb(new ListBuf[K + 1]);
+    EdgeList E[LVL_MAX + 1];
+    E[0] = in;
+    E[1] = leaf_top ? X.list() : L1.list();
+    for (int k = 1; k < K; ++k) {
+      const bool last = k + 1 == K;
+      if (!last) TRY(Lb[k + 1].alloc(c, caps[k + 1], s));
+      state[k] = host_splitmix64_at(c->cfg.seed, c->pivot_counter++);
+      const u64 *mk = &c->ds->count[CNT_LVL + k];
+      PROF(MST_K_PIVOT, 16.0 * (double)c->cfg.pivot_sample, -1, 0.0, -1, 0.0,
+           if (!launch_pivot_coop(E[k], caps[k], state[k], c->cfg.pivot_sample, c->sample_buf, c->pivot_scratch,
+                                  &piv[k], s, mk))
+               launch_pivot(E[k], caps[k], mk, state[k], c->cfg.pivot_sample, c->sample_buf, &piv[k], s));
+      CompactArgs pk{};
+      pk.shape = shape;
+      pk.in = E[k];
+      pk.m = caps[k];
+      pk.m_dev = mk;
+      pk.out = last ? X.out : Lb[k + 1].out;
+      pk.out_cap = last ? X.cap : Lb[k + 1].cap;
+      pk.pivot_dev = &piv[k];
+      pk.n = n;
+      pk.best = last ? best : nullptr;
+      pk.kl = kl;
+      record_ends(pk);
+      pk.st = next_scan(c, CNT_LVL + k + 1);
+      PROF_TERMS(MST_K_PARTITION, 0.0, 0.0, launch_compact(CM_PARTITION, pk, caps[k], s),
+                 ProfTerm{CNT_LVL + k, 16.0, 16.0}, ProfTerm{CNT_LVL + k + 1, 16.0, 16.0});
+      E[k + 1] = last ? X.list() : Lb[k + 1].list();
+    }
+    TRY(boruvka_planned(X, Y, CNT_LVL + K, cur_u != nullptr, exec));
+
+    // levels K-1 .. 0: contract P and mark the giant component, filter the
+    // level's heavy edges into X, and solve them
+    for (int k = K - 1; k >= 0; --k) {
+      if (k + 1 >= 2 && k + 1 < K) Lb[k + 1].mem.release();  // list k+1 is not read again
+      const u64 *mk = k == 0 ? nullptr : &c->ds->count[CNT_LVL + k];
+      launch_giant_root(E[k], caps[k], host_mix64(state[k]), parent, n, &c->ds->giant_root, s, mk);
+      PROF(MST_K_JUMP, 8.125 * (double)n, -1, 0.0, -1, 0.0,
+           launch_jump(nullptr, nullptr, n, n, parent, best, 0, &c->ds->jump_flag, c->sms, s, 4096,
+                       &c->ds->giant_root, gbits));
+      CompactArgs cf{};
+      cf.shape = shape;
+      cf.in = E[k];
+      cf.m = caps[k];
+      cf.m_dev = mk;
+      cf.out = X.out;
+      cf.out_cap = X.cap;
+      cf.label = parent;
+      cf.giant_bits = gbits;
+      cf.pivot_dev = &piv[k];
+      cf.n = n;
+      cf.best = best;  // the survivors are expected to be sparse (Theorem 1)
+      cf.kl = kl;
+      record_ends(cf);
+      cf.st = next_scan(c, CNT_LVL + LVL_MAX + k);
+      // the pass streams the whole list; the method reads only its heavy
+      // edges (the list less its light list k+1)
+      const double per = E[k].id ? 16.0 : 12.0;
+      const double fixed = k == 0 ? per * (double)m0 : 0.0;
+      PROF_TERMS(MST_K_FILTER, fixed, fixed, launch_compact(CM_FILTER, cf, caps[k], s),
+                 ProfTerm{k == 0 ? -1 : CNT_LVL + k, per, per}, ProfTerm{CNT_LVL + k + 1, 0.0, -per},
+                 ProfTerm{CNT_LVL + LVL_MAX + k, 16.0, 16.0});
+      TRY(boruvka_planned(X, Y, CNT_LVL + LVL_MAX + k, cur_u != nullptr, exec));
+    }
+    return MST_OK;
+  }
+
+  // Back to the state init() left (the host-driven path after a plan that
+  // did not hold).
+  mst_status restart() {
+    CK(cudaMemsetAsync(best, 0xff, (size_t)n * 8, s));
+    launch_iota(parent, n, c->sms, s);
+    CK(cudaMemsetAsync(bits, 0, (m + 31) / 32 * 4, s));
+    TRY(clear_device_flags(c, s));
+    CK(cudaMemsetAsync(c->wsum, 0, WSUM_SLOTS * sizeof(u64), s));
+    c->pivot_counter = 0;
+    rounds = 0;
+    return MST_OK;
+  }
+
   // The ids come from the chosen-edge bitmap; the total from the counters the
   // hooking kernels added each chosen edge's weight into (no gather of w).
-  mst_status finalize(uint32_t *out_ids, uint32_t *out_count, u64 *total_weight) {
+  mst_status finalize(uint32_t *out_ids, uint32_t *out_count, u64 *total_weight, uint32_t tolerated = 0) {
     PROF(MST_K_FINALIZE, (double)((m + 31) / 32 * 4), CNT_AUX, 4.0, -1, 0.0,
          launch_finalize(bits, m, nullptr, out_ids, out_count, total_weight, next_scan(c, CNT_AUX), s);
          launch_wsum_total(c->wsum, total_weight, s));
-    return readback(c, s);
+    return readback(c, s, tolerated);
   }
 };
 
@@ -1194,6 +1486,7 @@ mst_status solve_device(mst_ctx *c, uint32_t n, uint64_t m, const uint32_t *src,
   }
   Solve S(c, s, n, m);
   TRY(S.init());
+  ++c->solves;
   S.src = src;
   S.dst = dst;
   S.w_in = w;
@@ -1210,6 +1503,18 @@ mst_status solve_device(mst_ctx *c, uint32_t n, uint64_t m, const uint32_t *src,
     else
       TRY(S.boruvka(local.list(), m_local, false, true, true));
   } else if (filt) {
+    if (S.plan_eligible()) {
+      bool planned = false;
+      TRY(S.filter_planned(planned));
+      if (planned) {
+        ++c->planned;
+        constexpr uint32_t replan = ERR_OVERFLOW | ERR_HANDBACK;
+        TRY(S.finalize(out_ids, out_count, total_weight, replan));
+        if (!(c->hs->err & replan) && !c->hs->jump_flag) return MST_OK;
+        ++c->plan_fallbacks;
+      }
+      TRY(S.restart());
+    }
     TRY(S.filter(in, m, true, 0));
   } else {
     TRY(S.boruvka(in, m, true));
@@ -1236,6 +1541,7 @@ mst_status validate_cfg(const mst_config *cfg) {
   if (cfg->tile_vertices < 32 || cfg->tile_vertices > 4096) return MST_ERR_INVALID_ARG;
   if (cfg->spin_limit < 1) return MST_ERR_INVALID_ARG;
   if (shape_index(cfg->block_threads, cfg->items_per_thread) < 0) return MST_ERR_INVALID_ARG;
+  if (cfg->filter_plan < 0 || cfg->filter_plan > 1) return MST_ERR_INVALID_ARG;
   return MST_OK;
 }
 
@@ -1483,6 +1789,7 @@ void mst_config_default(mst_config *cfg) {
   cfg->spin_limit = 1u << 21;  // about a second of polling at the measured poll rate
   cfg->block_threads = 0;      // 0: 256 threads per block
   cfg->items_per_thread = 0;   // 0: 8 edges per thread
+  cfg->filter_plan = 1;
 }
 
 const char *mst_status_string(mst_status s) {
@@ -1623,6 +1930,15 @@ mst_status mst_profile_classes(mst_handle h, uint32_t mask) {
 mst_status mst_profile_get(mst_handle h, int kind, mst_kernel_stats *out) {
   if (!h || !out || kind < 0 || kind >= MST_K_COUNT) return MST_ERR_INVALID_ARG;
   *out = h->prof[kind];
+  return MST_OK;
+}
+
+mst_status mst_host_counters_get(mst_handle h, mst_host_counters *out) {
+  if (!h || !out) return MST_ERR_INVALID_ARG;
+  out->solves = h->solves;
+  out->readbacks = h->readbacks;
+  out->planned = h->planned;
+  out->plan_fallbacks = h->plan_fallbacks;
   return MST_OK;
 }
 

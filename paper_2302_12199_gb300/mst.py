@@ -48,6 +48,11 @@ class KernelStats(ctypes.Structure):
                 ("min_bytes", ctypes.c_double)]
 
 
+class HostCounters(ctypes.Structure):
+    _fields_ = [("solves", ctypes.c_uint64), ("readbacks", ctypes.c_uint64), ("planned", ctypes.c_uint64),
+                ("plan_fallbacks", ctypes.c_uint64)]
+
+
 class MstConfig(ctypes.Structure):
     _fields_ = [("device", ctypes.c_int), ("variant", ctypes.c_int), ("dedupe", ctypes.c_int),
                 ("tile_contract", ctypes.c_int), ("tile_vertices", ctypes.c_uint32),
@@ -57,7 +62,8 @@ class MstConfig(ctypes.Structure):
                 ("filter_carry", ctypes.c_int), ("filter_split", ctypes.c_int),
                 ("min_edges_sort", ctypes.c_int), ("jump_steps", ctypes.c_uint32),
                 ("tile_filter", ctypes.c_int), ("spin_limit", ctypes.c_uint32),
-                ("block_threads", ctypes.c_uint32), ("items_per_thread", ctypes.c_uint32)]
+                ("block_threads", ctypes.c_uint32), ("items_per_thread", ctypes.c_uint32),
+                ("filter_plan", ctypes.c_int)]
 
 
 _P = ctypes.c_void_p
@@ -88,6 +94,7 @@ _SIGNATURES = {
     "mst_profile_enable": (_I, [_P, _I]),
     "mst_profile_classes": (_I, [_P, _U32]),
     "mst_profile_get": (_I, [_P, _I, ctypes.POINTER(KernelStats)]),
+    "mst_host_counters_get": (_I, [_P, ctypes.POINTER(HostCounters)]),
     "mst_pivot_noalloc": (_I, [_U64, _P, _P, _U64, _U32, _P, _P]),
 }
 
@@ -218,6 +225,12 @@ class Solver:
             self._check(self.lib.mst_profile_get(self.h, k, ctypes.byref(st)), "mst_profile_get")
             out[name] = (int(st.launches), float(st.ms), float(st.bytes)) + ((float(st.min_bytes),) if with_min else ())
         return out
+
+    def host_counters(self) -> dict:
+        """mst_host_counters_get: solves, readbacks, planned, plan_fallbacks since the handle was made."""
+        hc = HostCounters()
+        self._check(self.lib.mst_host_counters_get(self.h, ctypes.byref(hc)), "mst_host_counters_get")
+        return {k: int(getattr(hc, k)) for k, _ in HostCounters._fields_}
 
     def workspace_bytes(self, n: int, m: int) -> int:
         return int(self.lib.mst_workspace_bytes(n, m, ctypes.byref(self.cfg)))

@@ -622,6 +622,83 @@ def test_filter_carry_on_and_off_agree(dev, family):
                 s.close()
 
 
+def two_halves_heavy_between(n: int, m: int, seed: int) -> W.Graph:
+    """Light edges (w 1..100, 60% of them) inside each half of the vertices,
+    heavy edges (w 101..255) only between the halves: a pivot at the median
+    leaves two light components, so the filter keeps every heavy edge (40% of
+    m, far more than n)."""
+    rng = np.random.default_rng(seed)
+    h, ml = n // 2, (3 * m) // 5
+    side = rng.integers(0, 2, ml)
+    a = rng.integers(0, h, ml) + side * h
+    b = rng.integers(0, h, ml) + side * h
+    hu = rng.integers(0, h, m - ml)
+    hv = rng.integers(h, n, m - ml)
+    src = np.concatenate([a, hu]).astype(np.uint32)
+    dst = np.concatenate([b, hv]).astype(np.uint32)
+    w = np.concatenate([rng.integers(1, 101, ml), rng.integers(101, 256, m - ml)]).astype(np.uint32)
+    perm = rng.permutation(m)
+    return W.Graph(n, src[perm], dst[perm], w[perm])
+
+
+def light_path_under_heavy(n: int, extra: int, seed: int) -> W.Graph:
+    """A path 0-1-...-(n-1) whose weights rise along it, under `extra` random
+    heavier edges: in the first round every path vertex hooks to its
+    predecessor, a chain far longer than the jumps a round graph holds."""
+    rng = np.random.default_rng(seed)
+    src = np.concatenate([np.arange(n - 1), rng.integers(0, n, extra)]).astype(np.uint32)
+    dst = np.concatenate([np.arange(1, n), rng.integers(0, n, extra)]).astype(np.uint32)
+    w = np.concatenate([np.arange(1, n), n + rng.integers(0, 1 << 20, extra)]).astype(np.uint32)
+    perm = rng.permutation(src.size)
+    return W.Graph(n, src[perm], dst[perm], w[perm])
+
+
+@pytest.mark.parametrize("family", ["rmat", "gnm", "rgg2", "rhg", "leaf_top", "overflow", "long_chain"])
+def test_filter_plan_on_and_off_agree(dev, family):
+    """Filter-Borůvka (Alg. 2) with the recursion planned from the top-level
+    light count (list lengths kept on the device, two readbacks per solve,
+    three when the layout must be read first) gives the oracle's forest, as
+    does the host-driven recursion.  Where the plan cannot hold (the filter
+    keeps more edges than the round lists hold; a light path whose hooking
+    chain outruns the jumps before the round graph) the solve starts over on
+    the host-driven path, with the same result."""
+    g = {
+        "rmat": lambda: W.rmat(17, 1 << 21, 91),
+        "gnm": lambda: W.gnm(1 << 15, 1 << 20, 92),
+        "rgg2": lambda: W.rgg(2, 1 << 16, 20.0, 93),
+        "rhg": lambda: W.rhg(1 << 16, 24.0, 94),
+        "leaf_top": lambda: W.gnm(1 << 16, 70000, 95),  # the top level's light list is the deepest
+        "overflow": lambda: two_halves_heavy_between(1 << 12, 1 << 20, 96),
+        "long_chain": lambda: light_path_under_heavy(1 << 16, 1 << 19, 97),
+    }[family]()
+    kid, ktot = oracle.kruskal(g.n, g.src, g.dst, g.w)
+    src, dst, w = to_dev(g.src, dev), to_dev(g.dst, dev), to_dev(g.w, dev)
+    must_fall_back = family == "overflow"
+    may_fall_back = family == "long_chain"  # (concurrent walks may finish the chain's jump in time)
+    for plan in (1, 0):
+        s = Solver(0, variant="filter", filter_plan=plan, filter_min_edges=1 << 12, pivot_sample=4096)
+        try:
+            for rep in range(3):
+                before = s.host_counters()
+                ids, tot = s.solve(g.n, src, dst, w).to_host()
+                assert np.array_equal(ids, kid) and tot == ktot, (plan, rep)
+                hc = s.host_counters()
+                d = {k: hc[k] - before[k] for k in hc}
+                assert d["solves"] == 1
+                if not plan:
+                    assert d["planned"] == 0
+                    continue
+                assert d["planned"] == 1, d
+                if may_fall_back:
+                    assert d["plan_fallbacks"] <= 1, d
+                    continue
+                assert d["plan_fallbacks"] == (1 if must_fall_back else 0), d
+                if not must_fall_back:
+                    assert d["readbacks"] <= (3 if family == "leaf_top" else 2), d
+        finally:
+            s.close()
+
+
 @pytest.mark.parametrize("family", ["rmat", "gnm", "star", "rgg2", "degenerate"])
 def test_min_edges_sort_on_and_off_agree(dev, family):
     """minEdges as segmented minima over the edge ends sorted by vertex gives the
@@ -745,9 +822,12 @@ def test_full_size_workloads_equal_kruskal(dev, workload):
     s = Solver(0, **cfg)
     try:
         ids, tot = gpu_msf(s, g.n, g.src, g.dst, g.w, dev)
+        hc = s.host_counters()
     finally:
         s.close()
         torch.cuda.empty_cache()
     kid, ktot = oracle.kruskal(g.n, g.src, g.dst, g.w)
     assert ids.size == kid.size and np.array_equal(ids, kid), workload
     assert tot == ktot, workload
+    if workload == "rmat_filter":  # the planned recursion held: two host readbacks for the solve
+        assert hc["planned"] == 1 and hc["plan_fallbacks"] == 0 and hc["readbacks"] <= 2, hc
