@@ -620,7 +620,7 @@ def measure_batched(args, rank: int, world: int, local_rank: int, dev, dist, com
     import torch
 
     from paper_2302_12199_gb300 import workloads as W
-    from paper_2302_12199_gb300.autotune import autotune, label
+    from paper_2302_12199_gb300.autotune import RELABEL_SHAPE_CANDIDATES, autotune, label
     from paper_2302_12199_gb300.mst import Solver
 
     G = args.graphs
@@ -659,7 +659,7 @@ def measure_batched(args, rank: int, world: int, local_rank: int, dev, dist, com
     if args.no_autotune:
         best, tuning = dict(variant="boruvka", dedupe="none", tile_contract=0), []
     else:
-        best, tuning = autotune(trial, reps=3)
+        best, tuning = autotune(trial, reps=3, relabel_shapes=RELABEL_SHAPE_CANDIDATES)
     for k in list(trial_solver):
         trial_solver.pop(k).close()
     if args.base_case is not None:
@@ -681,9 +681,8 @@ def measure_batched(args, rank: int, world: int, local_rank: int, dev, dist, com
             timed_batch(solver)
         solver.profile(False)
         stats_all = solver.profile_stats()
-        # the dominant class among those whose bytes are counted (the graph
-    # class's are not: its kernels are counted in no class)
-    dom = max((k for k in stats_all if stats_all[k][2] > 0), key=lambda k: stats_all[k][1])
+        # the dominant class among those whose bytes are counted
+        dom = max((k for k in stats_all if stats_all[k][2] > 0), key=lambda k: stats_all[k][1])
 
     uuid = None
     try:

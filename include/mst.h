@@ -116,6 +116,11 @@ typedef struct {
                                   call reads back twice.  If a list outgrows its planned capacity or a
                                   round needs the host, the call starts over on the host-driven path
                                   (same result).  0: the host reads every level's counts */
+  uint32_t relabel_block_threads;    /* threads per block of the relabel compaction, which runs in every
+                                        Borůvka round, mostly on short lists: 128, 256 or 512; both
+                                        relabel fields 0: 128 x 4, measured fastest on GB300 (more,
+                                        smaller tiles spread a short list over more SMs) */
+  uint32_t relabel_items_per_thread; /* edges per thread of the relabel compaction: 4, 8 or 16 */
 } mst_config;
 
 /* Fills *cfg with the defaults (Borůvka variant, automatic dedupe, pivot sample

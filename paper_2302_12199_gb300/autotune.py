@@ -31,6 +31,14 @@ DEFAULT_CANDIDATES: Tuple[dict, ...] = (
 SHAPE_CANDIDATES: Tuple[dict, ...] = tuple(dict(block_threads=b, items_per_thread=i)
                                            for b in (128, 256, 512) for i in (4, 8, 16))
 
+# The relabel compaction's own tile shape (it runs in every Borůvka round),
+# tuned last, on top of the best configuration and shape.
+RELABEL_SHAPE_CANDIDATES: Tuple[dict, ...] = tuple(dict(relabel_block_threads=b, relabel_items_per_thread=i)
+                                                   for b in (128, 256, 512) for i in (4, 8, 16))
+
+# The values a configuration gets for keys it does not set.
+_DEFAULTS = dict(block_threads=256, items_per_thread=8, relabel_block_threads=128, relabel_items_per_thread=4)
+
 _cache: Dict[str, dict] = {}
 
 
@@ -40,16 +48,19 @@ def label(cfg: dict) -> str:
 
 def autotune(trial: Callable[[dict], float], candidates: Iterable[dict] = DEFAULT_CANDIDATES, reps: int = 2,
              key: str | None = None,
-             shapes: Iterable[dict] | None = SHAPE_CANDIDATES) -> Tuple[dict, List[Tuple[str, float]]]:
+             shapes: Iterable[dict] | None = SHAPE_CANDIDATES,
+             relabel_shapes: Iterable[dict] | None = None) -> Tuple[dict, List[Tuple[str, float]]]:
     """Returns (best configuration, [(label, best seconds)] for every trial).
 
     trial(cfg) runs one solve of the workload with configuration cfg and
     returns its duration in seconds (the caller times it on the device).  Each
     candidate gets one untimed run and `reps` timed runs; its score is the
     fastest timed run.  The candidates are tried first; then each of `shapes`
-    (kernel tile shapes; None or empty: none) is tried on top of the best of
-    them.  With `key`, the choice is remembered for the process and later
-    calls with the same key return it without trials."""
+    (kernel tile shapes; None or empty: none) on top of the best of them; then
+    each of `relabel_shapes` (e.g. RELABEL_SHAPE_CANDIDATES) on top of the best
+    so far.  Shapes equal to what the configuration already runs are skipped.
+    With `key`, the choice is remembered for the process and later calls with
+    the same key return it without trials."""
     if key is not None and key in _cache:
         return dict(_cache[key]), []
     results: List[Tuple[str, float]] = []
@@ -67,12 +78,12 @@ def autotune(trial: Callable[[dict], float], candidates: Iterable[dict] = DEFAUL
         run(cfg)
     if best is None:
         raise ValueError("autotune needs at least one candidate")
-    base = dict(best)
-    defaults = dict(block_threads=256, items_per_thread=8)  # the shape a configuration without one gets
-    for shape in shapes or ():
-        if all(base.get(k, defaults.get(k)) == v for k, v in shape.items()):
-            continue  # already timed
-        run({**base, **shape})
+    for stage in (shapes, relabel_shapes):
+        base = dict(best)
+        for shape in stage or ():
+            if all(base.get(k, _DEFAULTS.get(k)) == v for k, v in shape.items()):
+                continue  # already timed
+            run({**base, **shape})
     if key is not None:
         _cache[key] = dict(best)
     return best, results

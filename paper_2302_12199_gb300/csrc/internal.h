@@ -140,6 +140,10 @@ inline int shape_index(uint32_t block_threads, uint32_t items_per_thread) {
   const int i = it == 4 ? 0 : it == 8 ? 1 : it == 16 ? 2 : -1;
   return (b < 0 || i < 0) ? -1 : 1 + 3 * b + i;
 }
+// The relabel compaction's shape: both zero is 128 x 4 (shape 1).
+inline int relabel_shape_index(uint32_t block_threads, uint32_t items_per_thread) {
+  return (block_threads == 0 && items_per_thread == 0) ? 1 : shape_index(block_threads, items_per_thread);
+}
 inline uint32_t shape_tile(int shape) {
   static const uint32_t b[3] = {128, 256, 512}, i[3] = {4, 8, 16};
   return shape <= 0 ? 2048u : b[(shape - 1) / 3] * i[(shape - 1) % 3];

@@ -484,10 +484,12 @@ struct Solve {
   uint32_t *parent = nullptr, *act[2] = {nullptr, nullptr}, *bits = nullptr;
   int wbits = 32;  // bits of the largest weight (set with the key layout)
   int rounds = 0;
-  int shape = 0;   // tile shape of the compaction and hook kernels (shape_index of the configuration)
+  int shape = 0;   // tile shape of the partition / filter compactions and the hook (shape_index)
+  int rshape = 1;  // tile shape of the relabel compaction (relabel_shape_index)
 
   Solve(mst_ctx *c_, cudaStream_t s_, uint32_t n_, uint64_t m_)
-      : c(c_), s(s_), n(n_), m(m_), shape(shape_index(c_->cfg.block_threads, c_->cfg.items_per_thread)) {}
+      : c(c_), s(s_), n(n_), m(m_), shape(shape_index(c_->cfg.block_threads, c_->cfg.items_per_thread)),
+        rshape(relabel_shape_index(c_->cfg.relabel_block_threads, c_->cfg.relabel_items_per_thread)) {}
 
   mst_status init(uint32_t *parent_external = nullptr, uint32_t *bits_external = nullptr) {
     TRY(best_b.alloc(c, (size_t)n * 8, s));
@@ -656,7 +658,7 @@ struct Solve {
       RoundList &out = (cur.u == X.out.u) ? Y : X;
       TRY(zero_round_state(c, s));
       CompactArgs ca{};
-      ca.shape = shape;
+      ca.shape = rshape;
       ca.in = cur;
       ca.m = cur_m;
       ca.out = out.out;
@@ -891,7 +893,7 @@ struct Solve {
     for (int half = 0; half < 2; ++half) {
       const int in = half, out = 1 - half;
       CompactArgs ca{};
-      ca.shape = shape;
+      ca.shape = rshape;
       ca.in = L[in]->list();
       ca.m = cap;
       ca.m_dev = &g->ce[in];
@@ -1038,7 +1040,7 @@ struct Solve {
     TRY(out.alloc(c, mcut, s));
     TRY(zero_counters(c, s));
     CompactArgs ca{};
-    ca.shape = shape;
+    ca.shape = rshape;
     ca.in = cutl.list();
     ca.m = mcut;
     ca.m_dev = &c->ds->count[CNT_CUT];
@@ -1542,6 +1544,7 @@ mst_status validate_cfg(const mst_config *cfg) {
   if (cfg->spin_limit < 1) return MST_ERR_INVALID_ARG;
   if (shape_index(cfg->block_threads, cfg->items_per_thread) < 0) return MST_ERR_INVALID_ARG;
   if (cfg->filter_plan < 0 || cfg->filter_plan > 1) return MST_ERR_INVALID_ARG;
+  if (relabel_shape_index(cfg->relabel_block_threads, cfg->relabel_items_per_thread) < 0) return MST_ERR_INVALID_ARG;
   return MST_OK;
 }
 
@@ -1790,6 +1793,8 @@ void mst_config_default(mst_config *cfg) {
   cfg->block_threads = 0;      // 0: 256 threads per block
   cfg->items_per_thread = 0;   // 0: 8 edges per thread
   cfg->filter_plan = 1;
+  cfg->relabel_block_threads = 0;     // 0 and 0: 128 x 4
+  cfg->relabel_items_per_thread = 0;
 }
 
 const char *mst_status_string(mst_status s) {
@@ -2213,7 +2218,8 @@ static mst_status step_compact(mst_handle h, CompactMode mode, uint32_t n, uint6
   if (clear_device_flags(h, s) != MST_OK) return record_cuda(h, __LINE__);
   const EdgeList E{d_u, d_v, d_w, d_id};
   CompactArgs a{};
-  a.shape = shape_index(h->cfg.block_threads, h->cfg.items_per_thread);
+  a.shape = mode == CM_RELABEL ? relabel_shape_index(h->cfg.relabel_block_threads, h->cfg.relabel_items_per_thread)
+                               : shape_index(h->cfg.block_threads, h->cfg.items_per_thread);
   a.in = E;
   a.m = m;
   a.out = EdgeOut{d_ou, d_ov, d_ow, d_oid};

@@ -63,7 +63,8 @@ class MstConfig(ctypes.Structure):
                 ("min_edges_sort", ctypes.c_int), ("jump_steps", ctypes.c_uint32),
                 ("tile_filter", ctypes.c_int), ("spin_limit", ctypes.c_uint32),
                 ("block_threads", ctypes.c_uint32), ("items_per_thread", ctypes.c_uint32),
-                ("filter_plan", ctypes.c_int)]
+                ("filter_plan", ctypes.c_int), ("relabel_block_threads", ctypes.c_uint32),
+                ("relabel_items_per_thread", ctypes.c_uint32)]
 
 
 _P = ctypes.c_void_p

@@ -32,6 +32,7 @@ def test_default_config(lib):
     assert cfg.jump_steps == 64 and cfg.tile_filter == 0
     assert cfg.filter_carry == 0
     assert cfg.spin_limit == 1 << 21 and cfg.block_threads == 0 and cfg.items_per_thread == 0
+    assert cfg.filter_plan == 1 and cfg.relabel_block_threads == 0 and cfg.relabel_items_per_thread == 0
 
 
 def test_bad_kernel_shapes_are_refused_without_device(lib):
@@ -43,6 +44,13 @@ def test_bad_kernel_shapes_are_refused_without_device(lib):
         cfg.block_threads, cfg.items_per_thread = bt, it
         h = ctypes.c_void_p()
         assert lib.mst_create(ctypes.byref(h), ctypes.byref(cfg)) == 1, (bt, it)
+        lib.mst_config_default(ctypes.byref(cfg))
+        cfg.relabel_block_threads, cfg.relabel_items_per_thread = bt, it  # the relabel compaction's own shape
+        assert lib.mst_create(ctypes.byref(h), ctypes.byref(cfg)) == 1, ("relabel", bt, it)
+    for flag in (-1, 2):
+        lib.mst_config_default(ctypes.byref(cfg))
+        cfg.filter_plan = flag
+        assert lib.mst_create(ctypes.byref(h), ctypes.byref(cfg)) == 1, ("filter_plan", flag)
 
 
 def test_status_strings(lib):

@@ -474,6 +474,24 @@ def test_every_kernel_shape_equals_kruskal(dev, threads, items):
             s.close()
 
 
+@pytest.mark.parametrize("items", [4, 8, 16])
+@pytest.mark.parametrize("threads", [128, 256, 512])
+def test_every_relabel_shape_equals_kruskal(dev, threads, items):
+    """The relabel compaction's own tile shape (every Borůvka round's pass;
+    `relabel_block_threads` x `relabel_items_per_thread`) gives Kruskal's
+    forest in every build, in host-driven rounds, round graphs and the planned
+    Filter-Borůvka, with packed and unpacked keys and with hash dedupe."""
+    for name in ("rmat_filter", "rgg2d", "gnm_hash", "path"):
+        g, cfg, (kid, ktot) = _shape_case(name)
+        s = Solver(0, relabel_block_threads=threads, relabel_items_per_thread=items, **cfg)
+        try:
+            for rep in range(2):
+                ids, tot = gpu_msf(s, g.n, g.src, g.dst, g.w, dev)
+                assert np.array_equal(ids, kid) and tot == ktot, (name, rep)
+        finally:
+            s.close()
+
+
 def test_ordered_scan_wait_that_runs_out_is_an_error(dev):
     """The ordered output scan is the one place where blocks wait on each
     other (a tile polls the prefixes its predecessors publish), and that wait

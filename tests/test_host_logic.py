@@ -58,6 +58,30 @@ def test_autotune_tunes_the_kernel_shape_on_the_best_configuration():
     assert len(res) == 2 + 8
 
 
+def test_autotune_relabel_shape_stage_runs_on_the_best_shape():
+    """The relabel compaction's shapes are tried last, on top of the best
+    configuration and kernel shape, skipping the default 128 x 4."""
+    from paper_2302_12199_gb300.autotune import RELABEL_SHAPE_CANDIDATES, SHAPE_CANDIDATES
+    seen = []
+
+    def trial(cfg):
+        seen.append(dict(cfg))
+        t = 2.0
+        if cfg.get("block_threads") == 128 and cfg.get("items_per_thread") == 16:
+            t -= 0.5
+        if cfg.get("relabel_block_threads") == 256 and cfg.get("relabel_items_per_thread") == 8:
+            t -= 0.25
+        return t
+    best, res = autotune(trial, [dict(k="a")], reps=1, shapes=SHAPE_CANDIDATES,
+                         relabel_shapes=RELABEL_SHAPE_CANDIDATES)
+    assert best == dict(k="a", block_threads=128, items_per_thread=16, relabel_block_threads=256,
+                        relabel_items_per_thread=8)
+    relabel = [c for c in seen if "relabel_block_threads" in c]
+    assert all(c["block_threads"] == 128 and c["items_per_thread"] == 16 for c in relabel)
+    assert len({(c["relabel_block_threads"], c["relabel_items_per_thread"]) for c in relabel}) == 8
+    assert len(res) == 1 + 8 + 8
+
+
 class _FakeSlot:
     """Stands in for a GPU solver slot: 'solves' a batch after a short sleep and
     returns per-graph answers that encode the graph, so routing is checked."""
