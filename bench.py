@@ -397,6 +397,8 @@ def gpu_main(args, rank: int, world: int, local_rank: int):
         cfg["tile_filter"] = args.tile_filter
     if args.filter_plan is not None:
         cfg["filter_plan"] = args.filter_plan
+    if args.pivot_quantile is not None:
+        cfg["pivot_quantile"] = args.pivot_quantile
     g = gen(W)
     n, m = g.n, g.m
     src = torch.from_numpy(g.src.view(np.int32)).to(dev)
@@ -1002,6 +1004,8 @@ def main():
     ap.add_argument("--min-edges-sort", type=int, default=None, choices=[0, 1])
     ap.add_argument("--tile-filter", type=int, default=None, choices=[0, 1])
     ap.add_argument("--filter-plan", type=int, default=None, choices=[0, 1])
+    ap.add_argument("--pivot-quantile", type=float, default=None,
+                    help="Filter-Borůvka: pivot rank in its sample as a fraction (0.5 = the sample median)")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "gpu":
         args.warmup = 3

@@ -24,7 +24,11 @@
  * the Borůvka round loop and the Filter-Borůvka recursion are steered by
  * counts (list lengths, active components) that the host reads back on that
  * stream, so a solve is stream-ordered but not asynchronous to the host.  A
- * handle must not be used by two host threads at once.
+ * handle must not be used by two host threads at once; different handles may
+ * solve at the same time from different threads (each on its own stream): a
+ * solve grows its buffers in stream order and never waits for the whole
+ * device.  mst_create and mst_destroy do wait for the device, so create and
+ * destroy handles while no other thread is capturing a CUDA graph.
  *
  * Errors: every call returns an mst_status.  Errors detected on the device
  * (vertex ids out of range, a bounded loop that ran out of iterations) are
@@ -68,9 +72,8 @@ typedef struct {
   uint64_t seed;               /* seed of the pivot sampling stream */
   uint64_t filter_min_edges;   /* isSparse: lists shorter than this are not partitioned */
   float filter_max_avg_degree; /* isSparse: stop partitioning at average degree 2m/n <= this (the paper's
-                                  Section 6.3 uses 4; the default 1.25 is measured on GB300: the range
-                                  1.0-1.5 is flat, and 1.25 keeps the number of levels stable where
-                                  halving lists reach m = n/2) */
+                                  Section 6.3 uses 4; the default 1.25 is measured on GB300, where the range
+                                  0.75-2.5 is flat with the default pivot quantile) */
   int base_case;               /* 1 (default): once a Borůvka call's live components (<= 4096) and
                                   edges (<= 6144) fit one block's shared memory, finish its rounds in
                                   one launch (the role of the paper's base case, Section 4.4); 0: run
@@ -121,10 +124,18 @@ typedef struct {
                                         relabel fields 0: 128 x 4, measured fastest on GB300 (more,
                                         smaller tiles spread a short list over more SMs) */
   uint32_t relabel_items_per_thread; /* edges per thread of the relabel compaction: 4, 8 or 16 */
+  float pivot_quantile;        /* Filter-Borůvka: the pivot is the sample key of rank floor(q * pivot_sample),
+                                  so about a share q of each list is light (Alg. 2 PivotSelection takes the
+                                  median, q = 0.5).  1/64 <= q <= 1/2.  A smaller q writes shorter light lists
+                                  and needs fewer recursion levels, while the filter meets more heavy edges
+                                  (over all levels about the same number); every q computes the same forest.
+                                  Default 0.125, measured on GB300: RMAT n=2^24 m=2^28 takes 7.16 / 5.54 /
+                                  5.25 / 5.35 ms at q = 1/2, 1/4, 1/8, 1/16 (flat from 3/32 to 5/32) */
 } mst_config;
 
 /* Fills *cfg with the defaults (Borůvka variant, automatic dedupe, pivot sample
- * 2^16, isSparse average degree 1.25, lists below 2^20 edges not partitioned). */
+ * 2^16 split at its 1/8 quantile, isSparse average degree 1.25, lists below
+ * 2^20 edges not partitioned). */
 void mst_config_default(mst_config *cfg);
 
 /* Creates a handle on cfg->device (cfg == NULL: defaults on device 0). */

@@ -25,6 +25,11 @@ DEFAULT_CANDIDATES: Tuple[dict, ...] = (
     dict(variant="boruvka", dedupe="none", tile_contract=0, min_edges_sort=1),
 )
 
+# The Filter-Borůvka pivot's rank in its sample (the light share of each
+# list; Alg. 2 takes the median, 1/2).  Tuned on the best configuration when
+# that is the filter variant.
+QUANTILE_CANDIDATES: Tuple[dict, ...] = tuple(dict(pivot_quantile=q) for q in (0.5, 0.25, 0.125, 0.0625))
+
 # Tile shapes of the compaction and hook kernels: threads per block x items
 # per thread.  Tuned on top of the best configuration above (every shape
 # computes the same forest).
@@ -37,7 +42,8 @@ RELABEL_SHAPE_CANDIDATES: Tuple[dict, ...] = tuple(dict(relabel_block_threads=b,
                                                    for b in (128, 256, 512) for i in (4, 8, 16))
 
 # The values a configuration gets for keys it does not set.
-_DEFAULTS = dict(block_threads=256, items_per_thread=8, relabel_block_threads=128, relabel_items_per_thread=4)
+_DEFAULTS = dict(block_threads=256, items_per_thread=8, relabel_block_threads=128, relabel_items_per_thread=4,
+                 pivot_quantile=0.125)
 
 _cache: Dict[str, dict] = {}
 
@@ -49,18 +55,20 @@ def label(cfg: dict) -> str:
 def autotune(trial: Callable[[dict], float], candidates: Iterable[dict] = DEFAULT_CANDIDATES, reps: int = 2,
              key: str | None = None,
              shapes: Iterable[dict] | None = SHAPE_CANDIDATES,
-             relabel_shapes: Iterable[dict] | None = None) -> Tuple[dict, List[Tuple[str, float]]]:
+             relabel_shapes: Iterable[dict] | None = None,
+             quantiles: Iterable[dict] | None = QUANTILE_CANDIDATES) -> Tuple[dict, List[Tuple[str, float]]]:
     """Returns (best configuration, [(label, best seconds)] for every trial).
 
     trial(cfg) runs one solve of the workload with configuration cfg and
     returns its duration in seconds (the caller times it on the device).  Each
     candidate gets one untimed run and `reps` timed runs; its score is the
-    fastest timed run.  The candidates are tried first; then each of `shapes`
-    (kernel tile shapes; None or empty: none) on top of the best of them; then
-    each of `relabel_shapes` (e.g. RELABEL_SHAPE_CANDIDATES) on top of the best
-    so far.  Shapes equal to what the configuration already runs are skipped.
-    With `key`, the choice is remembered for the process and later calls with
-    the same key return it without trials."""
+    fastest timed run.  The candidates are tried first; then, if the best of
+    them is the filter variant, each of `quantiles` (pivot ranks; None or
+    empty: none) on top of it; then each of `shapes` (kernel tile shapes) on
+    top of the best so far; then each of `relabel_shapes` (e.g.
+    RELABEL_SHAPE_CANDIDATES).  Settings equal to what the configuration
+    already runs are skipped.  With `key`, the choice is remembered for the
+    process and later calls with the same key return it without trials."""
     if key is not None and key in _cache:
         return dict(_cache[key]), []
     results: List[Tuple[str, float]] = []
@@ -78,8 +86,10 @@ def autotune(trial: Callable[[dict], float], candidates: Iterable[dict] = DEFAUL
         run(cfg)
     if best is None:
         raise ValueError("autotune needs at least one candidate")
-    for stage in (shapes, relabel_shapes):
+    for stage in (quantiles, shapes, relabel_shapes):
         base = dict(best)
+        if stage is quantiles and base.get("variant") != "filter":
+            continue
         for shape in stage or ():
             if all(base.get(k, _DEFAULTS.get(k)) == v for k, v in shape.items()):
                 continue  # already timed

@@ -171,14 +171,16 @@ void launch_jump(const uint32_t *act, const u64 *count_dev, uint64_t count_host,
 void launch_range_check(const uint32_t *x, uint64_t count, uint32_t bound, uint32_t *err, int sms, cudaStream_t s);
 void launch_hash_insert(EdgeList in, uint64_t m, HashSlot *table, uint64_t tmask, uint32_t *err, int sms,
                         cudaStream_t s);
+// The pivot is the sample key of rank `rank` (0-based); a rank >= sample
+// means sample / 2, the sample median of Alg. 2.
 void launch_pivot(EdgeList in, uint64_t m, const u64 *m_dev, u64 state, uint32_t sample, u64 *sample_buf,
-                  u64 *pivot_out, cudaStream_t s);
+                  u64 *pivot_out, cudaStream_t s, uint32_t rank = ~0u);
 // Pivot selection by a cooperative multi-block radix select (same result as
 // launch_pivot); `scratch` holds pivot_scratch_bytes().  False if the
 // cooperative launch was refused.
 size_t pivot_scratch_bytes();
 bool launch_pivot_coop(EdgeList in, uint64_t m, u64 state, uint32_t sample, u64 *keys, void *scratch,
-                       u64 *pivot_out, cudaStream_t s, const u64 *m_dev = nullptr);
+                       u64 *pivot_out, cudaStream_t s, const u64 *m_dev = nullptr, uint32_t rank = ~0u);
 // w == nullptr: ids and count only (total_weight untouched).
 void launch_finalize(const uint32_t *bits, uint64_t m, const uint32_t *w, uint32_t *out_ids, uint32_t *out_count,
                      u64 *total_weight, ScanState st, cudaStream_t s);

@@ -649,17 +649,24 @@ __device__ __forceinline__ void read_striped_smem(const uint32_t *p, uint32_t (&
   }
 }
 
-// Input stages plus one output stage of T items.
-template <int B, int I>
-constexpr size_t tma_smem_bytes() { return sizeof(EdgeStage<B * I>) * (TMA_STAGES + 1); }
+// S input stages plus one output stage of T items.
+template <int B, int I, int S = TMA_STAGES>
+constexpr size_t tma_smem_bytes() { return sizeof(EdgeStage<B * I>) * (S + 1); }
+
+// Input stages of the persistent compaction per mode: the partition has no
+// gathers, so it keeps PARTITION_STAGES tiles per block in flight.
+constexpr int PARTITION_STAGES = 1;
+template <int MODE>
+__host__ __device__ constexpr int tma_stages() { return MODE == CM_PARTITION ? PARTITION_STAGES : TMA_STAGES; }
 
 template <int MODE, int B, int I>
 __global__ void __launch_bounds__(B, Shape<B, I>::minb(Shape<B, I>::tma_regs)) compact_tma_kernel(CompactArgs a) {
   constexpr int T = Shape<B, I>::T;
+  constexpr int NS = tma_stages<MODE>();  // input stages
   extern __shared__ __align__(128) unsigned char smem_dyn[];
-  EdgeStage<T> *stage = reinterpret_cast<EdgeStage<T> *>(smem_dyn);  // TMA_STAGES input stages + 1 output stage
-  EdgeStage<T> *out = stage + TMA_STAGES;
-  __shared__ __align__(8) u64 mbar[TMA_STAGES];
+  EdgeStage<T> *stage = reinterpret_cast<EdgeStage<T> *>(smem_dyn);  // NS input stages + 1 output stage
+  EdgeStage<T> *out = stage + NS;
+  __shared__ __align__(8) u64 mbar[NS];
   __shared__ uint32_t s_warp[B / 32 + 1];
   __shared__ uint32_t s_base[1];
   __shared__ uint32_t s_abort;
@@ -668,10 +675,10 @@ __global__ void __launch_bounds__(B, Shape<B, I>::minb(Shape<B, I>::tma_regs)) c
   const uint64_t ntiles = (m + T - 1) / T, nfull = m / T;
   const uint64_t G = gridDim.x;
   if (threadIdx.x == 0) {
-    for (int s = 0; s < TMA_STAGES; ++s) mbar_init(&mbar[s], 1);
+    for (int s = 0; s < NS; ++s) mbar_init(&mbar[s], 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     s_abort = 0;
-    for (int s = 0; s < TMA_STAGES; ++s) {
+    for (int s = 0; s < NS; ++s) {
       const uint64_t tile = blockIdx.x + (uint64_t)s * G;
       if (tile < nfull) issue_tile<T>(a, tile, &stage[s], &mbar[s]);
     }
@@ -682,12 +689,12 @@ __global__ void __launch_bounds__(B, Shape<B, I>::minb(Shape<B, I>::tma_regs)) c
   for (;; ++it) {
     const uint64_t tile = blockIdx.x + it * G;
     if (tile >= ntiles) break;
-    const int si = (int)(it % TMA_STAGES);
+    const int si = (int)(it % NS);
     EdgeStage<T> *st = &stage[si];
     const uint64_t tb = tile * T;
     uint32_t eu[I], ev[I], ew[I], ei[I];
     if (tile < nfull) {
-      if (!mbar_wait_bounded(&mbar[si], (uint32_t)((it / TMA_STAGES) & 1))) atomicOr(&s_abort, 1u);
+      if (!mbar_wait_bounded(&mbar[si], (uint32_t)((it / NS) & 1))) atomicOr(&s_abort, 1u);
       __syncthreads();
       if (s_abort) break;
       read_striped_smem<B, I>(st->u, eu);
@@ -699,9 +706,9 @@ __global__ void __launch_bounds__(B, Shape<B, I>::minb(Shape<B, I>::tma_regs)) c
 #pragma unroll
         for (int k = 0; k < I; ++k) ei[k] = (uint32_t)(tb + item_off<B>(k));
       }
-      __syncthreads();  // the stage is consumed: refill it with the tile TMA_STAGES ahead
+      __syncthreads();  // the stage is consumed: refill it with the tile NS ahead
       if (threadIdx.x == 0) {
-        const uint64_t next = tile + (uint64_t)TMA_STAGES * G;
+        const uint64_t next = tile + (uint64_t)NS * G;
         if (next < nfull) issue_tile<T>(a, next, st, &mbar[si]);
       }
     } else {  // the partial last tile: plain loads
@@ -742,9 +749,9 @@ __global__ void __launch_bounds__(B, Shape<B, I>::minb(Shape<B, I>::tma_regs)) c
   __syncthreads();
   if (s_abort && threadIdx.x == 0) {
     atomicOr(a.st.err, ERR_TMA);
-    for (uint64_t k = it; k < it + TMA_STAGES; ++k) {
+    for (uint64_t k = it; k < it + NS; ++k) {
       const uint64_t tile = blockIdx.x + k * G;
-      if (tile < nfull) mbar_wait_bounded(&mbar[k % TMA_STAGES], (uint32_t)((k / TMA_STAGES) & 1));
+      if (tile < nfull) mbar_wait_bounded(&mbar[k % NS], (uint32_t)((k / NS) & 1));
     }
   }
 }
@@ -1372,11 +1379,13 @@ __global__ void pivot_sample_kernel(EdgeList in, uint64_t m_host, const u64 *m_d
   }
 }
 
-// The sample key of rank sample/2, by radix selection in one block: bytes are
-// fixed from the most significant one that differs between the sample's
-// minimum and maximum, using a 256-bin histogram per byte.
+// The sample key of rank `rank` (0-based, < sample; sample / 2 is the median
+// of Alg. 2), by radix selection in one block: bytes are fixed from the most
+// significant one that differs between the sample's minimum and maximum,
+// using a 256-bin histogram per byte.
 constexpr int SEL_THREADS = 1024;
-__global__ void __launch_bounds__(SEL_THREADS) pivot_select_kernel(const u64 *keys, uint32_t sample, u64 *out) {
+__global__ void __launch_bounds__(SEL_THREADS) pivot_select_kernel(const u64 *keys, uint32_t sample, uint32_t rank0,
+                                                                   u64 *out) {
   __shared__ uint32_t hist[256];
   __shared__ u64 s_red[2][SEL_THREADS / 32];
   __shared__ u64 s_prefix, s_mask;
@@ -1420,7 +1429,7 @@ __global__ void __launch_bounds__(SEL_THREADS) pivot_select_kernel(const u64 *ke
   if (threadIdx.x == 0) {
     s_mask = start + 8 >= 64 ? 0ULL : ~((1ULL << (start + 8)) - 1ULL);
     s_prefix = mn & s_mask;
-    s_rank = sample / 2;
+    s_rank = rank0;
   }
   const uint32_t iters = (sample + SEL_THREADS - 1) / SEL_THREADS;
   for (int shift = start; shift >= 0; shift -= 8) {
@@ -1478,8 +1487,8 @@ struct PivotScratch {
 };
 
 __global__ void __launch_bounds__(PSEL_THREADS) pivot_coop_kernel(EdgeList in, uint64_t m_bound, const u64 *m_dev,
-                                                                 u64 state, uint32_t sample, u64 *keys,
-                                                                 PivotScratch *ps, u64 *out) {
+                                                                 u64 state, uint32_t sample, uint32_t rank0,
+                                                                 u64 *keys, PivotScratch *ps, u64 *out) {
   const uint64_t m = m_dev ? min((uint64_t)*m_dev, m_bound) : m_bound;
   namespace cg = cooperative_groups;
   cg::grid_group grid = cg::this_grid();
@@ -1532,7 +1541,7 @@ __global__ void __launch_bounds__(PSEL_THREADS) pivot_coop_kernel(EdgeList in, u
     const int top = low + PSEL_BITS;  // bits >= top are shared by every key
     s_mask = top >= 64 ? 0ULL : ~((1ULL << top) - 1ULL);
     s_prefix = mn & s_mask;
-    s_rank = sample / 2;
+    s_rank = rank0;
   }
   __syncthreads();
   for (int pass = 0;; ++pass) {
@@ -2724,7 +2733,8 @@ template <int MODE, int B, int I>
 static void launch_compact_shaped(const CompactArgs &a, uint64_t max_count, bool aligned, cudaStream_t s) {
   constexpr int T = B * I;
   constexpr size_t stage_bytes = 16 * (size_t)T;  // compact_kernel's staging buffer
-  constexpr bool tma_fits = tma_smem_bytes<B, I>() <= 200 * 1024;
+  constexpr int NS = tma_stages<MODE>();
+  constexpr bool tma_fits = tma_smem_bytes<B, I, NS>() <= 200 * 1024;
   static int attrs = 0, tma_blocks = 0;
   if (!attrs) {  // prefer shared memory over L1; allow the staging buffer; size the persistent grid
     cudaFuncSetAttribute(compact_kernel<MODE, true, B, I>, cudaFuncAttributePreferredSharedMemoryCarveout,
@@ -2733,12 +2743,12 @@ static void launch_compact_shaped(const CompactArgs &a, uint64_t max_count, bool
                          (int)stage_bytes);
     if constexpr (tma_fits) {
       cudaFuncSetAttribute(compact_tma_kernel<MODE, B, I>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)tma_smem_bytes<B, I>());
+                           (int)tma_smem_bytes<B, I, NS>());
       int dev = 0, sms = 0, per_sm = 0;
       cudaGetDevice(&dev);
       cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
       cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, compact_tma_kernel<MODE, B, I>, B,
-                                                    tma_smem_bytes<B, I>());
+                                                    tma_smem_bytes<B, I, NS>());
       tma_blocks = sms * per_sm;
     }
     cudaGetLastError();
@@ -2747,8 +2757,8 @@ static void launch_compact_shaped(const CompactArgs &a, uint64_t max_count, bool
   const uint64_t tiles = (max_count + T - 1) / T;
   if (tiles == 0) return;
   if constexpr (tma_fits) {
-    if (aligned && tma_blocks > 0 && tiles >= (uint64_t)tma_blocks * TMA_STAGES) {
-      compact_tma_kernel<MODE, B, I><<<(unsigned)tma_blocks, B, tma_smem_bytes<B, I>(), s>>>(a);
+    if (aligned && tma_blocks > 0 && tiles >= (uint64_t)tma_blocks * NS) {
+      compact_tma_kernel<MODE, B, I><<<(unsigned)tma_blocks, B, tma_smem_bytes<B, I, NS>(), s>>>(a);
       return;
     }
   }
@@ -2898,19 +2908,22 @@ void launch_hash_insert(EdgeList in, uint64_t m, HashSlot *table, uint64_t tmask
   hash_insert_kernel<<<grid_for((m + BLOCK - 1) / BLOCK, sms, 8), BLOCK, 0, s>>>(in, m, table, tmask, err);
 }
 
+static inline uint32_t select_rank(uint32_t sample, uint32_t rank) { return rank < sample ? rank : sample / 2; }
+
 void launch_pivot(EdgeList in, uint64_t m, const u64 *m_dev, u64 state, uint32_t sample, u64 *sample_buf,
-                  u64 *pivot_out, cudaStream_t s) {
+                  u64 *pivot_out, cudaStream_t s, uint32_t rank) {
   const unsigned g = (sample + BLOCK - 1) / BLOCK;
   pivot_sample_kernel<<<g > 0 ? g : 1, BLOCK, 0, s>>>(in, m, m_dev, state, sample, sample_buf);
-  pivot_select_kernel<<<1, SEL_THREADS, 0, s>>>(sample_buf, sample, pivot_out);
+  pivot_select_kernel<<<1, SEL_THREADS, 0, s>>>(sample_buf, sample, select_rank(sample, rank), pivot_out);
 }
 
 size_t pivot_scratch_bytes() { return sizeof(PivotScratch); }
 
 bool launch_pivot_coop(EdgeList in, uint64_t m, u64 state, uint32_t sample, u64 *keys, void *scratch,
-                       u64 *pivot_out, cudaStream_t s, const u64 *m_dev) {
+                       u64 *pivot_out, cudaStream_t s, const u64 *m_dev, uint32_t rank) {
   PivotScratch *ps = static_cast<PivotScratch *>(scratch);
-  void *args[] = {&in, &m, &m_dev, &state, &sample, &keys, &ps, &pivot_out};
+  uint32_t r = select_rank(sample, rank);
+  void *args[] = {&in, &m, &m_dev, &state, &sample, &r, &keys, &ps, &pivot_out};
   if (cudaLaunchCooperativeKernel((const void *)pivot_coop_kernel, dim3(PSEL_BLOCKS), dim3(PSEL_THREADS), args, 0, s) ==
       cudaSuccess)
     return true;

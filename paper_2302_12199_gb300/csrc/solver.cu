@@ -6,6 +6,7 @@
 // scratch from it in stream order and returns it at the end, so repeated solves
 // reuse the same memory without device-wide synchronisation.
 #include <algorithm>
+#include <cmath>
 #include <cstddef>
 #include <cstdint>
 #include <cstring>
@@ -196,17 +197,20 @@ struct RoundList {
 };
 
 // Points X and Y at the handle's round lists, first growing them (a quarter
-// above `need`, in steps of 2^16 edges, after the device is idle: earlier
-// work may still read the old ones) when they hold fewer than `need` edges.
-mst_status round_lists(mst_ctx *c, uint64_t need, RoundList &X, RoundList &Y) {
+// above `need`, in steps of 2^16 edges) when they hold fewer than `need`
+// edges.  The growth is stream-ordered on s: the old lists are freed after the
+// work queued on s so far (calls return only after their work is done, so no
+// earlier call still reads them), and nothing waits for the whole device, which
+// other threads may be using (or capturing graphs on) at the same time.
+mst_status round_lists(mst_ctx *c, uint64_t need, RoundList &X, RoundList &Y, cudaStream_t s) {
   if (!c->rl_mem || c->rl_cap < need) {
     const uint64_t want = round_up(std::max<uint64_t>(need + need / 4, 1ULL << 16), 1ULL << 16);
-    CK(cudaDeviceSynchronize());
-    if (c->rl_mem) cudaFree(c->rl_mem);
+    if (c->rl_mem) CK(cudaFreeAsync(c->rl_mem, s));
     c->rl_mem = nullptr;
     c->rl_cap = 0;
-    if (cudaMalloc(&c->rl_mem, 8 * round_up(want * 4 + 16, 256)) != cudaSuccess) {
+    if (cudaMallocAsync(&c->rl_mem, 8 * round_up(want * 4 + 16, 256), s) != cudaSuccess) {
       cudaGetLastError();
+      c->rl_mem = nullptr;
       return MST_ERR_OOM;
     }
     c->rl_cap = want;
@@ -225,19 +229,20 @@ mst_status round_lists(mst_ctx *c, uint64_t need, RoundList &X, RoundList &Y) {
 mst_status ensure_status(mst_ctx *c, uint64_t max_items, cudaStream_t s) {
   const uint64_t tiles = (max_items + TILE_ITEMS - 1) / TILE_ITEMS + 1;
   if (tiles <= c->status_cap) return MST_OK;
-  CK(cudaStreamSynchronize(s));
-  if (c->status) cudaFree(c->status);
+  // stream-ordered, like the round lists: no wait for the whole device
+  if (c->status) CK(cudaFreeAsync(c->status, s));
   c->status = nullptr;
   c->status_cap = 0;
   const uint64_t cap = next_pow2(tiles < 4096 ? 4096 : tiles);
-  if (cudaMalloc(&c->status, cap * sizeof(u64)) != cudaSuccess) {
+  if (cudaMallocAsync(&c->status, cap * sizeof(u64), s) != cudaSuccess) {
     cudaGetLastError();
+    c->status = nullptr;
     return MST_ERR_OOM;
   }
-  CK(cudaMemset(c->status, 0, cap * sizeof(u64)));
+  CK(cudaMemsetAsync(c->status, 0, cap * sizeof(u64), s));
   c->status_cap = cap;
   c->epoch = 0;
-  CK(cudaMemset(c->ds->tile_ctr, 0, sizeof(c->ds->tile_ctr)));
+  CK(cudaMemsetAsync(c->ds->tile_ctr, 0, sizeof(c->ds->tile_ctr), s));
   return MST_OK;
 }
 
@@ -633,7 +638,7 @@ struct Solve {
     ++rounds;
 
     RoundList X, Y;  // the handle's round lists (lists only shrink within a call: mE edges suffice)
-    TRY(round_lists(c, mE, X, Y));
+    TRY(round_lists(c, mE, X, Y, s));
     ListBuf T;
     Buf table_b;
     EdgeList cur = E;
@@ -1058,6 +1063,15 @@ struct Solve {
     return MST_OK;
   }
 
+  // Rank of the pivot in its sample, and the expected light part of a list of
+  // mE edges split there (Alg. 2 takes the sample median: rank s / 2, half).
+  uint32_t pivot_rank() const {
+    const uint32_t smp = c->cfg.pivot_sample;
+    const uint32_t r = (uint32_t)std::floor((double)c->cfg.pivot_quantile * (double)smp);
+    return r < smp ? r : smp - 1;
+  }
+  uint64_t light_est(uint64_t mE) const { return (uint64_t)((double)c->cfg.pivot_quantile * (double)mE); }
+
   bool is_sparse(uint64_t mE) const {
     return mE < c->cfg.filter_min_edges || 2.0 * (double)mE <= (double)c->cfg.filter_max_avg_degree * (double)n;
   }
@@ -1101,12 +1115,13 @@ struct Solve {
     const u64 state = host_splitmix64_at(c->cfg.seed, c->pivot_counter++);
     PROF(MST_K_PIVOT, 16.0 * (double)c->cfg.pivot_sample, -1, 0.0, -1, 0.0,
          if (!launch_pivot_coop(E, mE, state, c->cfg.pivot_sample, c->sample_buf, c->pivot_scratch, &c->ds->pivot,
-                                s)) launch_pivot(E, mE, nullptr, state, c->cfg.pivot_sample, c->sample_buf,
-                                                 &c->ds->pivot, s));
+                                s, nullptr, pivot_rank())) launch_pivot(E, mE, nullptr, state, c->cfg.pivot_sample,
+                                                                        c->sample_buf, &c->ds->pivot, s,
+                                                                        pivot_rank()));
     const double in_bytes = (E.id ? 16.0 : 12.0) * (double)mE;
-    // the light half goes straight to Borůvka rounds when it will be sparse:
+    // the light part goes straight to Borůvka rounds when it will be sparse:
     // the partition pass then also performs that call's first minEdges
-    const bool fuse_light = is_sparse(mE / 2);
+    const bool fuse_light = is_sparse(light_est(mE));
     ListBuf L;
     TRY(L.alloc(c, mE, s));
     CompactArgs cp{};
@@ -1240,10 +1255,11 @@ struct Solve {
   // Filter-Borůvka (Alg. 2) with the recursion laid out by the host ahead of
   // time and every list length kept in device memory.  The top-level
   // partition's light count (one readback, which also brings the largest
-  // weight for the key layout) fixes the plan: light lists halve from level to
-  // level (the pivot is the median of the sample), so the host knows how many
-  // levels reach isSparse and gives each list a capacity a little above half
-  // of its parent's.  The levels then run without the host reading anything:
+  // weight for the key layout) fixes the plan: light lists shrink by the
+  // pivot's quantile q from level to level (q of each list is light: 1/2 for
+  // the sample median of Alg. 2), so the host knows how many levels reach
+  // isSparse and gives each list a capacity a little above q of its parent's.
+  // The levels then run without the host reading anything:
   // pivot and partition from device counts, and the deepest light list and
   // each level's filtered heavy edges solved by Borůvka rounds whose first
   // hooking runs before the round graph and whose loop the device ends.  A
@@ -1258,15 +1274,21 @@ struct Solve {
            f.dedupe != MST_DEDUPE_HASH && f.dedupe != MST_DEDUPE_SORT && !is_sparse(m);
   }
   // Capacity planned for the light list of a list of at most `cap` edges:
-  // half of it plus 1/32 of it and 2^16 (the light share of a list split at
-  // a sample median of 2^16 keys strays from 1/2 by about 2^-9 of the list).
-  static uint64_t light_cap(uint64_t cap) { return std::min<uint64_t>(cap, cap / 2 + cap / 32 + (1ULL << 16)); }
+  // its expected light share (pivot_quantile, 1/2 for the sample median) plus
+  // 1/32 of it and 2^16 (the light share of a list split at a quantile of a
+  // sample of 2^16 keys strays from it by at most about 2^-9 of the list).
+  uint64_t light_cap(uint64_t cap) const {
+    return std::min<uint64_t>(cap, light_est(cap) + cap / 32 + (1ULL << 16));
+  }
   // The round lists of a plan: the deepest light list, and each level's
-  // filtered heavy edges in turn (room for n of them, or for every heavy edge
-  // of the input if that is fewer; the filter is expected to keep far fewer,
-  // Theorem 1).
+  // filtered heavy edges in turn: room for n / (2q) of them with a light share
+  // q (n at the median), or for every edge of the input if that is fewer.  By
+  // Theorem 1 the heavy edges that survive a filter against the forest of a
+  // sample of rate q number about n / q in expectation at most; on the graphs
+  // measured they are far fewer.
   uint64_t plan_round_edges(uint64_t deepest_cap) const {
-    const uint64_t heavy = std::min<uint64_t>(n, light_cap(m));
+    const double per_n = 0.5 / (double)c->cfg.pivot_quantile;
+    const uint64_t heavy = std::min<uint64_t>((uint64_t)(per_n * (double)n), m);
     return std::max<uint64_t>(std::max<uint64_t>(deepest_cap, heavy), 1ULL << 16);
   }
 
@@ -1308,7 +1330,7 @@ struct Solve {
   mst_status filter_planned(bool &planned) {
     planned = false;
     const uint64_t m0 = m;
-    const bool leaf_top = is_sparse(m0 / 2);  // the top level's light list is expected to be the deepest
+    const bool leaf_top = is_sparse(light_est(m0));  // the top level's light list is expected to be the deepest
     if (leaf_top && !layout_set) TRY(choose_layout(w_in));
     Buf piv_b, gbits_b;
     TRY(piv_b.alloc(c, LVL_MAX * sizeof(u64), s));
@@ -1318,7 +1340,7 @@ struct Solve {
     CK(cudaMemsetAsync(&c->ds->count[CNT_LVL], 0, 2 * LVL_MAX * sizeof(u64), s));
     const uint64_t cap1 = light_cap(m0);
     RoundList X, Y;
-    TRY(round_lists(c, plan_round_edges(leaf_top ? cap1 : 0), X, Y));
+    TRY(round_lists(c, plan_round_edges(leaf_top ? cap1 : 0), X, Y, s));
     ListBuf L1;
     if (!leaf_top) TRY(L1.alloc(c, cap1, s));
 
@@ -1327,8 +1349,9 @@ struct Solve {
     u64 state[LVL_MAX];
     state[0] = host_splitmix64_at(c->cfg.seed, c->pivot_counter++);
     PROF(MST_K_PIVOT, 16.0 * (double)c->cfg.pivot_sample, -1, 0.0, -1, 0.0,
-         if (!launch_pivot_coop(in, m0, state[0], c->cfg.pivot_sample, c->sample_buf, c->pivot_scratch, &piv[0], s))
-             launch_pivot(in, m0, nullptr, state[0], c->cfg.pivot_sample, c->sample_buf, &piv[0], s));
+         if (!launch_pivot_coop(in, m0, state[0], c->cfg.pivot_sample, c->sample_buf, c->pivot_scratch, &piv[0], s,
+                                nullptr, pivot_rank()))
+             launch_pivot(in, m0, nullptr, state[0], c->cfg.pivot_sample, c->sample_buf, &piv[0], s, pivot_rank()));
     CompactArgs cp{};
     cp.shape = shape;
     cp.in = in;
@@ -1360,14 +1383,14 @@ struct Solve {
     uint64_t caps[LVL_MAX + 1];
     caps[0] = m0;
     caps[1] = leaf_top ? X.cap : m1;
-    for (uint64_t est = m1; !is_sparse(est); est /= 2) {
+    for (uint64_t est = m1; !is_sparse(est); est = light_est(est)) {
       if (K + 1 >= LVL_MAX) return MST_OK;  // deeper than a plan holds
       caps[K + 1] = light_cap(caps[K]);
       ++K;
     }
     if (leaf_top != (K == 1)) return MST_OK;  // the light count moved the deepest level: host-driven
     const uint64_t need = plan_round_edges(caps[K]);
-    if (need > X.cap) TRY(round_lists(c, need, X, Y));  // (not when leaf_top: X already holds list 1)
+    if (need > X.cap) TRY(round_lists(c, need, X, Y, s));  // (not when leaf_top: X already holds list 1)
     planned = true;
     CK(cudaMemsetAsync(&c->ds->jump_flag, 0, sizeof(uint32_t), s));
     uint32_t *A[2] = {act[0], act[1]};
@@ -1387,8 +1410,9 @@ struct Solve {
       const u64 *mk = &c->ds->count[CNT_LVL + k];
       PROF(MST_K_PIVOT, 16.0 * (double)c->cfg.pivot_sample, -1, 0.0, -1, 0.0,
            if (!launch_pivot_coop(E[k], caps[k], state[k], c->cfg.pivot_sample, c->sample_buf, c->pivot_scratch,
-                                  &piv[k], s, mk))
-               launch_pivot(E[k], caps[k], mk, state[k], c->cfg.pivot_sample, c->sample_buf, &piv[k], s));
+                                  &piv[k], s, mk, pivot_rank()))
+               launch_pivot(E[k], caps[k], mk, state[k], c->cfg.pivot_sample, c->sample_buf, &piv[k], s,
+                            pivot_rank()));
       CompactArgs pk{};
       pk.shape = shape;
       pk.in = E[k];
@@ -1545,6 +1569,7 @@ mst_status validate_cfg(const mst_config *cfg) {
   if (shape_index(cfg->block_threads, cfg->items_per_thread) < 0) return MST_ERR_INVALID_ARG;
   if (cfg->filter_plan < 0 || cfg->filter_plan > 1) return MST_ERR_INVALID_ARG;
   if (relabel_shape_index(cfg->relabel_block_threads, cfg->relabel_items_per_thread) < 0) return MST_ERR_INVALID_ARG;
+  if (!(cfg->pivot_quantile >= 1.0f / 64.0f && cfg->pivot_quantile <= 0.5f)) return MST_ERR_INVALID_ARG;
   return MST_OK;
 }
 
@@ -1777,9 +1802,9 @@ void mst_config_default(mst_config *cfg) {
   cfg->pivot_sample = 1u << 16;
   cfg->seed = 0x2302121990ULL;
   cfg->filter_min_edges = 1ULL << 20;
-  // measured on GB300 (the paper uses 4 on its cluster): RMAT n=2^24 m=2^28 takes 9.72 / 9.42 / 9.40 /
-  // 9.42 / 9.60 ms at 0.9 / 1.0 / 1.1 / 1.5 / 2.0.  1.25 sits between the average degrees 1 and 2 where
-  // halving lists land, so a pivot a little off the median does not change the number of levels.
+  // measured on GB300 (the paper uses 4 on its cluster): with median pivots RMAT n=2^24 m=2^28 took 9.72 /
+  // 9.42 / 9.40 / 9.42 / 9.60 ms at 0.9 / 1.0 / 1.1 / 1.5 / 2.0, and with the default 1/8-quantile pivots
+  // 5.26 / 5.28 / 5.27 ms at 0.75 / 1.25 / 2.5 (the lists 2^28 -> 2^25 -> 2^22 stop at the same level).
   cfg->filter_max_avg_degree = 1.25f;
   cfg->base_case = 1;
   cfg->graph_rounds = 1;
@@ -1795,6 +1820,10 @@ void mst_config_default(mst_config *cfg) {
   cfg->filter_plan = 1;
   cfg->relabel_block_threads = 0;     // 0 and 0: 128 x 4
   cfg->relabel_items_per_thread = 0;
+  // Alg. 2 splits at the sample median; on GB300 a split at the 1/8 quantile measured fastest (RMAT n=2^24
+  // m=2^28: 7.16 ms at 1/2, 5.54 at 1/4, 5.25 at 1/8, 5.35 at 1/16): light lists an eighth as long and two
+  // partition levels instead of five, for the same total of filtered heavy edges.
+  cfg->pivot_quantile = 0.125f;
 }
 
 const char *mst_status_string(mst_status s) {

@@ -64,7 +64,7 @@ class MstConfig(ctypes.Structure):
                 ("tile_filter", ctypes.c_int), ("spin_limit", ctypes.c_uint32),
                 ("block_threads", ctypes.c_uint32), ("items_per_thread", ctypes.c_uint32),
                 ("filter_plan", ctypes.c_int), ("relabel_block_threads", ctypes.c_uint32),
-                ("relabel_items_per_thread", ctypes.c_uint32)]
+                ("relabel_items_per_thread", ctypes.c_uint32), ("pivot_quantile", ctypes.c_float)]
 
 
 _P = ctypes.c_void_p

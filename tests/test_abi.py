@@ -33,6 +33,7 @@ def test_default_config(lib):
     assert cfg.filter_carry == 0
     assert cfg.spin_limit == 1 << 21 and cfg.block_threads == 0 and cfg.items_per_thread == 0
     assert cfg.filter_plan == 1 and cfg.relabel_block_threads == 0 and cfg.relabel_items_per_thread == 0
+    assert cfg.pivot_quantile == 0.125
 
 
 def test_bad_kernel_shapes_are_refused_without_device(lib):
@@ -51,6 +52,10 @@ def test_bad_kernel_shapes_are_refused_without_device(lib):
         lib.mst_config_default(ctypes.byref(cfg))
         cfg.filter_plan = flag
         assert lib.mst_create(ctypes.byref(h), ctypes.byref(cfg)) == 1, ("filter_plan", flag)
+    for q in (0.0, 1.0 / 128, 0.51, 1.0, float("nan")):  # the pivot quantile is limited to [1/64, 1/2]
+        lib.mst_config_default(ctypes.byref(cfg))
+        cfg.pivot_quantile = q
+        assert lib.mst_create(ctypes.byref(h), ctypes.byref(cfg)) == 1, ("pivot_quantile", q)
 
 
 def test_status_strings(lib):

@@ -717,6 +717,39 @@ def test_filter_plan_on_and_off_agree(dev, family):
             s.close()
 
 
+@pytest.mark.parametrize("family", ["rmat", "gnm", "rgg2", "rhg", "star"])
+def test_pivot_quantile_equals_kruskal(dev, family):
+    """Filter-Borůvka with the pivot at other ranks of its sample than the
+    median (a light share q of every list; Alg. 2 takes q = 1/2) gives the
+    oracle's forest at every q, on the planned and the host-driven recursion:
+    the split only steers the work.  The planned solves must hold their plan
+    (no fallback), which checks the light-list capacities planned from q."""
+    g = {
+        "rmat": lambda: W.rmat(17, 1 << 21, 101),
+        "gnm": lambda: W.gnm(1 << 15, 1 << 20, 102),
+        "rgg2": lambda: W.rgg(2, 1 << 16, 20.0, 103),
+        "rhg": lambda: W.rhg(1 << 16, 24.0, 104),
+        "star": lambda: W.Graph(300001, np.zeros(300000, dtype=np.uint32), np.arange(1, 300001, dtype=np.uint32),
+                                (np.arange(300000, dtype=np.uint32) % 97 + 1).astype(np.uint32)),
+    }[family]()
+    kid, ktot = oracle.kruskal(g.n, g.src, g.dst, g.w)
+    src, dst, w = to_dev(g.src, dev), to_dev(g.dst, dev), to_dev(g.w, dev)
+    for q in (1.0 / 64, 1.0 / 8, 0.25, 0.375, 0.5):
+        for plan in (1, 0):
+            s = Solver(0, variant="filter", filter_plan=plan, pivot_quantile=q, filter_min_edges=1 << 12,
+                       pivot_sample=4096)
+            try:
+                for rep in range(2):
+                    before = s.host_counters()
+                    ids, tot = s.solve(g.n, src, dst, w).to_host()
+                    assert np.array_equal(ids, kid) and tot == ktot, (q, plan, rep)
+                    d = {k: v - before[k] for k, v in s.host_counters().items()}
+                    if plan and d["planned"]:
+                        assert d["plan_fallbacks"] == 0, (q, d)
+            finally:
+                s.close()
+
+
 @pytest.mark.parametrize("family", ["rmat", "gnm", "star", "rgg2", "degenerate"])
 def test_min_edges_sort_on_and_off_agree(dev, family):
     """minEdges as segmented minima over the edge ends sorted by vertex gives the

@@ -255,3 +255,59 @@ def test_batched_forest_capacity_residues(dev):
                 assert np.array_equal(ids[moff[g]:moff[g + 1]], kid) and int(tot[g]) == ktot, (total_n, g)
     finally:
         s.close()
+
+
+def test_concurrent_handles_grow_their_buffers(dev):
+    """Three host threads, each with its own handle and stream, solve batches
+    that grow from call to call, so every call regrows the handle's round lists
+    and scan status words and captures new round graphs while the other
+    threads launch and capture theirs (the server's pattern).  Every forest
+    equals Kruskal's."""
+    import threading
+    sizes = [(1 << 10, 1 << 13), (1 << 12, 1 << 15), (1 << 14, 1 << 17), (1 << 15, 1 << 19), (1 << 16, 1 << 20)]
+    cases = []
+    for k, (n, m) in enumerate(sizes):
+        a, b = W.gnm(n, m, 300 + k), W.rmat(max(10, n.bit_length() - 1), m // 2, 400 + k)
+        cases.append((a, b, oracle.kruskal(a.n, a.src, a.dst, a.w), oracle.kruskal(b.n, b.src, b.dst, b.w)))
+    errors = []
+
+    # handles are made (and closed) while no other thread is at work: mst_create
+    # and mst_destroy wait for the device
+    solvers = [Solver(0, variant="filter" if t != 1 else "boruvka", filter_min_edges=1 << 12, pivot_sample=4096)
+               for t in range(3)]
+
+    def worker(t):
+        torch.cuda.set_device(dev)
+        stream = torch.cuda.Stream(device=dev)
+        s = solvers[t]
+        try:
+            for rep in range(2):
+                for a, b, ea, eb in cases:
+                    with torch.cuda.stream(stream):
+                        src = to_dev(np.concatenate([a.src, b.src]), dev)
+                        dst = to_dev(np.concatenate([a.dst, b.dst]), dev)
+                        w = to_dev(np.concatenate([a.w, b.w]), dev)
+                        ids, moff, tot = s.solve_batched(np.array([a.n, b.n], np.uint32),
+                                                         np.array([0, a.m, a.m + b.m], np.uint64), src, dst, w,
+                                                         stream=stream)
+                        ids = ids.cpu().numpy().view(np.uint32)
+                        moff = moff.cpu().numpy().astype(np.int64)
+                        tot = tot.cpu().numpy().view(np.uint64)
+                    for g, (kid, ktot) in enumerate((ea, eb)):
+                        got = np.sort(ids[moff[g]:moff[g + 1]])
+                        if not (np.array_equal(got, kid) and int(tot[g]) == ktot):
+                            errors.append((t, rep, g))
+        except Exception as e:  # reported below
+            errors.append((t, repr(e)))
+        stream.synchronize()
+
+    threads = [threading.Thread(target=worker, args=(t,)) for t in range(3)]
+    try:
+        for th in threads:
+            th.start()
+        for th in threads:
+            th.join()
+    finally:
+        for s in solvers:
+            s.close()
+    assert not errors, errors

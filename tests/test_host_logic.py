@@ -58,6 +58,27 @@ def test_autotune_tunes_the_kernel_shape_on_the_best_configuration():
     assert len(res) == 2 + 8
 
 
+def test_autotune_quantile_stage_only_for_the_filter_variant():
+    """Pivot quantiles are tried on top of the best configuration only when it
+    is Filter-Borůvka (the plain variant has no pivot), skipping the library's
+    default quantile, and a faster quantile is kept."""
+    from paper_2302_12199_gb300.autotune import QUANTILE_CANDIDATES
+    seen = []
+
+    def trial(cfg):
+        seen.append(dict(cfg))
+        t = {"boruvka": 3.0, "filter": 2.0}[cfg["variant"]]
+        return t - (0.5 if cfg.get("pivot_quantile") == 0.25 else 0.0)
+    best, res = autotune(trial, [dict(variant="boruvka"), dict(variant="filter")], reps=1, shapes=None)
+    assert best == dict(variant="filter", pivot_quantile=0.25)
+    tried = [c["pivot_quantile"] for c in seen if "pivot_quantile" in c]
+    assert set(tried) == {q["pivot_quantile"] for q in QUANTILE_CANDIDATES} - {0.125}
+    assert all(c["variant"] == "filter" for c in seen if "pivot_quantile" in c)
+    seen.clear()
+    best, _ = autotune(lambda cfg: seen.append(dict(cfg)) or 1.0, [dict(variant="boruvka")], reps=1, shapes=None)
+    assert best == dict(variant="boruvka") and not any("pivot_quantile" in c for c in seen)
+
+
 def test_autotune_relabel_shape_stage_runs_on_the_best_shape():
     """The relabel compaction's shapes are tried last, on top of the best
     configuration and kernel shape, skipping the default 128 x 4."""
