@@ -66,30 +66,37 @@ WORKLOADS = {
 # them.  A full-size launch's traffic is taken as that ratio times its
 # algorithmic bytes (at scale 24 the 64 MB label array shares the L2 with a
 # longer stream, so the true ratio there is somewhat higher).  The ratio holds
-# only for the kernel source it was measured on: when the source region below
-# hashes differently, traffic is reported as null until it is captured again.
+# only for the kernel source it was measured on and for the pivot quantile
+# that set the levels' mix: when the source regions below hash differently, or
+# the quantile differs, traffic is reported as null until it is captured again.
 TRAFFIC = {
     "class": "filter",
     "kernel": "stream_warp_kernel<CM_FILTER>",
-    "dram_per_algorithmic_byte": 1.213,
-    "measured_on": "RMAT n=2^22 m=2^26, all 5 filter launches of one timed solve",
-    "source_sha256": "f8f1a81aee38983b2a663489b50a7f9213ccbb17b7bb689de5e76a0d41b8ce4f",
+    "dram_per_algorithmic_byte": 1.350,
+    "measured_on": "RMAT n=2^22 m=2^26, both filter launches of one timed solve (pivot quantile 1/8)",
+    "pivot_quantile": 0.125,
+    "source_sha256": "2efc922258f9e2223a044ff731482f057f73679849283ac00079ada9e50f2af7",
 }
-TRAFFIC_SOURCE = ("paper_2302_12199_gb300/csrc/kernels.cu",
-                  "__device__ __forceinline__ uint32_t keep_flags",
-                  "// --------------------------------------------------------------- min edges")
+TRAFFIC_SOURCE = (
+    ("paper_2302_12199_gb300/csrc/kernels.cu", "__device__ __forceinline__ uint32_t keep_flags",
+     "// Writes the kept items of a tile"),
+    ("paper_2302_12199_gb300/csrc/kernels.cu", "// ------------------------------------------------- warp-streamed passes",
+     "// --------------------------------------------------------------- min edges"),
+)
 
 
 def traffic_source_digest():
     import hashlib
-    path, start, end = TRAFFIC_SOURCE
-    try:
-        with open(os.path.join(ROOT, path)) as f:
-            text = f.read()
-        i, j = text.index(start), text.index(end)
-    except (OSError, ValueError):
-        return None
-    return hashlib.sha256(text[i:j].encode()).hexdigest()
+    h = hashlib.sha256()
+    for path, start, end in TRAFFIC_SOURCE:
+        try:
+            with open(os.path.join(ROOT, path)) as f:
+                text = f.read()
+            i, j = text.index(start), text.index(end)
+        except (OSError, ValueError):
+            return None
+        h.update(text[i:j].encode())
+    return h.hexdigest()
 
 
 def reduce_scalar(x: float, op: str, dist, device) -> float:
@@ -522,6 +529,7 @@ def gpu_main(args, rank: int, world: int, local_rank: int):
     achieved_min = kmin / (kms / 1e3) / 1e9
     traffic = None
     if (dom == TRAFFIC["class"] and TRAFFIC["dram_per_algorithmic_byte"] and nl
+            and abs(float(solver.cfg.pivot_quantile) - TRAFFIC["pivot_quantile"]) < 1e-6
             and traffic_source_digest() == TRAFFIC["source_sha256"]):
         traffic = TRAFFIC["dram_per_algorithmic_byte"] * kbytes / nl
     roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",

@@ -773,7 +773,7 @@ __global__ void __launch_bounds__(B, Shape<B, I>::minb(Shape<B, I>::tma_regs)) c
 // fills and when the warp finishes.  No block-wide barrier is on the path: a
 // warp waiting on its gathers never holds up another.
 //
-// The filter's shape is measured on GB300 (RMAT n=2^24, m=2^28, filter class
+// The filter's shape is measured on GB300 (RMAT n=2^24, m=2^28, median pivots, filter class
 // per solve): 32 warps x 4 edges per lane, one stage: 2.49 ms; 16 warps x 8,
 // two blocks per SM: 2.49; 24 x 8, one stage: 2.58; 24 x 8, two stages: 4.39;
 // the block-synchronous compaction kernel: 4.02.  Shared memory is the lever:
@@ -792,7 +792,21 @@ struct WarpShape {
   };
   static constexpr size_t smem = sizeof(Stage) * S * W + sizeof(Out) * W;
 };
-using FilterWarp = WarpShape<32, 4, 1, 32, 1>;
+// Its staging buffer holds 64 survivors per warp: every flush claims output
+// slots with one atomic add on the list counter, and with 1/8-quantile pivots
+// (the top level filters 7/8 of the input) 32 per warp made those adds queue
+// (filter class 2.49 ms; 64: 2.37; 96: 2.39; 128: 2.42, less L1).
+using FilterWarp = WarpShape<32, 4, 1, 64, 1>;
+// The partition keeps the light share q of its list (1/8 by default), so it
+// streams with sparse survivors too.  Its survivors are denser than the
+// filter's, and every flush claims its output slots with an atomic add on the
+// one list counter, so the staging buffer is large: measured on GB300 (RMAT
+// n=2^24, m=2^28, partition class per solve) 24 warps x 8 edges per lane with
+// 32 / 64 / 128 / 192 / 256 staged survivors per warp: 2.23 / 0.89 / 0.79 /
+// 0.78 / 0.87 ms (256 leaves little L1); 32 x 4 with 64: 0.98, two stages:
+// 0.97; 16 x 8 with 256: 0.86; the block kernel (256 x 8, one TMA stage):
+// 1.04 (two stages, two blocks per SM: 1.35).
+using PartitionWarp = WarpShape<24, 8, 1, 128, 1>;
 
 // Item k of lane l in a warp tile sits at (k / 4) * 128 + 4 l + k % 4, so each
 // 16-byte shared-memory read of the warp covers 512 contiguous bytes.
@@ -860,7 +874,8 @@ __device__ __forceinline__ void warp_flush(const CompactArgs &a, const typename 
 
 template <int MODE, class WS>
 __global__ void __launch_bounds__(WS::threads, WS::minb) stream_warp_kernel(CompactArgs a) {
-  static_assert(MODE == CM_FILTER || MODE == CM_HEAVY, "the warp-streamed pass serves the filter modes");
+  static_assert(MODE == CM_FILTER || MODE == CM_HEAVY || MODE == CM_PARTITION,
+                "the warp-streamed pass serves the filter modes and the partition");
   constexpr int I = WS::items, S = WS::stages, O = WS::out, T = WS::tile;
   using Stage = typename WS::Stage;
   using Out = typename WS::Out;
@@ -886,6 +901,7 @@ __global__ void __launch_bounds__(WS::threads, WS::minb) stream_warp_kernel(Comp
   __syncwarp();
   const u64 pivot = compact_pivot(a, MODE);
   uint32_t fill = 0;  // staged survivors (the same in every lane)
+  uint32_t wmax = 0;  // largest weight this lane read (partition with a.max_w)
   bool abort = false;
   uint64_t it = 0;
   for (;; ++it) {
@@ -933,6 +949,10 @@ __global__ void __launch_bounds__(WS::threads, WS::minb) stream_warp_kernel(Comp
       }
     }
     const uint32_t keep = keep_flags<MODE>(a, valid, pivot, eu, ev, ew, ei);
+    if (MODE == CM_PARTITION && a.max_w) {
+#pragma unroll
+      for (int k = 0; k < I; ++k) wmax = max(wmax, (valid >> k & 1) ? ew[k] : 0u);
+    }
     // warp-wide exclusive prefix of the kept counts: survivor ranks 0..total-1
     const uint32_t c = (uint32_t)__popc(keep);
     uint32_t incl = c;
@@ -968,6 +988,11 @@ __global__ void __launch_bounds__(WS::threads, WS::minb) stream_warp_kernel(Comp
   }
   if (!abort) {
     if (fill) warp_flush<WS>(a, o, fill);
+    if (MODE == CM_PARTITION && a.max_w) {  // the input's largest weight (key layout), one atomic per warp
+#pragma unroll
+      for (int d = 16; d > 0; d >>= 1) wmax = max(wmax, __shfl_xor_sync(0xffffffffu, wmax, d));
+      if (lane == 0 && wmax > __ldca(a.max_w)) atomicMax(a.max_w, wmax);
+    }
     return;
   }
   // A bulk copy never completed: this warp's remaining tiles were not read.
@@ -2808,6 +2833,9 @@ static void launch_compact_mode(const CompactArgs &a, uint64_t max_count, cudaSt
   const bool aligned = aligned16(a.in.u) && aligned16(a.in.v) && aligned16(a.in.w) && (!a.in.id || aligned16(a.in.id));
   if constexpr (MODE == CM_FILTER || MODE == CM_HEAVY) {
     if (aligned && launch_warp_stream<MODE, FilterWarp>(a, max_count, s)) return;
+  }
+  if constexpr (MODE == CM_PARTITION) {  // the default tile shape: the warp-streamed pass
+    if (aligned && a.shape == 0 && launch_warp_stream<MODE, PartitionWarp>(a, max_count, s)) return;
   }
   if constexpr (MODE == CM_RELABEL || MODE == CM_PARTITION) {
     switch (a.shape) {  // the shapes of shape_index
