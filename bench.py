@@ -707,11 +707,16 @@ def measure_batched(args, rank: int, world: int, local_rank: int, dev, dist, com
         time.sleep(0.3)
     solver.profile(True, classes=[dom] if dom else [])
     lat = []
+    hc0 = solver.host_counters()
     nvtx_mark(torch, "push")
     for _ in range(args.steps):
         dt, res = timed_batch(solver)
         lat.append(dt)
     nvtx_mark(torch, "pop")
+    hc1 = solver.host_counters()
+    host = {"readbacks_per_step": (hc1["readbacks"] - hc0["readbacks"]) / args.steps,
+            "planned_steps": hc1["planned"] - hc0["planned"],
+            "plan_fallbacks": hc1["plan_fallbacks"] - hc0["plan_fallbacks"]}
     solver.profile(False)
     clocks = sampler.stop()
     stats = solver.profile_stats()

@@ -33,8 +33,14 @@ struct DevState {
   uint32_t giant_root;  // root of the largest sampled component (filter fast path)
   uint32_t max_w;       // largest input weight (key layout)
   uint32_t local_samples;  // sampled local edges (automatic tile contraction)
-  uint32_t pad;
+  uint32_t giant_count;    // of the GIANT_SAMPLES sampled edge ends, those in the giant component
 };
+// Edge ends the giant-component root is sampled from.  The filter tests the
+// giant-component bitmap first only when at least GIANT_MIN_COUNT of them lie
+// in that component: otherwise (a batch of many small graphs has no giant
+// component) nearly every heavy edge needs its labels anyway, and the bitmap
+// gathers only add a dependent round trip.
+constexpr uint32_t GIANT_SAMPLES = 1024, GIANT_MIN_COUNT = 512;
 // CNT_LVL + k: length of the light list of recursion level k (level 0: the
 // input); CNT_LVL + LVL_MAX + k: the filtered heavy edges of level k.
 enum { CNT_EDGES = 0, CNT_ACTIVE = 1, CNT_TMP = 2, CNT_AUX = 3, CNT_USER = 4, CNT_CUT = 5, CNT_LVL = 6 };
@@ -93,6 +99,7 @@ struct CompactArgs {
   EdgeOut out;
   const uint32_t *label;   // relabel / filter
   const uint32_t *giant_bits;  // filter: bitmap of the vertices in the largest component, or nullptr
+  const uint32_t *giant_count; // filter: if set, the bitmap is used only when *giant_count >= GIANT_MIN_COUNT
   u64 pivot;               // partition / filter (used when pivot_dev == nullptr)
   const u64 *pivot_dev;
   u64 *best;               // if set: relax best[] of both ends with each survivor's key
@@ -106,6 +113,8 @@ struct CompactArgs {
   uint32_t *cur_u, *cur_v; // if set: cur_u[id], cur_v[id] = the survivor's written ends
   ScanState st;
   int shape;               // tile shape of the relabel / partition compaction (see shape_index)
+  int warp_partition;      // partition in the default shape: 1 runs the warp-streamed pass (for light
+                           //   shares up to 1/8, where its per-warp output claims stay few), 0 the block kernel
   uint64_t out_cap;        // if nonzero: output capacity; a tile that would write past it writes
                            //   nothing and sets ERR_OVERFLOW (with m_dev, m bounds the input count)
 };
@@ -190,7 +199,7 @@ void launch_wsum_total(const u64 *wsum, u64 *total, cudaStream_t s);
 // sampled edge ends (P is walked to the roots); launch_giant_bits also marks
 // its vertices (bit v set iff P[v] is that root; P fully contracted).
 void launch_giant_root(EdgeList in, uint64_t m, u64 state, const uint32_t *P, uint32_t n, uint32_t *root_tmp,
-                       cudaStream_t s, const u64 *m_dev = nullptr);
+                       cudaStream_t s, const u64 *m_dev = nullptr, uint32_t *count_out = nullptr);
 void launch_giant_bits(EdgeList in, uint64_t m, u64 state, const uint32_t *P, uint32_t n, uint32_t *root_tmp,
                        uint32_t *bits, int sms, cudaStream_t s);
 // tile-local contraction (Section 4.1)

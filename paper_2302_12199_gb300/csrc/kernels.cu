@@ -333,7 +333,8 @@ __device__ __forceinline__ u64 hash_lookup(const HashSlot *t, uint64_t mask, u64
 // item k; only items whose bit is set in `valid` can be kept.
 template <int MODE, int N>
 __device__ __forceinline__ uint32_t keep_flags(const CompactArgs &a, uint32_t valid, u64 pivot, uint32_t (&eu)[N],
-                                               uint32_t (&ev)[N], const uint32_t (&ew)[N], const uint32_t (&ei)[N]) {
+                                               uint32_t (&ev)[N], const uint32_t (&ew)[N], const uint32_t (&ei)[N],
+                                               const uint32_t *gbits) {
   uint32_t keep = 0;
 #pragma unroll
   for (int k = 0; k < N; ++k) {
@@ -357,13 +358,13 @@ __device__ __forceinline__ uint32_t keep_flags(const CompactArgs &a, uint32_t va
     }
     keep |= (ok ? 1u : 0u) << k;
   }
-  if (MODE == CM_HEAVY && a.giant_bits) {  // drop heavy edges inside the giant component; keep the ends
+  if (MODE == CM_HEAVY && gbits) {  // drop heavy edges inside the giant component; keep the ends
     uint32_t bu[N], bv[N];
 #pragma unroll
     for (int k = 0; k < N; ++k) {
       const bool h = keep >> k & 1;
-      bu[k] = h ? __ldg(a.giant_bits + (eu[k] >> 5)) : 0u;
-      bv[k] = h ? __ldg(a.giant_bits + (ev[k] >> 5)) : 0u;
+      bu[k] = h ? __ldg(gbits + (eu[k] >> 5)) : 0u;
+      bv[k] = h ? __ldg(gbits + (ev[k] >> 5)) : 0u;
     }
 #pragma unroll
     for (int k = 0; k < N; ++k)
@@ -374,13 +375,13 @@ __device__ __forceinline__ uint32_t keep_flags(const CompactArgs &a, uint32_t va
     // one component.  The bitmap words of all items are loaded together, then
     // the labels of the remaining items, so that each thread has one round of
     // independent loads in flight per step.
-    if (a.giant_bits) {
+    if (gbits) {
       uint32_t bu[N], bv[N];
 #pragma unroll
       for (int k = 0; k < N; ++k) {
         const bool h = keep >> k & 1;
-        bu[k] = h ? __ldg(a.giant_bits + (eu[k] >> 5)) : 0u;
-        bv[k] = h ? __ldg(a.giant_bits + (ev[k] >> 5)) : 0u;
+        bu[k] = h ? __ldg(gbits + (eu[k] >> 5)) : 0u;
+        bv[k] = h ? __ldg(gbits + (ev[k] >> 5)) : 0u;
       }
 #pragma unroll
       for (int k = 0; k < N; ++k)
@@ -554,7 +555,7 @@ __global__ void __launch_bounds__(B, Shape<B, I>::minb(Shape<B, I>::compact_regs
     }
   }
   const uint32_t valid = valid_items_s<B, I>(tb, m);
-  const uint32_t keep = keep_flags<MODE>(a, valid, compact_pivot(a, MODE), eu, ev, ew, ei);
+  const uint32_t keep = keep_flags<MODE>(a, valid, compact_pivot(a, MODE), eu, ev, ew, ei, a.giant_bits);
   if (a.max_w) {  // largest weight of the input, folded into this pass
     uint32_t mx = 0;
 #pragma unroll
@@ -726,7 +727,7 @@ __global__ void __launch_bounds__(B, Shape<B, I>::minb(Shape<B, I>::tma_regs)) c
       }
     }
     const uint32_t valid = valid_items_s<B, I>(tb, m);
-    const uint32_t keep = keep_flags<MODE>(a, valid, pivot, eu, ev, ew, ei);
+    const uint32_t keep = keep_flags<MODE>(a, valid, pivot, eu, ev, ew, ei, a.giant_bits);
     if (a.max_w) {
       uint32_t mx = 0;
 #pragma unroll
@@ -798,7 +799,9 @@ struct WarpShape {
 // (filter class 2.49 ms; 64: 2.37; 96: 2.39; 128: 2.42, less L1).
 using FilterWarp = WarpShape<32, 4, 1, 64, 1>;
 // The partition keeps the light share q of its list (1/8 by default), so it
-// streams with sparse survivors too.  Its survivors are denser than the
+// streams with sparse survivors too (for q up to 1/8; at larger shares the
+// flushes' claims on the one list counter made it slower than the block
+// kernel: batched mix, q = 1/4: 2.69 ms, q = 1/2: 6.24 ms).  Its survivors are denser than the
 // filter's, and every flush claims its output slots with an atomic add on the
 // one list counter, so the staging buffer is large: measured on GB300 (RMAT
 // n=2^24, m=2^28, partition class per solve) 24 warps x 8 edges per lane with
@@ -900,6 +903,9 @@ __global__ void __launch_bounds__(WS::threads, WS::minb) stream_warp_kernel(Comp
   }
   __syncwarp();
   const u64 pivot = compact_pivot(a, MODE);
+  // the giant-component bitmap, unless too few sampled edge ends lie in that
+  // component for its test to spare label gathers
+  const uint32_t *gbits = (a.giant_count && __ldg(a.giant_count) < GIANT_MIN_COUNT) ? nullptr : a.giant_bits;
   uint32_t fill = 0;  // staged survivors (the same in every lane)
   uint32_t wmax = 0;  // largest weight this lane read (partition with a.max_w)
   bool abort = false;
@@ -948,7 +954,7 @@ __global__ void __launch_bounds__(WS::threads, WS::minb) stream_warp_kernel(Comp
         }
       }
     }
-    const uint32_t keep = keep_flags<MODE>(a, valid, pivot, eu, ev, ew, ei);
+    const uint32_t keep = keep_flags<MODE>(a, valid, pivot, eu, ev, ew, ei, gbits);
     if (MODE == CM_PARTITION && a.max_w) {
 #pragma unroll
       for (int k = 0; k < I; ++k) wmax = max(wmax, (valid >> k & 1) ? ew[k] : 0u);
@@ -2578,10 +2584,10 @@ __global__ void tile_sample_kernel(EdgeList in, uint64_t m, uint32_t n, uint32_t
 // 1024 edges of the list are drawn with splitmix64, the root P[u] of each
 // sample's first endpoint is taken (P fully contracted), and the most frequent
 // root is written to *out (a sort in shared memory, then the longest run).
-constexpr int MODE_SAMPLES = 1024;
+constexpr int MODE_SAMPLES = (int)GIANT_SAMPLES;
 __global__ void __launch_bounds__(MODE_SAMPLES) giant_root_kernel(EdgeList in, uint64_t m_bound, const u64 *m_dev,
                                                                   u64 state, const uint32_t *P, uint32_t n,
-                                                                  uint32_t *out) {
+                                                                  uint32_t *out, uint32_t *count_out) {
   const uint64_t m = m_dev ? min((uint64_t)*m_dev, m_bound) : m_bound;
   __shared__ uint32_t s_r[MODE_SAMPLES];
   __shared__ uint32_t s_best[MODE_SAMPLES / 32], s_bestv[MODE_SAMPLES / 32];
@@ -2651,6 +2657,7 @@ __global__ void __launch_bounds__(MODE_SAMPLES) giant_root_kernel(EdgeList in, u
         r = s_bestv[i];
       }
     *out = r;
+    if (count_out) *count_out = r < n ? l : 0u;  // sampled ends in that component
   }
 }
 
@@ -2834,8 +2841,9 @@ static void launch_compact_mode(const CompactArgs &a, uint64_t max_count, cudaSt
   if constexpr (MODE == CM_FILTER || MODE == CM_HEAVY) {
     if (aligned && launch_warp_stream<MODE, FilterWarp>(a, max_count, s)) return;
   }
-  if constexpr (MODE == CM_PARTITION) {  // the default tile shape: the warp-streamed pass
-    if (aligned && a.shape == 0 && launch_warp_stream<MODE, PartitionWarp>(a, max_count, s)) return;
+  if constexpr (MODE == CM_PARTITION) {  // small light shares in the default tile shape: the warp-streamed pass
+    if (aligned && a.shape == 0 && a.warp_partition && launch_warp_stream<MODE, PartitionWarp>(a, max_count, s))
+      return;
   }
   if constexpr (MODE == CM_RELABEL || MODE == CM_PARTITION) {
     switch (a.shape) {  // the shapes of shape_index
@@ -2971,13 +2979,13 @@ void launch_finalize(const uint32_t *bits, uint64_t m, const uint32_t *w, uint32
 }
 
 void launch_giant_root(EdgeList in, uint64_t m, u64 state, const uint32_t *P, uint32_t n, uint32_t *root_tmp,
-                       cudaStream_t s, const u64 *m_dev) {
-  giant_root_kernel<<<1, MODE_SAMPLES, 0, s>>>(in, m, m_dev, state, P, n, root_tmp);
+                       cudaStream_t s, const u64 *m_dev, uint32_t *count_out) {
+  giant_root_kernel<<<1, MODE_SAMPLES, 0, s>>>(in, m, m_dev, state, P, n, root_tmp, count_out);
 }
 
 void launch_giant_bits(EdgeList in, uint64_t m, u64 state, const uint32_t *P, uint32_t n, uint32_t *root_tmp,
                        uint32_t *bits, int sms, cudaStream_t s) {
-  giant_root_kernel<<<1, MODE_SAMPLES, 0, s>>>(in, m, nullptr, state, P, n, root_tmp);
+  giant_root_kernel<<<1, MODE_SAMPLES, 0, s>>>(in, m, nullptr, state, P, n, root_tmp, nullptr);
   const uint64_t threads = ((uint64_t)n + 31) / 32 * 32;
   giant_bits_kernel<<<grid_for((threads + BLOCK - 1) / BLOCK, sms, 8), BLOCK, 0, s>>>(P, n, root_tmp, bits);
 }

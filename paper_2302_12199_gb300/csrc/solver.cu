@@ -1071,6 +1071,8 @@ struct Solve {
     return r < smp ? r : smp - 1;
   }
   uint64_t light_est(uint64_t mE) const { return (uint64_t)((double)c->cfg.pivot_quantile * (double)mE); }
+  // the warp-streamed partition pays off while the light share is small
+  int warp_partition() const { return c->cfg.pivot_quantile <= 0.125f ? 1 : 0; }
 
   bool is_sparse(uint64_t mE) const {
     return mE < c->cfg.filter_min_edges || 2.0 * (double)mE <= (double)c->cfg.filter_max_avg_degree * (double)n;
@@ -1093,7 +1095,7 @@ struct Solve {
   // count, and contract_finish completes the rare contraction that needs more.
   mst_status contract_and_mark_start(EdgeList E, uint64_t mE, u64 state, Buf &bits_b) {
     TRY(bits_b.alloc(c, ((size_t)n + 31) / 32 * 4, s));
-    launch_giant_root(E, mE, state, parent, n, &c->ds->giant_root, s);
+    launch_giant_root(E, mE, state, parent, n, &c->ds->giant_root, s, nullptr, &c->ds->giant_count);
     return jump_launch(nullptr, nullptr, n, n, 0, &c->ds->giant_root, bits_b.as<uint32_t>());
   }
   mst_status contract_and_mark_finish(Buf &bits_b) {
@@ -1126,6 +1128,7 @@ struct Solve {
     TRY(L.alloc(c, mE, s));
     CompactArgs cp{};
     cp.shape = shape;
+    cp.warp_partition = warp_partition();
     cp.in = E;
     cp.m = mE;
     cp.out = L.out;
@@ -1174,6 +1177,7 @@ struct Solve {
     cf.out = H.out;
     cf.label = parent;
     cf.giant_bits = giant_b.as<uint32_t>();
+    cf.giant_count = &c->ds->giant_count;
     cf.pivot = pivot;
     cf.n = n;
     cf.best = best;  // the survivors are expected to be sparse (Theorem 1)
@@ -1354,6 +1358,7 @@ struct Solve {
              launch_pivot(in, m0, nullptr, state[0], c->cfg.pivot_sample, c->sample_buf, &piv[0], s, pivot_rank()));
     CompactArgs cp{};
     cp.shape = shape;
+    cp.warp_partition = warp_partition();
     cp.in = in;
     cp.m = m0;
     cp.out = leaf_top ? X.out : L1.out;
@@ -1415,6 +1420,7 @@ struct Solve {
                             pivot_rank()));
       CompactArgs pk{};
       pk.shape = shape;
+      pk.warp_partition = warp_partition();
       pk.in = E[k];
       pk.m = caps[k];
       pk.m_dev = mk;
@@ -1437,7 +1443,8 @@ struct Solve {
     for (int k = K - 1; k >= 0; --k) {
       if (k + 1 >= 2 && k + 1 < K) Lb[k + 1].mem.release();  // list k+1 is not read again
       const u64 *mk = k == 0 ? nullptr : &c->ds->count[CNT_LVL + k];
-      launch_giant_root(E[k], caps[k], host_mix64(state[k]), parent, n, &c->ds->giant_root, s, mk);
+      launch_giant_root(E[k], caps[k], host_mix64(state[k]), parent, n, &c->ds->giant_root, s, mk,
+                        &c->ds->giant_count);
       PROF(MST_K_JUMP, 8.125 * (double)n, -1, 0.0, -1, 0.0,
            launch_jump(nullptr, nullptr, n, n, parent, best, 0, &c->ds->jump_flag, c->sms, s, 4096,
                        &c->ds->giant_root, gbits));
@@ -1450,6 +1457,7 @@ struct Solve {
       cf.out_cap = X.cap;
       cf.label = parent;
       cf.giant_bits = gbits;
+      cf.giant_count = &c->ds->giant_count;
       cf.pivot_dev = &piv[k];
       cf.n = n;
       cf.best = best;  // the survivors are expected to be sparse (Theorem 1)
@@ -2249,6 +2257,7 @@ static mst_status step_compact(mst_handle h, CompactMode mode, uint32_t n, uint6
   CompactArgs a{};
   a.shape = mode == CM_RELABEL ? relabel_shape_index(h->cfg.relabel_block_threads, h->cfg.relabel_items_per_thread)
                                : shape_index(h->cfg.block_threads, h->cfg.items_per_thread);
+  a.warp_partition = h->cfg.pivot_quantile <= 0.125f ? 1 : 0;  // the solves' choice for this configuration
   a.in = E;
   a.m = m;
   a.out = EdgeOut{d_ou, d_ov, d_ow, d_oid};

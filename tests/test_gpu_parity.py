@@ -357,6 +357,25 @@ def test_step_partition_and_filter(step_solver, dev):
     assert np.array_equal(host(Pd), S.roots(P))
 
 
+@pytest.mark.parametrize("q", [0.125, 0.5])
+def test_step_partition_warp_and_block_kernels(dev, q):
+    """The light part of a long list (3,000,017 edges: many tiles and a ragged
+    tail) at a pivot from a low and from the middle quantile of the sample,
+    through the warp-streamed pass (configurations with light shares up to
+    1/8) and the block kernel (larger shares), each against the step oracle:
+    the same records, and the same count."""
+    g = W.rmat(18, 3_000_017, 39)
+    ids = np.arange(g.m, dtype=np.uint32)
+    s = Solver(0, pivot_quantile=q)
+    try:
+        keys = np.sort((g.w.astype(np.uint64) << np.uint64(32)) | ids.astype(np.uint64))
+        pv = int(keys[int(q * (g.m - 1))])  # a pivot with about q of the list light
+        out = s.partition(*list_on_dev(dev, g.src, g.dst, g.w, ids), pivot=pv)
+        assert_same_list(out, S.partition_light(g.src, g.dst, g.w, ids, pv))
+    finally:
+        s.close()
+
+
 def light_fixed_point(n, src, dst, w, ids, pv):
     """P after Borůvka rounds on the light part (the state a filter step sees)."""
     P = np.arange(n, dtype=np.uint32)
