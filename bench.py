@@ -72,10 +72,10 @@ WORKLOADS = {
 TRAFFIC = {
     "class": "filter",
     "kernel": "stream_warp_kernel<CM_FILTER>",
-    "dram_per_algorithmic_byte": 1.350,
+    "dram_per_algorithmic_byte": 1.352,
     "measured_on": "RMAT n=2^22 m=2^26, both filter launches of one timed solve (pivot quantile 1/8)",
     "pivot_quantile": 0.125,
-    "source_sha256": "2efc922258f9e2223a044ff731482f057f73679849283ac00079ada9e50f2af7",
+    "source_sha256": "0b1e5497d08940e211b11f6cd66da2deb6af464638aae41aa6b7b9c2255e0ae5",
 }
 TRAFFIC_SOURCE = (
     ("paper_2302_12199_gb300/csrc/kernels.cu", "__device__ __forceinline__ uint32_t keep_flags",
