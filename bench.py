@@ -75,7 +75,7 @@ TRAFFIC = {
     "dram_per_algorithmic_byte": 1.352,
     "measured_on": "RMAT n=2^22 m=2^26, both filter launches of one timed solve (pivot quantile 1/8)",
     "pivot_quantile": 0.125,
-    "source_sha256": "0b1e5497d08940e211b11f6cd66da2deb6af464638aae41aa6b7b9c2255e0ae5",
+    "source_sha256": "a90ad8de4d5004aeb0ae6e62c8b2c6004d9762fb0085350b95469a5fbad917b5",
 }
 TRAFFIC_SOURCE = (
     ("paper_2302_12199_gb300/csrc/kernels.cu", "__device__ __forceinline__ uint32_t keep_flags",

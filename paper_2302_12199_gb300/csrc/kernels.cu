@@ -650,24 +650,19 @@ __device__ __forceinline__ void read_striped_smem(const uint32_t *p, uint32_t (&
   }
 }
 
-// S input stages plus one output stage of T items.
-template <int B, int I, int S = TMA_STAGES>
-constexpr size_t tma_smem_bytes() { return sizeof(EdgeStage<B * I>) * (S + 1); }
-
-// Input stages of the persistent compaction per mode: the partition has no
-// gathers, so it keeps PARTITION_STAGES tiles per block in flight.
-constexpr int PARTITION_STAGES = 1;
-template <int MODE>
-__host__ __device__ constexpr int tma_stages() { return MODE == CM_PARTITION ? PARTITION_STAGES : TMA_STAGES; }
+// Input stages plus one output stage of T items.  (Two input stages for the
+// partition, at two blocks per SM, measured slower on GB300: 1.35 against
+// 1.04 ms per C3 solve.)
+template <int B, int I>
+constexpr size_t tma_smem_bytes() { return sizeof(EdgeStage<B * I>) * (TMA_STAGES + 1); }
 
 template <int MODE, int B, int I>
 __global__ void __launch_bounds__(B, Shape<B, I>::minb(Shape<B, I>::tma_regs)) compact_tma_kernel(CompactArgs a) {
   constexpr int T = Shape<B, I>::T;
-  constexpr int NS = tma_stages<MODE>();  // input stages
   extern __shared__ __align__(128) unsigned char smem_dyn[];
-  EdgeStage<T> *stage = reinterpret_cast<EdgeStage<T> *>(smem_dyn);  // NS input stages + 1 output stage
-  EdgeStage<T> *out = stage + NS;
-  __shared__ __align__(8) u64 mbar[NS];
+  EdgeStage<T> *stage = reinterpret_cast<EdgeStage<T> *>(smem_dyn);  // TMA_STAGES input stages + 1 output stage
+  EdgeStage<T> *out = stage + TMA_STAGES;
+  __shared__ __align__(8) u64 mbar[TMA_STAGES];
   __shared__ uint32_t s_warp[B / 32 + 1];
   __shared__ uint32_t s_base[1];
   __shared__ uint32_t s_abort;
@@ -676,10 +671,10 @@ __global__ void __launch_bounds__(B, Shape<B, I>::minb(Shape<B, I>::tma_regs)) c
   const uint64_t ntiles = (m + T - 1) / T, nfull = m / T;
   const uint64_t G = gridDim.x;
   if (threadIdx.x == 0) {
-    for (int s = 0; s < NS; ++s) mbar_init(&mbar[s], 1);
+    for (int s = 0; s < TMA_STAGES; ++s) mbar_init(&mbar[s], 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     s_abort = 0;
-    for (int s = 0; s < NS; ++s) {
+    for (int s = 0; s < TMA_STAGES; ++s) {
       const uint64_t tile = blockIdx.x + (uint64_t)s * G;
       if (tile < nfull) issue_tile<T>(a, tile, &stage[s], &mbar[s]);
     }
@@ -690,12 +685,12 @@ __global__ void __launch_bounds__(B, Shape<B, I>::minb(Shape<B, I>::tma_regs)) c
   for (;; ++it) {
     const uint64_t tile = blockIdx.x + it * G;
     if (tile >= ntiles) break;
-    const int si = (int)(it % NS);
+    const int si = (int)(it % TMA_STAGES);
     EdgeStage<T> *st = &stage[si];
     const uint64_t tb = tile * T;
     uint32_t eu[I], ev[I], ew[I], ei[I];
     if (tile < nfull) {
-      if (!mbar_wait_bounded(&mbar[si], (uint32_t)((it / NS) & 1))) atomicOr(&s_abort, 1u);
+      if (!mbar_wait_bounded(&mbar[si], (uint32_t)((it / TMA_STAGES) & 1))) atomicOr(&s_abort, 1u);
       __syncthreads();
       if (s_abort) break;
       read_striped_smem<B, I>(st->u, eu);
@@ -707,9 +702,9 @@ __global__ void __launch_bounds__(B, Shape<B, I>::minb(Shape<B, I>::tma_regs)) c
 #pragma unroll
         for (int k = 0; k < I; ++k) ei[k] = (uint32_t)(tb + item_off<B>(k));
       }
-      __syncthreads();  // the stage is consumed: refill it with the tile NS ahead
+      __syncthreads();  // the stage is consumed: refill it with the tile TMA_STAGES ahead
       if (threadIdx.x == 0) {
-        const uint64_t next = tile + (uint64_t)NS * G;
+        const uint64_t next = tile + (uint64_t)TMA_STAGES * G;
         if (next < nfull) issue_tile<T>(a, next, st, &mbar[si]);
       }
     } else {  // the partial last tile: plain loads
@@ -750,9 +745,9 @@ __global__ void __launch_bounds__(B, Shape<B, I>::minb(Shape<B, I>::tma_regs)) c
   __syncthreads();
   if (s_abort && threadIdx.x == 0) {
     atomicOr(a.st.err, ERR_TMA);
-    for (uint64_t k = it; k < it + NS; ++k) {
+    for (uint64_t k = it; k < it + TMA_STAGES; ++k) {
       const uint64_t tile = blockIdx.x + k * G;
-      if (tile < nfull) mbar_wait_bounded(&mbar[k % NS], (uint32_t)((k / NS) & 1));
+      if (tile < nfull) mbar_wait_bounded(&mbar[k % TMA_STAGES], (uint32_t)((k / TMA_STAGES) & 1));
     }
   }
 }
@@ -799,16 +794,15 @@ struct WarpShape {
 // (filter class 2.49 ms; 64: 2.37; 96: 2.39; 128: 2.42, less L1).
 using FilterWarp = WarpShape<32, 4, 1, 64, 1>;
 // The partition keeps the light share q of its list (1/8 by default), so it
-// streams with sparse survivors too (for q up to 1/8; at larger shares the
-// flushes' claims on the one list counter made it slower than the block
-// kernel: batched mix, q = 1/4: 2.69 ms, q = 1/2: 6.24 ms).  Its survivors are denser than the
-// filter's, and every flush claims its output slots with an atomic add on the
-// one list counter, so the staging buffer is large: measured on GB300 (RMAT
-// n=2^24, m=2^28, partition class per solve) 24 warps x 8 edges per lane with
+// streams with sparse survivors too.  Its survivors are denser than the
+// filter's, and every flush claims its output slots with one atomic add on the
+// list counter, so its staging buffer is large.  Measured on GB300 (RMAT
+// n=2^24, m=2^28, partition class per solve): 24 warps x 8 edges per lane with
 // 32 / 64 / 128 / 192 / 256 staged survivors per warp: 2.23 / 0.89 / 0.79 /
 // 0.78 / 0.87 ms (256 leaves little L1); 32 x 4 with 64: 0.98, two stages:
-// 0.97; 16 x 8 with 256: 0.86; the block kernel (256 x 8, one TMA stage):
-// 1.04 (two stages, two blocks per SM: 1.35).
+// 0.97; 16 x 8 with 256: 0.86; the block kernel (256 x 8): 1.04.  At larger
+// light shares the claims pile up (batched mix: 2.69 ms at q = 1/4, 6.24 ms at
+// q = 1/2), so the solver uses this pass only for q up to 1/8.
 using PartitionWarp = WarpShape<24, 8, 1, 128, 1>;
 
 // Item k of lane l in a warp tile sits at (k / 4) * 128 + 4 l + k % 4, so each
@@ -2765,8 +2759,7 @@ template <int MODE, int B, int I>
 static void launch_compact_shaped(const CompactArgs &a, uint64_t max_count, bool aligned, cudaStream_t s) {
   constexpr int T = B * I;
   constexpr size_t stage_bytes = 16 * (size_t)T;  // compact_kernel's staging buffer
-  constexpr int NS = tma_stages<MODE>();
-  constexpr bool tma_fits = tma_smem_bytes<B, I, NS>() <= 200 * 1024;
+  constexpr bool tma_fits = tma_smem_bytes<B, I>() <= 200 * 1024;
   static int attrs = 0, tma_blocks = 0;
   if (!attrs) {  // prefer shared memory over L1; allow the staging buffer; size the persistent grid
     cudaFuncSetAttribute(compact_kernel<MODE, true, B, I>, cudaFuncAttributePreferredSharedMemoryCarveout,
@@ -2775,12 +2768,12 @@ static void launch_compact_shaped(const CompactArgs &a, uint64_t max_count, bool
                          (int)stage_bytes);
     if constexpr (tma_fits) {
       cudaFuncSetAttribute(compact_tma_kernel<MODE, B, I>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)tma_smem_bytes<B, I, NS>());
+                           (int)tma_smem_bytes<B, I>());
       int dev = 0, sms = 0, per_sm = 0;
       cudaGetDevice(&dev);
       cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
       cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, compact_tma_kernel<MODE, B, I>, B,
-                                                    tma_smem_bytes<B, I, NS>());
+                                                    tma_smem_bytes<B, I>());
       tma_blocks = sms * per_sm;
     }
     cudaGetLastError();
@@ -2789,8 +2782,8 @@ static void launch_compact_shaped(const CompactArgs &a, uint64_t max_count, bool
   const uint64_t tiles = (max_count + T - 1) / T;
   if (tiles == 0) return;
   if constexpr (tma_fits) {
-    if (aligned && tma_blocks > 0 && tiles >= (uint64_t)tma_blocks * NS) {
-      compact_tma_kernel<MODE, B, I><<<(unsigned)tma_blocks, B, tma_smem_bytes<B, I, NS>(), s>>>(a);
+    if (aligned && tma_blocks > 0 && tiles >= (uint64_t)tma_blocks * TMA_STAGES) {
+      compact_tma_kernel<MODE, B, I><<<(unsigned)tma_blocks, B, tma_smem_bytes<B, I>(), s>>>(a);
       return;
     }
   }
