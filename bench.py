@@ -512,13 +512,15 @@ def gpu_main(args, rank: int, world: int, local_rank: int):
     # (b) the steps as one mst_solve_host_many call: each step's inputs are
     # still copied from pinned host memory and its forest read back, but the
     # copy of step k+1 runs while step k is solved
-    # Three such calls, the median reported: the host link is shared with the
-    # machine's other GPUs and their jobs, and a run's rate moves with it, so
-    # the link alone is timed right before and right after as well.
+    # Five such calls, the median reported: the host link and the host itself
+    # are shared with the machine's other GPUs and their jobs, and single steps
+    # of a call have been seen to stall for tens of milliseconds (the GPU idle
+    # between two launches of a solve), so the link alone is timed right before
+    # and right after as well.
     solver.solve_host_many_ptr([step_spec] * 2)
     link_before = link_gbps(torch, dev, pin)
     runs = []
-    for _ in range(3):
+    for _ in range(5):
         if dist:
             dist.barrier()
         torch.cuda.synchronize(dev)
