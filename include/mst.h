@@ -129,8 +129,10 @@ typedef struct {
                                   median, q = 0.5).  1/64 <= q <= 1/2.  A smaller q writes shorter light lists
                                   and needs fewer recursion levels, while the filter meets more heavy edges
                                   (over all levels about the same number); every q computes the same forest.
-                                  Default 0.125, measured on GB300: RMAT n=2^24 m=2^28 takes 7.16 / 5.54 /
-                                  5.25 / 5.35 ms at q = 1/2, 1/4, 1/8, 1/16 (flat from 3/32 to 5/32) */
+                                  Default 0.125, measured on GB300: RMAT n=2^24 m=2^28 took 7.16 / 5.54 /
+                                  5.25 / 5.35 ms at q = 1/2, 1/4, 1/8, 1/16 (flat from 3/32 to 5/32; all
+                                  with the block-kernel partition, which runs for q > 1/8), 4.90 ms at 1/8
+                                  with the warp-streamed partition */
 } mst_config;
 
 /* Fills *cfg with the defaults (Borůvka variant, automatic dedupe, pivot sample
