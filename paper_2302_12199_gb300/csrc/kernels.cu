@@ -2760,12 +2760,15 @@ static void launch_compact_shaped(const CompactArgs &a, uint64_t max_count, bool
   constexpr int T = B * I;
   constexpr size_t stage_bytes = 16 * (size_t)T;  // compact_kernel's staging buffer
   constexpr bool tma_fits = tma_smem_bytes<B, I>() <= 200 * 1024;
-  static int attrs = 0, tma_blocks = 0;
-  if (!attrs) {  // prefer shared memory over L1; allow the staging buffer; size the persistent grid
+  // Set once per process (a function-local static is initialised exactly once,
+  // even when several host threads launch at the same time): prefer shared
+  // memory over L1, allow the staging buffer, size the persistent grid.
+  static const int tma_blocks = []() -> int {
     cudaFuncSetAttribute(compact_kernel<MODE, true, B, I>, cudaFuncAttributePreferredSharedMemoryCarveout,
                          cudaSharedmemCarveoutMaxShared);
     cudaFuncSetAttribute(compact_kernel<MODE, true, B, I>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)stage_bytes);
+    int blocks = 0;
     if constexpr (tma_fits) {
       cudaFuncSetAttribute(compact_tma_kernel<MODE, B, I>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)tma_smem_bytes<B, I>());
@@ -2774,11 +2777,11 @@ static void launch_compact_shaped(const CompactArgs &a, uint64_t max_count, bool
       cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
       cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, compact_tma_kernel<MODE, B, I>, B,
                                                     tma_smem_bytes<B, I>());
-      tma_blocks = sms * per_sm;
+      blocks = sms * per_sm;
     }
     cudaGetLastError();
-    attrs = 1;
-  }
+    return blocks;
+  }();
   const uint64_t tiles = (max_count + T - 1) / T;
   if (tiles == 0) return;
   if constexpr (tma_fits) {
@@ -2790,13 +2793,13 @@ static void launch_compact_shaped(const CompactArgs &a, uint64_t max_count, bool
   if (aligned) {
     compact_kernel<MODE, true, B, I><<<(unsigned)tiles, B, stage_bytes, s>>>(a);
   } else {  // unaligned lists: scalar loads in the default shape
-    static int attrs_u = 0;
-    if (!attrs_u) {
+    static const bool carveout_set = [] {  // once per process, as above
       cudaFuncSetAttribute(compact_kernel<MODE, false, BLOCK, ITEMS>, cudaFuncAttributePreferredSharedMemoryCarveout,
                            cudaSharedmemCarveoutMaxShared);
       cudaGetLastError();
-      attrs_u = 1;
-    }
+      return true;
+    }();
+    (void)carveout_set;
     compact_kernel<MODE, false, BLOCK, ITEMS><<<(unsigned)((max_count + TILE - 1) / TILE), BLOCK, 16 * TILE, s>>>(a);
   }
 }
@@ -2805,20 +2808,19 @@ static void launch_compact_shaped(const CompactArgs &a, uint64_t max_count, bool
 // launched, the caller uses the block kernels).
 template <int MODE, class WS>
 static bool launch_warp_stream(const CompactArgs &a, uint64_t max_count, cudaStream_t s) {
-  static int blocks = -1;  // resident blocks of the pass (0: not available)
-  if (blocks < 0) {
-    int dev = 0, sms = 0, per_sm = 0;
+  // resident blocks of the pass (0: not available); set once per process
+  static const int blocks = []() -> int {
+    int dev = 0, sms = 0, per_sm = 0, b = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (cudaFuncSetAttribute(stream_warp_kernel<MODE, WS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)WS::smem) == cudaSuccess &&
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, stream_warp_kernel<MODE, WS>, WS::threads, WS::smem) ==
             cudaSuccess)
-      blocks = sms * per_sm;
-    else
-      blocks = 0;
+      b = sms * per_sm;
     cudaGetLastError();
-  }
+    return b;
+  }();
   if (blocks <= 0) return false;
   const uint64_t wtiles = (max_count + WS::tile - 1) / WS::tile;
   const uint64_t want = (wtiles + WS::warps - 1) / WS::warps;
@@ -3006,14 +3008,17 @@ bool launch_tile_contract(uint32_t n, uint32_t B, uint64_t nlocal, const u64 *cu
                           const uint32_t *b_ends, const uint32_t *b_w, const uint32_t *b_id, uint32_t *parent,
                           uint32_t *bits, EdgeOut rest, u64 *rest_fill, uint32_t *err, cudaStream_t s,
                           int filter_heavy, u64 *wsum) {
-  static int smem_full = 0;
-  if (!smem_full) {
+  // set once per process, and only published once the attribute is in place
+  // (another host thread must not launch with the larger size before it is)
+  static const int smem_full = []() -> int {
     int dev = 0, optin = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-    smem_full = optin - 2048;  // static shared memory and slack
-    cudaFuncSetAttribute(tile_contract_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_full);
-  }
+    const int bytes = optin - 2048;  // static shared memory and slack
+    cudaFuncSetAttribute(tile_contract_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    cudaGetLastError();
+    return bytes;
+  }();
   const size_t vbytes = (size_t)B * (8 + 8 + 4 + 4 + 4);
   if ((size_t)smem_full <= vbytes) return false;
   const uint32_t ntiles = (uint32_t)(((uint64_t)n + B - 1) / B);
